@@ -1,0 +1,287 @@
+"""Seeded synthetic workloads: grids, supports, loads, materials and initial designs.
+
+This module holds problem *inputs* only -- no stencil, interpolation, update or any
+other arithmetic of the method -- so that the GPU path and the FP64 oracle can be fed
+identical instances without sharing code.  It imports nothing but numpy.
+
+The paper (PeTTO, arXiv 2509.06971) uses no datasets: every workload is a parametric
+box domain with supports and loads (Sec. 3.1 heat sink, Sec. 3.2 MBB beam, Sec. 3.3
+cantilever, Sec. 3.4 drone).  The instances below restate those shapes on unit-size
+cells; numbers that the paper does not fix are chosen here and documented.
+
+Index conventions: a node is (i, j, k) with 0 <= i <= nx, 0 <= j <= ny, 0 <= k <= nz;
+a Dirichlet box is ((lo_i, lo_j, lo_k), (hi_i, hi_j, hi_k), mask) with inclusive node
+ranges and bit a of ``mask`` fixing component a; a load is ((i, j, k), comp, value) with
+value the external nodal force (downward = negative y in 2D, negative z in 3D).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+ELASTIC, THERMAL = 0, 1
+SIMP_MODIFIED, SIMP_PAPER = 0, 1
+PROJECTED, PENALTY = 0, 1
+
+
+@dataclass
+class ProblemSpec:
+    name: str
+    dim: int
+    nx: int
+    ny: int
+    nz: int = 0
+    h: float = 1.0
+    physics: int = ELASTIC
+    nu: float = 0.3
+    # materials (Sec. 3.1 / 3.2 interpolation); for SIMP_MODIFIED moduli = [E0]
+    moduli: list = field(default_factory=lambda: [1.0])
+    e_min: float = 1e-9
+    penal: float = 3.0
+    interp: int = SIMP_MODIFIED
+    vol_frac: list = field(default_factory=lambda: [0.5])
+    loads: list = field(default_factory=list)          # [((i,j,k), comp, value)]
+    body_source: float = 0.0
+    boxes: list = field(default_factory=list)          # [((lo),(hi),mask)]
+    phi0: np.ndarray | None = None                     # [P, cells], cell (i,j,k) -> i + nx(j + ny k)
+    # state solver parameters in grid units (Sec. 2.2; Sec. 3.2 PT/APT systems)
+    apt_a: float = 0.99
+    apt_b: float = 0.25
+    pt_s1: float = 0.25
+    tol: float = 1e-6
+    check_every: int = 50
+    max_sweeps: int = 200000
+    local_dt: bool = True      # local pseudo-time steps b/diag(K), s1/diag(K) (an extension)
+    # design update and phase field (Sec. 2.3, 2.4; Sec. 3.1 weights)
+    vol_mode: int = PROJECTED
+    alpha_h: float = 0.1
+    kappa_v: float = 0.0
+    kappa_1: float = 0.0
+    gamma_g: float = 0.0
+    tau: float = 0.0
+    n_bisect: int = 60
+    design_steps: int = 1
+    precision: str = "f32"
+    storage: str = "f32"
+
+    @property
+    def n_phases(self) -> int:
+        return 1 if self.interp == SIMP_MODIFIED else len(self.moduli)
+
+    @property
+    def ncomp(self) -> int:
+        return self.dim if self.physics == ELASTIC else 1
+
+    @property
+    def ncells(self) -> int:
+        return self.nx * self.ny * (self.nz if self.dim == 3 else 1)
+
+    @property
+    def nnodes(self) -> int:
+        return (self.nx + 1) * (self.ny + 1) * ((self.nz + 1) if self.dim == 3 else 1)
+
+    def with_(self, **kw) -> "ProblemSpec":
+        return replace(self, **kw)
+
+
+# --------------------------------------------------------------- parameter maps
+
+def apt_params(h_p: float, elastic: bool = True, theta: float = 1.0, dim: int = 2):
+    """Paper constants in grid units (reading R5).  The paper's APT step is
+    dt2 = h_p/2 and theta = 1 with h_p its own cell size (Sec. 3.1, Sec. 3.2); its PT step
+    is dt1 = h_p^2/(2d) (Sec. 3.1: dx^2/4 in 2D; Sec. 3.3: dx^2/6 in 3D).  On a grid of
+    unit cells the same iteration has
+        elastic form: a = theta/(theta + dt2),  b = dt2^2/((theta + dt2) h_p^2)  (= a/4)
+        thermal form: a = 1 - dt2/theta,       b = dt2^2/(theta h_p^2)           (= 1/4)
+        PT:           s1 = 1/(2d)."""
+    dt2 = h_p / 2.0
+    if elastic:
+        a = theta / (theta + dt2)
+        b = (dt2 * dt2 / (theta + dt2)) / (h_p * h_p)
+    else:
+        a = 1.0 - dt2 / theta
+        b = (dt2 * dt2 / theta) / (h_p * h_p)
+    return a, b, 1.0 / (2 * dim)
+
+
+def local_step_params(n_max: int, c_a: float = 0.15):
+    """Defaults for local (Jacobi-scaled) pseudo-time steps, where the scaled operator
+    diag(K)^-1 K has its largest eigenvalue near 2 for any modulus field: APT b = 1, PT
+    s1 = 0.75, and momentum a = 1 - c_a / n_max (the slowest mode of an elliptic operator
+    on n_max cells scales as n_max^-2, so the best damping rate scales as 1/n_max)."""
+    return 1.0 - c_a / float(n_max), 1.0, 0.75
+
+
+def ch_params(h_p: float, dim: int, dt3_factor: float = 500.0, gamma: float = 3e-5, safety: float = 0.9):
+    """Cahn-Hilliard constants in grid units (Sec. 3.1: dt3 = 500 dx^4, gamma = 3e-5; D = 1,
+    reading R10): tau = dt3/h_p^2, gamma_g = gamma/h_p^2, with tau capped at ``safety`` times
+    the explicit stability bound tau (w''_max lam_L + gamma_g lam_L^2) <= 2, lam_L = 4d,
+    w''_max = 2 pi^2 / 64 for w = sin^2(pi phi)/64."""
+    tau = dt3_factor * h_p ** 2
+    gamma_g = gamma / h_p ** 2
+    lam_l = 4.0 * dim
+    wpp = 2.0 * math.pi ** 2 / 64.0
+    bound = 2.0 / (wpp * lam_l + gamma_g * lam_l ** 2)
+    return min(tau, safety * bound), gamma_g
+
+
+# --------------------------------------------------------------- builders
+
+def _uniform_phi(ncells: int, fracs) -> np.ndarray:
+    return np.stack([np.full(ncells, float(v)) for v in fracs])
+
+
+def mbb_halfbeam(nx: int = 60, ny: int = 20, seed: int = 1, precision: str = "f64") -> ProblemSpec:
+    """2D MBB half-beam (symmetry edge at x = 0): u_x = 0 on the left edge, u_y = 0 at the
+    bottom-right node, unit downward load at the top-left node; E0 = 1, Emin = 1e-9,
+    nu = 0.3, p = 3, V = 0.5, initial density 0.5 + U[-0.01, 0.01] (PCG64 ``seed``)."""
+    rng = np.random.default_rng(seed)
+    phi0 = 0.5 + rng.uniform(-0.01, 0.01, size=(1, nx * ny))
+    h_p = 1.0 / ny
+    a, b, s1 = local_step_params(nx)
+    tau, gg = ch_params(h_p, 2)
+    return ProblemSpec(
+        name=f"mbb_halfbeam_{nx}x{ny}", dim=2, nx=nx, ny=ny, vol_frac=[0.5],
+        boxes=[((0, 0, 0), (0, ny, 0), 0b01), ((nx, 0, 0), (nx, 0, 0), 0b10)],
+        loads=[((0, ny, 0), 1, -1.0)], phi0=phi0,
+        apt_a=a, apt_b=b, pt_s1=s1, tol=1e-8, tau=tau, gamma_g=gg, design_steps=50,
+        precision=precision, storage=precision)
+
+
+def cantilever2d(nx: int = 1024, ny: int = 512, vol: float = 0.4, load_cells: int = 8,
+                 precision: str = "f32") -> ProblemSpec:
+    """2D cantilever: clamped left edge; unit downward traction over the ``load_cells``
+    mid-height cell edges of the right edge, each edge's share split equally between its
+    two end nodes (reading R16)."""
+    assert ny % 2 == 0 and load_cells % 2 == 0 and load_cells <= ny
+    j0 = ny // 2 - load_cells // 2
+    per_edge = 1.0 / load_cells
+    loads = {}
+    for e in range(load_cells):
+        for jj in (j0 + e, j0 + e + 1):
+            loads[jj] = loads.get(jj, 0.0) + 0.5 * per_edge
+    h_p = 1.0 / ny
+    a, b, s1 = local_step_params(nx)
+    tau, gg = ch_params(h_p, 2)
+    return ProblemSpec(
+        name=f"cantilever2d_{nx}x{ny}", dim=2, nx=nx, ny=ny, vol_frac=[vol],
+        boxes=[((0, 0, 0), (0, ny, 0), 0b11)],
+        loads=[((nx, jj, 0), 1, -v) for jj, v in sorted(loads.items())],
+        phi0=_uniform_phi(nx * ny, [vol]),
+        apt_a=a, apt_b=b, pt_s1=s1, tol=1e-6, tau=tau, gamma_g=gg, design_steps=200,
+        precision=precision, storage=precision)
+
+
+def heat2d(n: int = 1024, vol: float = 0.4, precision: str = "f32") -> ProblemSpec:
+    """2D heat sink: k0 = 1, kmin = 1e-3, p = 3, uniform source 0.01 (Sec. 3.1), T = 0 on
+    the nodes of the left edge with 0.45 <= j/n <= 0.55 (reading R16)."""
+    j_lo = math.ceil(0.45 * n - 1e-9)
+    j_hi = math.floor(0.55 * n + 1e-9)
+    h_p = 1.0 / n
+    a, b, s1 = local_step_params(n)
+    tau, gg = ch_params(h_p, 2)
+    return ProblemSpec(
+        name=f"heat2d_{n}x{n}", dim=2, nx=n, ny=n, physics=THERMAL, moduli=[1.0], e_min=1e-3,
+        vol_frac=[vol], boxes=[((0, j_lo, 0), (0, j_hi, 0), 0b1)], body_source=0.01,
+        phi0=_uniform_phi(n * n, [vol]),
+        apt_a=a, apt_b=b, pt_s1=s1, tol=1e-6, tau=tau, gamma_g=gg, design_steps=200,
+        precision=precision, storage=precision)
+
+
+def _line_load_3d(nx: int, ny: int, js=None):
+    """Unit downward (-z) line load along the bottom edge (k = 0) of the x = nx face;
+    equal share per edge segment, end nodes half weight (reading R16)."""
+    loads = []
+    for j in range(ny + 1):
+        w = 1.0 / ny * (0.5 if j in (0, ny) else 1.0)
+        loads.append(((nx, j, 0), 2, -w))
+    return loads
+
+
+def cantilever3d(nx: int = 256, ny: int = 128, nz: int = 128, vol: float = 0.12,
+                 precision: str = "f32") -> ProblemSpec:
+    """3D cantilever: clamped x = 0 face, unit downward line load along the bottom edge of
+    the x = L face, E0 = 1, Emin = 1e-9, nu = 0.3, p = 3."""
+    h_p = 2.0 / nx
+    a, b, s1 = local_step_params(nx)
+    tau, gg = ch_params(h_p, 3)
+    return ProblemSpec(
+        name=f"cantilever3d_{nx}x{ny}x{nz}", dim=3, nx=nx, ny=ny, nz=nz, vol_frac=[vol],
+        boxes=[((0, 0, 0), (0, ny, nz), 0b111)], loads=_line_load_3d(nx, ny),
+        phi0=_uniform_phi(nx * ny * nz, [vol]),
+        apt_a=a, apt_b=b, pt_s1=s1, tol=1e-6, tau=tau, gamma_g=gg, design_steps=50,
+        precision=precision, storage=precision)
+
+
+def multimat3d(nx: int = 384, ny: int = 192, nz: int = 192, storage: str = "bf16") -> ProblemSpec:
+    """3D multi-material cantilever: phases (void, E = 1, E = 0.5) with volume fractions
+    (0.8, 0.1, 0.1), paper interpolation E = sum_i E_i rho_i^p with the void modulus 1e-9
+    (Sec. 3.3 uses three solids plus a soft void phase); BCs and load as the cantilever."""
+    base = cantilever3d(nx, ny, nz)
+    fr = [0.8, 0.1, 0.1]
+    return base.with_(name=f"multimat3d_{nx}x{ny}x{nz}_{storage}", moduli=[1e-9, 1.0, 0.5],
+                      interp=SIMP_PAPER, vol_frac=fr, phi0=_uniform_phi(nx * ny * nz, fr),
+                      kappa_1=0.0, storage=storage)
+
+
+def batch2d(n_instances: int = 48, seed: int = 5, lo: int = 128, hi_factor: float = 8.0) -> list:
+    """Batched 2D instances: n_x = 128 * 8^U rounded to a multiple of 8 (so 128..1024),
+    n_y = n_x / 2; cantilever or MBB half-beam by a fair coin; V ~ U[0.3, 0.5]; the load
+    node drawn uniformly along the loaded edge (PCG64 ``seed``)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for t in range(n_instances):
+        nx = int(round(lo * hi_factor ** rng.uniform()) / 8.0) * 8
+        nx = max(lo, min(int(lo * hi_factor), nx))
+        ny = nx // 2
+        vol = float(rng.uniform(0.3, 0.5))
+        cant = bool(rng.integers(0, 2))
+        j = int(rng.integers(0, ny + 1))
+        h_p = 1.0 / ny
+        a, b, s1 = local_step_params(nx)
+        tau, gg = ch_params(h_p, 2)
+        if cant:
+            boxes = [((0, 0, 0), (0, ny, 0), 0b11)]
+            loads = [((nx, j, 0), 1, -1.0)]
+        else:
+            boxes = [((0, 0, 0), (0, ny, 0), 0b01), ((nx, 0, 0), (nx, 0, 0), 0b10)]
+            loads = [((0, max(j, ny // 2), 0), 1, -1.0)]
+        out.append(ProblemSpec(
+            name=f"batch{t}_{'cant' if cant else 'mbb'}_{nx}x{ny}", dim=2, nx=nx, ny=ny, vol_frac=[vol],
+            boxes=boxes, loads=loads, phi0=_uniform_phi(nx * ny, [vol]),
+            apt_a=a, apt_b=b, pt_s1=s1, tol=1e-6, tau=tau, gamma_g=gg))
+    return out
+
+
+def multirhs3d(nx: int = 192, ny: int = 96, nz: int = 96, n_rhs: int = 4, seed: int = 5):
+    """3D cantilever with ``n_rhs`` unit downward point-load cases at seeded nodes on the
+    bottom edge of the x = L face.  Returns (spec without loads, list of load lists)."""
+    rng = np.random.default_rng(seed)
+    base = cantilever3d(nx, ny, nz)
+    js = rng.integers(0, ny + 1, size=n_rhs)
+    cases = [[((nx, int(j), 0), 2, -1.0)] for j in js]
+    return base.with_(name=f"multirhs3d_{nx}x{ny}x{nz}_r{n_rhs}", loads=cases[0]), cases
+
+
+def random_design(spec: ProblemSpec, seed: int, lo: float = 0.05, hi: float = 0.95) -> np.ndarray:
+    """A seeded non-uniform design field [P, cells] in [lo, hi] for operator tests."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=(spec.n_phases, spec.ncells))
+
+
+def random_state(spec: ProblemSpec, seed: int, scale: float = 1.0) -> np.ndarray:
+    """A seeded nodal field [ncomp, nodes] (node (i,j,k) -> i + (nx+1)(j + (ny+1)k))."""
+    rng = np.random.default_rng(seed)
+    return scale * rng.standard_normal(size=(spec.ncomp, spec.nnodes))
+
+
+CONFIGS = {
+    "mbb60x20_f64": lambda: mbb_halfbeam(),
+    "cantilever2d_1024x512": lambda: cantilever2d(),
+    "heat2d_1024": lambda: heat2d(),
+    "cantilever3d_256x128x128": lambda: cantilever3d(),
+    "multimat3d_384x192x192_bf16": lambda: multimat3d(storage="bf16"),
+    "multimat3d_384x192x192_f16": lambda: multimat3d(storage="f16"),
+}
