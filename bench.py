@@ -1,0 +1,309 @@
+#!/usr/bin/env python3
+"""Benchmark of the PeTTO hot path on GB300.
+
+One step = one PeTTO design iteration (Fig. 5 of the paper) on the chosen workload:
+APT solve of the state equation to relative residual 1e-6 (warm-started from the
+previous iteration's state), compliance sensitivity, design update with the volume
+multiplier, Cahn-Hilliard step, modulus refresh -- every part in libpetto's kernels.
+
+Metric: APT Gcell-sweeps/s over the whole timed design iterations (cells x sweeps /
+wall time on the device), with the sweep kernel's achieved HBM bandwidth against the
+measured copy peak, seconds per design iteration and sweeps per iteration.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+Under torchrun (N > 1) every rank runs its own replica of the workload (independent
+problems: weak scaling, no data-path collective); the barrier and max-over-ranks time
+use torch.distributed.  --impl reference times the FP64 CPU oracle on this host's cores
+(rank 0 only), each step a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2509_06971_gb300 import workloads as W  # noqa: E402
+
+WORKLOADS = {
+    "cantilever3d_256x128x128": lambda: W.cantilever3d(256, 128, 128),
+    "cantilever2d_1024x512": lambda: W.cantilever2d(1024, 512),
+    "heat2d_1024x1024": lambda: W.heat2d(1024),
+    "multimat3d_384x192x192_bf16": lambda: W.multimat3d(storage="bf16"),
+    "cantilever3d_64x32x32": lambda: W.cantilever3d(64, 32, 32),
+}
+DEFAULT_WORKLOAD = "cantilever3d_256x128x128"
+METRIC = "APT Gcell-sweeps/s & % HBM roofline; s/design-iter at rel.res 1e-6"
+
+
+def sweep_bytes(spec, tsize=4):
+    """Algorithmic bytes of one APT sweep: read+write of u and of w (node fields, ncomp
+    components each) and one read of the modulus (cell field)."""
+    return spec.nnodes * 4 * spec.ncomp * tsize + spec.ncells * tsize
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(spec, n_sweeps):
+    """Time n oracle APT sweeps (FP64, single thread) on the full grid of ``spec``.
+    Returns seconds.  Test/benchmark infrastructure only: the baseline, not the path."""
+    import numpy as np
+    from oracle import oracle as O
+    op = O.OracleProblem(spec.dim, spec.nx, spec.ny, spec.nz, h=spec.h, physics=spec.physics, nu=spec.nu,
+                         loads=spec.loads, body_source=spec.body_source, boxes=spec.boxes)
+    om = O.OracleMaterials(list(spec.moduli), spec.e_min, spec.penal, spec.interp)
+    E = om.modulus(spec.phi0)
+    F, fixed = op.load_vector(), op.fixed_mask()
+    u = np.zeros(op.ndof)
+    t0 = time.perf_counter()
+    op.solve(E, F, fixed, u, mode=0, n_apt=n_sweeps, n_pt=0, a=spec.apt_a, b=0.25, s1=0.25, check_every=0,
+             local_dt=False)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(spec, budget_s=12.0):
+    t1 = oracle_sample(spec, 1)
+    n = max(1, min(50, int(budget_s / max(t1, 1e-6))))
+    t = oracle_sample(spec, n) if n > 1 else t1
+    return {"value": spec.ncells * n / t / 1e9, "unit": "Gcell-sweeps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} FP64 oracle APT sweeps of the full {spec.nx}x{spec.ny}x{max(spec.nz, 1)} grid "
+                      f"(global pseudo-time step, single thread) = {t:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    spec = WORKLOADS[args.workload]()
+    n_per_step = 1
+    for _ in range(args.warmup):
+        oracle_sample(spec, n_per_step)
+    times = [oracle_sample(spec, n_per_step) for _ in range(args.steps)]
+    tot = sum(times)
+    value = spec.ncells * n_per_step * args.steps / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gcell-sweeps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "cells": spec.ncells, "parallelism": "cpu-1thread",
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": "Gcell-sweeps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{n_per_step} FP64 oracle APT sweep of the full grid per step"},
+            "e2e": {"value": value, "unit": "Gcell-sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2509_06971_gb300 import problem as PR
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = WORKLOADS[args.workload]()
+    prob = PR.Problem(spec)
+    solve_kw = dict(tol=args.tol, max_sweeps=args.max_sweeps, check_every=spec.check_every)
+
+    def design_iter():
+        hist, _ = prob.optimize(1, solve_kw=solve_kw)
+        return hist[-1]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        design_iter()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    gpu_idx = vis.split(",")[local] if vis else str(local)
+    clocks = ClockSampler(gpu_idx)
+    clocks.start()
+    prob.profile(True)
+    prob.profile_read()
+    launches0 = prob.launches
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    rows = [design_iter() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    launches = prob.launches - launches0
+    kern_ms, kern_n = prob.profile_read()
+    prob.profile(False)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    sweeps = sum(r["sweeps"] for r in rows)
+    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    tot = torch.tensor([float(sweeps) * spec.ncells], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    ms_max = float(t_max.item())
+    value = float(tot.item()) / (ms_max * 1e-3) / 1e9
+
+    peaks, peak_kind = measured_peaks()
+    per_launch_ms = kern_ms / max(kern_n, 1)
+    achieved = sweep_bytes(spec) / (per_launch_ms * 1e-3) / 1e9 if kern_n else None
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+
+    # end to end through the public API: design and state in from pinned host memory,
+    # one design iteration, design and state back out, every step
+    P, C = spec.n_phases, spec.ncomp
+    phi_h = torch.empty((P, spec.ncells), dtype=torch.float32, pin_memory=True).numpy()
+    u_h = torch.empty((C, spec.nnodes), dtype=torch.float32, pin_memory=True).numpy()
+    phi_h[:] = prob.get_design(dtype=np.float32)
+    u_h[:] = prob.get_state(dtype=np.float32)
+    torch.cuda.synchronize()
+    barrier()
+    e_steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    e_sweeps = 0
+    for _ in range(e_steps):
+        prob.set_design(phi_h)
+        prob.set_state(u_h)
+        r = design_iter()
+        e_sweeps += r["sweeps"]
+        phi_h[:] = prob.get_design(dtype=np.float32)
+        u_h[:] = prob.get_state(dtype=np.float32)
+    torch.cuda.synchronize()
+    e_secs = time.perf_counter() - t0
+    e_t = torch.tensor([e_secs], dtype=torch.float64, device=dev)
+    e_tot = torch.tensor([float(e_sweeps) * spec.ncells], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e_tot, op=dist.ReduceOp.SUM)
+    e_value = float(e_tot.item()) / float(e_t.item()) / 1e9
+    h2d = phi_h.nbytes + u_h.nbytes
+    d2h = phi_h.nbytes + u_h.nbytes + 8
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gcell-sweeps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "cells": spec.ncells, "nodes": spec.nnodes,
+                   "tol": args.tol, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2" if sweep_bytes(spec) > 129e6 else "working set fits in L2"},
+        "s_per_design_iter": ms_max * 1e-3 / args.steps,
+        "sweeps_per_design_iter": sweeps / args.steps,
+        "final_rel_res": rows[-1]["rel_res"], "compliance": rows[-1]["compliance"],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "apt sweep", "kernel_ms": per_launch_ms, "bytes_per_launch": sweep_bytes(spec),
+                     "peak_kind": peak_kind},
+        "e2e": {"value": e_value, "unit": "Gcell-sweeps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e_steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(spec)
+    if rank == 0:
+        print(json.dumps(line))
+    prob.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--max-sweeps", type=int, default=20000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,250 @@
+/*
+ * petto.h -- C ABI of the GB300 PeTTO hot path (pseudo-transient topology optimisation).
+ *
+ * Method: PeTTO, arXiv 2509.06971.  The library advances, on one GPU, the loop of
+ * Fig. 5: accelerated pseudo-transient (APT) and pseudo-transient (PT) sweeps of the
+ * state equation (Sec. 2.2; Sec. 3.2 PT/APT systems), the compliance sensitivity
+ * (Sec. 2.3), the design update with its volume terms (Sec. 2.3, Sec. 3.1) and an
+ * explicit Cahn-Hilliard step (Sec. 2.4).
+ *
+ * Conventions shared by every call
+ *   - Every call returns a petto_status and never throws or aborts.  On failure the
+ *     context keeps a message, readable with petto_last_error().
+ *   - Grids: nx, ny (, nz) cells of size h; nodes (i, j, k) with 0 <= i <= nx etc.
+ *     Host/device arrays exchanged through this API use the natural layouts
+ *       cell field  [P][cells]          cell (i,j,k)  -> i + nx*(j + ny*k)
+ *       node field  [C][nodes]          node (i,j,k)  -> i + (nx+1)*((j) + (ny+1)*k)
+ *     with C = nrhs * ncomp components (ncomp = dim for elasticity, 1 for heat),
+ *     component c = r*ncomp + a for load case r and displacement component a.
+ *     2D problems have k = 0 only.
+ *   - dtype arguments take PETTO_F32 or PETTO_F64 (design fields also PETTO_BF16 and
+ *     PETTO_F16).  on_device != 0 means the pointer is device memory of the context's
+ *     GPU, read or written on the context's stream; otherwise it is host memory and the
+ *     call returns after the copy has completed.
+ *   - Host arrays passed to petto_create are copied; the caller keeps ownership.
+ *   - A context owns all its device memory and is not thread-safe.
+ */
+#ifndef PETTO_H
+#define PETTO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct petto_ctx petto_ctx;
+
+typedef enum {
+    PETTO_OK = 0,
+    PETTO_EINVAL = 1,        /* invalid argument or inconsistent sizes */
+    PETTO_ENOMEM = 2,        /* device or host allocation failed */
+    PETTO_ECUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error) */
+    PETTO_ENOTCONV = 4,      /* solve hit max_sweeps before the tolerance; report valid */
+    PETTO_EDIVERGED = 5,     /* solve diverged even after the PT fallback */
+    PETTO_ETIMEOUT = 6,      /* a bounded device-side wait ran out */
+    PETTO_EUNSUPPORTED = 7   /* combination not built (e.g. dtype for this call) */
+} petto_status;
+
+enum { PETTO_ELASTIC = 0, PETTO_THERMAL = 1 };
+enum { PETTO_SIMP_MODIFIED = 0, PETTO_SIMP_PAPER = 1 };
+enum { PETTO_F32 = 0, PETTO_F64 = 1, PETTO_BF16 = 2, PETTO_F16 = 3 };
+enum { PETTO_VOL_PROJECTED = 0, PETTO_VOL_PENALTY = 1 };
+enum { PETTO_SOLVE_PAPER = 0, PETTO_SOLVE_TOL = 1 };
+enum { PETTO_SWEEP_APT = 0, PETTO_SWEEP_PT = 1 };
+
+/* Regular grid of nx x ny (x nz) cells of size h (dim = 2 or 3). */
+typedef struct {
+    int dim;
+    int64_t nx, ny, nz;
+    double h;
+} petto_grid;
+
+/* Material interpolation (Sec. 3.1 overall conductivity; Sec. 3.2 overall modulus).
+ *   interp PETTO_SIMP_MODIFIED (n_phases = 1): E = e_min + rho^penal (modulus[0] - e_min)
+ *   interp PETTO_SIMP_PAPER    (n_phases = P): E = sum_i modulus[i] rho_i^penal
+ * rho = clamp(phi, 0, 1).  nu is Poisson's ratio (2D elasticity is plane strain).
+ * modulus is copied (n_phases doubles). */
+typedef struct {
+    int physics;            /* PETTO_ELASTIC or PETTO_THERMAL */
+    int n_phases;
+    const double *modulus;
+    double e_min;
+    double nu;
+    double penal;
+    int interp;
+} petto_materials;
+
+/* Nodal loads (external force; Sec. 3.2 momentum balance) and a uniform heat source
+ * (Sec. 2.2; each cell gives body_source * h^d / 2^d to each of its corners).
+ *   node  [n][3]  (i, j, k) of each entry (k = 0 in 2D)
+ *   comp  [n]     displacement component a (0 for heat)
+ *   value [n]     force
+ *   rhs   [n]     load case r in [0, nrhs), or NULL for all entries in case 0
+ * Entries at the same node and component add.  All arrays are copied. */
+typedef struct {
+    int64_t n;
+    const int64_t *node;
+    const int32_t *comp;
+    const double *value;
+    const int32_t *rhs;
+    double body_source;
+} petto_loads;
+
+/* Dirichlet supports u_a = 0 (Sec. 3.1, 3.2 boundary conditions) as axis-aligned node
+ * boxes: box [n_boxes][6] = lo_i, lo_j, lo_k, hi_i, hi_j, hi_k (inclusive), and
+ * comp_mask [n_boxes] with bit a fixing component a.  At most 16 boxes. */
+typedef struct {
+    int n_boxes;
+    const int64_t *box;
+    const uint32_t *comp_mask;
+} petto_bcs;
+
+/* precision: PETTO_F32 or PETTO_F64 for the state fields and sweeps.
+ * storage:   design-field storage (PETTO_F32, PETTO_F64, PETTO_BF16, PETTO_F16); the
+ *            interpolation and all updates compute in the sweep precision.
+ * nrhs:      load cases solved together (1..4), sharing one modulus field.
+ * stream:    cudaStream_t for all work of this context (NULL = legacy default stream). */
+typedef struct {
+    int precision;
+    int storage;
+    int nrhs;
+    void *stream;
+} petto_options;
+
+/* Solve control (Sec. 2.2 hybrid schedule).
+ *   mode PETTO_SOLVE_PAPER: exactly n_apt APT sweeps then n_pt PT sweeps.
+ *   mode PETTO_SOLVE_TOL:   APT sweeps until a check sweep's input residual satisfies
+ *                            ||R|| <= tol ||F||, at most max_sweeps in total.
+ * APT sweep:  w <- a w + b' R,  u <- u + w;   PT sweep:  u <- u + s1' R;
+ * with b' = b, s1' = s1 (global step, the paper's form) or b' = b / diag(K),
+ * s1' = s1 / diag(K) per DOF when local_dt != 0 (local pseudo-time steps).
+ * w is zero at the start of every solve.  Every check_every-th sweep is a check sweep
+ * (the last sweep of a paper-mode solve is one too).  Divergence guard: a non-finite
+ * check residual resets u and w to zero, a residual above 10x the best seen resets w;
+ * either switches the rest of the solve to PT sweeps. */
+typedef struct {
+    int mode;
+    int64_t n_apt, n_pt;
+    double a, b, s1;
+    double tol;
+    int64_t max_sweeps;
+    int check_every;
+    int local_dt;
+} petto_solve_opts;
+
+/* res_norm = ||R|| over free DOFs and all load cases at the last check sweep's input
+ * state; rel_res = res_norm / f_norm; r_pde = ||R / h^d|| / (number of nodes), the
+ * paper's residual norm (Sec. 3.1). */
+typedef struct {
+    int64_t sweeps, apt_sweeps, pt_sweeps;
+    double res_norm, f_norm, rel_res, r_pde;
+    int converged, fell_back_to_pt;
+} petto_solve_report;
+
+/* Design update and phase field (Sec. 2.3, 2.4, 3.1).
+ *   g_i = alpha_h s_i / max_c |s_i| + kappa_1 (sum_j phi_j - 1)
+ *   vol_mode PETTO_VOL_PROJECTED: phi_i <- clamp(phi_i - g_i - lambda_i, 0, 1) with
+ *            lambda_i from n_bisect bisection halvings of [-2, 2] on mean phi_i = V_i
+ *   vol_mode PETTO_VOL_PENALTY:   phi_i <- phi_i - g_i - kappa_v (mean phi_i - V_i)
+ *   Cahn-Hilliard (ch_steps times): mu = w'(phi) - gamma_g L phi; phi <- phi + tau L mu
+ *   with w = sin^2(pi phi)/64 and L the no-flux cell Laplacian in grid units. */
+typedef struct {
+    int vol_mode;
+    double alpha_h, kappa_v, kappa_1, gamma_g, tau;
+    int ch_steps;
+    int n_bisect;
+} petto_pf_opts;
+
+/* metrics[0..7]: step, compliance, work F.u, rel_res, sweeps, seconds, mean phi_0, lambda_0 */
+typedef void (*petto_step_cb)(const double *metrics, void *user);
+
+/* Create a context: copies the problem, allocates device state, sets phi_i = vol_frac[i]
+ * (vol_frac has n_phases entries, the targets V_i of Sec. 2.3 J_v), u = w = 0.
+ * Errors: PETTO_EINVAL for bad sizes/options, PETTO_ENOMEM, PETTO_ECUDA. */
+petto_status petto_create(const petto_grid *grid, const petto_materials *mat, const petto_loads *loads,
+                          const petto_bcs *bcs, const double *vol_frac, const petto_options *opt,
+                          petto_ctx **out);
+
+/* Free every resource of the context (NULL is a no-op). */
+void petto_destroy(petto_ctx *ctx);
+
+/* Last error message of the context ("" if none); static text if ctx is NULL. */
+const char *petto_last_error(const petto_ctx *ctx);
+
+/* Name of a status code. */
+const char *petto_status_string(petto_status s);
+
+/* Design field phi [P][cells] in dtype; recomputes the modulus field (Sec. 3.2). */
+petto_status petto_set_design(petto_ctx *ctx, const void *phi, int dtype, int on_device);
+petto_status petto_get_design(petto_ctx *ctx, void *phi, int dtype, int on_device);
+
+/* State u (and APT increment w = u^n - u^{n-1}) [C][nodes]; w may be NULL (set: zero;
+ * get: not returned). */
+petto_status petto_set_state(petto_ctx *ctx, const void *u, const void *w, int dtype, int on_device);
+petto_status petto_get_state(petto_ctx *ctx, void *u, void *w, int dtype, int on_device);
+
+/* Modulus / conductivity field E [cells] (Sec. 3.1, 3.2 interpolation) of the design. */
+petto_status petto_get_modulus(petto_ctx *ctx, void *E, int dtype, int on_device);
+
+/* Exactly n sweeps of one kind (PETTO_SWEEP_APT / PETTO_SWEEP_PT) with the given
+ * constants, continuing from the current u and w (Sec. 2.2; Sec. 3.2 PT/APT systems).
+ * res_norm2 (may be NULL) receives sum R^2 of the last sweep's input state. */
+petto_status petto_sweep(petto_ctx *ctx, int kind, int64_t n, double a, double b, double s1, int local_dt,
+                         double *res_norm2);
+
+/* R = F - K u on free DOFs (0 on supports) for the current state; R [C][nodes] may be
+ * NULL; res_norm2 (may be NULL) receives sum R^2. */
+petto_status petto_residual(petto_ctx *ctx, double *res_norm2, void *R, int dtype, int on_device);
+
+/* Hybrid APT/PT solve of K(E) u = F from the current u (Sec. 2.2). */
+petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *opts, petto_solve_report *rep);
+
+/* Compliance C = sum_c E_c e_c (Sec. 2.3 J_h; Sec. 3.2 J_m) summed over load cases,
+ * external work F.u, and the sensitivity dC/dphi [P][cells] = -(dE/dphi_i) e_c (the
+ * total derivative at the current state, a hand-written adjoint of the self-adjoint
+ * compliance).  Any output pointer may be NULL.  The sensitivity is also kept in the
+ * context for petto_design_update. */
+petto_status petto_sensitivity(petto_ctx *ctx, double *compliance, double *work, void *dcdphi, int dtype,
+                               int on_device);
+
+/* Design update from the kept sensitivity (Sec. 2.3 combined objective, Sec. 3.1
+ * normalised step); lambda [P] (may be NULL) receives lambda_i (projected mode) or the
+ * mean of phi_i before the step (penalty mode).  Refreshes the modulus field. */
+petto_status petto_design_update(petto_ctx *ctx, const petto_pf_opts *opts, double *lambda);
+
+/* opts->ch_steps explicit Cahn-Hilliard steps (Sec. 2.4); refreshes the modulus field. */
+petto_status petto_cahn_hilliard(petto_ctx *ctx, const petto_pf_opts *opts);
+
+/* Design update then Cahn-Hilliard (the phi half of one PeTTO loop, Fig. 5);
+ * vol_out [P] (may be NULL) receives mean phi_i afterwards. */
+petto_status petto_phase_field_step(petto_ctx *ctx, const petto_pf_opts *opts, double *vol_out);
+
+/* n_steps PeTTO loops (Fig. 5): solve, sensitivity, update, Cahn-Hilliard.  cb (may be
+ * NULL) is called on the host after each loop with the metrics described above.
+ * Returns PETTO_ENOTCONV if any solve missed its tolerance (the loop still runs). */
+petto_status petto_optimize(petto_ctx *ctx, int n_steps, const petto_solve_opts *sopts,
+                            const petto_pf_opts *popts, petto_step_cb cb, void *user);
+
+/* Checkpoint of design, state and step counter to a file / back (same problem). */
+petto_status petto_save(petto_ctx *ctx, const char *path);
+petto_status petto_load(petto_ctx *ctx, const char *path);
+
+/* Wait for all work of the context's stream. */
+petto_status petto_synchronize(petto_ctx *ctx);
+
+/* Number of kernel launches this context has issued (for launch accounting). */
+int64_t petto_launch_count(const petto_ctx *ctx);
+
+/* Sweep-kernel timing.  While enabled, every sweep launch is bracketed by a pair of CUDA
+ * events on the context's stream; petto_profile_read waits for them and returns the summed
+ * device time (ms) and the number of timed sweep launches since the last read, then
+ * resets both.  Disabled by default. */
+petto_status petto_profile(petto_ctx *ctx, int enable);
+petto_status petto_profile_read(petto_ctx *ctx, double *sweep_ms, int64_t *sweeps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PETTO_H */

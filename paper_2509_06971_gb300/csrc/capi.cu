@@ -1,0 +1,983 @@
+// capi.cu -- the C ABI of libpetto (declared in include/petto.h): context, buffers,
+// problem descriptors, and the host-side control of the PeTTO loop (Fig. 5 of the paper):
+// hybrid APT/PT solve with convergence checks every k sweeps (Sec. 2.2), sensitivity
+// (Sec. 2.3), design update and Cahn-Hilliard step (Sec. 2.3, 2.4).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/petto.h"
+#include "petto_internal.cuh"
+
+using namespace petto;
+
+struct petto_ctx {
+    // problem
+    int dim = 2, physics = 0, ncomp = 2, nrhs = 1, P = 1, interp = 0, precision = 0, storage = 0;
+    int nx = 0, ny = 0, nz = 1;
+    double h = 1.0, nu = 0.3, e_min = 1e-9, penal = 3.0, body_source = 0.0;
+    std::vector<double> moduli, vol;
+    cudaStream_t stream = nullptr;
+    Layout L{};
+    Tiling tiling{};
+    OpConst k{};
+    BoxSet boxes{};
+    double lam0 = 0.0, mu0 = 0.0;
+    double f_norm = 0.0;
+    // device buffers
+    void *u[2] = {nullptr, nullptr};
+    void *w = nullptr, *E = nullptr, *phi = nullptr, *s = nullptr, *dscr = nullptr, *mu = nullptr;
+    void *rbuf = nullptr, *stage = nullptr;
+    size_t stage_bytes = 0;
+    double *scal = nullptr;
+    unsigned *counter = nullptr;
+    double *partials = nullptr;
+    int *tile_ptr = nullptr;
+    LoadEntry *loads = nullptr;
+    int n_loads = 0;
+    std::vector<LoadEntry> host_loads;
+    int cur = 0;
+    int64_t launches = 0;
+    int64_t step = 0;
+    bool have_sens = false;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    double prof_ms = 0.0;
+    int64_t prof_sweeps = 0;
+    std::string err;
+
+    size_t tsize() const { return precision == 0 ? 4 : 8; }
+    size_t ssize() const { return storage == 0 ? 4 : (storage == 1 ? 8 : 2); }
+    int ndofc() const { return nrhs * ncomp; }
+    size_t node_bytes() const { return (size_t)ndofc() * L.cstride * tsize(); }
+    RedBuf red() const { return RedBuf{partials, counter}; }
+};
+
+namespace {
+
+petto_status fail(petto_ctx *c, petto_status st, const std::string &msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+#define CK(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fail(ctx, PETTO_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+
+// ---------------------------------------------------------------- layout packing kernels
+
+template <typename A, typename B> __device__ __forceinline__ B cvt(A v) { return (B)v; }
+
+// natural [C][nodes] <-> padded [C][cstride]
+template <typename Src, typename Dst>
+__global__ void pack_nodes(Layout L, int C, const Src *__restrict__ src, Dst *__restrict__ dst, int to_padded) {
+    const int64_t nn = L.nnodes();
+    const int64_t tot = nn * C;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t / nn);
+        const int64_t n = t % nn;
+        const int i = (int)(n % L.NX);
+        const int64_t r = n / L.NX;
+        const int j = (int)(r % L.NY), k = (int)(r / L.NY);
+        const int64_t p = (int64_t)c * L.cstride + L.node(i, j, k);
+        if (to_padded) dst[p] = (Dst)src[t];
+        else dst[t] = (Dst)src[p];
+    }
+}
+
+// padded cell field -> natural [cells]
+template <typename Src, typename Dst>
+__global__ void unpack_cells(Layout L, const Src *__restrict__ src, Dst *__restrict__ dst) {
+    const int64_t nc = L.ncells();
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(c % L.nx);
+        const int64_t r = c / L.nx;
+        const int j = (int)(r % L.ny), k = (int)(r / L.ny);
+        dst[c] = (Dst)src[L.cell(i, j, k)];
+    }
+}
+
+template <typename Src, typename Dst> __device__ __forceinline__ Dst conv(Src v) { return (Dst)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 conv<float, __nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 conv<double, __nv_bfloat16>(double v) { return __double2bfloat16(v); }
+template <> __device__ __forceinline__ __half conv<float, __half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __half conv<double, __half>(double v) { return __double2half(v); }
+template <> __device__ __forceinline__ float conv<__nv_bfloat16, float>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ double conv<__nv_bfloat16, double>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+template <> __device__ __forceinline__ float conv<__half, float>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ double conv<__half, double>(__half v) { return (double)__half2float(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 conv<__nv_bfloat16, __nv_bfloat16>(__nv_bfloat16 v) { return v; }
+template <> __device__ __forceinline__ __half conv<__half, __half>(__half v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 conv<__half, __nv_bfloat16>(__half v) { return __float2bfloat16_rn(__half2float(v)); }
+template <> __device__ __forceinline__ __half conv<__nv_bfloat16, __half>(__nv_bfloat16 v) { return __float2half_rn(__bfloat162float(v)); }
+
+template <typename Src, typename Dst>
+__global__ void convert_flat(int64_t n, const Src *__restrict__ src, Dst *__restrict__ dst) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = conv<Src, Dst>(src[t]);
+}
+
+__global__ void fill_phase(int64_t nc, int P, const double *__restrict__ vals, int storage, void *phi) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nc * P; t += (int64_t)gridDim.x * blockDim.x) {
+        const double v = vals[t / nc];
+        if (storage == 0) static_cast<float *>(phi)[t] = (float)v;
+        else if (storage == 1) static_cast<double *>(phi)[t] = v;
+        else if (storage == 2) static_cast<__nv_bfloat16 *>(phi)[t] = __double2bfloat16(v);
+        else static_cast<__half *>(phi)[t] = __double2half(v);
+    }
+}
+
+int grid_of(int64_t n) {
+    int64_t g = (n + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
+}
+
+template <typename F>
+cudaError_t dispatch_dtype(int dtype, F &&f) {
+    switch (dtype) {
+        case PETTO_F32: return f(float{});
+        case PETTO_F64: return f(double{});
+        case PETTO_BF16: return f(__nv_bfloat16{});
+        case PETTO_F16: return f(__half{});
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t dtype_size(int dtype) { return dtype == PETTO_F64 ? 8 : (dtype == PETTO_F32 ? 4 : 2); }
+
+petto_status ensure_stage(petto_ctx *ctx, size_t bytes) {
+    if (ctx->stage_bytes >= bytes) return PETTO_OK;
+    if (ctx->stage) cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    CK(cudaMalloc(&ctx->stage, bytes));
+    ctx->stage_bytes = bytes;
+    return PETTO_OK;
+}
+
+DesignArgs design_args(const petto_ctx *ctx) {
+    DesignArgs d{};
+    d.L = ctx->L;
+    d.P = ctx->P;
+    d.interp = ctx->interp;
+    d.storage = ctx->storage;
+    d.precision = ctx->precision;
+    d.penal = ctx->penal;
+    d.e_min = ctx->e_min;
+    for (int p = 0; p < (int)ctx->moduli.size() && p < MAX_PHASES; ++p) d.moduli[p] = ctx->moduli[p];
+    return d;
+}
+
+petto_status refresh_material(petto_ctx *ctx) {
+    DesignArgs d = design_args(ctx);
+    CK(launch_material(d, ctx->phi, ctx->E, ctx->stream));
+    ctx->launches++;
+    return PETTO_OK;
+}
+
+// --- node field transfer (natural layout, dtype) to/from a padded device buffer
+petto_status node_in(petto_ctx *ctx, const void *src, int dtype, int on_device, void *dst_padded) {
+    const int C = ctx->ndofc();
+    const int64_t n = (int64_t)C * ctx->L.nnodes();
+    const void *dsrc = src;
+    if (dtype != PETTO_F32 && dtype != PETTO_F64) return fail(ctx, PETTO_EUNSUPPORTED, "node fields are f32/f64");
+    if (!on_device) {
+        petto_status st = ensure_stage(ctx, n * dtype_size(dtype));
+        if (st != PETTO_OK) return st;
+        CK(cudaMemcpyAsync(ctx->stage, src, n * dtype_size(dtype), cudaMemcpyHostToDevice, ctx->stream));
+        dsrc = ctx->stage;
+    }
+    const Layout L = ctx->L;
+    cudaStream_t s = ctx->stream;
+    const int prec = ctx->precision;
+    CK(dispatch_dtype(dtype, [&](auto sv) -> cudaError_t {
+        using S = decltype(sv);
+        if (prec == 0) pack_nodes<S, float><<<grid_of(n), 256, 0, s>>>(L, C, (const S *)dsrc, (float *)dst_padded, 1);
+        else pack_nodes<S, double><<<grid_of(n), 256, 0, s>>>(L, C, (const S *)dsrc, (double *)dst_padded, 1);
+        return cudaGetLastError();
+    }));
+    ctx->launches++;
+    if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
+    return PETTO_OK;
+}
+
+petto_status node_out(petto_ctx *ctx, const void *src_padded, void *dst, int dtype, int on_device) {
+    const int C = ctx->ndofc();
+    const int64_t n = (int64_t)C * ctx->L.nnodes();
+    if (dtype != PETTO_F32 && dtype != PETTO_F64) return fail(ctx, PETTO_EUNSUPPORTED, "node fields are f32/f64");
+    void *ddst = dst;
+    if (!on_device) {
+        petto_status st = ensure_stage(ctx, n * dtype_size(dtype));
+        if (st != PETTO_OK) return st;
+        ddst = ctx->stage;
+    }
+    const Layout L = ctx->L;
+    cudaStream_t s = ctx->stream;
+    const int prec = ctx->precision;
+    CK(dispatch_dtype(dtype, [&](auto dv) -> cudaError_t {
+        using D = decltype(dv);
+        if (prec == 0) pack_nodes<float, D><<<grid_of(n), 256, 0, s>>>(L, C, (const float *)src_padded, (D *)ddst, 0);
+        else pack_nodes<double, D><<<grid_of(n), 256, 0, s>>>(L, C, (const double *)src_padded, (D *)ddst, 0);
+        return cudaGetLastError();
+    }));
+    ctx->launches++;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(dst, ctx->stage, n * dtype_size(dtype), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return PETTO_OK;
+}
+
+// flat cell-field transfer with dtype conversion (design phi, sensitivity)
+petto_status flat_in(petto_ctx *ctx, const void *src, int dtype, int on_device, void *dst, int dst_dtype, int64_t n) {
+    const void *dsrc = src;
+    if (!on_device) {
+        petto_status st = ensure_stage(ctx, n * dtype_size(dtype));
+        if (st != PETTO_OK) return st;
+        CK(cudaMemcpyAsync(ctx->stage, src, n * dtype_size(dtype), cudaMemcpyHostToDevice, ctx->stream));
+        dsrc = ctx->stage;
+    }
+    cudaStream_t s = ctx->stream;
+    CK(dispatch_dtype(dtype, [&](auto sv) -> cudaError_t {
+        using S = decltype(sv);
+        return dispatch_dtype(dst_dtype, [&](auto dv) -> cudaError_t {
+            using D = decltype(dv);
+            convert_flat<S, D><<<grid_of(n), 256, 0, s>>>(n, (const S *)dsrc, (D *)dst);
+            return cudaGetLastError();
+        });
+    }));
+    ctx->launches++;
+    if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
+    return PETTO_OK;
+}
+
+petto_status flat_out(petto_ctx *ctx, const void *src, int src_dtype, void *dst, int dtype, int on_device, int64_t n) {
+    void *ddst = dst;
+    if (!on_device) {
+        petto_status st = ensure_stage(ctx, n * dtype_size(dtype));
+        if (st != PETTO_OK) return st;
+        ddst = ctx->stage;
+    }
+    cudaStream_t s = ctx->stream;
+    CK(dispatch_dtype(src_dtype, [&](auto sv) -> cudaError_t {
+        using S = decltype(sv);
+        return dispatch_dtype(dtype, [&](auto dv) -> cudaError_t {
+            using D = decltype(dv);
+            convert_flat<S, D><<<grid_of(n), 256, 0, s>>>(n, (const S *)src, (D *)ddst);
+            return cudaGetLastError();
+        });
+    }));
+    ctx->launches++;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(dst, ctx->stage, n * dtype_size(dtype), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return PETTO_OK;
+}
+
+SweepArgs base_sweep_args(petto_ctx *ctx) {
+    SweepArgs a{};
+    a.L = ctx->L;
+    a.physics = ctx->physics;
+    a.ncomp = ctx->ncomp;
+    a.nrhs = ctx->nrhs;
+    a.k = ctx->k;
+    a.boxes = ctx->boxes;
+    a.E = ctx->E;
+    a.tile_ptr = ctx->tile_ptr;
+    a.loads = ctx->loads;
+    a.res2 = ctx->scal + SC_RES;
+    a.red = ctx->red();
+    return a;
+}
+
+// one sweep kind (0 APT, 1 PT) from u[cur] into u[1-cur]; flips cur
+petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, int local_dt, bool want_res) {
+    SweepArgs A = base_sweep_args(ctx);
+    A.mode = kind;
+    A.local_dt = local_dt;
+    A.want_res = want_res ? 1 : 0;
+    A.a = a;
+    A.b = b;
+    A.s1 = s1;
+    A.u_in = ctx->u[ctx->cur];
+    A.u_out = ctx->u[1 - ctx->cur];
+    A.w = ctx->w;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ctx->profiling) {
+        for (cudaEvent_t *e : {&e0, &e1}) {
+            if (!ctx->ev_free.empty()) {
+                *e = ctx->ev_free.back();
+                ctx->ev_free.pop_back();
+            } else {
+                CK(cudaEventCreate(e));
+            }
+        }
+        CK(cudaEventRecord(e0, ctx->stream));
+    }
+    CK(launch_sweep(A, ctx->tiling, ctx->precision, ctx->stream));
+    if (ctx->profiling) {
+        CK(cudaEventRecord(e1, ctx->stream));
+        ctx->ev_pending.emplace_back(e0, e1);
+    }
+    ctx->launches++;
+    ctx->cur ^= 1;
+    return PETTO_OK;
+}
+
+petto_status read_scal(petto_ctx *ctx, double *host) {
+    CK(cudaMemcpyAsync(host, ctx->scal, sizeof(double) * SC_N, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PETTO_OK;
+}
+
+
+void build_opconst(petto_ctx *ctx) {
+    const int d = ctx->dim;
+    const double hs = std::pow(ctx->h, d - 2);
+    const double nq = (double)(1 << d);
+    const double lam = ctx->nu / ((1.0 + ctx->nu) * (1.0 - 2.0 * ctx->nu));
+    const double mu = 1.0 / (2.0 * (1.0 + ctx->nu));
+    ctx->lam0 = lam;
+    ctx->mu0 = mu;
+    OpConst &k = ctx->k;
+    k.ce_par = 2.0 / nq * hs * (lam + 2.0 * mu);
+    k.ce_perp = 2.0 / nq * hs * mu;
+    k.cf_lam = hs * lam / nq;
+    k.cf_mu = hs * mu / nq;
+    k.ct = 2.0 / nq * hs;
+    k.cdiag = ctx->physics == 0 ? 2.0 / nq * hs * (lam + (d + 1) * mu) : 2.0 / nq * hs * d;
+    k.src = ctx->body_source * std::pow(ctx->h, d) / nq;
+}
+
+petto_status drain_profile(petto_ctx *ctx) {
+    for (auto &pr : ctx->ev_pending) {
+        CK(cudaEventSynchronize(pr.second));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        ctx->prof_ms += ms;
+        ctx->prof_sweeps++;
+        ctx->ev_free.push_back(pr.first);
+        ctx->ev_free.push_back(pr.second);
+    }
+    ctx->ev_pending.clear();
+    return PETTO_OK;
+}
+
+}  // namespace
+
+// ==================================================================== C ABI
+
+extern "C" {
+
+const char *petto_status_string(petto_status s) {
+    switch (s) {
+        case PETTO_OK: return "PETTO_OK";
+        case PETTO_EINVAL: return "PETTO_EINVAL";
+        case PETTO_ENOMEM: return "PETTO_ENOMEM";
+        case PETTO_ECUDA: return "PETTO_ECUDA";
+        case PETTO_ENOTCONV: return "PETTO_ENOTCONV";
+        case PETTO_EDIVERGED: return "PETTO_EDIVERGED";
+        case PETTO_ETIMEOUT: return "PETTO_ETIMEOUT";
+        case PETTO_EUNSUPPORTED: return "PETTO_EUNSUPPORTED";
+    }
+    return "PETTO_UNKNOWN";
+}
+
+const char *petto_last_error(const petto_ctx *ctx) {
+    if (!ctx) return "no context";
+    return ctx->err.c_str();
+}
+
+int64_t petto_launch_count(const petto_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+petto_status petto_profile(petto_ctx *ctx, int enable) {
+    if (!ctx) return PETTO_EINVAL;
+    petto_status st = drain_profile(ctx);
+    if (st != PETTO_OK) return st;
+    ctx->profiling = enable != 0;
+    return PETTO_OK;
+}
+
+petto_status petto_profile_read(petto_ctx *ctx, double *sweep_ms, int64_t *sweeps) {
+    if (!ctx) return PETTO_EINVAL;
+    petto_status st = drain_profile(ctx);
+    if (st != PETTO_OK) return st;
+    if (sweep_ms) *sweep_ms = ctx->prof_ms;
+    if (sweeps) *sweeps = ctx->prof_sweeps;
+    ctx->prof_ms = 0.0;
+    ctx->prof_sweeps = 0;
+    return PETTO_OK;
+}
+
+void petto_destroy(petto_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto &pr : ctx->ev_pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (auto e : ctx->ev_free) cudaEventDestroy(e);
+    void *bufs[] = {ctx->u[0], ctx->u[1], ctx->w, ctx->E, ctx->phi, ctx->s, ctx->dscr, ctx->mu, ctx->rbuf,
+                    ctx->stage, ctx->scal, ctx->counter, ctx->tile_ptr, ctx->loads, ctx->partials};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete ctx;
+}
+
+petto_status petto_create(const petto_grid *grid, const petto_materials *mat, const petto_loads *loads,
+                          const petto_bcs *bcs, const double *vol_frac, const petto_options *opt, petto_ctx **out) {
+    if (!out) return PETTO_EINVAL;
+    *out = nullptr;
+    if (!grid || !mat || !vol_frac || !opt) return PETTO_EINVAL;
+    if (grid->dim != 2 && grid->dim != 3) return PETTO_EINVAL;
+    if (grid->nx < 1 || grid->ny < 1 || (grid->dim == 3 && grid->nz < 1)) return PETTO_EINVAL;
+    if (grid->nx > (1 << 24) || grid->ny > (1 << 24) || grid->nz > (1 << 24) || !(grid->h > 0)) return PETTO_EINVAL;
+    if (opt->precision != PETTO_F32 && opt->precision != PETTO_F64) return PETTO_EINVAL;
+    if (opt->storage < PETTO_F32 || opt->storage > PETTO_F16) return PETTO_EINVAL;
+    if (opt->nrhs < 1 || opt->nrhs > MAX_RHS) return PETTO_EINVAL;
+    if (mat->physics != PETTO_ELASTIC && mat->physics != PETTO_THERMAL) return PETTO_EINVAL;
+    if (mat->n_phases < 1 || mat->n_phases > MAX_PHASES || !mat->modulus) return PETTO_EINVAL;
+    if (mat->interp == PETTO_SIMP_MODIFIED && mat->n_phases != 1) return PETTO_EINVAL;
+    if (mat->physics == PETTO_ELASTIC && !(mat->nu > -1.0 && mat->nu < 0.5)) return PETTO_EINVAL;
+
+    petto_ctx *ctx = new (std::nothrow) petto_ctx();
+    if (!ctx) return PETTO_ENOMEM;
+    ctx->dim = grid->dim;
+    ctx->nx = (int)grid->nx;
+    ctx->ny = (int)grid->ny;
+    ctx->nz = grid->dim == 3 ? (int)grid->nz : 1;
+    ctx->h = grid->h;
+    ctx->physics = mat->physics;
+    ctx->ncomp = mat->physics == PETTO_ELASTIC ? grid->dim : 1;
+    ctx->nrhs = opt->nrhs;
+    ctx->P = mat->n_phases;
+    ctx->interp = mat->interp;
+    ctx->nu = mat->nu;
+    ctx->e_min = mat->e_min;
+    ctx->penal = mat->penal;
+    ctx->precision = opt->precision;
+    ctx->storage = opt->storage;
+    ctx->stream = (cudaStream_t)opt->stream;
+    ctx->moduli.assign(mat->modulus, mat->modulus + mat->n_phases);
+    ctx->vol.assign(vol_frac, vol_frac + mat->n_phases);
+    ctx->body_source = loads ? loads->body_source : 0.0;
+    if (ctx->body_source != 0.0 && ctx->physics != PETTO_THERMAL) {
+        delete ctx;
+        return PETTO_EINVAL;
+    }
+    ctx->L = make_layout(ctx->dim, ctx->nx, ctx->ny, ctx->nz);
+    ctx->tiling = choose_tiling(ctx->L, ctx->physics, ctx->precision);
+    build_opconst(ctx);
+
+    // supports
+    if (bcs && bcs->n_boxes > 0) {
+        if (bcs->n_boxes > MAX_BOXES || !bcs->box || !bcs->comp_mask) {
+            petto_destroy(ctx);
+            return PETTO_EINVAL;
+        }
+        ctx->boxes.n = bcs->n_boxes;
+        for (int q = 0; q < bcs->n_boxes; ++q) {
+            for (int a = 0; a < 3; ++a) {
+                ctx->boxes.b[q].lo[a] = (int)bcs->box[6 * q + a];
+                ctx->boxes.b[q].hi[a] = (int)bcs->box[6 * q + 3 + a];
+            }
+            ctx->boxes.b[q].mask = bcs->comp_mask[q];
+        }
+    }
+    auto is_fixed = [&](int i, int j, int k, int a) {
+        for (int q = 0; q < ctx->boxes.n; ++q) {
+            const Box &b = ctx->boxes.b[q];
+            if (i >= b.lo[0] && i <= b.hi[0] && j >= b.lo[1] && j <= b.hi[1] && k >= b.lo[2] && k <= b.hi[2] &&
+                ((b.mask >> a) & 1u))
+                return true;
+        }
+        return false;
+    };
+
+    // nodal loads: merge duplicates, group per sweep tile
+    std::map<std::tuple<int, int, int, int>, double> merged;  // (tile, node, comp) -> value
+    const int NX = ctx->L.NX, NY = ctx->L.NY, NZ = ctx->L.NZ;
+    if (loads && loads->n > 0) {
+        if (!loads->node || !loads->comp || !loads->value) {
+            petto_destroy(ctx);
+            return PETTO_EINVAL;
+        }
+        for (int64_t e = 0; e < loads->n; ++e) {
+            const int i = (int)loads->node[3 * e], j = (int)loads->node[3 * e + 1];
+            const int k = ctx->dim == 3 ? (int)loads->node[3 * e + 2] : 0;
+            const int a = loads->comp[e];
+            const int r = loads->rhs ? loads->rhs[e] : 0;
+            if (i < 0 || i >= NX || j < 0 || j >= NY || k < 0 || k >= NZ || a < 0 || a >= ctx->ncomp || r < 0 ||
+                r >= ctx->nrhs) {
+                ctx->err = "load entry out of range";
+                petto_destroy(ctx);
+                return PETTO_EINVAL;
+            }
+            const int tile = ctx->tiling.tile_of(i, j, k);
+            const int n = (int)((int64_t)i + (int64_t)NX * ((int64_t)j + (int64_t)NY * k));
+            merged[std::make_tuple(tile, n, r * ctx->ncomp + a, 0)] += loads->value[e];
+        }
+    }
+    const int ntiles = ctx->tiling.ntiles();
+    std::vector<int> tptr(ntiles + 1, 0);
+    double f2 = 0.0;
+    for (auto &kv : merged) {
+        const int tile = std::get<0>(kv.first), n = std::get<1>(kv.first), c = std::get<2>(kv.first);
+        const int i = n % NX, j = (n / NX) % NY, k = n / (NX * NY);
+        LoadEntry le{};
+        le.node = ctx->L.node(i, j, k);
+        le.comp = c;
+        le.vald = kv.second;
+        le.valf = (float)kv.second;
+        ctx->host_loads.push_back(le);
+        tptr[tile + 1]++;
+        const int a = c % ctx->ncomp;
+        if (!is_fixed(i, j, k, a)) {
+            double F = kv.second;
+            if (ctx->body_source != 0.0) {
+                const int cnt = ((i > 0) + (i < ctx->nx)) * ((j > 0) + (j < ctx->ny)) *
+                                (ctx->dim == 3 ? ((k > 0) + (k < ctx->nz)) : 1);
+                F += ctx->k.src * cnt;
+            }
+            f2 += F * F;
+        }
+    }
+    for (int t = 0; t < ntiles; ++t) tptr[t + 1] += tptr[t];
+    ctx->n_loads = (int)ctx->host_loads.size();
+    // ||F|| over free DOFs: body source at nodes without point loads
+    if (ctx->body_source != 0.0) {
+        std::vector<char> has(ctx->nrhs * (size_t)NX * NY * NZ, 0);
+        for (auto &kv : merged) has[(size_t)std::get<2>(kv.first) * NX * NY * NZ + std::get<1>(kv.first)] = 1;
+        for (int r = 0; r < ctx->nrhs; ++r)
+            for (int k = 0; k < NZ; ++k)
+                for (int j = 0; j < NY; ++j)
+                    for (int i = 0; i < NX; ++i) {
+                        const size_t n = (size_t)i + (size_t)NX * (j + (size_t)NY * k);
+                        if (has[(size_t)r * NX * NY * NZ + n] || is_fixed(i, j, k, 0)) continue;
+                        const int cnt = ((i > 0) + (i < ctx->nx)) * ((j > 0) + (j < ctx->ny)) *
+                                        (ctx->dim == 3 ? ((k > 0) + (k < ctx->nz)) : 1);
+                        const double F = ctx->k.src * cnt;
+                        f2 += F * F;
+                    }
+    }
+    ctx->f_norm = std::sqrt(f2);
+
+    // device buffers
+    const size_t nb = ctx->node_bytes();
+    const size_t eb = ctx->L.estride * ctx->tsize();
+    const int64_t nc = ctx->L.ncells();
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    };
+    alloc(&ctx->u[0], nb);
+    alloc(&ctx->u[1], nb);
+    alloc(&ctx->w, nb);
+    alloc(&ctx->E, eb);
+    alloc(&ctx->phi, (size_t)ctx->P * nc * ctx->ssize());
+    alloc(&ctx->s, (size_t)ctx->P * nc * ctx->tsize());
+    alloc(&ctx->dscr, (size_t)ctx->P * nc * ctx->tsize());
+    alloc(&ctx->mu, (size_t)nc * ctx->tsize());
+    alloc((void **)&ctx->scal, sizeof(double) * SC_N);
+    alloc((void **)&ctx->counter, sizeof(unsigned) * 4);
+    alloc((void **)&ctx->partials, sizeof(double) * reduction_capacity(ctx->L, ntiles, ctx->P));
+    alloc((void **)&ctx->tile_ptr, sizeof(int) * (ntiles + 1));
+    alloc((void **)&ctx->loads, sizeof(LoadEntry) * std::max(1, ctx->n_loads));
+    if (e != cudaSuccess) {
+        petto_status st = e == cudaErrorMemoryAllocation ? PETTO_ENOMEM : PETTO_ECUDA;
+        cudaGetLastError();
+        petto_destroy(ctx);
+        return st;
+    }
+    // group loads by tile in the order of tptr
+    std::vector<LoadEntry> sorted(ctx->host_loads.size());
+    {
+        std::vector<int> pos(tptr.begin(), tptr.end() - 1);
+        int idx = 0;
+        for (auto &kv : merged) sorted[pos[std::get<0>(kv.first)]++] = ctx->host_loads[idx++];
+    }
+    ctx->host_loads = sorted;
+    cudaStream_t s = ctx->stream;
+    e = cudaMemsetAsync(ctx->u[0], 0, nb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->u[1], 0, nb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->w, 0, nb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->E, 0, eb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->scal, 0, sizeof(double) * SC_N, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counter, 0, sizeof(unsigned) * 4, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->tile_ptr, tptr.data(), sizeof(int) * (ntiles + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && ctx->n_loads > 0)
+        e = cudaMemcpyAsync(ctx->loads, ctx->host_loads.data(), sizeof(LoadEntry) * ctx->n_loads,
+                            cudaMemcpyHostToDevice, s);
+    // phi = V
+    double *dvol = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&dvol, sizeof(double) * ctx->P);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dvol, ctx->vol.data(), sizeof(double) * ctx->P, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        fill_phase<<<grid_of(nc * ctx->P), 256, 0, s>>>(nc, ctx->P, dvol, ctx->storage, ctx->phi);
+        e = cudaGetLastError();
+        ctx->launches++;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (dvol) cudaFree(dvol);
+    if (e != cudaSuccess) {
+        petto_destroy(ctx);
+        return PETTO_ECUDA;
+    }
+    petto_status st = refresh_material(ctx);
+    if (st != PETTO_OK) {
+        petto_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return PETTO_OK;
+}
+
+petto_status petto_synchronize(petto_ctx *ctx) {
+    if (!ctx) return PETTO_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PETTO_OK;
+}
+
+petto_status petto_set_design(petto_ctx *ctx, const void *phi, int dtype, int on_device) {
+    if (!ctx || !phi) return fail(ctx, PETTO_EINVAL, "null argument");
+    const int64_t n = (int64_t)ctx->P * ctx->L.ncells();
+    petto_status st = flat_in(ctx, phi, dtype, on_device, ctx->phi, ctx->storage, n);
+    if (st != PETTO_OK) return st;
+    ctx->have_sens = false;
+    return refresh_material(ctx);
+}
+
+petto_status petto_get_design(petto_ctx *ctx, void *phi, int dtype, int on_device) {
+    if (!ctx || !phi) return fail(ctx, PETTO_EINVAL, "null argument");
+    return flat_out(ctx, ctx->phi, ctx->storage, phi, dtype, on_device, (int64_t)ctx->P * ctx->L.ncells());
+}
+
+petto_status petto_set_state(petto_ctx *ctx, const void *u, const void *w, int dtype, int on_device) {
+    if (!ctx || !u) return fail(ctx, PETTO_EINVAL, "null argument");
+    petto_status st = node_in(ctx, u, dtype, on_device, ctx->u[ctx->cur]);
+    if (st != PETTO_OK) return st;
+    if (w) return node_in(ctx, w, dtype, on_device, ctx->w);
+    CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
+    if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
+    return PETTO_OK;
+}
+
+petto_status petto_get_state(petto_ctx *ctx, void *u, void *w, int dtype, int on_device) {
+    if (!ctx || !u) return fail(ctx, PETTO_EINVAL, "null argument");
+    petto_status st = node_out(ctx, ctx->u[ctx->cur], u, dtype, on_device);
+    if (st != PETTO_OK || !w) return st;
+    return node_out(ctx, ctx->w, w, dtype, on_device);
+}
+
+petto_status petto_get_modulus(petto_ctx *ctx, void *E, int dtype, int on_device) {
+    if (!ctx || !E) return fail(ctx, PETTO_EINVAL, "null argument");
+    if (dtype != PETTO_F32 && dtype != PETTO_F64) return fail(ctx, PETTO_EUNSUPPORTED, "modulus is f32/f64");
+    const int64_t nc = ctx->L.ncells();
+    void *ddst = E;
+    if (!on_device) {
+        petto_status st = ensure_stage(ctx, nc * dtype_size(dtype));
+        if (st != PETTO_OK) return st;
+        ddst = ctx->stage;
+    }
+    const Layout L = ctx->L;
+    cudaStream_t s = ctx->stream;
+    if (ctx->precision == 0) {
+        if (dtype == PETTO_F32) unpack_cells<float, float><<<grid_of(nc), 256, 0, s>>>(L, (const float *)ctx->E, (float *)ddst);
+        else unpack_cells<float, double><<<grid_of(nc), 256, 0, s>>>(L, (const float *)ctx->E, (double *)ddst);
+    } else {
+        if (dtype == PETTO_F32) unpack_cells<double, float><<<grid_of(nc), 256, 0, s>>>(L, (const double *)ctx->E, (float *)ddst);
+        else unpack_cells<double, double><<<grid_of(nc), 256, 0, s>>>(L, (const double *)ctx->E, (double *)ddst);
+    }
+    CK(cudaGetLastError());
+    ctx->launches++;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(E, ctx->stage, nc * dtype_size(dtype), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return PETTO_OK;
+}
+
+petto_status petto_sweep(petto_ctx *ctx, int kind, int64_t n, double a, double b, double s1, int local_dt,
+                         double *res_norm2) {
+    if (!ctx || n < 0 || (kind != PETTO_SWEEP_APT && kind != PETTO_SWEEP_PT))
+        return fail(ctx, PETTO_EINVAL, "bad sweep arguments");
+    for (int64_t t = 0; t < n; ++t) {
+        petto_status st = one_sweep(ctx, kind, a, b, s1, local_dt, res_norm2 && t == n - 1);
+        if (st != PETTO_OK) return st;
+    }
+    if (res_norm2) {
+        if (n == 0) {
+            *res_norm2 = 0.0;
+            return PETTO_OK;
+        }
+        CK(cudaMemcpyAsync(res_norm2, ctx->scal + SC_RES, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return PETTO_OK;
+}
+
+petto_status petto_residual(petto_ctx *ctx, double *res_norm2, void *R, int dtype, int on_device) {
+    if (!ctx) return PETTO_EINVAL;
+    if (!ctx->rbuf) CK(cudaMalloc(&ctx->rbuf, ctx->node_bytes()));
+    CK(cudaMemsetAsync(ctx->rbuf, 0, ctx->node_bytes(), ctx->stream));
+    SweepArgs A = base_sweep_args(ctx);
+    A.mode = 2;
+    A.want_res = 1;
+    A.u_in = ctx->u[ctx->cur];
+    A.u_out = nullptr;
+    A.w = ctx->rbuf;
+    CK(launch_sweep(A, ctx->tiling, ctx->precision, ctx->stream));
+    ctx->launches++;
+    if (res_norm2) {
+        CK(cudaMemcpyAsync(res_norm2, ctx->scal + SC_RES, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (R) return node_out(ctx, ctx->rbuf, R, dtype, on_device);
+    return PETTO_OK;
+}
+
+petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_solve_report *rep) {
+    if (!ctx || !o) return fail(ctx, PETTO_EINVAL, "null argument");
+    if (o->mode != PETTO_SOLVE_PAPER && o->mode != PETTO_SOLVE_TOL) return fail(ctx, PETTO_EINVAL, "bad mode");
+    if (o->n_apt < 0 || o->n_pt < 0 || o->max_sweeps < 0 || o->check_every < 0)
+        return fail(ctx, PETTO_EINVAL, "negative count");
+    CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
+    const int64_t total = o->mode == PETTO_SOLVE_PAPER ? o->n_apt + o->n_pt : o->max_sweeps;
+    const int ce = o->check_every;
+    int64_t sweeps = 0, na = 0, np = 0;
+    bool use_pt = false, fell = false, conv = false;
+    double best = INFINITY, last = NAN;
+    double scal[SC_N];
+    while (sweeps < total) {
+        const bool apt = !use_pt && (o->mode == PETTO_SOLVE_TOL || sweeps < o->n_apt);
+        const bool check = ce > 0 && (sweeps + 1) % ce == 0;
+        const bool final_report = (sweeps + 1 == total);
+        petto_status st = one_sweep(ctx, apt ? 0 : 1, o->a, o->b, o->s1, o->local_dt, check || final_report);
+        if (st != PETTO_OK) return st;
+        if (apt) ++na; else ++np;
+        ++sweeps;
+        if (check || final_report) {
+            st = read_scal(ctx, scal);
+            if (st != PETTO_OK) return st;
+            const double rn = std::sqrt(scal[SC_RES]);
+            last = rn;
+            if (!check) break;
+            if (!std::isfinite(rn)) {
+                CK(cudaMemsetAsync(ctx->u[ctx->cur], 0, ctx->node_bytes(), ctx->stream));
+                CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
+                use_pt = true;
+                fell = true;
+                continue;
+            }
+            if (rn > 10.0 * best && !use_pt) {
+                CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
+                use_pt = true;
+                fell = true;
+            }
+            if (rn < best) best = rn;
+            if (o->mode == PETTO_SOLVE_TOL && rn <= o->tol * ctx->f_norm) {
+                conv = true;
+                break;
+            }
+        }
+    }
+    if (rep) {
+        rep->sweeps = sweeps;
+        rep->apt_sweeps = na;
+        rep->pt_sweeps = np;
+        rep->res_norm = last;
+        rep->f_norm = ctx->f_norm;
+        rep->rel_res = ctx->f_norm > 0 ? last / ctx->f_norm : NAN;
+        rep->r_pde = last / std::pow(ctx->h, ctx->dim) / (double)ctx->L.nnodes();
+        rep->converged = conv ? 1 : 0;
+        rep->fell_back_to_pt = fell ? 1 : 0;
+    }
+    if (!std::isfinite(last)) return fail(ctx, PETTO_EDIVERGED, "residual not finite after PT fallback");
+    if (o->mode == PETTO_SOLVE_TOL && !conv) return PETTO_ENOTCONV;
+    return PETTO_OK;
+}
+
+petto_status petto_sensitivity(petto_ctx *ctx, double *compliance, double *work, void *dcdphi, int dtype,
+                               int on_device) {
+    if (!ctx) return PETTO_EINVAL;
+    CK(cudaMemsetAsync(ctx->scal + SC_SMAX, 0, sizeof(double) * MAX_PHASES, ctx->stream));
+    SensArgs sa{};
+    sa.L = ctx->L;
+    sa.physics = ctx->physics;
+    sa.ncomp = ctx->ncomp;
+    sa.nrhs = ctx->nrhs;
+    sa.k = ctx->k;
+    sa.lam = ctx->lam0;
+    sa.mu = ctx->mu0;
+    sa.h = ctx->h;
+    DesignArgs d = design_args(ctx);
+    CK(launch_sensitivity(sa, d, ctx->u[ctx->cur], ctx->E, ctx->phi, ctx->s, ctx->scal, ctx->red(), ctx->stream));
+    ctx->launches++;
+    CK(launch_work(ctx->L, ctx->ncomp, ctx->nrhs, ctx->precision, ctx->loads, ctx->n_loads, ctx->u[ctx->cur],
+                   ctx->k.src, ctx->scal, ctx->red(), ctx->stream));
+    ctx->launches++;
+    ctx->have_sens = true;
+    if (compliance || work) {
+        double sc[SC_N];
+        petto_status st = read_scal(ctx, sc);
+        if (st != PETTO_OK) return st;
+        if (compliance) *compliance = sc[SC_C];
+        if (work) *work = sc[SC_W];
+    }
+    if (dcdphi)
+        return flat_out(ctx, ctx->s, ctx->precision == 0 ? PETTO_F32 : PETTO_F64, dcdphi, dtype, on_device,
+                        (int64_t)ctx->P * ctx->L.ncells());
+    return PETTO_OK;
+}
+
+petto_status petto_design_update(petto_ctx *ctx, const petto_pf_opts *o, double *lambda) {
+    if (!ctx || !o) return fail(ctx, PETTO_EINVAL, "null argument");
+    if (!ctx->have_sens) return fail(ctx, PETTO_EINVAL, "petto_design_update needs petto_sensitivity first");
+    if (o->vol_mode != PETTO_VOL_PROJECTED && o->vol_mode != PETTO_VOL_PENALTY)
+        return fail(ctx, PETTO_EINVAL, "bad vol_mode");
+    if (o->n_bisect < 0 || o->n_bisect > 200) return fail(ctx, PETTO_EINVAL, "n_bisect out of range");
+    UpdateArgs ua{};
+    ua.ncell = ctx->L.ncells();
+    ua.P = ctx->P;
+    ua.vol_mode = o->vol_mode;
+    ua.n_bisect = o->n_bisect;
+    ua.precision = ctx->precision;
+    ua.storage = ctx->storage;
+    ua.alpha_h = o->alpha_h;
+    ua.kappa_v = o->kappa_v;
+    ua.kappa_1 = o->kappa_1;
+    for (int p = 0; p < ctx->P; ++p) ua.V[p] = ctx->vol[p];
+    if (o->vol_mode == PETTO_VOL_PENALTY) {
+        CK(launch_mean(ctx->L, ctx->P, ctx->storage, ctx->phi, ctx->scal, ctx->red(), ctx->stream));
+        ctx->launches++;
+    }
+    CK(launch_update(ua, ctx->phi, ctx->s, ctx->dscr, ctx->scal, ctx->red(), ctx->stream, &ctx->launches));
+    ctx->have_sens = false;
+    petto_status st = refresh_material(ctx);
+    if (st != PETTO_OK) return st;
+    if (lambda) {
+        double sc[SC_N];
+        st = read_scal(ctx, sc);
+        if (st != PETTO_OK) return st;
+        for (int p = 0; p < ctx->P; ++p) lambda[p] = o->vol_mode == PETTO_VOL_PROJECTED ? sc[SC_LAM + p] : sc[SC_MEAN + p];
+    }
+    return PETTO_OK;
+}
+
+petto_status petto_cahn_hilliard(petto_ctx *ctx, const petto_pf_opts *o) {
+    if (!ctx || !o) return fail(ctx, PETTO_EINVAL, "null argument");
+    if (o->ch_steps < 0) return fail(ctx, PETTO_EINVAL, "negative ch_steps");
+    for (int t = 0; t < o->ch_steps; ++t)
+        CK(launch_ch(ctx->L, ctx->P, ctx->storage, ctx->precision, o->gamma_g, o->tau, ctx->phi, ctx->mu, ctx->stream,
+                     &ctx->launches));
+    return refresh_material(ctx);
+}
+
+petto_status petto_phase_field_step(petto_ctx *ctx, const petto_pf_opts *o, double *vol_out) {
+    petto_status st = petto_design_update(ctx, o, nullptr);
+    if (st != PETTO_OK) return st;
+    st = petto_cahn_hilliard(ctx, o);
+    if (st != PETTO_OK) return st;
+    if (vol_out) {
+        CK(launch_mean(ctx->L, ctx->P, ctx->storage, ctx->phi, ctx->scal, ctx->red(), ctx->stream));
+        ctx->launches++;
+        double sc[SC_N];
+        st = read_scal(ctx, sc);
+        if (st != PETTO_OK) return st;
+        for (int p = 0; p < ctx->P; ++p) vol_out[p] = sc[SC_MEAN + p];
+    }
+    return PETTO_OK;
+}
+
+petto_status petto_optimize(petto_ctx *ctx, int n_steps, const petto_solve_opts *so, const petto_pf_opts *po,
+                            petto_step_cb cb, void *user) {
+    if (!ctx || !so || !po || n_steps < 0) return fail(ctx, PETTO_EINVAL, "bad arguments");
+    bool notconv = false;
+    for (int t = 0; t < n_steps; ++t) {
+        const auto t0 = std::chrono::steady_clock::now();
+        petto_solve_report rep{};
+        petto_status st = petto_pt_solve(ctx, so, &rep);
+        if (st == PETTO_ENOTCONV) notconv = true;
+        else if (st != PETTO_OK) return st;
+        double C = 0, W = 0, lam[MAX_PHASES] = {0}, vol[MAX_PHASES] = {0};
+        st = petto_sensitivity(ctx, &C, &W, nullptr, PETTO_F64, 0);
+        if (st != PETTO_OK) return st;
+        st = petto_design_update(ctx, po, lam);
+        if (st != PETTO_OK) return st;
+        st = petto_cahn_hilliard(ctx, po);
+        if (st != PETTO_OK) return st;
+        ctx->step++;
+        if (cb) {
+            CK(launch_mean(ctx->L, ctx->P, ctx->storage, ctx->phi, ctx->scal, ctx->red(), ctx->stream));
+            ctx->launches++;
+            double sc[SC_N];
+            st = read_scal(ctx, sc);
+            if (st != PETTO_OK) return st;
+            for (int p = 0; p < ctx->P; ++p) vol[p] = sc[SC_MEAN + p];
+            const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            const double m[8] = {(double)ctx->step, C, W, rep.rel_res, (double)rep.sweeps, secs, vol[0], lam[0]};
+            cb(m, user);
+        }
+    }
+    return notconv ? PETTO_ENOTCONV : PETTO_OK;
+}
+
+// checkpoint: magic, sizes, step, then phi (storage dtype), u, w (precision, natural layout)
+petto_status petto_save(petto_ctx *ctx, const char *path) {
+    if (!ctx || !path) return fail(ctx, PETTO_EINVAL, "null argument");
+    const int64_t nc = (int64_t)ctx->P * ctx->L.ncells();
+    const int64_t nn = (int64_t)ctx->ndofc() * ctx->L.nnodes();
+    const int pdt = ctx->precision == 0 ? PETTO_F32 : PETTO_F64;
+    std::vector<char> phi(nc * ctx->ssize()), u(nn * ctx->tsize()), w(nn * ctx->tsize());
+    petto_status st = flat_out(ctx, ctx->phi, ctx->storage, phi.data(), ctx->storage, 0, nc);
+    if (st == PETTO_OK) st = node_out(ctx, ctx->u[ctx->cur], u.data(), pdt, 0);
+    if (st == PETTO_OK) st = node_out(ctx, ctx->w, w.data(), pdt, 0);
+    if (st != PETTO_OK) return st;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(ctx, PETTO_EINVAL, std::string("cannot open ") + path);
+    const int64_t hdr[10] = {0x6f74746570LL, 1, ctx->dim, ctx->nx, ctx->ny, ctx->nz, ctx->P, ctx->ndofc(),
+                             ctx->precision * 16 + ctx->storage, ctx->step};
+    bool ok = std::fwrite(hdr, sizeof(hdr), 1, f) == 1 && std::fwrite(phi.data(), 1, phi.size(), f) == phi.size() &&
+              std::fwrite(u.data(), 1, u.size(), f) == u.size() && std::fwrite(w.data(), 1, w.size(), f) == w.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? PETTO_OK : fail(ctx, PETTO_EINVAL, "write failed");
+}
+
+petto_status petto_load(petto_ctx *ctx, const char *path) {
+    if (!ctx || !path) return fail(ctx, PETTO_EINVAL, "null argument");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, PETTO_EINVAL, std::string("cannot open ") + path);
+    int64_t hdr[10];
+    const int64_t nc = (int64_t)ctx->P * ctx->L.ncells();
+    const int64_t nn = (int64_t)ctx->ndofc() * ctx->L.nnodes();
+    bool ok = std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == 0x6f74746570LL && hdr[1] == 1 &&
+              hdr[2] == ctx->dim && hdr[3] == ctx->nx && hdr[4] == ctx->ny && hdr[5] == ctx->nz && hdr[6] == ctx->P &&
+              hdr[7] == ctx->ndofc() && hdr[8] == ctx->precision * 16 + ctx->storage;
+    std::vector<char> phi(nc * ctx->ssize()), u(nn * ctx->tsize()), w(nn * ctx->tsize());
+    ok = ok && std::fread(phi.data(), 1, phi.size(), f) == phi.size() && std::fread(u.data(), 1, u.size(), f) == u.size() &&
+         std::fread(w.data(), 1, w.size(), f) == w.size();
+    std::fclose(f);
+    if (!ok) return fail(ctx, PETTO_EINVAL, "checkpoint does not match this problem");
+    const int pdt = ctx->precision == 0 ? PETTO_F32 : PETTO_F64;
+    petto_status st = flat_in(ctx, phi.data(), ctx->storage, 0, ctx->phi, ctx->storage, nc);
+    if (st == PETTO_OK) st = node_in(ctx, u.data(), pdt, 0, ctx->u[ctx->cur]);
+    if (st == PETTO_OK) st = node_in(ctx, w.data(), pdt, 0, ctx->w);
+    if (st != PETTO_OK) return st;
+    ctx->step = hdr[9];
+    ctx->have_sens = false;
+    return refresh_material(ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,433 @@
+// design.cu -- material interpolation, compliance sensitivity, design update with its
+// volume multiplier, and the explicit Cahn-Hilliard step (PeTTO, arXiv 2509.06971).
+//
+//   material      E_c = e_min + rho^p (E0 - e_min)      (one phase, modified SIMP) or
+//                 E_c = sum_i E_i rho_i^p               (P phases; Sec. 3.1 overall
+//                 conductivity, Sec. 3.2 overall Young's modulus), rho = clamp(phi, 0, 1)
+//   sensitivity   s_{i,c} = dC/dphi_{i,c} = -(dE_c/dphi_{i,c}) e_c, the total derivative
+//                 of the self-adjoint compliance (Sec. 2.3 J_h, Sec. 3.2 J_m), with the
+//                 unit-modulus cell energy e_c evaluated from the edge/face expansion of
+//                 the corner-quadrature energy (see sweep.cu)
+//   update        g_i = alpha_h s_i / max|s_i| + kappa_1 (sum_j phi_j - 1)  (Sec. 2.3, 3.1);
+//                 projected: phi_i <- clamp(phi_i - g_i - lambda_i, 0, 1), lambda_i by
+//                 bisection on [-2, 2] with FP64 sums, all on the device (no host sync);
+//                 penalty:   phi_i <- phi_i - g_i - kappa_v (mean phi_i - V_i)
+//   Cahn-Hilliard mu = w'(phi) - gamma_g L phi,  phi <- phi + tau L mu,  w = sin^2(pi phi)/64,
+//                 L the no-flux cell Laplacian (Sec. 2.4; forward Euler in pseudo-time)
+#include <algorithm>
+
+#include "petto_internal.cuh"
+
+namespace petto {
+namespace {
+
+__device__ __forceinline__ void cell_ijk(const Layout &L, int64_t c, int &i, int &j, int &k) {
+    i = (int)(c % L.nx);
+    const int64_t r = c / L.nx;
+    j = (int)(r % L.ny);
+    k = (int)(r / L.ny);
+}
+
+template <typename T> __device__ __forceinline__ T clamp01(T x) { return x < T(0) ? T(0) : (x > T(1) ? T(1) : x); }
+
+template <typename T>
+__device__ __forceinline__ T interp_E(const DesignArgs &d, const T *rho) {
+    if (d.interp == 0) return (T)d.e_min + pow(rho[0], (T)d.penal) * ((T)d.moduli[0] - (T)d.e_min);
+    T s = 0;
+    for (int p = 0; p < d.P; ++p) s += (T)d.moduli[p] * pow(rho[p], (T)d.penal);
+    return s;
+}
+
+// derivative of the interpolation; 0 where the clamp is flat (phi outside [0, 1])
+template <typename T>
+__device__ __forceinline__ T interp_dE(const DesignArgs &d, int p, T phi) {
+    if (phi < T(0) || phi > T(1)) return T(0);
+    const T slope = d.interp == 0 ? (T)d.moduli[0] - (T)d.e_min : (T)d.moduli[p];
+    return (T)d.penal * pow(phi, (T)d.penal - T(1)) * slope;
+}
+
+template <typename T, typename S>
+__global__ void material_kernel(const DesignArgs d, const S *__restrict__ phi, T *__restrict__ E) {
+    const int64_t nc = d.L.ncells();
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        T rho[MAX_PHASES];
+        for (int p = 0; p < d.P; ++p) rho[p] = clamp01<T>((T)Store<S>::ld(phi, (int64_t)p * nc + c));
+        int i, j, k;
+        cell_ijk(d.L, c, i, j, k);
+        E[d.L.cell(i, j, k)] = interp_E<T>(d, rho);
+    }
+}
+
+// unit-modulus cell energy e_c (twice the corner-quadrature strain energy per unit E)
+template <typename T>
+__device__ __forceinline__ T cell_energy(const SensArgs &sa, const T (&ul)[8][3]) {
+    const int d = sa.L.dim, nq = 1 << d;
+    const T hs = (T)(d == 3 ? sa.h : 1.0);  // h^(d-2)
+    T edge = 0, face = 0;
+    if (sa.physics == 1) {
+        for (int b = 0; b < d; ++b)
+            for (int q = 0; q < nq; ++q)
+                if (!((q >> b) & 1)) {
+                    const T t = ul[q | (1 << b)][0] - ul[q][0];
+                    edge += t * t;
+                }
+        return T(2) * hs * edge / (T)nq;
+    }
+    const T lam = (T)sa.lam, mu = (T)sa.mu;
+    for (int b = 0; b < d; ++b)
+        for (int q = 0; q < nq; ++q)
+            if (!((q >> b) & 1)) {
+                for (int a = 0; a < d; ++a) {
+                    const T t = ul[q | (1 << b)][a] - ul[q][a];
+                    edge += (a == b ? lam + T(2) * mu : mu) * t * t;
+                }
+            }
+    // faces spanned by (a, b); in 3D two of each (third-axis bit t = 0, 1)
+    for (int a = 0; a < d; ++a)
+        for (int b = a + 1; b < d; ++b) {
+            const int c = 3 - a - b;
+            const int nt = d == 3 ? 2 : 1;
+            for (int t = 0; t < nt; ++t) {
+                T Aa = 0, Ab = 0, Ba = 0, Bb = 0;  // sums of the two a-edges / b-edges
+                for (int q = 0; q < nq; ++q) {
+                    if (d == 3 && (((q >> c) & 1) != t)) continue;
+                    if (!((q >> a) & 1)) {
+                        Aa += ul[q | (1 << a)][a] - ul[q][a];
+                        Ab += ul[q | (1 << a)][b] - ul[q][b];
+                    }
+                    if (!((q >> b) & 1)) {
+                        Ba += ul[q | (1 << b)][a] - ul[q][a];
+                        Bb += ul[q | (1 << b)][b] - ul[q][b];
+                    }
+                }
+                // means are sums / 2
+                face += lam * (Aa * Bb) * T(0.25) + mu * (Ab * Ba) * T(0.25);
+            }
+        }
+    // e = 2 h^(d-2) [ edge / 2^d + face / 2^(d-2) ]
+    return T(2) * hs * (edge / (T)nq + face * T(4) / (T)nq);
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(256) sensitivity_kernel(const SensArgs sa, const DesignArgs d,
+                                                          const T *__restrict__ u, const T *__restrict__ E,
+                                                          const S *__restrict__ phi, T *__restrict__ s,
+                                                          double *scal, const RedBuf rb) {
+    __shared__ double sh[32];
+    const Layout &L = sa.L;
+    const int64_t nc = L.ncells();
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double comp = 0.0;
+    double smax[MAX_PHASES];
+    for (int p = 0; p < d.P; ++p) smax[p] = 0.0;
+    if (c < nc) {
+        int i, j, k;
+        cell_ijk(L, c, i, j, k);
+        const int nq = 1 << L.dim;
+        T e = 0;
+        for (int r = 0; r < sa.nrhs; ++r) {
+            T ul[8][3];
+            for (int q = 0; q < nq; ++q) {
+                const int64_t n = L.node(i + (q & 1), j + ((q >> 1) & 1), L.dim == 3 ? k + ((q >> 2) & 1) : 0);
+                for (int a = 0; a < sa.ncomp; ++a) ul[q][a] = u[(int64_t)(r * sa.ncomp + a) * L.cstride + n];
+            }
+            e += cell_energy<T>(sa, ul);
+        }
+        const T Ec = E[L.cell(i, j, k)];
+        comp = (double)Ec * (double)e;
+        for (int p = 0; p < d.P; ++p) {
+            const T ph = (T)Store<S>::ld(phi, (int64_t)p * nc + c);
+            const T sv = -interp_dE<T>(d, p, ph) * e;
+            s[(int64_t)p * nc + c] = sv;
+            smax[p] = fabs((double)sv);
+        }
+    }
+    for (int p = 0; p < d.P; ++p) {
+        double m = warp_max(smax[p]);
+        if ((threadIdx.x & 31) == 0 && m > 0.0) atomic_max_nonneg(&scal[SC_SMAX + p], m);
+    }
+    const double tot = block_sum(comp, sh);
+    if (publish_partial(tot, rb, blockIdx.x, gridDim.x)) {
+        const double t = sum_partials(rb, 0, gridDim.x, sh);
+        if (threadIdx.x == 0) {
+            scal[SC_C] = t;
+            *rb.counter = 0u;
+        }
+    }
+}
+
+template <typename T>
+__global__ void work_kernel(const Layout L, int ncomp, int nrhs, const LoadEntry *__restrict__ loads, int n_loads,
+                            const T *__restrict__ u, double src, double *scal, const RedBuf rb) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t l = tid; l < n_loads; l += stride) acc += loads[l].vald * (double)u[(int64_t)loads[l].comp * L.cstride + loads[l].node];
+    if (src != 0.0) {
+        const int64_t nn = L.nnodes();
+        for (int64_t n = tid; n < nn; n += stride) {
+            const int i = (int)(n % L.NX);
+            const int64_t r = n / L.NX;
+            const int j = (int)(r % L.NY), k = (int)(r / L.NY);
+            const int cnt = ((i > 0) + (i < L.nx)) * ((j > 0) + (j < L.ny)) * (L.dim == 3 ? ((k > 0) + (k < L.nz)) : 1);
+            for (int rr = 0; rr < nrhs; ++rr) acc += src * cnt * (double)u[(int64_t)(rr * ncomp) * L.cstride + L.node(i, j, k)];
+        }
+    }
+    const double t = block_sum(acc, sh);
+    if (publish_partial(t, rb, blockIdx.x, gridDim.x)) {
+        const double tt = sum_partials(rb, 0, gridDim.x, sh);
+        if (threadIdx.x == 0) {
+            scal[SC_W] = tt;
+            *rb.counter = 0u;
+        }
+    }
+}
+
+// -------------------------------------------------------------- design update
+
+template <typename T, typename S>
+__global__ void upd_prepare(const UpdateArgs ua, S *__restrict__ phi, const T *__restrict__ s, T *__restrict__ dbuf,
+                            const double *__restrict__ scal) {
+    const int64_t nc = ua.ncell;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        T tot = 0;
+        T ph[MAX_PHASES];
+        for (int p = 0; p < ua.P; ++p) {
+            ph[p] = (T)Store<S>::ld(phi, (int64_t)p * nc + c);
+            tot += ph[p];
+        }
+        for (int p = 0; p < ua.P; ++p) {
+            const double smax = scal[SC_SMAX + p];
+            T g = smax > 0.0 ? (T)ua.alpha_h * s[(int64_t)p * nc + c] / (T)smax : T(0);
+            g += (T)ua.kappa_1 * (tot - T(1));
+            const T dv = ph[p] - g;
+            if (ua.vol_mode == 0) {
+                dbuf[(int64_t)p * nc + c] = dv;
+            } else {
+                const T nv = dv - (T)ua.kappa_v * ((T)scal[SC_MEAN + p] - (T)ua.V[p]);
+                Store<S>::st(phi, (int64_t)p * nc + c, nv);
+            }
+        }
+    }
+}
+
+__global__ void bis_init(int P, double *scal) {
+    const int p = threadIdx.x;
+    if (p < P) {
+        scal[SC_LO + p] = -2.0;
+        scal[SC_HI + p] = 2.0;
+    }
+}
+
+// One bisection halving for every phase: grid (blocks, P).  Each block publishes its
+// partial sum of clamp(d - mid, 0, 1); the last block sums each phase's partials in block
+// order and moves that phase's bracket.
+template <typename T>
+__global__ void __launch_bounds__(256) bis_step(const UpdateArgs ua, const T *__restrict__ dbuf, double *scal,
+                                                const RedBuf rb) {
+    __shared__ double sh[32];
+    const int p = blockIdx.y;
+    const int64_t nc = ua.ncell;
+    const double mid = 0.5 * (scal[SC_LO + p] + scal[SC_HI + p]);
+    double acc = 0.0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)dbuf[(int64_t)p * nc + c] - mid;
+        acc += v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+    }
+    const double t = block_sum(acc, sh);
+    if (publish_partial(t, rb, (int64_t)p * gridDim.x + blockIdx.x, gridDim.x * gridDim.y)) {
+        for (int q = 0; q < ua.P; ++q) {
+            const double m = sum_partials(rb, (int64_t)q * gridDim.x, gridDim.x, sh) / (double)nc;
+            if (threadIdx.x == 0) {
+                volatile double *vs = scal;
+                const double md = 0.5 * (vs[SC_LO + q] + vs[SC_HI + q]);
+                if (m > ua.V[q]) vs[SC_LO + q] = md;
+                else vs[SC_HI + q] = md;
+            }
+        }
+        if (threadIdx.x == 0) *rb.counter = 0u;
+    }
+}
+
+template <typename T, typename S>
+__global__ void upd_apply(const UpdateArgs ua, S *__restrict__ phi, const T *__restrict__ dbuf, double *scal) {
+    const int p = blockIdx.y;
+    const int64_t nc = ua.ncell;
+    const double lam = 0.5 * (scal[SC_LO + p] + scal[SC_HI + p]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) scal[SC_LAM + p] = lam;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)dbuf[(int64_t)p * nc + c] - lam;
+        Store<S>::st(phi, (int64_t)p * nc + c, (T)(v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v)));
+    }
+}
+
+// -------------------------------------------------------------- Cahn-Hilliard
+
+template <typename T, typename S>
+__device__ __forceinline__ T lap_at(const Layout &L, const S *v, int64_t c, int i, int j, int k) {
+    const T x = (T)Store<S>::ld(v, c);
+    T s = 0;
+    if (i > 0) s += (T)Store<S>::ld(v, c - 1) - x;
+    if (i < L.nx - 1) s += (T)Store<S>::ld(v, c + 1) - x;
+    if (j > 0) s += (T)Store<S>::ld(v, c - L.nx) - x;
+    if (j < L.ny - 1) s += (T)Store<S>::ld(v, c + L.nx) - x;
+    if (L.dim == 3) {
+        const int64_t pl = (int64_t)L.nx * L.ny;
+        if (k > 0) s += (T)Store<S>::ld(v, c - pl) - x;
+        if (k < L.nz - 1) s += (T)Store<S>::ld(v, c + pl) - x;
+    }
+    return s;
+}
+
+__device__ __forceinline__ float dwell(float x) { return sinpif(2.0f * x) * (float)(3.14159265358979323846 / 64.0); }
+__device__ __forceinline__ double dwell(double x) { return sinpi(2.0 * x) * (3.14159265358979323846 / 64.0); }
+
+template <typename T, typename S>
+__global__ void ch_mu(const Layout L, const S *__restrict__ phi, T *__restrict__ mu, double gamma_g) {
+    const int64_t nc = L.ncells();
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_ijk(L, c, i, j, k);
+        const T ph = (T)Store<S>::ld(phi, c);
+        mu[c] = dwell(ph) - (T)gamma_g * lap_at<T, S>(L, phi, c, i, j, k);
+    }
+}
+
+template <typename T, typename S>
+__global__ void ch_phi(const Layout L, S *__restrict__ phi, const T *__restrict__ mu, double tau) {
+    const int64_t nc = L.ncells();
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        int i, j, k;
+        cell_ijk(L, c, i, j, k);
+        const T nv = (T)Store<S>::ld(phi, c) + (T)tau * lap_at<T, T>(L, mu, c, i, j, k);
+        Store<S>::st(phi, c, nv);
+    }
+}
+
+template <typename S>
+__global__ void mean_kernel(int64_t nc, int P, const S *__restrict__ phi, double *scal, const RedBuf rb) {
+    __shared__ double sh[32];
+    const int p = blockIdx.y;
+    double acc = 0.0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)Store<S>::ld(phi, (int64_t)p * nc + c);
+    const double t = block_sum(acc, sh);
+    if (publish_partial(t, rb, (int64_t)p * gridDim.x + blockIdx.x, gridDim.x * gridDim.y)) {
+        for (int q = 0; q < P; ++q) {
+            const double m = sum_partials(rb, (int64_t)q * gridDim.x, gridDim.x, sh);
+            if (threadIdx.x == 0) scal[SC_MEAN + q] = m / (double)nc;
+        }
+        if (threadIdx.x == 0) *rb.counter = 0u;
+    }
+}
+
+int grid_for(int64_t n, int block, int cap = 152 * 16) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- dispatch helpers
+
+#define PETTO_DISPATCH_STORAGE(storage, SVAR, ...)                      \
+    switch (storage) {                                                  \
+        case 0: { using SVAR = float; __VA_ARGS__; } break;             \
+        case 1: { using SVAR = double; __VA_ARGS__; } break;            \
+        case 2: { using SVAR = __nv_bfloat16; __VA_ARGS__; } break;     \
+        case 3: { using SVAR = __half; __VA_ARGS__; } break;            \
+        default: return cudaErrorInvalidValue;                          \
+    }
+
+#define PETTO_DISPATCH_PREC(prec, TVAR, ...)                            \
+    if ((prec) == 0) { using TVAR = float; __VA_ARGS__; }               \
+    else { using TVAR = double; __VA_ARGS__; }
+
+cudaError_t launch_material(const DesignArgs &d, const void *phi, void *E, cudaStream_t s) {
+    const int g = grid_for(d.L.ncells(), 256);
+    PETTO_DISPATCH_PREC(d.precision, T,
+        PETTO_DISPATCH_STORAGE(d.storage, S,
+            material_kernel<T, S><<<g, 256, 0, s>>>(d, static_cast<const S *>(phi), static_cast<T *>(E))))
+    return cudaGetLastError();
+}
+
+int64_t reduction_capacity(const Layout &L, int ntiles, int P) {
+    int64_t c = ntiles;
+    c = std::max<int64_t>(c, (L.ncells() + 255) / 256);
+    c = std::max<int64_t>(c, (int64_t)152 * 4 * P);
+    c = std::max<int64_t>(c, (int64_t)152 * 16);
+    return c + 64;
+}
+
+cudaError_t launch_sensitivity(const SensArgs &sa, const DesignArgs &d, const void *u, const void *E,
+                               const void *phi, void *sbuf, double *scal, RedBuf rb, cudaStream_t st) {
+    const int64_t nc = sa.L.ncells();
+    const int g = (int)((nc + 255) / 256);
+    PETTO_DISPATCH_PREC(d.precision, T,
+        PETTO_DISPATCH_STORAGE(d.storage, S,
+            sensitivity_kernel<T, S><<<g, 256, 0, st>>>(sa, d, static_cast<const T *>(u), static_cast<const T *>(E),
+                                                        static_cast<const S *>(phi), static_cast<T *>(sbuf), scal, rb)))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_work(const Layout &L, int ncomp, int nrhs, int precision, const LoadEntry *loads, int n_loads,
+                        const void *u, double body_src, double *scal, RedBuf rb, cudaStream_t st) {
+    const int g = body_src != 0.0 ? grid_for(L.nnodes(), 256) : 1;
+    PETTO_DISPATCH_PREC(precision, T,
+        work_kernel<T><<<g, 256, 0, st>>>(L, ncomp, nrhs, loads, n_loads, static_cast<const T *>(u), body_src, scal, rb))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mean(const Layout &L, int P, int storage, const void *phi, double *scal, RedBuf rb,
+                        cudaStream_t st) {
+    const int64_t nc = L.ncells();
+    dim3 grid(grid_for(nc, 256, 152 * 4), P);
+    PETTO_DISPATCH_STORAGE(storage, S,
+        mean_kernel<S><<<grid, 256, 0, st>>>(nc, P, static_cast<const S *>(phi), scal, rb))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(const UpdateArgs &ua, void *phi, const void *s, void *dscratch, double *scal,
+                          RedBuf rb, cudaStream_t st, int64_t *launches) {
+    const int g = grid_for(ua.ncell, 256);
+    PETTO_DISPATCH_PREC(ua.precision, T,
+        PETTO_DISPATCH_STORAGE(ua.storage, S,
+            upd_prepare<T, S><<<g, 256, 0, st>>>(ua, static_cast<S *>(phi), static_cast<const T *>(s),
+                                                 static_cast<T *>(dscratch), scal)))
+    *launches += 1;
+    if (ua.vol_mode != 0) return cudaGetLastError();
+    bis_init<<<1, 32, 0, st>>>(ua.P, scal);
+    *launches += 1;
+    dim3 grid(grid_for(ua.ncell, 256, 152 * 4), ua.P);
+    for (int it = 0; it < ua.n_bisect; ++it) {
+        PETTO_DISPATCH_PREC(ua.precision, T,
+            bis_step<T><<<grid, 256, 0, st>>>(ua, static_cast<const T *>(dscratch), scal, rb))
+        *launches += 1;
+    }
+    dim3 grid2(g, ua.P);
+    PETTO_DISPATCH_PREC(ua.precision, T,
+        PETTO_DISPATCH_STORAGE(ua.storage, S,
+            upd_apply<T, S><<<grid2, 256, 0, st>>>(ua, static_cast<S *>(phi), static_cast<const T *>(dscratch), scal)))
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ch(const Layout &L, int P, int storage, int precision, double gamma_g, double tau, void *phi,
+                      void *mu_scratch, cudaStream_t st, int64_t *launches) {
+    const int64_t nc = L.ncells();
+    const int g = grid_for(nc, 256);
+    for (int p = 0; p < P; ++p) {
+        PETTO_DISPATCH_PREC(precision, T,
+            PETTO_DISPATCH_STORAGE(storage, S,
+                S *ph = static_cast<S *>(phi) + (int64_t)p * nc;
+                ch_mu<T, S><<<g, 256, 0, st>>>(L, ph, static_cast<T *>(mu_scratch), gamma_g);
+                ch_phi<T, S><<<g, 256, 0, st>>>(L, ph, static_cast<const T *>(mu_scratch), tau)))
+        *launches += 2;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace petto

@@ -1,0 +1,255 @@
+// petto_internal.cuh -- device layout, kernel parameter blocks and launchers of libpetto.
+//
+// Device layout (GB300 HBM).  Every node field is stored per component (structure of
+// arrays) with a one-node ring of zeros around the grid, so that the stencil kernels
+// read neighbours without bounds tests; rows are padded to a multiple of 32 elements
+// (128 B in FP32) and node i = 0 sits at element offset OX = 4 of its row (16-byte
+// aligned).  Cell fields used by the sweeps (the modulus E) carry the same zero ring,
+// so missing cells outside the domain contribute nothing.  Design fields phi, the
+// sensitivity and the update scratch use the compact natural layout [P][cells].
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace petto {
+
+constexpr int OX = 4;          // element offset of node/cell i = 0 within a padded row
+constexpr int MAX_BOXES = 16;  // Dirichlet boxes per problem
+constexpr int MAX_RHS = 4;     // load cases solved together
+constexpr int MAX_PHASES = 8;  // design phases
+
+struct Layout {
+    int dim;
+    int nx, ny, nz;        // cells (nz = 1 in 2D)
+    int NX, NY, NZ;        // nodes (NZ = 1 in 2D)
+    int64_t SX, SY, SZ;    // padded node pitches (elements); SZ = 1 plane in 2D
+    int64_t CX, CY, CZ;    // padded cell pitches
+    int64_t cstride;       // elements per node component (SX * SY * SZ)
+    int64_t estride;       // elements of the padded cell field (CX * CY * CZ)
+
+    __host__ __device__ __forceinline__ int64_t node(int i, int j, int k) const {
+        return ((int64_t)(k + (dim == 3 ? 1 : 0)) * SY + (j + 1)) * SX + (i + OX);
+    }
+    __host__ __device__ __forceinline__ int64_t cell(int i, int j, int k) const {
+        return ((int64_t)(k + (dim == 3 ? 1 : 0)) * CY + (j + 1)) * CX + (i + OX);
+    }
+    __host__ __device__ __forceinline__ int64_t ncells() const { return (int64_t)nx * ny * nz; }
+    __host__ __device__ __forceinline__ int64_t nnodes() const { return (int64_t)NX * NY * NZ; }
+};
+
+Layout make_layout(int dim, int nx, int ny, int nz);
+
+struct Box {
+    int lo[3], hi[3];
+    unsigned mask;
+};
+
+struct BoxSet {
+    int n;
+    Box b[MAX_BOXES];
+};
+
+// Sparse nodal load, stored in the padded node index space and grouped per sweep tile.
+struct LoadEntry {
+    int64_t node;   // padded node index
+    int comp;       // component c = r * ncomp + a
+    float valf;
+    double vald;
+};
+
+// Scratch of the deterministic grid reductions (see publish_partial below).
+struct RedBuf {
+    double *partials;
+    unsigned *counter;
+};
+
+// Constants of the discrete operator (unit modulus, scaled by h^(d-2)); see sweep.cu.
+struct OpConst {
+    double ce_par, ce_perp;   // edge force: (2/2^d) h^(d-2) (lam+2mu), (2/2^d) h^(d-2) mu
+    double cf_lam, cf_mu;     // face corner force: h^(d-2)/2^d * lam, * mu
+    double cdiag;             // diag(K) = cdiag * (sum of adjacent cell moduli)
+    double ct;                // thermal edge conductance factor (2/2^d) h^(d-2)
+    double src;               // nodal body source per adjacent cell: f h^d / 2^d
+};
+
+struct SweepArgs {
+    Layout L;
+    int physics;              // 0 elastic, 1 thermal
+    int ncomp, nrhs;
+    int mode;                 // 0 APT, 1 PT, 2 residual only (writes R to w_or_r)
+    int local_dt;
+    int want_res;
+    double a, b, s1;
+    OpConst k;
+    BoxSet boxes;
+    const void *u_in;
+    void *u_out;
+    void *w;                  // APT increment (in place) or R output (mode 2)
+    const void *E;
+    const int *tile_ptr;      // per-tile CSR of loads
+    const LoadEntry *loads;
+    double *res2;             // receives sum R^2 (if want_res)
+    RedBuf red;
+};
+
+// ---------------------------------------------------------------- reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum of one double per thread; result valid in thread 0.  Needs a
+// 32-double shared scratch.  All threads of the block must call it.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    const int lane = threadIdx.x & 31;
+    const int wid = (threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z)) >> 5;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+    (void)lane;
+    v = warp_sum(v);
+    __syncthreads();
+    if ((tid & 31) == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (tid < 32) {
+        r = tid < nw ? sh[tid] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+// Deterministic grid reduction: every block publishes its partial at partials[idx];
+// the last block to arrive (atomic ticket) sums the partials in index order, so the
+// result does not depend on block scheduling.  The ticket counter is reset by that last
+// block, so kernels on one stream can reuse the same buffer one after another.
+__device__ __forceinline__ int block_tid() { return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z); }
+__device__ __forceinline__ int block_nthreads() { return blockDim.x * blockDim.y * blockDim.z; }
+
+// v: the block's total, valid in thread 0.  Returns true in every thread of the last block.
+__device__ __forceinline__ bool publish_partial(double v, const RedBuf &rb, int64_t idx, unsigned total) {
+    __shared__ bool last;
+    if (block_tid() == 0) {
+        rb.partials[idx] = v;
+        __threadfence();
+        last = (atomicAdd(rb.counter, 1u) == total - 1u);
+    }
+    __syncthreads();
+    return last;
+}
+
+// Called by all threads of the last block: ordered sum of partials[off, off + n).
+__device__ __forceinline__ double sum_partials(const RedBuf &rb, int64_t off, int64_t n, double *sh) {
+    __threadfence();
+    const volatile double *p = rb.partials;
+    double acc = 0.0;
+    for (int64_t i = block_tid(); i < n; i += block_nthreads()) acc += p[off + i];
+    return block_sum(acc, sh);
+}
+
+// atomic max for non-negative floating values through their ordered bit patterns
+__device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
+    atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+// ---------------------------------------------------------------- storage types
+
+template <typename S> struct Store;
+template <> struct Store<float> {
+    __device__ __forceinline__ static float ld(const float *p, int64_t i) { return p[i]; }
+    __device__ __forceinline__ static void st(float *p, int64_t i, float v) { p[i] = v; }
+};
+template <> struct Store<double> {
+    __device__ __forceinline__ static double ld(const double *p, int64_t i) { return p[i]; }
+    __device__ __forceinline__ static void st(double *p, int64_t i, double v) { p[i] = v; }
+};
+template <> struct Store<__nv_bfloat16> {
+    __device__ __forceinline__ static float ld(const __nv_bfloat16 *p, int64_t i) { return __bfloat162float(p[i]); }
+    __device__ __forceinline__ static void st(__nv_bfloat16 *p, int64_t i, float v) { p[i] = __float2bfloat16_rn(v); }
+};
+template <> struct Store<__half> {
+    __device__ __forceinline__ static float ld(const __half *p, int64_t i) { return __half2float(p[i]); }
+    __device__ __forceinline__ static void st(__half *p, int64_t i, float v) { p[i] = __float2half_rn(v); }
+};
+
+// ---------------------------------------------------------------- launchers
+
+// Sweep tiling used by the load lists: returns the tile id of a node for the kernel
+// that will run (all sweep kernels of one context share one tiling).
+struct Tiling {
+    int bx, by;        // threads per block in x, y (nodes per tile in x, y)
+    int zs;            // nodes per tile in z (3D), 1 in 2D
+    int gx, gy, gz;    // tiles per axis
+    int ox, oy;        // output nodes per tile in x, y (== bx, by for gather kernels)
+    int kind;          // 0 = gather kernel, 1 = z-marching 3D kernel
+    __host__ int tile_of(int i, int j, int k) const {
+        return (i / ox) + gx * ((j / oy) + gy * (k / zs));
+    }
+    int ntiles() const { return gx * gy * gz; }
+};
+
+Tiling choose_tiling(const Layout &L, int physics, int precision);
+
+cudaError_t launch_sweep(const SweepArgs &a, const Tiling &t, int precision, cudaStream_t s);
+
+struct DesignArgs {
+    Layout L;
+    int P, interp, storage, precision;
+    double penal, e_min;
+    double moduli[MAX_PHASES];
+};
+
+cudaError_t launch_material(const DesignArgs &d, const void *phi, void *E, cudaStream_t s);
+
+struct SensArgs {
+    Layout L;
+    int physics, ncomp, nrhs;
+    OpConst k;
+    double lam, mu;      // unit Lame constants (elastic)
+    double h;
+};
+
+// scal layout (device doubles): [0] sum R^2, [1] compliance, [2] work, [8..8+P) max|s_i|,
+// [16..16+P) lo_i, [24..24+P) hi_i, [32..32+P) sums, [40..40+P) mean_i, [48..48+P) lambda_i
+constexpr int SC_RES = 0, SC_C = 1, SC_W = 2, SC_SMAX = 8, SC_LO = 16, SC_HI = 24, SC_SUM = 32,
+              SC_MEAN = 40, SC_LAM = 48, SC_N = 64;
+
+cudaError_t launch_sensitivity(const SensArgs &sa, const DesignArgs &d, const void *u, const void *E,
+                               const void *phi, void *s, double *scal, RedBuf rb, cudaStream_t st);
+
+cudaError_t launch_work(const Layout &L, int ncomp, int nrhs, int precision, const LoadEntry *loads, int n_loads,
+                        const void *u, double body_src, double *scal, RedBuf rb, cudaStream_t st);
+
+// partial-sum capacity (doubles) a problem of this size needs
+int64_t reduction_capacity(const Layout &L, int ntiles, int P);
+
+struct UpdateArgs {
+    int64_t ncell;
+    int P, vol_mode, n_bisect, precision, storage;
+    double alpha_h, kappa_v, kappa_1;
+    double V[MAX_PHASES];
+};
+
+cudaError_t launch_update(const UpdateArgs &ua, void *phi, const void *s, void *dscratch, double *scal,
+                          RedBuf rb, cudaStream_t st, int64_t *launches);
+
+cudaError_t launch_ch(const Layout &L, int P, int storage, int precision, double gamma_g, double tau,
+                      void *phi, void *mu_scratch, cudaStream_t st, int64_t *launches);
+
+cudaError_t launch_mean(const Layout &L, int P, int storage, const void *phi, double *scal, RedBuf rb,
+                        cudaStream_t st);
+
+}  // namespace petto

@@ -1,0 +1,472 @@
+// sweep.cu -- fused PT / APT sweep kernels (Sec. 2.2; Sec. 3.2 PT and APT systems).
+//
+// The discrete operator.  The paper discretises the momentum balance and the heat
+// equation by finite differences without fixing the stencil.  This library uses the
+// corner-quadrature energy: in every cell, at each corner, the gradient is taken from
+// the one-sided differences along the cell edges meeting there, and the cell energy is
+// the corner average times h^d.  Expanding that energy gives two kinds of terms, which
+// is the form the kernels evaluate:
+//   * edge terms   W_e = h^(d-2)/2^d * Ebar_e * [(lam+2mu) A_par^2 + mu |A_perp|^2]
+//                  with A = u(end) - u(start) along the grid edge e and Ebar_e the sum of
+//                  the moduli of the 2^(d-1) cells around e;
+//   * face terms   W_f = h^(d-2)/2^(d-2) * Etil_f * [lam Abar_a Bbar_b + mu Abar_b Bbar_a]
+//                  for each face f spanned by axes (a, b), with Abar (Bbar) the mean of the
+//                  difference vectors of its two a- (b-) edges and Etil_f the sum of the
+//                  moduli of the cells sharing f (elasticity only; Sec. 3.2 stress law with
+//                  the Lame parameters of Sec. 3.2, plane strain in 2D).
+// Heat conduction keeps only the edge terms with the scalar temperature.  K u is the
+// gradient of sum_e W_e + sum_f W_f.  The FP64 oracle evaluates the corner definition
+// literally with a cell loop; these kernels gather, per node, the forces of its incident
+// edges and faces, so the two agree only if the expansion above is right.
+//
+// One sweep (APT):  R = F - K u (0 on supports);  w <- a w + b' R;  u' <- u + w
+//          (PT):    u' <- u + s1' R
+// with b' = b or b / diag(K) (local pseudo-time step), u read from one buffer and written
+// to the other (ping-pong), w updated in place.  sum R^2 over free DOFs is accumulated in
+// FP64 when requested (the residual norm of Sec. 3.1, for convergence checks).
+#include "petto_internal.cuh"
+
+namespace petto {
+
+Layout make_layout(int dim, int nx, int ny, int nz) {
+    Layout L{};
+    L.dim = dim;
+    L.nx = nx;
+    L.ny = ny;
+    L.nz = dim == 3 ? nz : 1;
+    L.NX = nx + 1;
+    L.NY = ny + 1;
+    L.NZ = dim == 3 ? nz + 1 : 1;
+    auto rup = [](int64_t v, int64_t m) { return (v + m - 1) / m * m; };
+    L.SX = rup(L.NX + OX + 1, 32);
+    L.SY = L.NY + 2;
+    L.SZ = dim == 3 ? L.NZ + 2 : 1;
+    L.CX = rup(nx + OX + 1, 32);
+    L.CY = ny + 2;
+    L.CZ = dim == 3 ? L.nz + 2 : 1;
+    L.cstride = L.SX * L.SY * L.SZ;
+    L.estride = L.CX * L.CY * L.CZ;
+    return L;
+}
+
+namespace {
+
+constexpr int GATHER3_ZS = 4;
+
+__device__ __forceinline__ unsigned fixed_mask(const BoxSet &bs, int i, int j, int k) {
+    unsigned m = 0;
+    for (int q = 0; q < bs.n; ++q) {
+        const Box &b = bs.b[q];
+        if (i >= b.lo[0] && i <= b.hi[0] && j >= b.lo[1] && j <= b.hi[1] && k >= b.lo[2] && k <= b.hi[2]) m |= b.mask;
+    }
+    return m;
+}
+
+template <typename T> __device__ __forceinline__ T load_val(const LoadEntry &e);
+template <> __device__ __forceinline__ float load_val<float>(const LoadEntry &e) { return e.valf; }
+template <> __device__ __forceinline__ double load_val<double>(const LoadEntry &e) { return e.vald; }
+
+// ------------------------------------------------------------- 2D operator
+// U[dy][dx][a] for offsets -1..1 around the node, Ec[cy][cx] for the 4 adjacent cells
+// (cell (i-1+cx, j-1+cy)).
+template <typename T>
+__device__ __forceinline__ void ku_elastic_2d(const T (&U)[3][3][2], const T (&Ec)[2][2], const OpConst &k,
+                                              T (&Ku)[2]) {
+    const T cpar = (T)k.ce_par, cperp = (T)k.ce_perp, cl = (T)k.cf_lam, cm = (T)k.cf_mu;
+    Ku[0] = Ku[1] = T(0);
+    // edges along x (b = 0) and y (b = 1)
+    {
+        const T Em = Ec[0][0] + Ec[1][0], Ep = Ec[0][1] + Ec[1][1];  // x-edges: cells left / right
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const T c = a == 0 ? cpar : cperp;
+            Ku[a] += c * (Em * (U[1][1][a] - U[1][0][a]) - Ep * (U[1][2][a] - U[1][1][a]));
+        }
+    }
+    {
+        const T Em = Ec[0][0] + Ec[0][1], Ep = Ec[1][0] + Ec[1][1];  // y-edges: cells below / above
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const T c = a == 1 ? cpar : cperp;
+            Ku[a] += c * (Em * (U[1][1][a] - U[0][1][a]) - Ep * (U[2][1][a] - U[1][1][a]));
+        }
+    }
+    // the four cells as faces spanned by (x, y); the node is at local corner (al, be)
+#pragma unroll
+    for (int al = 0; al < 2; ++al)
+#pragma unroll
+        for (int be = 0; be < 2; ++be) {
+            const T Et = Ec[1 - be][1 - al];
+            // offsets of the face's corner (0,0) relative to the node
+            const int x0 = 1 - al, y0 = 1 - be;  // index into U of local corner (0,0)
+            T SA[2], SB[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                SA[c] = (U[y0][x0 + 1][c] - U[y0][x0][c]) + (U[y0 + 1][x0 + 1][c] - U[y0 + 1][x0][c]);
+                SB[c] = (U[y0 + 1][x0][c] - U[y0][x0][c]) + (U[y0 + 1][x0 + 1][c] - U[y0][x0 + 1][c]);
+            }
+            // a = x, b = y
+            const T Ga = Et * (cl * SB[1] + cm * SA[1]);
+            const T Gb = Et * (cm * SB[0] + cl * SA[0]);
+            const T Ha = Et * (cl * SB[1] - cm * SA[1]);
+            const T Hb = Et * (cm * SB[0] - cl * SA[0]);
+            if (al == 1 && be == 1) { Ku[0] += Ga; Ku[1] += Gb; }
+            if (al == 0 && be == 0) { Ku[0] -= Ga; Ku[1] -= Gb; }
+            if (al == 1 && be == 0) { Ku[0] += Ha; Ku[1] += Hb; }
+            if (al == 0 && be == 1) { Ku[0] -= Ha; Ku[1] -= Hb; }
+        }
+}
+
+template <typename T>
+__device__ __forceinline__ T ku_thermal_2d(const T (&U)[3][3], const T (&Ec)[2][2], const OpConst &k) {
+    const T ct = (T)k.ct;
+    const T Exm = Ec[0][0] + Ec[1][0], Exp = Ec[0][1] + Ec[1][1];
+    const T Eym = Ec[0][0] + Ec[0][1], Eyp = Ec[1][0] + Ec[1][1];
+    return ct * (Exm * (U[1][1] - U[1][0]) - Exp * (U[1][2] - U[1][1]) + Eym * (U[1][1] - U[0][1]) -
+                 Eyp * (U[2][1] - U[1][1]));
+}
+
+// ------------------------------------------------------------- 3D operator
+// U[dz][dy][dx][a], Ec[cz][cy][cx] (cell (i-1+cx, j-1+cy, k-1+cz)).
+template <typename T>
+__device__ __forceinline__ T Uat(const T (&U)[3][3][3][3], int ox, int oy, int oz, int c) {
+    return U[oz + 1][oy + 1][ox + 1][c];
+}
+
+template <typename T>
+__device__ __forceinline__ T Eat(const T (&Ec)[2][2][2], int cx, int cy, int cz) {
+    return Ec[cz][cy][cx];
+}
+
+template <typename T>
+__device__ __forceinline__ void ku_elastic_3d(const T (&U)[3][3][3][3], const T (&Ec)[2][2][2], const OpConst &k,
+                                              T (&Ku)[3]) {
+    const T cpar = (T)k.ce_par, cperp = (T)k.ce_perp, cl = (T)k.cf_lam, cm = (T)k.cf_mu;
+    Ku[0] = Ku[1] = Ku[2] = T(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        T Em = 0, Ep = 0;
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                int c0[3], c1[3];
+                // the two free cell indices run over the other axes
+                const int o1 = (b + 1) % 3, o2 = (b + 2) % 3;
+                c0[b] = 0; c0[o1] = p; c0[o2] = q;
+                c1[b] = 1; c1[o1] = p; c1[o2] = q;
+                Em += Eat(Ec, c0[0], c0[1], c0[2]);
+                Ep += Eat(Ec, c1[0], c1[1], c1[2]);
+            }
+        int m[3] = {0, 0, 0}, pl[3] = {0, 0, 0};
+        m[b] = -1;
+        pl[b] = 1;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const T c = a == b ? cpar : cperp;
+            const T u0 = Uat(U, 0, 0, 0, a);
+            Ku[a] += c * (Em * (u0 - Uat(U, m[0], m[1], m[2], a)) - Ep * (Uat(U, pl[0], pl[1], pl[2], a) - u0));
+        }
+    }
+    // faces spanned by (a, b) with a < b; c is the third axis
+#pragma unroll
+    for (int pa = 0; pa < 3; ++pa) {
+        const int a = pa == 2 ? 1 : 0;
+        const int b = pa == 0 ? 1 : 2;
+        const int c = 3 - a - b;
+#pragma unroll
+        for (int al = 0; al < 2; ++al)
+#pragma unroll
+            for (int be = 0; be < 2; ++be) {
+                T Et = 0;
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    int ci[3];
+                    ci[a] = 1 - al; ci[b] = 1 - be; ci[c] = cc;
+                    Et += Eat(Ec, ci[0], ci[1], ci[2]);
+                }
+                T SA[2], SB[2];  // components (a, b) only
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int comp = q == 0 ? a : b;
+                    T sa = 0, sb = 0;
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        int s0[3] = {0, 0, 0}, s1[3] = {0, 0, 0};
+                        // a-edge at local b-offset t: (-al, t-be) -> (1-al, t-be)
+                        s0[a] = -al; s0[b] = t - be;
+                        s1[a] = 1 - al; s1[b] = t - be;
+                        sa += Uat(U, s1[0], s1[1], s1[2], comp) - Uat(U, s0[0], s0[1], s0[2], comp);
+                        // b-edge at local a-offset t: (t-al, -be) -> (t-al, 1-be)
+                        int r0[3] = {0, 0, 0}, r1[3] = {0, 0, 0};
+                        r0[a] = t - al; r0[b] = -be;
+                        r1[a] = t - al; r1[b] = 1 - be;
+                        sb += Uat(U, r1[0], r1[1], r1[2], comp) - Uat(U, r0[0], r0[1], r0[2], comp);
+                    }
+                    SA[q] = sa;
+                    SB[q] = sb;
+                }
+                const T Ga = Et * (cl * SB[1] + cm * SA[1]);
+                const T Gb = Et * (cm * SB[0] + cl * SA[0]);
+                const T Ha = Et * (cl * SB[1] - cm * SA[1]);
+                const T Hb = Et * (cm * SB[0] - cl * SA[0]);
+                if (al == 1 && be == 1) { Ku[a] += Ga; Ku[b] += Gb; }
+                if (al == 0 && be == 0) { Ku[a] -= Ga; Ku[b] -= Gb; }
+                if (al == 1 && be == 0) { Ku[a] += Ha; Ku[b] += Hb; }
+                if (al == 0 && be == 1) { Ku[a] -= Ha; Ku[b] -= Hb; }
+            }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T ku_thermal_3d(const T (&U)[3][3][3], const T (&Ec)[2][2][2], const OpConst &k) {
+    const T ct = (T)k.ct;
+    T acc = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        T Em = 0, Ep = 0;
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                int c0[3], c1[3];
+                const int o1 = (b + 1) % 3, o2 = (b + 2) % 3;
+                c0[b] = 0; c0[o1] = p; c0[o2] = q;
+                c1[b] = 1; c1[o1] = p; c1[o2] = q;
+                Em += Ec[c0[2]][c0[1]][c0[0]];
+                Ep += Ec[c1[2]][c1[1]][c1[0]];
+            }
+        int m[3] = {0, 0, 0}, pl[3] = {0, 0, 0};
+        m[b] = -1;
+        pl[b] = 1;
+        const T u0 = U[1][1][1];
+        acc += Em * (u0 - U[m[2] + 1][m[1] + 1][m[0] + 1]) - Ep * (U[pl[2] + 1][pl[1] + 1][pl[0] + 1] - u0);
+    }
+    return ct * acc;
+}
+
+// ------------------------------------------------------------- update
+template <typename T>
+struct Upd {
+    const SweepArgs &A;
+    double res;
+    __device__ __forceinline__ void apply(int64_t idx_c, int c, bool fixed, T Ku, T F, T diag, T *uo, const T *ui,
+                                          T *w) {
+        T R = fixed ? T(0) : F - Ku;
+        if (A.want_res) res += (double)R * (double)R;
+        const T u = ui[idx_c];
+        if (A.mode == 0) {
+            const T step = A.local_dt ? (T)A.b / diag : (T)A.b;
+            const T wn = fixed ? T(0) : (T)A.a * w[idx_c] + step * R;
+            w[idx_c] = wn;
+            uo[idx_c] = fixed ? T(0) : u + wn;
+        } else if (A.mode == 1) {
+            const T step = A.local_dt ? (T)A.s1 / diag : (T)A.s1;
+            uo[idx_c] = fixed ? T(0) : u + step * R;
+        } else {
+            w[idx_c] = R;
+        }
+        (void)c;
+    }
+};
+
+// block total of sum R^2, then the deterministic grid reduction into *res2
+__device__ __forceinline__ void finish_res(const SweepArgs &A, double res) {
+    __shared__ double sh[32];
+    if (!A.want_res) return;
+    const double r = block_sum(res, sh);
+    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    const int64_t bid = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+    if (publish_partial(r, A.red, bid, nb)) {
+        const double t = sum_partials(A.red, 0, nb, sh);
+        if (block_tid() == 0) {
+            *A.res2 = t;
+            *A.red.counter = 0u;
+        }
+    }
+}
+
+// ------------------------------------------------------------- 2D gather kernel
+template <typename T, int PHYS>
+__global__ void __launch_bounds__(256) sweep2d_gather(const SweepArgs A) {
+    const Layout &L = A.L;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const T *__restrict__ ui = static_cast<const T *>(A.u_in);
+    T *__restrict__ uo = static_cast<T *>(A.u_out);
+    T *__restrict__ w = static_cast<T *>(A.w);
+    const T *__restrict__ E = static_cast<const T *>(A.E);
+    Upd<T> up{A, 0.0};
+    if (i < L.NX && j < L.NY) {
+        T Ec[2][2];
+#pragma unroll
+        for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+            for (int cx = 0; cx < 2; ++cx) Ec[cy][cx] = __ldg(&E[L.cell(i - 1 + cx, j - 1 + cy, 0)]);
+        const T S = Ec[0][0] + Ec[0][1] + Ec[1][0] + Ec[1][1];
+        const T diag = (T)A.k.cdiag * S;
+        const unsigned fm = fixed_mask(A.boxes, i, j, 0);
+        const int64_t n0 = L.node(i, j, 0);
+        const int tile = blockIdx.x + gridDim.x * blockIdx.y;
+        const int l0 = A.tile_ptr[tile], l1 = A.tile_ptr[tile + 1];
+        const int ncnt = ((i > 0) + (i < L.nx)) * ((j > 0) + (j < L.ny));
+        for (int r = 0; r < A.nrhs; ++r) {
+            if (PHYS == 0) {
+                T U[3][3][2];
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const T *uc = ui + (int64_t)(r * 2 + a) * L.cstride;
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) U[dy][dx][a] = __ldg(&uc[n0 + (dy - 1) * L.SX + (dx - 1)]);
+                }
+                T Ku[2];
+                ku_elastic_2d<T>(U, Ec, A.k, Ku);
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const int c = r * 2 + a;
+                    T F = 0;
+                    for (int l = l0; l < l1; ++l)
+                        if (A.loads[l].node == n0 && A.loads[l].comp == c) F += load_val<T>(A.loads[l]);
+                    const int64_t idx = (int64_t)c * L.cstride + n0;
+                    up.apply(idx, c, (fm >> a) & 1u, Ku[a], F, diag, uo, ui, w);
+                }
+            } else {
+                T U[3][3];
+                const T *uc = ui + (int64_t)r * L.cstride;
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) U[dy][dx] = __ldg(&uc[n0 + (dy - 1) * L.SX + (dx - 1)]);
+                const T Ku = ku_thermal_2d<T>(U, Ec, A.k);
+                T F = (T)A.k.src * (T)ncnt;
+                for (int l = l0; l < l1; ++l)
+                    if (A.loads[l].node == n0 && A.loads[l].comp == r) F += load_val<T>(A.loads[l]);
+                const int64_t idx = (int64_t)r * L.cstride + n0;
+                up.apply(idx, r, fm & 1u, Ku, F, diag, uo, ui, w);
+            }
+        }
+    }
+    finish_res(A, up.res);
+}
+
+// ------------------------------------------------------------- 3D gather kernel
+template <typename T, int PHYS>
+__global__ void __launch_bounds__(128) sweep3d_gather(const SweepArgs A) {
+    const Layout &L = A.L;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int kb = blockIdx.z * GATHER3_ZS;
+    const T *__restrict__ ui = static_cast<const T *>(A.u_in);
+    T *__restrict__ uo = static_cast<T *>(A.u_out);
+    T *__restrict__ w = static_cast<T *>(A.w);
+    const T *__restrict__ E = static_cast<const T *>(A.E);
+    Upd<T> up{A, 0.0};
+    const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int l0 = A.tile_ptr[tile], l1 = A.tile_ptr[tile + 1];
+    if (i < L.NX && j < L.NY) {
+        const int ke = min(kb + GATHER3_ZS, L.NZ);
+        for (int k = kb; k < ke; ++k) {
+            T Ec[2][2][2];
+#pragma unroll
+            for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+                for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+                    for (int cx = 0; cx < 2; ++cx) Ec[cz][cy][cx] = __ldg(&E[L.cell(i - 1 + cx, j - 1 + cy, k - 1 + cz)]);
+            T S = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) S += Ec[q >> 2][(q >> 1) & 1][q & 1];
+            const T diag = (T)A.k.cdiag * S;
+            const unsigned fm = fixed_mask(A.boxes, i, j, k);
+            const int64_t n0 = L.node(i, j, k);
+            const int ncnt = ((i > 0) + (i < L.nx)) * ((j > 0) + (j < L.ny)) * ((k > 0) + (k < L.nz));
+            for (int r = 0; r < A.nrhs; ++r) {
+                if (PHYS == 0) {
+                    T U[3][3][3][3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const T *uc = ui + (int64_t)(r * 3 + a) * L.cstride;
+#pragma unroll
+                        for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                                for (int dx = 0; dx < 3; ++dx)
+                                    U[dz][dy][dx][a] = __ldg(&uc[n0 + (dz - 1) * L.SX * L.SY + (dy - 1) * L.SX + (dx - 1)]);
+                    }
+                    T Ku[3];
+                    ku_elastic_3d<T>(U, Ec, A.k, Ku);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const int c = r * 3 + a;
+                        T F = 0;
+                        for (int l = l0; l < l1; ++l)
+                            if (A.loads[l].node == n0 && A.loads[l].comp == c) F += load_val<T>(A.loads[l]);
+                        up.apply((int64_t)c * L.cstride + n0, c, (fm >> a) & 1u, Ku[a], F, diag, uo, ui, w);
+                    }
+                } else {
+                    T U[3][3][3];
+                    const T *uc = ui + (int64_t)r * L.cstride;
+#pragma unroll
+                    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                            for (int dx = 0; dx < 3; ++dx)
+                                U[dz][dy][dx] = __ldg(&uc[n0 + (dz - 1) * L.SX * L.SY + (dy - 1) * L.SX + (dx - 1)]);
+                    const T Ku = ku_thermal_3d<T>(U, Ec, A.k);
+                    T F = (T)A.k.src * (T)ncnt;
+                    for (int l = l0; l < l1; ++l)
+                        if (A.loads[l].node == n0 && A.loads[l].comp == r) F += load_val<T>(A.loads[l]);
+                    up.apply((int64_t)r * L.cstride + n0, r, fm & 1u, Ku, F, diag, uo, ui, w);
+                }
+            }
+        }
+    }
+    finish_res(A, up.res);
+}
+
+}  // namespace
+
+Tiling choose_tiling(const Layout &L, int physics, int precision) {
+    (void)physics;
+    (void)precision;
+    Tiling t{};
+    if (L.dim == 2) {
+        t.bx = 32; t.by = 8; t.zs = 1; t.kind = 0;
+    } else {
+        t.bx = 32; t.by = 4; t.zs = GATHER3_ZS; t.kind = 0;
+    }
+    t.ox = t.bx;
+    t.oy = t.by;
+    t.gx = (L.NX + t.ox - 1) / t.ox;
+    t.gy = (L.NY + t.oy - 1) / t.oy;
+    t.gz = (L.NZ + t.zs - 1) / t.zs;
+    return t;
+}
+
+cudaError_t launch_sweep(const SweepArgs &a, const Tiling &t, int precision, cudaStream_t s) {
+    dim3 block(t.bx, t.by, 1), grid(t.gx, t.gy, t.gz);
+    if (a.L.dim == 2) {
+        if (precision == 0) {
+            if (a.physics == 0) sweep2d_gather<float, 0><<<grid, block, 0, s>>>(a);
+            else sweep2d_gather<float, 1><<<grid, block, 0, s>>>(a);
+        } else {
+            if (a.physics == 0) sweep2d_gather<double, 0><<<grid, block, 0, s>>>(a);
+            else sweep2d_gather<double, 1><<<grid, block, 0, s>>>(a);
+        }
+    } else {
+        if (precision == 0) {
+            if (a.physics == 0) sweep3d_gather<float, 0><<<grid, block, 0, s>>>(a);
+            else sweep3d_gather<float, 1><<<grid, block, 0, s>>>(a);
+        } else {
+            if (a.physics == 0) sweep3d_gather<double, 0><<<grid, block, 0, s>>>(a);
+            else sweep3d_gather<double, 1><<<grid, block, 0, s>>>(a);
+        }
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace petto

@@ -1,0 +1,309 @@
+"""Thin Python layer over the C ABI: a ``Problem`` owning one ``petto_ctx``.
+
+All numerics run in libpetto's CUDA kernels; this module only marshals arrays and
+structs.  Arrays may be numpy arrays (host) or CUDA torch tensors (device, read and
+written on the context's stream).  Layouts are the natural ones of include/petto.h:
+design [P, cells] with cell (i,j,k) -> i + nx(j + ny k); state [C, nodes] with node
+(i,j,k) -> i + (nx+1)(j + (ny+1)k).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import capi as C
+
+_DT = {np.dtype(np.float32): C.PETTO_F32, np.dtype(np.float64): C.PETTO_F64}
+_STORAGE = {"f32": C.PETTO_F32, "f64": C.PETTO_F64, "bf16": C.PETTO_BF16, "f16": C.PETTO_F16}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_cuda_tensor(x) -> bool:
+    try:
+        torch = _torch()
+    except ImportError:
+        return False
+    return isinstance(x, torch.Tensor) and x.is_cuda
+
+
+def _tensor_dtype(t) -> int:
+    torch = _torch()
+    m = {torch.float32: C.PETTO_F32, torch.float64: C.PETTO_F64, torch.bfloat16: C.PETTO_BF16,
+         torch.float16: C.PETTO_F16}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported tensor dtype {t.dtype}")
+    return m[t.dtype]
+
+
+class Problem:
+    """One PeTTO instance on the GPU (grid, materials, loads, supports, design, state)."""
+
+    def __init__(self, spec, *, nrhs: int = 1, load_cases=None, stream=None, precision: str | None = None,
+                 storage: str | None = None):
+        self.spec = spec
+        self.lib = C.load()
+        prec = precision or spec.precision
+        stor = storage or spec.storage
+        self.precision = C.PETTO_F64 if prec == "f64" else C.PETTO_F32
+        self.np_dtype = np.float64 if prec == "f64" else np.float32
+        self.storage = _STORAGE[stor]
+        self.nrhs = nrhs
+        self.ncomp = spec.ncomp
+        self.P = spec.n_phases
+        self.ncells = spec.ncells
+        self.nnodes = spec.nnodes
+        if stream is None:
+            try:
+                torch = _torch()
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+            except ImportError:
+                stream = None
+        self.stream = stream
+        cases = load_cases if load_cases is not None else [spec.loads]
+        if len(cases) != nrhs:
+            raise ValueError("need one load list per load case")
+        nodes, comps, vals, rhs = [], [], [], []
+        for r, case in enumerate(cases):
+            for node, comp, val in case:
+                node = list(node) + [0] * (3 - len(node))
+                nodes.extend(node[:3])
+                comps.append(comp)
+                vals.append(val)
+                rhs.append(r)
+        self._keep = []
+        n = len(vals)
+        node_a = (ctypes.c_int64 * max(1, len(nodes)))(*nodes)
+        comp_a = (ctypes.c_int32 * max(1, n))(*comps)
+        val_a = (ctypes.c_double * max(1, n))(*vals)
+        rhs_a = (ctypes.c_int32 * max(1, n))(*rhs)
+        loads = C.petto_loads(n, node_a, comp_a, val_a, rhs_a, float(spec.body_source))
+        boxes = []
+        masks = []
+        for lo, hi, mask in spec.boxes:
+            lo = list(lo) + [0] * (3 - len(lo))
+            hi = list(hi) + [0] * (3 - len(hi))
+            boxes.extend(lo[:3] + hi[:3])
+            masks.append(mask)
+        box_a = (ctypes.c_int64 * max(1, len(boxes)))(*boxes)
+        mask_a = (ctypes.c_uint32 * max(1, len(masks)))(*masks)
+        bcs = C.petto_bcs(len(masks), box_a, mask_a)
+        mod = (ctypes.c_double * len(spec.moduli))(*spec.moduli)
+        mat = C.petto_materials(spec.physics, self.P, mod, spec.e_min, spec.nu, spec.penal, spec.interp)
+        grid = C.petto_grid(spec.dim, spec.nx, spec.ny, spec.nz if spec.dim == 3 else 0, spec.h)
+        vol = (ctypes.c_double * self.P)(*spec.vol_frac)
+        opt = C.petto_options(self.precision, self.storage, nrhs, ctypes.c_void_p(stream) if stream else None)
+        ctx = ctypes.c_void_p()
+        st = self.lib.petto_create(ctypes.byref(grid), ctypes.byref(mat), ctypes.byref(loads), ctypes.byref(bcs),
+                                   vol, ctypes.byref(opt), ctypes.byref(ctx))
+        if st != C.PETTO_OK:
+            raise C.PettoError(st, "petto_create failed")
+        self.ctx = ctx
+        if spec.phi0 is not None:
+            self.set_design(np.asarray(spec.phi0, dtype=np.float64))
+
+    # --------------------------------------------------------------- lifecycle
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.petto_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _ck(self, st, allow=(C.PETTO_OK,)):
+        return C.check(self.ctx, st, allow)
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.petto_launch_count(self.ctx))
+
+    def profile(self, enable: bool = True):
+        self._ck(self.lib.petto_profile(self.ctx, int(bool(enable))))
+
+    def profile_read(self):
+        """(summed sweep-kernel device milliseconds, timed sweep launches) since last read."""
+        ms, n = ctypes.c_double(0.0), ctypes.c_int64(0)
+        self._ck(self.lib.petto_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def synchronize(self):
+        self._ck(self.lib.petto_synchronize(self.ctx))
+
+    # --------------------------------------------------------------- fields
+    def _in(self, x, allowed=(C.PETTO_F32, C.PETTO_F64)):
+        if _is_cuda_tensor(x):
+            x = x.contiguous()
+            dt = _tensor_dtype(x)
+            if dt not in allowed:
+                raise TypeError("dtype not accepted here")
+            return x, ctypes.c_void_p(x.data_ptr()), dt, 1
+        a = np.ascontiguousarray(x)
+        if a.dtype not in _DT:
+            a = a.astype(np.float64)
+        return a, a.ctypes.data_as(ctypes.c_void_p), _DT[a.dtype], 0
+
+    def set_design(self, phi):
+        keep, ptr, dt, dev = self._in(phi, (C.PETTO_F32, C.PETTO_F64, C.PETTO_BF16, C.PETTO_F16))
+        self._ck(self.lib.petto_set_design(self.ctx, ptr, dt, dev))
+
+    def get_design(self, dtype=np.float64) -> np.ndarray:
+        out = np.empty((self.P, self.ncells), dtype=dtype)
+        self._ck(self.lib.petto_get_design(self.ctx, out.ctypes.data_as(ctypes.c_void_p), _DT[out.dtype], 0))
+        return out
+
+    def set_state(self, u, w=None):
+        ku, pu, dt, dev = self._in(u)
+        if w is not None:
+            kw, pw, dtw, devw = self._in(w)
+            assert dtw == dt and devw == dev
+        else:
+            pw = None
+        self._ck(self.lib.petto_set_state(self.ctx, pu, pw, dt, dev))
+
+    def get_state(self, with_w: bool = False, dtype=np.float64):
+        shape = (self.nrhs * self.ncomp, self.nnodes)
+        u = np.empty(shape, dtype=dtype)
+        w = np.empty(shape, dtype=dtype) if with_w else None
+        self._ck(self.lib.petto_get_state(self.ctx, u.ctypes.data_as(ctypes.c_void_p),
+                                          w.ctypes.data_as(ctypes.c_void_p) if with_w else None, _DT[u.dtype], 0))
+        return (u, w) if with_w else u
+
+    def get_modulus(self, dtype=np.float64) -> np.ndarray:
+        E = np.empty(self.ncells, dtype=dtype)
+        self._ck(self.lib.petto_get_modulus(self.ctx, E.ctypes.data_as(ctypes.c_void_p), _DT[E.dtype], 0))
+        return E
+
+    # --------------------------------------------------------------- solver
+    def sweep(self, kind: int, n: int, a: float = 0.0, b: float = 0.0, s1: float = 0.0, local_dt: bool = False,
+              want_res: bool = True):
+        r = ctypes.c_double(0.0)
+        self._ck(self.lib.petto_sweep(self.ctx, kind, int(n), float(a), float(b), float(s1), int(bool(local_dt)),
+                                      ctypes.byref(r) if want_res else None))
+        return r.value if want_res else None
+
+    def residual(self, with_field: bool = True, dtype=np.float64):
+        r = ctypes.c_double(0.0)
+        R = np.empty((self.nrhs * self.ncomp, self.nnodes), dtype=dtype) if with_field else None
+        self._ck(self.lib.petto_residual(self.ctx, ctypes.byref(r),
+                                         R.ctypes.data_as(ctypes.c_void_p) if with_field else None,
+                                         _DT[np.dtype(dtype)], 0))
+        return r.value, R
+
+    def solve_opts(self, mode=C.PETTO_SOLVE_TOL, **kw) -> C.petto_solve_opts:
+        s = self.spec
+        return C.petto_solve_opts(mode, int(kw.get("n_apt", 0)), int(kw.get("n_pt", 0)), float(kw.get("a", s.apt_a)),
+                                  float(kw.get("b", s.apt_b)), float(kw.get("s1", s.pt_s1)),
+                                  float(kw.get("tol", s.tol)), int(kw.get("max_sweeps", s.max_sweeps)),
+                                  int(kw.get("check_every", s.check_every)),
+                                  int(bool(kw.get("local_dt", s.local_dt))))
+
+    def solve(self, mode=C.PETTO_SOLVE_TOL, **kw) -> dict:
+        o = self.solve_opts(mode, **kw)
+        rep = C.petto_solve_report()
+        st = self._ck(self.lib.petto_pt_solve(self.ctx, ctypes.byref(o), ctypes.byref(rep)),
+                      allow=(C.PETTO_OK, C.PETTO_ENOTCONV))
+        return {"sweeps": rep.sweeps, "apt_sweeps": rep.apt_sweeps, "pt_sweeps": rep.pt_sweeps,
+                "res_norm": rep.res_norm, "f_norm": rep.f_norm, "rel_res": rep.rel_res, "r_pde": rep.r_pde,
+                "converged": bool(rep.converged), "fell_back_to_pt": bool(rep.fell_back_to_pt),
+                "status": st}
+
+    # --------------------------------------------------------------- design
+    def sensitivity(self, out=None, want_field: bool = True):
+        """(compliance, work, dC/dphi) -- out may be a CUDA tensor [P, cells] (f32/f64)."""
+        Cv, Wv = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        if out is not None and _is_cuda_tensor(out):
+            self._ck(self.lib.petto_sensitivity(self.ctx, ctypes.byref(Cv), ctypes.byref(Wv),
+                                                ctypes.c_void_p(out.data_ptr()), _tensor_dtype(out), 1))
+            return Cv.value, Wv.value, out
+        s = np.empty((self.P, self.ncells), dtype=np.float64) if want_field else None
+        self._ck(self.lib.petto_sensitivity(self.ctx, ctypes.byref(Cv), ctypes.byref(Wv),
+                                            s.ctypes.data_as(ctypes.c_void_p) if want_field else None,
+                                            C.PETTO_F64, 0))
+        return Cv.value, Wv.value, s
+
+    def pf_opts(self, **kw) -> C.petto_pf_opts:
+        s = self.spec
+        return C.petto_pf_opts(int(kw.get("vol_mode", s.vol_mode)), float(kw.get("alpha_h", s.alpha_h)),
+                               float(kw.get("kappa_v", s.kappa_v)), float(kw.get("kappa_1", s.kappa_1)),
+                               float(kw.get("gamma_g", s.gamma_g)), float(kw.get("tau", s.tau)),
+                               int(kw.get("ch_steps", 1)), int(kw.get("n_bisect", s.n_bisect)))
+
+    def design_update(self, **kw) -> np.ndarray:
+        o = self.pf_opts(**kw)
+        lam = (ctypes.c_double * self.P)()
+        self._ck(self.lib.petto_design_update(self.ctx, ctypes.byref(o), lam))
+        return np.array(lam[:])
+
+    def cahn_hilliard(self, **kw):
+        o = self.pf_opts(**kw)
+        self._ck(self.lib.petto_cahn_hilliard(self.ctx, ctypes.byref(o)))
+
+    def phase_field_step(self, **kw) -> np.ndarray:
+        o = self.pf_opts(**kw)
+        vol = (ctypes.c_double * self.P)()
+        self._ck(self.lib.petto_phase_field_step(self.ctx, ctypes.byref(o), vol))
+        return np.array(vol[:])
+
+    def optimize(self, n_steps: int, solve_kw: dict | None = None, pf_kw: dict | None = None, log=None):
+        so = self.solve_opts(**(solve_kw or {}))
+        po = self.pf_opts(**(pf_kw or {}))
+        hist = []
+
+        def _cb(m, user):
+            row = {"step": int(m[0]), "compliance": m[1], "work": m[2], "rel_res": m[3], "sweeps": int(m[4]),
+                   "seconds": m[5], "mean_phi0": m[6], "lambda0": m[7]}
+            hist.append(row)
+            if log:
+                log(row)
+
+        cb = C.petto_step_cb(_cb)
+        st = self._ck(self.lib.petto_optimize(self.ctx, int(n_steps), ctypes.byref(so), ctypes.byref(po), cb, None),
+                      allow=(C.PETTO_OK, C.PETTO_ENOTCONV))
+        return hist, st
+
+    def save(self, path: str):
+        self._ck(self.lib.petto_save(self.ctx, path.encode()))
+
+    def load(self, path: str):
+        self._ck(self.lib.petto_load(self.ctx, path.encode()))
+
+
+class PettoCompliance:
+    """torch.autograd.Function factory: C(phi) = F.u(phi) with u solved on the GPU, and
+    dC/dphi from the hand-written adjoint kernel (the compliance is self-adjoint, so the
+    adjoint state is u itself; Sec. 2.3 computes this derivative by AD instead)."""
+
+    @staticmethod
+    def apply(phi, problem: Problem, **solve_kw):
+        torch = _torch()
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, x):
+                problem.set_design(x.detach())
+                problem.solve(**solve_kw)
+                grad = torch.empty_like(x, dtype=torch.float64 if problem.precision == C.PETTO_F64 else torch.float32)
+                Cv, _, _ = problem.sensitivity(out=grad)
+                ctx.save_for_backward(grad)
+                return torch.tensor(Cv, dtype=torch.float64, device=x.device)
+
+            @staticmethod
+            def backward(ctx, g):
+                (grad,) = ctx.saved_tensors
+                return (g * grad).to(phi.dtype), None
+
+        return _Fn.apply(phi)

@@ -1,0 +1,327 @@
+"""GPU (libpetto, CUDA sm_103a) against the FP64 oracle, element by element.
+
+Tolerances (from the stated targets):
+  * one FP64 sweep, sensitivity, update, CH step: 1e-12 relative (max-abs / max-abs)
+  * FP32 fields after sweeps: 1e-5 relative L2 per field
+  * converged compliance: 1e-4 relative; final density after design steps: 1e-3 mean-abs
+Sizes span several sweep tiles (32 x 8 in 2D, 32 x 4 x 4 in 3D) with ragged tails.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2509_06971_gb300 import workloads as W
+from tests._util import nodes_to_oracle, oracle_materials, oracle_problem, oracle_to_nodes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2509_06971_gb300 import problem as PR
+    return PR
+
+
+def relmax(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def specs_small():
+    return {
+        "elastic2d": W.cantilever2d(70, 46, load_cells=6).with_(loads=W.cantilever2d(70, 46, load_cells=6).loads
+                                                              + [((13, 46, 0), 0, 0.3)]),
+        "mbb2d": W.mbb_halfbeam(67, 21),
+        "elastic3d": W.cantilever3d(37, 13, 11),
+        "thermal2d": W.heat2d(66).with_(boxes=[((0, 29, 0), (0, 37, 0), 1), ((66, 0, 0), (66, 3, 0), 1)]),
+        "thermal3d": W.cantilever3d(21, 9, 10).with_(physics=W.THERMAL, moduli=[1.0], e_min=1e-3,
+                                                      boxes=[((0, 2, 3), (0, 6, 7), 1)], loads=[((21, 4, 5), 0, 0.5)],
+                                                      body_source=0.01),
+    }
+
+
+def _setup(P, spec, seed, precision="f64", storage=None):
+    spec = spec.with_(precision=precision, storage=storage or precision)
+    prob = P.Problem(spec)
+    phi = W.random_design(spec, seed=seed, lo=0.05, hi=0.95)
+    prob.set_design(phi)
+    op, om = oracle_problem(spec), oracle_materials(spec)
+    return spec, prob, op, om, phi
+
+
+@pytest.mark.parametrize("name", list(specs_small()))
+@pytest.mark.parametrize("kind", ["apt", "apt_local", "pt", "pt_local"])
+def test_single_sweep_fp64(P, name, kind):
+    spec = specs_small()[name]
+    spec, prob, op, om, phi = _setup(P, spec, seed=1)
+    u0 = W.random_state(spec, seed=2)
+    w0 = W.random_state(spec, seed=3, scale=0.1)
+    prob.set_state(u0, w0)
+    a, b, s1 = 0.93, 0.21, 0.17
+    local = kind.endswith("local")
+    if local:
+        b, s1 = 0.9, 0.7
+    apt = kind.startswith("apt")
+    r2 = prob.sweep(0 if apt else 1, 1, a, b, s1, local)
+    ug, wg = prob.get_state(with_w=True)
+    E = om.modulus(phi)
+    assert relmax(prob.get_modulus(), E) < 1e-14
+    F, fixed = op.load_vector(), op.fixed_mask()
+    uo, wo = nodes_to_oracle(u0), nodes_to_oracle(w0)
+    if apt:
+        r2o = op.apt_sweep(E, F, fixed, a, b, uo, wo, local_dt=local)
+        assert relmax(wg, oracle_to_nodes(wo, spec.ncomp)) < 1e-12
+    else:
+        r2o = op.pt_sweep(E, F, fixed, s1, uo, local_dt=local)
+    assert relmax(ug, oracle_to_nodes(uo, spec.ncomp)) < 1e-12
+    assert abs(r2 - r2o) < 1e-12 * r2o
+    prob.close()
+
+
+@pytest.mark.parametrize("name", ["elastic2d", "elastic3d", "thermal2d", "thermal3d"])
+def test_residual_field_fp64(P, name):
+    spec = specs_small()[name]
+    spec, prob, op, om, phi = _setup(P, spec, seed=4)
+    u0 = W.random_state(spec, seed=5)
+    prob.set_state(u0)
+    r2, R = prob.residual()
+    Ro, r2o = op.residual(om.modulus(phi), op.load_vector(), op.fixed_mask(), nodes_to_oracle(u0))
+    assert relmax(R, oracle_to_nodes(Ro, spec.ncomp)) < 1e-12
+    assert abs(r2 - r2o) < 1e-12 * r2o
+    prob.close()
+
+
+@pytest.mark.parametrize("name", ["elastic2d", "elastic3d", "thermal2d"])
+def test_fp32_sweeps_rel_l2(P, name):
+    spec = specs_small()[name]
+    spec, prob, op, om, phi = _setup(P, spec, seed=6, precision="f32")
+    u0 = W.random_state(spec, seed=7)
+    prob.set_state(u0.astype(np.float32))
+    a, b = 0.95, 0.9
+    prob.sweep(0, 20, a, b, 0.0, True)
+    ug, wg = prob.get_state(with_w=True)
+    E = om.modulus(np.asarray(phi, np.float32).astype(np.float64))
+    F, fixed = op.load_vector(), op.fixed_mask()
+    uo = nodes_to_oracle(u0.astype(np.float32).astype(np.float64))
+    wo = np.zeros_like(uo)
+    for _ in range(20):
+        op.apt_sweep(E, F, fixed, a, b, uo, wo, local_dt=True)
+    uo_n, wo_n = oracle_to_nodes(uo, spec.ncomp), oracle_to_nodes(wo, spec.ncomp)
+    for c in range(spec.ncomp):
+        assert rel_l2(ug[c], uo_n[c]) < 1e-5
+        assert rel_l2(wg[c], wo_n[c]) < 1e-5
+    prob.close()
+
+
+@pytest.mark.parametrize("name", ["mbb2d", "elastic3d", "thermal2d", "thermal3d"])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_sensitivity_and_compliance(P, name, precision):
+    spec = specs_small()[name]
+    spec, prob, op, om, phi = _setup(P, spec, seed=8, precision=precision)
+    u0 = W.random_state(spec, seed=9)
+    prob.set_state(u0.astype(prob.np_dtype))
+    Cg, Wg, sg = prob.sensitivity()
+    phi_o = np.asarray(phi, prob.np_dtype).astype(np.float64)
+    uo = nodes_to_oracle(u0.astype(prob.np_dtype))
+    E = om.modulus(phi_o)
+    so, Co = om.sensitivity(phi_o, E, op.cell_energy(uo))
+    Wo = float(op.load_vector() @ uo)
+    tol = 1e-12 if precision == "f64" else 1e-5
+    assert abs(Cg - Co) < tol * abs(Co)
+    assert abs(Wg - Wo) < tol * max(abs(Wo), 1e-30) + tol * abs(Co) * 1e-3
+    if precision == "f64":
+        assert relmax(sg, so) < tol
+    else:
+        assert rel_l2(sg, so) < tol
+    prob.close()
+
+
+def test_multiphase_sensitivity_fp64(P):
+    spec = W.cantilever2d(40, 20, load_cells=4).with_(moduli=[1e-3, 1.0, 0.5], interp=W.SIMP_PAPER,
+                                                       vol_frac=[0.6, 0.2, 0.2])
+    spec, prob, op, om, phi = _setup(P, spec, seed=10)
+    u0 = W.random_state(spec, seed=11)
+    prob.set_state(u0)
+    Cg, _, sg = prob.sensitivity()
+    so, Co = om.sensitivity(phi, om.modulus(phi), op.cell_energy(nodes_to_oracle(u0)))
+    assert abs(Cg - Co) < 1e-12 * Co
+    assert relmax(sg, so) < 1e-12
+    prob.close()
+
+
+@pytest.mark.parametrize("vol_mode", [W.PROJECTED, W.PENALTY])
+@pytest.mark.parametrize("nph", [1, 3])
+def test_design_update_fp64(P, vol_mode, nph):
+    base = W.mbb_halfbeam(45, 17)
+    if nph == 3:
+        base = base.with_(moduli=[1e-3, 1.0, 0.5], interp=W.SIMP_PAPER, vol_frac=[0.5, 0.3, 0.2])
+    spec, prob, op, om, phi = _setup(P, base, seed=12)
+    u0 = W.random_state(spec, seed=13)
+    prob.set_state(u0)
+    _, _, sg = prob.sensitivity()
+    kw = dict(vol_mode=vol_mode, alpha_h=0.1, kappa_v=0.37, kappa_1=0.05 if nph == 3 else 0.0, n_bisect=60)
+    lam_g = prob.design_update(**kw)
+    phi_o = phi.copy()
+    lam_o = O.update(phi_o, sg, spec.vol_frac, **kw)
+    assert relmax(prob.get_design(), phi_o) < 1e-12
+    assert np.abs(lam_g - lam_o).max() < 1e-12
+    if vol_mode == W.PROJECTED:
+        assert np.abs(prob.get_design().mean(axis=1) - np.array(spec.vol_frac)).max() < 1e-12
+    prob.close()
+
+
+@pytest.mark.parametrize("name,storage", [("mbb2d", "f64"), ("elastic3d", "f64"), ("elastic3d", "f32")])
+def test_cahn_hilliard_fp64(P, name, storage):
+    spec = specs_small()[name]
+    prec = "f64" if storage == "f64" else "f32"
+    spec, prob, op, om, phi = _setup(P, spec, seed=14, precision=prec)
+    prob.cahn_hilliard(gamma_g=spec.gamma_g, tau=spec.tau, ch_steps=3)
+    phi_o = np.asarray(phi, prob.np_dtype).astype(np.float64).copy()
+    for _ in range(3):
+        op.ch_step(phi_o, spec.gamma_g, spec.tau)
+    tol = 1e-12 if prec == "f64" else 1e-6
+    assert relmax(prob.get_design(), phi_o) < tol
+    prob.close()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_converged_compliance_matches_direct_solve(P, dim):
+    """FP32 APT solve to 1e-6 relative residual: compliance within 1e-4 of the oracle's
+    direct solve on the same design."""
+    spec = W.cantilever2d(48, 24, load_cells=4) if dim == 2 else W.cantilever3d(16, 8, 8)
+    spec, prob, op, om, phi = _setup(P, spec, seed=15, precision="f32")
+    rep = prob.solve(tol=1e-6, max_sweeps=200000)
+    assert rep["converged"]
+    Cg, Wg, _ = prob.sensitivity()
+    E = om.modulus(np.asarray(phi, np.float32).astype(np.float64))
+    u = op.direct_solve(E, op.load_vector(), op.fixed_mask())
+    Co = float(op.load_vector() @ u)
+    assert abs(Cg - Co) < 1e-4 * Co
+    assert abs(Wg - Co) < 1e-4 * Co
+    prob.close()
+
+
+def test_multi_rhs_matches_single_cases(P):
+    spec, cases = W.multirhs3d(14, 7, 7, n_rhs=3, seed=2)
+    spec = spec.with_(precision="f64", storage="f64")
+    prob = P.Problem(spec, nrhs=3, load_cases=cases)
+    phi = W.random_design(spec, seed=16)
+    prob.set_design(phi)
+    rng = np.random.default_rng(3)
+    u0 = rng.standard_normal((9, spec.nnodes))
+    prob.set_state(u0)
+    prob.sweep(0, 3, 0.9, 0.8, 0.0, True)
+    ug = prob.get_state()
+    om = oracle_materials(spec)
+    E = om.modulus(phi)
+    for r, case in enumerate(cases):
+        op = oracle_problem(spec, loads=case)
+        uo = nodes_to_oracle(u0[3 * r:3 * r + 3])
+        wo = np.zeros_like(uo)
+        for _ in range(3):
+            op.apt_sweep(E, op.load_vector(), op.fixed_mask(), 0.9, 0.8, uo, wo, local_dt=True)
+        assert relmax(ug[3 * r:3 * r + 3], oracle_to_nodes(uo, 3)) < 1e-12
+    prob.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 0), (1, 1, 1), (2, 1, 0), (1, 2, 3), (33, 1, 0), (1, 5, 9)])
+def test_degenerate_grids(P, shape):
+    nx, ny, nz = shape
+    dim = 3 if nz else 2
+    spec = W.ProblemSpec(name="tiny", dim=dim, nx=nx, ny=ny, nz=nz, precision="f64", storage="f64",
+                         boxes=[((0, 0, 0), (0, ny, nz), (1 << dim) - 1)],
+                         loads=[((nx, ny, nz if dim == 3 else 0), dim - 1, -1.0)], vol_frac=[0.5])
+    prob = P.Problem(spec)
+    phi = W.random_design(spec, seed=17)
+    prob.set_design(phi)
+    u0 = W.random_state(spec, seed=18)
+    prob.set_state(u0)
+    prob.sweep(0, 2, 0.9, 0.8, 0.0, True)
+    op, om = oracle_problem(spec), oracle_materials(spec)
+    uo, wo = nodes_to_oracle(u0), np.zeros(op.ndof)
+    for _ in range(2):
+        op.apt_sweep(om.modulus(phi), op.load_vector(), op.fixed_mask(), 0.9, 0.8, uo, wo, local_dt=True)
+    assert relmax(prob.get_state(), oracle_to_nodes(uo, dim)) < 1e-12
+    prob.close()
+
+
+def test_no_load_and_all_fixed(P):
+    spec = W.ProblemSpec(name="free", dim=2, nx=9, ny=5, precision="f64", storage="f64", vol_frac=[0.5])
+    prob = P.Problem(spec)
+    rep = prob.solve(tol=1e-6, max_sweeps=100, check_every=10)
+    assert rep["f_norm"] == 0.0 and not rep["converged"]
+    prob.close()
+    spec2 = spec.with_(boxes=[((0, 0, 0), (9, 5, 0), 3)], loads=[((4, 2, 0), 0, 1.0)])
+    prob = P.Problem(spec2)
+    prob.set_state(np.ones((2, spec2.nnodes)))
+    r2, R = prob.residual()
+    assert r2 == 0.0 and np.all(R == 0)
+    prob.sweep(0, 1, 0.9, 0.8, 0.0, True)
+    assert np.all(prob.get_state() == 0)
+    prob.close()
+
+
+def test_design_loop_mbb_fp64(P):
+    """PeTTO loops (Fig. 5) on the 60 x 20 MBB half-beam in FP64: each step solves to
+    1e-8 relative residual; after the steps the density is within 1e-3 mean-abs of the
+    oracle's run and the compliance within 1e-4."""
+    steps = 8
+    spec = W.mbb_halfbeam()
+    prob = P.Problem(spec)
+    hist, _ = prob.optimize(steps, solve_kw=dict(tol=1e-8, max_sweeps=200000, check_every=25),
+                            pf_kw=dict(alpha_h=0.1))
+    op, om = oracle_problem(spec), oracle_materials(spec)
+    F, fixed = op.load_vector(), op.fixed_mask()
+    phi, u = spec.phi0.copy(), np.zeros(op.ndof)
+    for t in range(steps):
+        m = O.design_step(op, om, phi, u, F, fixed, spec.vol_frac,
+                          dict(mode=1, a=spec.apt_a, b=spec.apt_b, s1=spec.pt_s1, tol=1e-8, max_sweeps=200000,
+                               check_every=25, local_dt=True),
+                          dict(alpha_h=0.1, gamma_g=spec.gamma_g, tau=spec.tau))
+        assert abs(hist[t]["compliance"] - m["compliance"]) < 1e-4 * m["compliance"]
+    assert np.abs(prob.get_design() - phi).mean() < 1e-3
+    prob.close()
+
+
+def test_checkpoint_roundtrip(P, tmp_path):
+    spec = W.mbb_halfbeam(30, 10)
+    prob = P.Problem(spec)
+    prob.optimize(2, solve_kw=dict(tol=1e-8, check_every=25))
+    path = str(tmp_path / "ck.bin")
+    prob.save(path)
+    h1, _ = prob.optimize(1, solve_kw=dict(tol=1e-8, check_every=25))
+    d1 = prob.get_design()
+    prob2 = P.Problem(spec)
+    prob2.load(path)
+    h2, _ = prob2.optimize(1, solve_kw=dict(tol=1e-8, check_every=25))
+    assert h1[0]["compliance"] == h2[0]["compliance"]
+    assert np.array_equal(prob2.get_design(), d1)
+    prob.close()
+    prob2.close()
+
+
+def test_autograd_function_matches_finite_difference(P):
+    torch = pytest.importorskip("torch")
+    from paper_2509_06971_gb300.problem import PettoCompliance
+    spec = W.cantilever2d(16, 8, load_cells=2).with_(precision="f64", storage="f64")
+    prob = P.Problem(spec)
+    phi = torch.tensor(W.random_design(spec, seed=19, lo=0.2, hi=0.8), dtype=torch.float64, device="cuda",
+                       requires_grad=True)
+    kw = dict(tol=1e-12, max_sweeps=400000, check_every=20)
+    Cv = PettoCompliance.apply(phi, prob, **kw)
+    Cv.backward()
+    g = phi.grad.detach().cpu().numpy()
+    rng = np.random.default_rng(20)
+    for c in rng.integers(0, spec.ncells, size=4):
+        d = torch.zeros_like(phi)
+        d[0, c] = 1e-4
+        cp = PettoCompliance.apply((phi + d).detach(), prob, **kw).item()
+        cm = PettoCompliance.apply((phi - d).detach(), prob, **kw).item()
+        fd = (cp - cm) / 2e-4
+        assert abs(fd - g[0, c]) < 1e-5 * abs(g[0, c]) + 1e-9
+    prob.close()
