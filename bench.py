@@ -289,6 +289,29 @@ def run_ours(args):
     return 0
 
 
+def run_sweeps_only(args):
+    """N APT sweeps from a seeded state: few launches, for ncu captures of the sweep."""
+    import torch
+    from paper_2509_06971_gb300 import problem as PR
+    torch.cuda.set_device(0)
+    spec = WORKLOADS[args.workload]()
+    prob = PR.Problem(spec)
+    u0 = W.random_state(spec, seed=1, scale=1e-3).astype("float32")
+    prob.set_state(u0)
+    prob.sweep(0, 2, 0.99, 0.9, 0.75, True)
+    torch.cuda.synchronize()
+    prob.profile(True)
+    prob.profile_read()
+    prob.sweep(0, args.sweeps_only, 0.99, 0.9, 0.75, True)
+    ms, n = prob.profile_read()
+    per = ms / max(n, 1)
+    print(json.dumps({"workload": args.workload, "sweeps": n, "ms_per_sweep": per,
+                      "GBps": sweep_bytes(spec) / (per * 1e-3) / 1e9,
+                      "Gcell_sweeps_per_s": spec.ncells / (per * 1e-3) / 1e9}))
+    prob.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -299,7 +322,11 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--max-sweeps", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweeps-only", type=int, default=0,
+                    help="only run this many APT sweeps of the workload (for profiler captures)")
     args = ap.parse_args()
+    if args.sweeps_only:
+        return run_sweeps_only(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

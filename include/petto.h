@@ -116,13 +116,21 @@ typedef struct {
  *   mode PETTO_SOLVE_PAPER: exactly n_apt APT sweeps then n_pt PT sweeps.
  *   mode PETTO_SOLVE_TOL:   APT sweeps until a check sweep's input residual satisfies
  *                            ||R|| <= tol ||F||, at most max_sweeps in total.
- * APT sweep:  w <- a w + b' R,  u <- u + w;   PT sweep:  u <- u + s1' R;
+ * APT sweep:  w <- a_k w + b' R,  u <- u + w;   PT sweep:  u <- u + s1' R;
  * with b' = b, s1' = s1 (global step, the paper's form) or b' = b / diag(K),
  * s1' = s1 / diag(K) per DOF when local_dt != 0 (local pseudo-time steps).
+ * momentum 0: a_k = a (the paper's fixed damping).  momentum 1 (adaptive restart, an
+ * extension): a_k = min(a, (k-1)/(k+2)) with k the sweeps since the last restart; every
+ * 4th sweep tests <R, w> of its input and, when negative, restarts the momentum at the
+ * next sweep (decided on the device).
+ * refine 1 (FP32 contexts, tolerance mode): an FP32 state cannot represent a solution
+ * much below relative residual ~1e-4 for stiff problems, so the solve runs FP32 sweeps
+ * on corrections of an FP64 state: each round computes the FP64 defect F - K u64, solves
+ * K d = defect by FP32 sweeps to 1e-3 of it, and adds d to u64 (iterative refinement).
  * w is zero at the start of every solve.  Every check_every-th sweep is a check sweep
  * (the last sweep of a paper-mode solve is one too).  Divergence guard: a non-finite
- * check residual resets u and w to zero, a residual above 10x the best seen resets w;
- * either switches the rest of the solve to PT sweeps. */
+ * check residual resets u and w to zero, a residual above 10x (fixed momentum) or 100x
+ * (adaptive) the best seen resets w; either switches the rest of the solve to PT. */
 typedef struct {
     int mode;
     int64_t n_apt, n_pt;
@@ -131,6 +139,8 @@ typedef struct {
     int64_t max_sweeps;
     int check_every;
     int local_dt;
+    int momentum;
+    int refine;
 } petto_solve_opts;
 
 /* res_norm = ||R|| over free DOFs and all load cases at the last check sweep's input

@@ -71,8 +71,8 @@ def _load():
                 "or_residual": (_D, [g, _P, _P, _P, _P, _P]),
                 "or_diag_K": (None, [g, _P, _P]),
                 "or_pt_sweep": (_D, [g, _P, _P, _P, _D, _P, _P, _P]),
-                "or_apt_sweep": (_D, [g, _P, _P, _P, _D, _D, _P, _P, _P, _P]),
-                "or_solve": (None, [g, _P, _P, _P, _I, _L, _L, _D, _D, _D, _D, _L, _I, _I, _P, _P, _P]),
+                "or_apt_sweep": (_D, [g, _P, _P, _P, _D, _D, _P, _P, _P, _P, _P]),
+                "or_solve": (None, [g, _P, _P, _P, _I, _L, _L, _D, _D, _D, _D, _L, _I, _I, _I, _P, _P, _P]),
                 "or_material": (None, [_L, _I, _P, _P, _D, _D, _I, _P]),
                 "or_sensitivity": (_D, [_L, _I, _P, _P, _D, _D, _I, _P, _P, _P]),
                 "or_update": (None, [_L, _I, _P, _P, _P, _I, _D, _D, _D, _I, _P]),
@@ -237,17 +237,18 @@ class OracleProblem:
         R = np.empty(self.ndof)
         dinv = self._dinv(E, local_dt)
         return _load().or_apt_sweep(ctypes.byref(self._g), _ptr(E), _ptr(F), _ptr(fixed), float(a), float(b),
-                                    None if dinv is None else _ptr(dinv), _ptr(u), _ptr(w), _ptr(R))
+                                    None if dinv is None else _ptr(dinv), _ptr(u), _ptr(w), _ptr(R), None)
 
     def solve(self, E, F, fixed, u, *, mode=1, n_apt=0, n_pt=0, a=0.9, b=0.25, s1=0.25, tol=1e-8,
-              max_sweeps=100000, check_every=50, local_dt=False) -> dict:
-        """Hybrid APT -> PT schedule (Sec. 2.2).  In place on u; returns the report."""
+              max_sweeps=100000, check_every=50, local_dt=False, momentum=0) -> dict:
+        """Hybrid APT -> PT schedule (Sec. 2.2).  In place on u; returns the report.
+        momentum=1 selects the adaptive-restart momentum (see or_solve)."""
         E, F = _f64(E), _f64(F)
         w = np.zeros(self.ndof)
         rep = np.zeros(8)
         _load().or_solve(ctypes.byref(self._g), _ptr(E), _ptr(F), _ptr(fixed), int(mode), int(n_apt), int(n_pt),
                          float(a), float(b), float(s1), float(tol), int(max_sweeps), int(check_every),
-                         int(bool(local_dt)), _ptr(u), _ptr(w), _ptr(rep))
+                         int(bool(local_dt)), int(momentum), _ptr(u), _ptr(w), _ptr(rep))
         return {"sweeps": int(rep[0]), "apt_sweeps": int(rep[1]), "pt_sweeps": int(rep[2]),
                 "res_norm": rep[3], "f_norm": rep[4],
                 "rel_res": rep[3] / rep[4] if rep[4] > 0 else float("nan"),

@@ -263,11 +263,17 @@ double or_pt_sweep(const or_grid *g, const double *E, const double *F, const uin
  *   elastic (forward damping difference):  a = theta/(theta+dt2), b = dt2^2/((theta+dt2) h^d)
  *   thermal (backward damping difference): a = 1 - dt2/theta,      b = dt2^2/(theta h^d)
  * With dinv != NULL, b is replaced by b dinv (local time stepping, as for PT).
- * Returns sum R^2 of the input state. */
+ * Returns sum R^2 of the input state; dot (may be NULL) receives sum R.w of the input
+ * residual and the input increment. */
 double or_apt_sweep(const or_grid *g, const double *E, const double *F, const uint8_t *fixed,
-                    double a, double b, const double *dinv, double *u, double *w, double *Rwork) {
+                    double a, double b, const double *dinv, double *u, double *w, double *Rwork, double *dot) {
     const int64_t nd = or_ndof(g);
     double s = or_residual(g, E, F, fixed, u, Rwork);
+    if (dot) {
+        double d = 0.0;
+        for (int64_t r = 0; r < nd; ++r) d += Rwork[r] * w[r];
+        *dot = d;
+    }
     for (int64_t r = 0; r < nd; ++r) {
         if (fixed[r]) {
             w[r] = 0.0;
@@ -290,11 +296,17 @@ double or_apt_sweep(const or_grid *g, const double *E, const double *F, const ui
  * a non-finite residual resets u and w to 0; a residual above 10x the best seen resets
  * w to 0; either switches the rest of the solve to PT sweeps.
  * local_dt != 0 uses the local pseudo-time steps s1/diag(K), b/diag(K) throughout.
+ * momentum 0 keeps the APT damping a fixed (the paper's form).  momentum 1 (adaptive
+ * restart, an extension of the fixed damping): the APT sweep with index t (counted from 0
+ * within the solve) uses a_t = min(a, (k-1)/(k+2)), k = t - t_restart (0 when k <= 0);
+ * every sweep with t % 4 == 3 computes <R_t, w_t> of its input residual and increment
+ * and, when that is negative (the last step went uphill in energy), sets t_restart = t + 1.
+ * The guard factor is 10 for fixed and 100 for adaptive momentum.
  * rep: [0] sweeps, [1] APT sweeps, [2] PT sweeps, [3] last checked ||R||, [4] ||F||,
  *      [5] converged flag, [6] fell-back-to-PT flag.                              */
 void or_solve(const or_grid *g, const double *E, const double *F, const uint8_t *fixed, int mode,
               int64_t n_apt, int64_t n_pt, double a, double b, double s1, double tol,
-              int64_t max_sweeps, int check_every, int local_dt, double *u, double *w, double *rep) {
+              int64_t max_sweeps, int check_every, int local_dt, int momentum, double *u, double *w, double *rep) {
     const int64_t nd = or_ndof(g);
     double *R = (double *)malloc(sizeof(double) * (size_t)nd);
     double *dinv = NULL;
@@ -311,11 +323,25 @@ void or_solve(const or_grid *g, const double *E, const double *F, const uint8_t 
     int64_t sweeps = 0, n_a = 0, n_p = 0;
     int use_pt = 0, fell = 0, conv = 0;
     double best = INFINITY, last = NAN;
+    int64_t t_restart = 0;
+    const double guard = momentum ? 100.0 : 10.0;
     const int64_t total = mode == 0 ? n_apt + n_pt : max_sweeps;
     while (sweeps < total) {
         int apt = !use_pt && (mode == 1 || sweeps < n_apt);
-        double r2 = apt ? or_apt_sweep(g, E, F, fixed, a, b, dinv, u, w, R)
-                        : or_pt_sweep(g, E, F, fixed, s1, dinv, u, R);
+        double r2;
+        if (apt) {
+            double at = a, dot = 0.0;
+            const int test = momentum && (sweeps % 4 == 3);
+            if (momentum) {
+                const int64_t k = sweeps - t_restart;
+                const double sched = k <= 0 ? 0.0 : (double)(k - 1) / (double)(k + 2);
+                at = sched < a ? sched : a;
+            }
+            r2 = or_apt_sweep(g, E, F, fixed, at, b, dinv, u, w, R, test ? &dot : NULL);
+            if (test && dot < 0.0) t_restart = sweeps + 1;
+        } else {
+            r2 = or_pt_sweep(g, E, F, fixed, s1, dinv, u, R);
+        }
         if (apt) ++n_a; else ++n_p;
         ++sweeps;
         if (check_every > 0 && sweeps % check_every == 0) {
@@ -326,7 +352,7 @@ void or_solve(const or_grid *g, const double *E, const double *F, const uint8_t 
                 use_pt = 1; fell = 1;
                 continue;
             }
-            if (rn > 10.0 * best && !use_pt) {
+            if (rn > guard * best && !use_pt) {
                 for (int64_t r = 0; r < nd; ++r) w[r] = 0.0;
                 use_pt = 1; fell = 1;
             }

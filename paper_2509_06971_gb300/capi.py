@@ -53,7 +53,8 @@ class petto_options(ctypes.Structure):
 
 class petto_solve_opts(ctypes.Structure):
     _fields_ = [("mode", _int), ("n_apt", _i64), ("n_pt", _i64), ("a", _dbl), ("b", _dbl), ("s1", _dbl),
-                ("tol", _dbl), ("max_sweeps", _i64), ("check_every", _int), ("local_dt", _int)]
+                ("tol", _dbl), ("max_sweeps", _i64), ("check_every", _int), ("local_dt", _int),
+                ("momentum", _int), ("refine", _int)]
 
 
 class petto_solve_report(ctypes.Structure):

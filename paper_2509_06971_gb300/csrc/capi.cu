@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <utility>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -25,7 +26,8 @@ struct petto_ctx {
     std::vector<double> moduli, vol;
     cudaStream_t stream = nullptr;
     Layout L{};
-    Tiling tiling{};
+    Tiling tiling{};   // tiling of the sweep kernel
+    Tiling gtiling{};  // tiling of the node-gather kernels (FP64 defect of the refinement)
     OpConst k{};
     BoxSet boxes{};
     double lam0 = 0.0, mu0 = 0.0;
@@ -38,10 +40,11 @@ struct petto_ctx {
     double *scal = nullptr;
     unsigned *counter = nullptr;
     double *partials = nullptr;
-    int *tile_ptr = nullptr;
-    LoadEntry *loads = nullptr;
+    int *tile_ptr = nullptr, *gtile_ptr = nullptr;
+    LoadEntry *loads = nullptr, *gloads = nullptr;
     int n_loads = 0;
-    std::vector<LoadEntry> host_loads;
+    double *ctrl = nullptr;
+    void *u64 = nullptr, *r64 = nullptr, *rhs32 = nullptr;
     int cur = 0;
     int64_t launches = 0;
     int64_t step = 0;
@@ -298,15 +301,31 @@ SweepArgs base_sweep_args(petto_ctx *ctx) {
     a.loads = ctx->loads;
     a.res2 = ctx->scal + SC_RES;
     a.red = ctx->red();
+    a.ctrl = ctx->ctrl;
+    a.rhs = nullptr;
     return a;
 }
 
+// Per-sweep controls beyond the constants: adaptive momentum, its restart test, the
+// index of the sweep within the solve, and an optional dense right-hand side.
+struct SweepCtl {
+    int adaptive = 0;
+    int test_dot = 0;
+    long long idx = 0;
+    const void *rhs = nullptr;
+};
+
 // one sweep kind (0 APT, 1 PT) from u[cur] into u[1-cur]; flips cur
-petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, int local_dt, bool want_res) {
+petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, int local_dt, bool want_res,
+                       const SweepCtl &sc = SweepCtl()) {
     SweepArgs A = base_sweep_args(ctx);
     A.mode = kind;
     A.local_dt = local_dt;
     A.want_res = want_res ? 1 : 0;
+    A.adaptive = sc.adaptive;
+    A.test_dot = kind == 0 && sc.adaptive ? sc.test_dot : 0;
+    A.sweep_idx = sc.idx;
+    A.rhs = sc.rhs;
     A.a = a;
     A.b = b;
     A.s1 = s1;
@@ -429,7 +448,8 @@ void petto_destroy(petto_ctx *ctx) {
     }
     for (auto e : ctx->ev_free) cudaEventDestroy(e);
     void *bufs[] = {ctx->u[0], ctx->u[1], ctx->w, ctx->E, ctx->phi, ctx->s, ctx->dscr, ctx->mu, ctx->rbuf,
-                    ctx->stage, ctx->scal, ctx->counter, ctx->tile_ptr, ctx->loads, ctx->partials};
+                    ctx->stage, ctx->scal, ctx->counter, ctx->tile_ptr, ctx->loads, ctx->partials,
+                    ctx->gtile_ptr, ctx->gloads, ctx->ctrl, ctx->u64, ctx->r64, ctx->rhs32};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete ctx;
@@ -477,7 +497,7 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
         return PETTO_EINVAL;
     }
     ctx->L = make_layout(ctx->dim, ctx->nx, ctx->ny, ctx->nz);
-    ctx->tiling = choose_tiling(ctx->L, ctx->physics, ctx->precision);
+    ctx->tiling = choose_tiling(ctx->L, ctx->physics, ctx->precision, ctx->nrhs);
     build_opconst(ctx);
 
     // supports
@@ -505,8 +525,9 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
         return false;
     };
 
-    // nodal loads: merge duplicates, group per sweep tile
-    std::map<std::tuple<int, int, int, int>, double> merged;  // (tile, node, comp) -> value
+    // nodal loads: merge duplicates (node, component) and keep them sorted by the tile of
+    // each sweep kernel that looks them up
+    std::map<std::pair<int64_t, int>, double> merged;  // (natural node, component) -> value
     const int NX = ctx->L.NX, NY = ctx->L.NY, NZ = ctx->L.NZ;
     if (loads && loads->n > 0) {
         if (!loads->node || !loads->comp || !loads->value) {
@@ -524,47 +545,61 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
                 petto_destroy(ctx);
                 return PETTO_EINVAL;
             }
-            const int tile = ctx->tiling.tile_of(i, j, k);
-            const int n = (int)((int64_t)i + (int64_t)NX * ((int64_t)j + (int64_t)NY * k));
-            merged[std::make_tuple(tile, n, r * ctx->ncomp + a, 0)] += loads->value[e];
+            const int64_t n = (int64_t)i + (int64_t)NX * ((int64_t)j + (int64_t)NY * k);
+            merged[std::make_pair(n, r * ctx->ncomp + a)] += loads->value[e];
         }
     }
-    const int ntiles = ctx->tiling.ntiles();
-    std::vector<int> tptr(ntiles + 1, 0);
+    ctx->gtiling = gather_tiling(ctx->L);
+    auto table = [&](const Tiling &t, std::vector<int> &tptr, std::vector<LoadEntry> &ent) {
+        const int nt = t.ntiles();
+        tptr.assign(nt + 1, 0);
+        std::vector<std::pair<int, LoadEntry>> tmp;
+        for (auto &kv : merged) {
+            const int64_t n = kv.first.first;
+            const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / ((int64_t)NX * NY));
+            LoadEntry le{};
+            le.node = ctx->L.node(i, j, k);
+            le.comp = kv.first.second;
+            le.vald = kv.second;
+            le.valf = (float)kv.second;
+            tmp.emplace_back(t.tile_of(i, j, k), le);
+        }
+        std::stable_sort(tmp.begin(), tmp.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
+        ent.clear();
+        for (auto &pr : tmp) {
+            tptr[pr.first + 1]++;
+            ent.push_back(pr.second);
+        }
+        for (int q = 0; q < nt; ++q) tptr[q + 1] += tptr[q];
+    };
+    std::vector<int> tptr, gptr;
+    std::vector<LoadEntry> tent, gent;
+    table(ctx->tiling, tptr, tent);
+    table(ctx->gtiling, gptr, gent);
+    const int ntiles = ctx->tiling.ntiles(), gntiles = ctx->gtiling.ntiles();
+    ctx->n_loads = (int)tent.size();
+    // ||F|| over free DOFs (point loads plus the body source)
     double f2 = 0.0;
     for (auto &kv : merged) {
-        const int tile = std::get<0>(kv.first), n = std::get<1>(kv.first), c = std::get<2>(kv.first);
-        const int i = n % NX, j = (n / NX) % NY, k = n / (NX * NY);
-        LoadEntry le{};
-        le.node = ctx->L.node(i, j, k);
-        le.comp = c;
-        le.vald = kv.second;
-        le.valf = (float)kv.second;
-        ctx->host_loads.push_back(le);
-        tptr[tile + 1]++;
-        const int a = c % ctx->ncomp;
-        if (!is_fixed(i, j, k, a)) {
-            double F = kv.second;
-            if (ctx->body_source != 0.0) {
-                const int cnt = ((i > 0) + (i < ctx->nx)) * ((j > 0) + (j < ctx->ny)) *
-                                (ctx->dim == 3 ? ((k > 0) + (k < ctx->nz)) : 1);
-                F += ctx->k.src * cnt;
-            }
-            f2 += F * F;
+        const int64_t n = kv.first.first;
+        const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / ((int64_t)NX * NY));
+        const int a = kv.first.second % ctx->ncomp;
+        if (is_fixed(i, j, k, a)) continue;
+        double F = kv.second;
+        if (ctx->body_source != 0.0) {
+            const int cnt = ((i > 0) + (i < ctx->nx)) * ((j > 0) + (j < ctx->ny)) *
+                            (ctx->dim == 3 ? ((k > 0) + (k < ctx->nz)) : 1);
+            F += ctx->k.src * cnt;
         }
+        f2 += F * F;
     }
-    for (int t = 0; t < ntiles; ++t) tptr[t + 1] += tptr[t];
-    ctx->n_loads = (int)ctx->host_loads.size();
-    // ||F|| over free DOFs: body source at nodes without point loads
     if (ctx->body_source != 0.0) {
-        std::vector<char> has(ctx->nrhs * (size_t)NX * NY * NZ, 0);
-        for (auto &kv : merged) has[(size_t)std::get<2>(kv.first) * NX * NY * NZ + std::get<1>(kv.first)] = 1;
         for (int r = 0; r < ctx->nrhs; ++r)
             for (int k = 0; k < NZ; ++k)
                 for (int j = 0; j < NY; ++j)
                     for (int i = 0; i < NX; ++i) {
-                        const size_t n = (size_t)i + (size_t)NX * (j + (size_t)NY * k);
-                        if (has[(size_t)r * NX * NY * NZ + n] || is_fixed(i, j, k, 0)) continue;
+                        const int64_t n = (int64_t)i + (int64_t)NX * (j + (int64_t)NY * k);
+                        if (merged.count(std::make_pair(n, r)) || is_fixed(i, j, k, 0)) continue;
                         const int cnt = ((i > 0) + (i < ctx->nx)) * ((j > 0) + (j < ctx->ny)) *
                                         (ctx->dim == 3 ? ((k > 0) + (k < ctx->nz)) : 1);
                         const double F = ctx->k.src * cnt;
@@ -591,23 +626,18 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
     alloc(&ctx->mu, (size_t)nc * ctx->tsize());
     alloc((void **)&ctx->scal, sizeof(double) * SC_N);
     alloc((void **)&ctx->counter, sizeof(unsigned) * 4);
-    alloc((void **)&ctx->partials, sizeof(double) * reduction_capacity(ctx->L, ntiles, ctx->P));
+    alloc((void **)&ctx->partials, sizeof(double) * reduction_capacity(ctx->L, std::max(ntiles, gntiles), ctx->P));
     alloc((void **)&ctx->tile_ptr, sizeof(int) * (ntiles + 1));
     alloc((void **)&ctx->loads, sizeof(LoadEntry) * std::max(1, ctx->n_loads));
+    alloc((void **)&ctx->gtile_ptr, sizeof(int) * (gntiles + 1));
+    alloc((void **)&ctx->gloads, sizeof(LoadEntry) * std::max(1, ctx->n_loads));
+    alloc((void **)&ctx->ctrl, sizeof(double) * CT_N);
     if (e != cudaSuccess) {
         petto_status st = e == cudaErrorMemoryAllocation ? PETTO_ENOMEM : PETTO_ECUDA;
         cudaGetLastError();
         petto_destroy(ctx);
         return st;
     }
-    // group loads by tile in the order of tptr
-    std::vector<LoadEntry> sorted(ctx->host_loads.size());
-    {
-        std::vector<int> pos(tptr.begin(), tptr.end() - 1);
-        int idx = 0;
-        for (auto &kv : merged) sorted[pos[std::get<0>(kv.first)]++] = ctx->host_loads[idx++];
-    }
-    ctx->host_loads = sorted;
     cudaStream_t s = ctx->stream;
     e = cudaMemsetAsync(ctx->u[0], 0, nb, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->u[1], 0, nb, s);
@@ -617,9 +647,13 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counter, 0, sizeof(unsigned) * 4, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->tile_ptr, tptr.data(), sizeof(int) * (ntiles + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->gtile_ptr, gptr.data(), sizeof(int) * (gntiles + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && ctx->n_loads > 0)
-        e = cudaMemcpyAsync(ctx->loads, ctx->host_loads.data(), sizeof(LoadEntry) * ctx->n_loads,
-                            cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(ctx->loads, tent.data(), sizeof(LoadEntry) * ctx->n_loads, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && ctx->n_loads > 0)
+        e = cudaMemcpyAsync(ctx->gloads, gent.data(), sizeof(LoadEntry) * ctx->n_loads, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ctrl, 0, sizeof(double) * CT_N, s);
     // phi = V
     double *dvol = nullptr;
     if (e == cudaSuccess) e = cudaMalloc(&dvol, sizeof(double) * ctx->P);
@@ -748,63 +782,190 @@ petto_status petto_residual(petto_ctx *ctx, double *res_norm2, void *R, int dtyp
     return PETTO_OK;
 }
 
+}  // extern "C"
+
+// set one device control word (stream-ordered, no host staging)
+__global__ void set_ctrl_kernel(double *ctrl, int slot, double v) { ctrl[slot] = v; }
+
+namespace {
+
+// flat conversions / updates over whole padded node fields
+__global__ void f32_to_f64(int64_t n, const float *__restrict__ a, double *__restrict__ b) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        b[t] = (double)a[t];
+}
+__global__ void f64_to_f32(int64_t n, const double *__restrict__ a, float *__restrict__ b) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        b[t] = (float)a[t];
+}
+__global__ void add_f32_to_f64(int64_t n, const float *__restrict__ d, double *__restrict__ u) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        u[t] += (double)d[t];
+}
+
+struct SolveState {
+    int64_t sweeps = 0, na = 0, np = 0, total = 0;
+    bool use_pt = false, fell = false;
+    double best = INFINITY, last = NAN;
+    int since_improve = 0;
+    double improve_ref = INFINITY;
+};
+
+petto_status set_ctrl(petto_ctx *ctx, int slot, double v) {
+    set_ctrl_kernel<<<1, 1, 0, ctx->stream>>>(ctx->ctrl, slot, v);
+    CK(cudaGetLastError());
+    ctx->launches++;
+    return PETTO_OK;
+}
+
+// Sweep until a check sweep's residual is <= stop_abs, the budget ends, or (stall_checks > 0)
+// the residual has not fallen 10% over stall_checks checks.  Returns 1 when stop_abs was
+// reached, 0 otherwise.  Applies the divergence guard.
+petto_status sweep_phase(petto_ctx *ctx, const petto_solve_opts *o, SolveState &S, double stop_abs, int64_t n_apt,
+                         int stall_checks, const void *rhs, int *reached) {
+    *reached = 0;
+    const int ce = o->check_every;
+    const double guard = o->momentum ? 100.0 : 10.0;
+    double scal[SC_N];
+    while (S.sweeps < S.total) {
+        const bool apt = !S.use_pt && (o->mode == PETTO_SOLVE_TOL || S.sweeps < n_apt);
+        const bool check = ce > 0 && (S.sweeps + 1) % ce == 0;
+        const bool final_report = (S.sweeps + 1 == S.total);
+        SweepCtl sc;
+        sc.adaptive = o->momentum ? 1 : 0;
+        sc.test_dot = (S.sweeps % 4) == 3;
+        sc.idx = S.sweeps;
+        sc.rhs = rhs;
+        petto_status st = one_sweep(ctx, apt ? 0 : 1, o->a, o->b, o->s1, o->local_dt, check || final_report, sc);
+        if (st != PETTO_OK) return st;
+        if (apt) ++S.na; else ++S.np;
+        ++S.sweeps;
+        if (!(check || final_report)) continue;
+        st = read_scal(ctx, scal);
+        if (st != PETTO_OK) return st;
+        const double rn = std::sqrt(scal[SC_RES]);
+        S.last = rn;
+        if (!check) break;
+        if (!std::isfinite(rn)) {
+            CK(cudaMemsetAsync(ctx->u[ctx->cur], 0, ctx->node_bytes(), ctx->stream));
+            CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
+            S.use_pt = true;
+            S.fell = true;
+            continue;
+        }
+        if (rn > guard * S.best && !S.use_pt) {
+            CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
+            S.use_pt = true;
+            S.fell = true;
+        }
+        if (rn < S.best) S.best = rn;
+        if (rn <= stop_abs) {
+            *reached = 1;
+            break;
+        }
+        if (rn < 0.9 * S.improve_ref) {
+            S.improve_ref = rn;
+            S.since_improve = 0;
+        } else if (stall_checks > 0 && ++S.since_improve >= stall_checks) {
+            break;
+        }
+    }
+    return PETTO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_solve_report *rep) {
     if (!ctx || !o) return fail(ctx, PETTO_EINVAL, "null argument");
     if (o->mode != PETTO_SOLVE_PAPER && o->mode != PETTO_SOLVE_TOL) return fail(ctx, PETTO_EINVAL, "bad mode");
     if (o->n_apt < 0 || o->n_pt < 0 || o->max_sweeps < 0 || o->check_every < 0)
         return fail(ctx, PETTO_EINVAL, "negative count");
     CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
-    const int64_t total = o->mode == PETTO_SOLVE_PAPER ? o->n_apt + o->n_pt : o->max_sweeps;
-    const int ce = o->check_every;
-    int64_t sweeps = 0, na = 0, np = 0;
-    bool use_pt = false, fell = false, conv = false;
-    double best = INFINITY, last = NAN;
-    double scal[SC_N];
-    while (sweeps < total) {
-        const bool apt = !use_pt && (o->mode == PETTO_SOLVE_TOL || sweeps < o->n_apt);
-        const bool check = ce > 0 && (sweeps + 1) % ce == 0;
-        const bool final_report = (sweeps + 1 == total);
-        petto_status st = one_sweep(ctx, apt ? 0 : 1, o->a, o->b, o->s1, o->local_dt, check || final_report);
+    petto_status st = set_ctrl(ctx, CT_RESTART_AT, 0.0);
+    if (st != PETTO_OK) return st;
+    SolveState S;
+    S.total = o->mode == PETTO_SOLVE_PAPER ? o->n_apt + o->n_pt : o->max_sweeps;
+    const double fn = ctx->f_norm;
+    const bool refine = o->mode == PETTO_SOLVE_TOL && o->refine && ctx->precision == PETTO_F32 && o->tol < 1e-3;
+    bool conv = false;
+    int reached = 0;
+    double true_res = NAN;
+    if (!refine) {
+        const double stop = o->mode == PETTO_SOLVE_TOL ? o->tol * fn : -1.0;
+        st = sweep_phase(ctx, o, S, stop, o->n_apt, 0, nullptr, &reached);
         if (st != PETTO_OK) return st;
-        if (apt) ++na; else ++np;
-        ++sweeps;
-        if (check || final_report) {
+        conv = reached != 0;
+    } else {
+        // FP32 sweeps on the state itself down to 1e-3 (or a stall), then rounds of FP64
+        // iterative refinement: defect in FP64, correction by FP32 sweeps.
+        st = sweep_phase(ctx, o, S, 1e-3 * fn, 0, 8, nullptr, &reached);
+        if (st != PETTO_OK) return st;
+        const size_t nb64 = (size_t)ctx->ndofc() * ctx->L.cstride * sizeof(double);
+        const int64_t nel = (int64_t)ctx->ndofc() * ctx->L.cstride;
+        if (!ctx->u64) CK(cudaMalloc(&ctx->u64, nb64));
+        if (!ctx->r64) CK(cudaMalloc(&ctx->r64, nb64));
+        if (!ctx->rhs32) CK(cudaMalloc(&ctx->rhs32, ctx->node_bytes()));
+        cudaStream_t s = ctx->stream;
+        f32_to_f64<<<grid_of(nel), 256, 0, s>>>(nel, (const float *)ctx->u[ctx->cur], (double *)ctx->u64);
+        CK(cudaGetLastError());
+        ctx->launches++;
+        double scal[SC_N];
+        while (true) {
+            SweepArgs R = base_sweep_args(ctx);
+            R.mode = 2;
+            R.want_res = 1;
+            R.u_in = ctx->u64;
+            R.w = ctx->r64;
+            R.tile_ptr = ctx->gtile_ptr;
+            R.loads = ctx->gloads;
+            CK(launch_residual64(R, ctx->gtiling, s));
+            ctx->launches++;
             st = read_scal(ctx, scal);
             if (st != PETTO_OK) return st;
-            const double rn = std::sqrt(scal[SC_RES]);
-            last = rn;
-            if (!check) break;
-            if (!std::isfinite(rn)) {
-                CK(cudaMemsetAsync(ctx->u[ctx->cur], 0, ctx->node_bytes(), ctx->stream));
-                CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
-                use_pt = true;
-                fell = true;
-                continue;
-            }
-            if (rn > 10.0 * best && !use_pt) {
-                CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
-                use_pt = true;
-                fell = true;
-            }
-            if (rn < best) best = rn;
-            if (o->mode == PETTO_SOLVE_TOL && rn <= o->tol * ctx->f_norm) {
+            true_res = std::sqrt(scal[SC_RES]);
+            if (true_res <= o->tol * fn) {
                 conv = true;
                 break;
             }
+            if (S.sweeps >= S.total || !std::isfinite(true_res)) break;
+            f64_to_f32<<<grid_of(nel), 256, 0, s>>>(nel, (const double *)ctx->r64, (float *)ctx->rhs32);
+            CK(cudaGetLastError());
+            CK(cudaMemsetAsync(ctx->u[ctx->cur], 0, ctx->node_bytes(), s));
+            CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), s));
+            st = set_ctrl(ctx, CT_RESTART_AT, (double)S.sweeps);
+            if (st != PETTO_OK) return st;
+            ctx->launches++;
+            S.best = INFINITY;
+            S.improve_ref = INFINITY;
+            S.since_improve = 0;
+            S.use_pt = false;
+            const double stop = std::max(1e-3 * true_res, 0.5 * o->tol * fn);
+            st = sweep_phase(ctx, o, S, stop, 0, 8, ctx->rhs32, &reached);
+            if (st != PETTO_OK) return st;
+            add_f32_to_f64<<<grid_of(nel), 256, 0, s>>>(nel, (const float *)ctx->u[ctx->cur], (double *)ctx->u64);
+            CK(cudaGetLastError());
+            ctx->launches++;
         }
+        f64_to_f32<<<grid_of(nel), 256, 0, s>>>(nel, (const double *)ctx->u64, (float *)ctx->u[ctx->cur]);
+        CK(cudaGetLastError());
+        CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), s));
+        ctx->launches++;
+        S.last = true_res;
     }
     if (rep) {
-        rep->sweeps = sweeps;
-        rep->apt_sweeps = na;
-        rep->pt_sweeps = np;
-        rep->res_norm = last;
-        rep->f_norm = ctx->f_norm;
-        rep->rel_res = ctx->f_norm > 0 ? last / ctx->f_norm : NAN;
-        rep->r_pde = last / std::pow(ctx->h, ctx->dim) / (double)ctx->L.nnodes();
+        rep->sweeps = S.sweeps;
+        rep->apt_sweeps = S.na;
+        rep->pt_sweeps = S.np;
+        rep->res_norm = S.last;
+        rep->f_norm = fn;
+        rep->rel_res = fn > 0 ? S.last / fn : NAN;
+        rep->r_pde = S.last / std::pow(ctx->h, ctx->dim) / (double)ctx->L.nnodes();
         rep->converged = conv ? 1 : 0;
-        rep->fell_back_to_pt = fell ? 1 : 0;
+        rep->fell_back_to_pt = S.fell ? 1 : 0;
     }
-    if (!std::isfinite(last)) return fail(ctx, PETTO_EDIVERGED, "residual not finite after PT fallback");
+    if (!std::isfinite(S.last)) return fail(ctx, PETTO_EDIVERGED, "residual not finite after PT fallback");
     if (o->mode == PETTO_SOLVE_TOL && !conv) return PETTO_ENOTCONV;
     return PETTO_OK;
 }

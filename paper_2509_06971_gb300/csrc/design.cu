@@ -359,7 +359,7 @@ int64_t reduction_capacity(const Layout &L, int ntiles, int P) {
     c = std::max<int64_t>(c, (L.ncells() + 255) / 256);
     c = std::max<int64_t>(c, (int64_t)152 * 4 * P);
     c = std::max<int64_t>(c, (int64_t)152 * 16);
-    return c + 64;
+    return 2 * c + 64;
 }
 
 cudaError_t launch_sensitivity(const SensArgs &sa, const DesignArgs &d, const void *u, const void *E,

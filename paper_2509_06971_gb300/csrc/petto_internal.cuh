@@ -75,6 +75,11 @@ struct OpConst {
     double src;               // nodal body source per adjacent cell: f h^d / 2^d
 };
 
+// Device-side solve control words (doubles in the ctrl array).
+constexpr int CT_RESTART_AT = 0;  // sweep index at which the APT momentum last restarted
+constexpr int CT_DOT = 1;         // last tested <R, w> (for inspection)
+constexpr int CT_N = 4;
+
 struct SweepArgs {
     Layout L;
     int physics;              // 0 elastic, 1 thermal
@@ -82,6 +87,11 @@ struct SweepArgs {
     int mode;                 // 0 APT, 1 PT, 2 residual only (writes R to w_or_r)
     int local_dt;
     int want_res;
+    int adaptive;             // APT momentum a_k = min(a, (k-1)/(k+2)), k sweeps since the last restart
+    int test_dot;             // this sweep tests <R, w_in> < 0 and schedules a restart
+    long long sweep_idx;      // index of this sweep within the solve
+    double *ctrl;             // solve control words (CT_*)
+    const void *rhs;          // dense right-hand side [C][cstride] replacing the loads, or null
     double a, b, s1;
     OpConst k;
     BoxSet boxes;
@@ -201,7 +211,13 @@ struct Tiling {
     int ntiles() const { return gx * gy * gz; }
 };
 
-Tiling choose_tiling(const Layout &L, int physics, int precision);
+// The z-marching kernel serves 3D elasticity in FP32 with one load case; every other
+// combination uses the node-gather kernels.
+Tiling choose_tiling(const Layout &L, int physics, int precision, int nrhs);
+Tiling gather_tiling(const Layout &L);
+cudaError_t launch_residual64(const SweepArgs &a, const Tiling &gather, cudaStream_t s);
+void march3d_tiling(const Layout &L, Tiling &t);
+cudaError_t launch_march3d(const SweepArgs &a, const Tiling &t, cudaStream_t s);
 
 cudaError_t launch_sweep(const SweepArgs &a, const Tiling &t, int precision, cudaStream_t s);
 

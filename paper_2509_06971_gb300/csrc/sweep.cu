@@ -246,18 +246,32 @@ __device__ __forceinline__ T ku_thermal_3d(const T (&U)[3][3][3], const T (&Ec)[
 }
 
 // ------------------------------------------------------------- update
+// APT momentum of this sweep: fixed a, or the adaptive-restart schedule read from the
+// device control words (the same value in every thread of every block).
+template <typename T>
+__device__ __forceinline__ T apt_momentum(const SweepArgs &A) {
+    if (!A.adaptive) return (T)A.a;
+    const long long k = A.sweep_idx - (long long)A.ctrl[CT_RESTART_AT];
+    if (k <= 0) return T(0);
+    const T sched = (T)(k - 1) / (T)(k + 2);
+    return sched < (T)A.a ? sched : (T)A.a;
+}
+
 template <typename T>
 struct Upd {
     const SweepArgs &A;
-    double res;
-    __device__ __forceinline__ void apply(int64_t idx_c, int c, bool fixed, T Ku, T F, T diag, T *uo, const T *ui,
-                                          T *w) {
+    T a_eff;
+    T res, dot;
+    __device__ __forceinline__ void apply(int64_t idx_c, bool fixed, T Ku, T F, T diag, T *uo, const T *ui, T *w) {
+        if (A.rhs) F = static_cast<const T *>(A.rhs)[idx_c];
         T R = fixed ? T(0) : F - Ku;
-        if (A.want_res) res += (double)R * (double)R;
+        if (A.want_res) res += R * R;
         const T u = ui[idx_c];
         if (A.mode == 0) {
             const T step = A.local_dt ? (T)A.b / diag : (T)A.b;
-            const T wn = fixed ? T(0) : (T)A.a * w[idx_c] + step * R;
+            const T wi = w[idx_c];
+            if (A.test_dot) dot += R * wi;
+            const T wn = fixed ? T(0) : a_eff * wi + step * R;
             w[idx_c] = wn;
             uo[idx_c] = fixed ? T(0) : u + wn;
         } else if (A.mode == 1) {
@@ -266,28 +280,35 @@ struct Upd {
         } else {
             w[idx_c] = R;
         }
-        (void)c;
     }
 };
 
-// block total of sum R^2, then the deterministic grid reduction into *res2
-__device__ __forceinline__ void finish_res(const SweepArgs &A, double res) {
+// Block totals of sum R^2 and sum R.w, then one deterministic grid reduction: partials
+// of R^2 at [0, nb), of R.w at [nb, 2 nb); the last block writes *res2 and, on a test
+// sweep, schedules a momentum restart at the next sweep when <R, w> < 0.
+__device__ __forceinline__ void finish_sweep(const SweepArgs &A, double res, double dot, int64_t bid) {
     __shared__ double sh[32];
-    if (!A.want_res) return;
-    const double r = block_sum(res, sh);
+    if (!A.want_res && !A.test_dot) return;
     const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
-    const int64_t bid = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z);
+    const double r = A.want_res ? block_sum(res, sh) : 0.0;
+    const double d = A.test_dot ? block_sum(dot, sh) : 0.0;
+    if (block_tid() == 0) A.red.partials[(int64_t)nb + bid] = d;
     if (publish_partial(r, A.red, bid, nb)) {
-        const double t = sum_partials(A.red, 0, nb, sh);
+        const double t = A.want_res ? sum_partials(A.red, 0, nb, sh) : 0.0;
+        const double td = A.test_dot ? sum_partials(A.red, nb, nb, sh) : 0.0;
         if (block_tid() == 0) {
-            *A.res2 = t;
+            if (A.want_res) *A.res2 = t;
+            if (A.test_dot) {
+                A.ctrl[CT_DOT] = td;
+                if (td < 0.0) A.ctrl[CT_RESTART_AT] = (double)(A.sweep_idx + 1);
+            }
             *A.red.counter = 0u;
         }
     }
 }
 
 // ------------------------------------------------------------- 2D gather kernel
-template <typename T, int PHYS>
+template <typename T, int PHYS, typename TE = T>
 __global__ void __launch_bounds__(256) sweep2d_gather(const SweepArgs A) {
     const Layout &L = A.L;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -295,14 +316,14 @@ __global__ void __launch_bounds__(256) sweep2d_gather(const SweepArgs A) {
     const T *__restrict__ ui = static_cast<const T *>(A.u_in);
     T *__restrict__ uo = static_cast<T *>(A.u_out);
     T *__restrict__ w = static_cast<T *>(A.w);
-    const T *__restrict__ E = static_cast<const T *>(A.E);
-    Upd<T> up{A, 0.0};
+    const TE *__restrict__ E = static_cast<const TE *>(A.E);
+    Upd<T> up{A, apt_momentum<T>(A), T(0), T(0)};
     if (i < L.NX && j < L.NY) {
         T Ec[2][2];
 #pragma unroll
         for (int cy = 0; cy < 2; ++cy)
 #pragma unroll
-            for (int cx = 0; cx < 2; ++cx) Ec[cy][cx] = __ldg(&E[L.cell(i - 1 + cx, j - 1 + cy, 0)]);
+            for (int cx = 0; cx < 2; ++cx) Ec[cy][cx] = (T)__ldg(&E[L.cell(i - 1 + cx, j - 1 + cy, 0)]);
         const T S = Ec[0][0] + Ec[0][1] + Ec[1][0] + Ec[1][1];
         const T diag = (T)A.k.cdiag * S;
         const unsigned fm = fixed_mask(A.boxes, i, j, 0);
@@ -330,7 +351,7 @@ __global__ void __launch_bounds__(256) sweep2d_gather(const SweepArgs A) {
                     for (int l = l0; l < l1; ++l)
                         if (A.loads[l].node == n0 && A.loads[l].comp == c) F += load_val<T>(A.loads[l]);
                     const int64_t idx = (int64_t)c * L.cstride + n0;
-                    up.apply(idx, c, (fm >> a) & 1u, Ku[a], F, diag, uo, ui, w);
+                    up.apply(idx, (fm >> a) & 1u, Ku[a], F, diag, uo, ui, w);
                 }
             } else {
                 T U[3][3];
@@ -344,15 +365,15 @@ __global__ void __launch_bounds__(256) sweep2d_gather(const SweepArgs A) {
                 for (int l = l0; l < l1; ++l)
                     if (A.loads[l].node == n0 && A.loads[l].comp == r) F += load_val<T>(A.loads[l]);
                 const int64_t idx = (int64_t)r * L.cstride + n0;
-                up.apply(idx, r, fm & 1u, Ku, F, diag, uo, ui, w);
+                up.apply(idx, fm & 1u, Ku, F, diag, uo, ui, w);
             }
         }
     }
-    finish_res(A, up.res);
+    finish_sweep(A, (double)up.res, (double)up.dot, blockIdx.x + (int64_t)gridDim.x * blockIdx.y);
 }
 
 // ------------------------------------------------------------- 3D gather kernel
-template <typename T, int PHYS>
+template <typename T, int PHYS, typename TE = T>
 __global__ void __launch_bounds__(128) sweep3d_gather(const SweepArgs A) {
     const Layout &L = A.L;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -361,8 +382,8 @@ __global__ void __launch_bounds__(128) sweep3d_gather(const SweepArgs A) {
     const T *__restrict__ ui = static_cast<const T *>(A.u_in);
     T *__restrict__ uo = static_cast<T *>(A.u_out);
     T *__restrict__ w = static_cast<T *>(A.w);
-    const T *__restrict__ E = static_cast<const T *>(A.E);
-    Upd<T> up{A, 0.0};
+    const TE *__restrict__ E = static_cast<const TE *>(A.E);
+    Upd<T> up{A, apt_momentum<T>(A), T(0), T(0)};
     const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int l0 = A.tile_ptr[tile], l1 = A.tile_ptr[tile + 1];
     if (i < L.NX && j < L.NY) {
@@ -374,7 +395,7 @@ __global__ void __launch_bounds__(128) sweep3d_gather(const SweepArgs A) {
 #pragma unroll
                 for (int cy = 0; cy < 2; ++cy)
 #pragma unroll
-                    for (int cx = 0; cx < 2; ++cx) Ec[cz][cy][cx] = __ldg(&E[L.cell(i - 1 + cx, j - 1 + cy, k - 1 + cz)]);
+                    for (int cx = 0; cx < 2; ++cx) Ec[cz][cy][cx] = (T)__ldg(&E[L.cell(i - 1 + cx, j - 1 + cy, k - 1 + cz)]);
             T S = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) S += Ec[q >> 2][(q >> 1) & 1][q & 1];
@@ -404,7 +425,7 @@ __global__ void __launch_bounds__(128) sweep3d_gather(const SweepArgs A) {
                         T F = 0;
                         for (int l = l0; l < l1; ++l)
                             if (A.loads[l].node == n0 && A.loads[l].comp == c) F += load_val<T>(A.loads[l]);
-                        up.apply((int64_t)c * L.cstride + n0, c, (fm >> a) & 1u, Ku[a], F, diag, uo, ui, w);
+                        up.apply((int64_t)c * L.cstride + n0, (fm >> a) & 1u, Ku[a], F, diag, uo, ui, w);
                     }
                 } else {
                     T U[3][3][3];
@@ -420,19 +441,17 @@ __global__ void __launch_bounds__(128) sweep3d_gather(const SweepArgs A) {
                     T F = (T)A.k.src * (T)ncnt;
                     for (int l = l0; l < l1; ++l)
                         if (A.loads[l].node == n0 && A.loads[l].comp == r) F += load_val<T>(A.loads[l]);
-                    up.apply((int64_t)r * L.cstride + n0, r, fm & 1u, Ku, F, diag, uo, ui, w);
+                    up.apply((int64_t)r * L.cstride + n0, fm & 1u, Ku, F, diag, uo, ui, w);
                 }
             }
         }
     }
-    finish_res(A, up.res);
+    finish_sweep(A, (double)up.res, (double)up.dot, tile);
 }
 
 }  // namespace
 
-Tiling choose_tiling(const Layout &L, int physics, int precision) {
-    (void)physics;
-    (void)precision;
+Tiling gather_tiling(const Layout &L) {
     Tiling t{};
     if (L.dim == 2) {
         t.bx = 32; t.by = 8; t.zs = 1; t.kind = 0;
@@ -447,7 +466,31 @@ Tiling choose_tiling(const Layout &L, int physics, int precision) {
     return t;
 }
 
+Tiling choose_tiling(const Layout &L, int physics, int precision, int nrhs) {
+    if (L.dim == 3 && physics == 0 && precision == 0 && nrhs == 1) {
+        Tiling t{};
+        march3d_tiling(L, t);
+        return t;
+    }
+    return gather_tiling(L);
+}
+
+// FP64 residual R = F - K(E) u of an FP64 state with the FP32 modulus field (mode 2):
+// the defect of the iterative refinement around FP32 sweeps.
+cudaError_t launch_residual64(const SweepArgs &a, const Tiling &t, cudaStream_t s) {
+    dim3 block(t.bx, t.by, 1), grid(t.gx, t.gy, t.gz);
+    if (a.L.dim == 2) {
+        if (a.physics == 0) sweep2d_gather<double, 0, float><<<grid, block, 0, s>>>(a);
+        else sweep2d_gather<double, 1, float><<<grid, block, 0, s>>>(a);
+    } else {
+        if (a.physics == 0) sweep3d_gather<double, 0, float><<<grid, block, 0, s>>>(a);
+        else sweep3d_gather<double, 1, float><<<grid, block, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sweep(const SweepArgs &a, const Tiling &t, int precision, cudaStream_t s) {
+    if (t.kind == 1) return launch_march3d(a, t, s);
     dim3 block(t.bx, t.by, 1), grid(t.gx, t.gy, t.gz);
     if (a.L.dim == 2) {
         if (precision == 0) {

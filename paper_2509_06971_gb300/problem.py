@@ -204,12 +204,17 @@ class Problem:
         return r.value, R
 
     def solve_opts(self, mode=C.PETTO_SOLVE_TOL, **kw) -> C.petto_solve_opts:
+        """Defaults: the workload's constants; momentum = 1 (adaptive restart, with the
+        momentum cap a = 1 unless given), refine = 1 (FP64 refinement for FP32 states)."""
         s = self.spec
-        return C.petto_solve_opts(mode, int(kw.get("n_apt", 0)), int(kw.get("n_pt", 0)), float(kw.get("a", s.apt_a)),
+        momentum = int(kw.get("momentum", s.momentum))
+        a = float(kw.get("a", 1.0 if momentum else s.apt_a))
+        return C.petto_solve_opts(mode, int(kw.get("n_apt", 0)), int(kw.get("n_pt", 0)), a,
                                   float(kw.get("b", s.apt_b)), float(kw.get("s1", s.pt_s1)),
                                   float(kw.get("tol", s.tol)), int(kw.get("max_sweeps", s.max_sweeps)),
                                   int(kw.get("check_every", s.check_every)),
-                                  int(bool(kw.get("local_dt", s.local_dt))))
+                                  int(bool(kw.get("local_dt", s.local_dt))), momentum,
+                                  int(bool(kw.get("refine", True))))
 
     def solve(self, mode=C.PETTO_SOLVE_TOL, **kw) -> dict:
         o = self.solve_opts(mode, **kw)

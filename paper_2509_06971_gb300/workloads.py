@@ -54,6 +54,7 @@ class ProblemSpec:
     check_every: int = 50
     max_sweeps: int = 200000
     local_dt: bool = True      # local pseudo-time steps b/diag(K), s1/diag(K) (an extension)
+    momentum: int = 1          # 0: fixed APT damping a; 1: adaptive-restart momentum (an extension)
     # design update and phase field (Sec. 2.3, 2.4; Sec. 3.1 weights)
     vol_mode: int = PROJECTED
     alpha_h: float = 0.1
@@ -109,9 +110,9 @@ def apt_params(h_p: float, elastic: bool = True, theta: float = 1.0, dim: int = 
 def local_step_params(n_max: int, c_a: float = 0.15):
     """Defaults for local (Jacobi-scaled) pseudo-time steps, where the scaled operator
     diag(K)^-1 K has its largest eigenvalue near 2 for any modulus field: APT b = 1, PT
-    s1 = 0.75, and momentum a = 1 - c_a / n_max (the slowest mode of an elliptic operator
+    s1 = 0.75, b = 0.9, and momentum a = 1 - c_a / n_max (the slowest mode of an elliptic operator
     on n_max cells scales as n_max^-2, so the best damping rate scales as 1/n_max)."""
-    return 1.0 - c_a / float(n_max), 1.0, 0.75
+    return 1.0 - c_a / float(n_max), 0.9, 0.75
 
 
 def ch_params(h_p: float, dim: int, dt3_factor: float = 500.0, gamma: float = 3e-5, safety: float = 0.9):

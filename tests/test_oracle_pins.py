@@ -173,7 +173,7 @@ def _small_cantilever(dim):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
-@pytest.mark.parametrize("kind", ["apt_global", "apt_local", "pt_local"])
+@pytest.mark.parametrize("kind", ["apt_global", "apt_local", "apt_adaptive", "pt_local"])
 def test_iterations_converge_to_direct_solve(dim, kind):
     """PT and APT fixed points are K u = F: the converged field equals a sparse direct
     solve of the assembled K within 1e-8 relative."""
@@ -186,6 +186,9 @@ def test_iterations_converge_to_direct_solve(dim, kind):
     elif kind == "apt_local":
         rep = p.solve(E, F, fixed, u, mode=1, a=0.97, b=1.0, tol=1e-12, max_sweeps=400000, check_every=10,
                       local_dt=True)
+    elif kind == "apt_adaptive":
+        rep = p.solve(E, F, fixed, u, mode=1, a=1.0, b=0.9, tol=1e-12, max_sweeps=400000, check_every=10,
+                      local_dt=True, momentum=1)
     else:
         rep = p.solve(E, F, fixed, u, mode=0, n_apt=0, n_pt=400000, s1=0.75, check_every=0, local_dt=True)
     assert rep["fell_back_to_pt"] is False
@@ -412,8 +415,8 @@ def test_design_loop_compliance_decreases():
     Cs = []
     for _ in range(4):
         m = O.design_step(p, mat, phi, u, F, fixed, spec.vol_frac,
-                          dict(mode=1, a=0.97, b=1.0, s1=0.75, tol=1e-10, max_sweeps=200000, check_every=10,
-                               local_dt=True),
+                          dict(mode=1, a=1.0, b=0.9, s1=0.75, tol=1e-10, max_sweeps=200000, check_every=10,
+                               local_dt=True, momentum=1),
                           dict(alpha_h=0.1, gamma_g=spec.gamma_g, tau=spec.tau))
         Cs.append(m["compliance"])
         assert abs(m["work"] - m["compliance"]) < 1e-8 * m["compliance"]
