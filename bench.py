@@ -117,6 +117,19 @@ def dist_setup():
     return world, rank, local
 
 
+def aggregate(ms, work, device, world):
+    """Whole-job aggregation across ranks: the slowest rank's time and the summed work
+    (cell-sweeps).  Uses torch.distributed when world > 1 (NCCL on GPUs, gloo on CPU)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    w = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 def oracle_sample(spec, n_sweeps):
     """Time n oracle APT sweeps (FP64, single thread) on the full grid of ``spec``.
     Returns seconds.  Test/benchmark infrastructure only: the baseline, not the path."""
@@ -217,13 +230,8 @@ def run_ours(args):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     sweeps = sum(r["sweeps"] for r in rows)
-    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
-    tot = torch.tensor([float(sweeps) * spec.ncells], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-    ms_max = float(t_max.item())
-    value = float(tot.item()) / (ms_max * 1e-3) / 1e9
+    ms_max, tot = aggregate(ms, float(sweeps) * spec.ncells, dev, world)
+    value = tot / (ms_max * 1e-3) / 1e9
 
     peaks, peak_kind = measured_peaks()
     per_launch_ms = kern_ms / max(kern_n, 1)
@@ -251,12 +259,8 @@ def run_ours(args):
         u_h[:] = prob.get_state(dtype=np.float32)
     torch.cuda.synchronize()
     e_secs = time.perf_counter() - t0
-    e_t = torch.tensor([e_secs], dtype=torch.float64, device=dev)
-    e_tot = torch.tensor([float(e_sweeps) * spec.ncells], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e_tot, op=dist.ReduceOp.SUM)
-    e_value = float(e_tot.item()) / float(e_t.item()) / 1e9
+    e_t, e_tot = aggregate(e_secs, float(e_sweeps) * spec.ncells, dev, world)
+    e_value = e_tot / e_t / 1e9
     h2d = phi_h.nbytes + u_h.nbytes
     d2h = phi_h.nbytes + u_h.nbytes + 8
 
