@@ -253,6 +253,34 @@ int64_t petto_launch_count(const petto_ctx *ctx);
 petto_status petto_profile(petto_ctx *ctx, int enable);
 petto_status petto_profile_read(petto_ctx *ctx, double *sweep_ms, int64_t *sweeps);
 
+/* Allocation-free residual norm.  The paper has no counterpart: this entry point exists
+ * for callers that must not allocate GPU memory themselves -- code running under a memory
+ * manager that owns every device byte (a framework's caching allocator, a fixed arena of
+ * a long-running service) or a time-critical loop in which a cudaMalloc would stall the
+ * device.  It needs no context: the caller passes every input and output, and the kernel
+ * keeps the scratch of its reduction in one array compiled into this library (about
+ * 128 KB, present on every GPU that loads the library until the process exits).
+ *
+ * Computes *norm2 = sum over free DOFs of (F - K(E) u)^2 for linear elasticity in FP32
+ * (the operator of petto_residual, plane strain in 2D):
+ *   grid   dim 2 or 3, nx, ny (, nz) cells of size h; at most 4 194 304 nodes
+ *          ((nx+1)(ny+1)(nz+1)); larger grids return PETTO_EINVAL
+ *   nu     Poisson's ratio
+ *   u      device [dim][nodes] displacements, natural node order
+ *   E      device [cells] moduli, natural cell order
+ *   F      device [dim][nodes] nodal loads, or NULL for none
+ *   fixed  device [dim][nodes] bytes, nonzero = supported DOF (excluded), or NULL
+ *   norm2  host double receiving the result; the call returns after it is written
+ *   stream cudaStream_t to run on (NULL = legacy default stream)
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  The first call on a
+ * device looks up the device address of the scratch array (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  Every call clears the ticket counter of the
+ * reduction before launching.  All calls share the one scratch array: calls that overlap
+ * on the GPU (different streams, or different host threads on one device) race and must
+ * be serialised by the caller. */
+petto_status petto_residual_norm_static(const petto_grid *grid, double nu, const float *u, const float *E,
+                                        const float *F, const uint8_t *fixed, double *norm2, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,6 +95,7 @@ _SIGS = {
     "petto_launch_count": (_i64, [_vp]),
     "petto_profile": (_int, [_vp, _int]),
     "petto_profile_read": (_int, [_vp, _P(_dbl), _P(_i64)]),
+    "petto_residual_norm_static": (_int, [_P(petto_grid), _dbl, _vp, _vp, _vp, _vp, _P(_dbl), _vp]),
 }
 EXPORTED = tuple(_SIGS)
 

@@ -513,3 +513,175 @@ cudaError_t launch_sweep(const SweepArgs &a, const Tiling &t, int precision, cud
 }
 
 }  // namespace petto
+
+// ============================================================================
+// Allocation-free residual norm (petto_residual_norm_static in include/petto.h).
+//
+// A variant of the residual mode of the gather kernel above for callers that cannot
+// allocate device memory: inputs in the natural layouts, bounds handled per neighbour
+// instead of by the zero ring, and the scratch of the deterministic grid reduction (one
+// partial per block, the result, the ticket counter) in one file-scope device array of
+// fixed size instead of context-owned memory.
+// ============================================================================
+#include <mutex>
+
+#include "../../include/petto.h"
+
+namespace petto {
+namespace {
+
+constexpr int NA_BLOCK = 256;                    // threads (nodes) per block
+constexpr int NA_MAX_BLOCKS = 16384;             // at most 16384 * 256 = 4 194 304 nodes
+constexpr int NA_RESULT = NA_MAX_BLOCKS;         // slot of the total
+constexpr int NA_TICKET = NA_MAX_BLOCKS + 1;     // slot whose low word is the ticket counter
+constexpr int NA_WORDS = NA_MAX_BLOCKS + 8;      // 131 136 bytes in all
+
+// Shared by every call of the entry point on a device, kept between calls.
+static __device__ __align__(256) double g_na_scratch[NA_WORDS];
+
+template <int DIM>
+__global__ void __launch_bounds__(NA_BLOCK) residual_norm_natural(int nx, int ny, int nz, OpConst k,
+                                                                   const float *__restrict__ u,
+                                                                   const float *__restrict__ E,
+                                                                   const float *__restrict__ F,
+                                                                   const unsigned char *__restrict__ fixed,
+                                                                   double *scratch) {
+    __shared__ double sh[32];
+    const int NX = nx + 1, NY = ny + 1, NZ = DIM == 3 ? nz + 1 : 1;
+    const int64_t nn = (int64_t)NX * NY * NZ;
+    const int64_t n = (int64_t)blockIdx.x * NA_BLOCK + threadIdx.x;
+    double acc = 0.0;
+    if (n < nn) {
+        const int i = (int)(n % NX);
+        const int64_t r = n / NX;
+        const int j = (int)(r % NY), kk = (int)(r / NY);
+        auto uat = [&](int a, int di, int dj, int dk) -> float {
+            const int ii = i + di, jj = j + dj, k2 = kk + dk;
+            if (ii < 0 || ii >= NX || jj < 0 || jj >= NY || k2 < 0 || k2 >= NZ) return 0.f;
+            return __ldg(&u[(int64_t)a * nn + ii + (int64_t)NX * (jj + (int64_t)NY * k2)]);
+        };
+        auto eat = [&](int ci, int cj, int ck) -> float {
+            if (ci < 0 || ci >= nx || cj < 0 || cj >= ny || (DIM == 3 && (ck < 0 || ck >= nz))) return 0.f;
+            return __ldg(&E[ci + (int64_t)nx * (cj + (int64_t)ny * (DIM == 3 ? ck : 0))]);
+        };
+        float Ku[3] = {0.f, 0.f, 0.f};
+        if (DIM == 2) {
+            float U[3][3][2], Ec[2][2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) U[dy][dx][a] = uat(a, dx - 1, dy - 1, 0);
+#pragma unroll
+            for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+                for (int cx = 0; cx < 2; ++cx) Ec[cy][cx] = eat(i - 1 + cx, j - 1 + cy, 0);
+            float K2[2];
+            ku_elastic_2d<float>(U, Ec, k, K2);
+            Ku[0] = K2[0];
+            Ku[1] = K2[1];
+        } else {
+            float U[3][3][3][3], Ec[2][2][2];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                        for (int dx = 0; dx < 3; ++dx) U[dz][dy][dx][a] = uat(a, dx - 1, dy - 1, dz - 1);
+#pragma unroll
+            for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+                for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+                    for (int cx = 0; cx < 2; ++cx) Ec[cz][cy][cx] = eat(i - 1 + cx, j - 1 + cy, kk - 1 + cz);
+            ku_elastic_3d<float>(U, Ec, k, Ku);
+        }
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const int64_t idx = (int64_t)a * nn + n;
+            if (fixed && fixed[idx]) continue;
+            const float R = (F ? F[idx] : 0.f) - Ku[a];
+            acc += (double)R * (double)R;
+        }
+    }
+    // deterministic reduction through the static scratch: partials in block order
+    const double b = block_sum(acc, sh);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        scratch[blockIdx.x] = b;
+        __threadfence();
+        last = atomicAdd(reinterpret_cast<unsigned *>(&scratch[NA_TICKET]), 1u) == gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        const volatile double *p = scratch;
+        double s = 0.0;
+        for (int q = threadIdx.x; q < (int)gridDim.x; q += NA_BLOCK) s += p[q];
+        const double t = block_sum(s, sh);
+        if (threadIdx.x == 0) {
+            scratch[NA_RESULT] = t;
+            *reinterpret_cast<unsigned *>(&scratch[NA_TICKET]) = 0u;
+        }
+    }
+}
+
+// Device address of g_na_scratch, looked up once per device (host code may not use the
+// symbol itself as a device address).
+std::mutex g_na_mutex;
+double *g_na_ptr[64] = {nullptr};
+
+}  // namespace
+}  // namespace petto
+
+extern "C" petto_status petto_residual_norm_static(const petto_grid *grid, double nu, const float *u,
+                                                   const float *E, const float *F, const uint8_t *fixed,
+                                                   double *norm2, void *stream) {
+    using namespace petto;
+    if (!grid || !u || !E || !norm2) return PETTO_EINVAL;
+    if (grid->dim != 2 && grid->dim != 3) return PETTO_EINVAL;
+    if (grid->nx < 1 || grid->ny < 1 || (grid->dim == 3 && grid->nz < 1) || !(grid->h > 0)) return PETTO_EINVAL;
+    if (!(nu > -1.0 && nu < 0.5)) return PETTO_EINVAL;
+    const int64_t NX = grid->nx + 1, NY = grid->ny + 1, NZ = grid->dim == 3 ? grid->nz + 1 : 1;
+    if (NX > (1 << 24) || NY > (1 << 24) || NZ > (1 << 24)) return PETTO_EINVAL;
+    const int64_t nn = NX * NY * NZ;
+    const int64_t blocks = (nn + NA_BLOCK - 1) / NA_BLOCK;
+    if (blocks > NA_MAX_BLOCKS) return PETTO_EINVAL;  // more than 4 194 304 nodes
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PETTO_ECUDA;
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_na_mutex);
+        if (!g_na_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) return PETTO_ECUDA;
+            g_na_ptr[dev] = static_cast<double *>(p);
+        }
+        scratch = g_na_ptr[dev];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the ticket counter must start at zero (an interrupted earlier call could have left it)
+    if (cudaMemsetAsync(scratch + NA_TICKET, 0, sizeof(double), s) != cudaSuccess) return PETTO_ECUDA;
+    const int d = grid->dim;
+    const double hs = std::pow(grid->h, d - 2), nq = (double)(1 << d);
+    const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = 1.0 / (2.0 * (1.0 + nu));
+    OpConst k{};
+    k.ce_par = 2.0 / nq * hs * (lam + 2.0 * mu);
+    k.ce_perp = 2.0 / nq * hs * mu;
+    k.cf_lam = hs * lam / nq;
+    k.cf_mu = hs * mu / nq;
+    if (d == 2)
+        residual_norm_natural<2><<<(unsigned)blocks, NA_BLOCK, 0, s>>>((int)grid->nx, (int)grid->ny, 0, k, u, E, F,
+                                                                       fixed, scratch);
+    else
+        residual_norm_natural<3><<<(unsigned)blocks, NA_BLOCK, 0, s>>>((int)grid->nx, (int)grid->ny, (int)grid->nz, k,
+                                                                       u, E, F, fixed, scratch);
+    if (cudaGetLastError() != cudaSuccess) return PETTO_ECUDA;
+    if (cudaMemcpyAsync(norm2, scratch + NA_RESULT, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PETTO_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PETTO_ECUDA;
+    return PETTO_OK;
+}
