@@ -123,10 +123,14 @@ typedef struct {
  * extension): a_k = min(a, (k-1)/(k+2)) with k the sweeps since the last restart; every
  * 4th sweep tests <R, w> of its input and, when negative, restarts the momentum at the
  * next sweep (decided on the device).
- * refine 1 (FP32 contexts, tolerance mode): an FP32 state cannot represent a solution
- * much below relative residual ~1e-4 for stiff problems, so the solve runs FP32 sweeps
- * on corrections of an FP64 state: each round computes the FP64 defect F - K u64, solves
- * K d = defect by FP32 sweeps to 1e-3 of it, and adds d to u64 (iterative refinement).
+ * refine 1 (FP32 contexts, tolerance mode, tol < 1e-3): an FP32 state cannot represent a
+ * solution much below relative residual ~1e-4 for stiff problems, so the solve sweeps the
+ * FP32 state to 1e-2, then continues the same iteration on u = u64 + d with u64 in FP64:
+ * whenever the check residual has fallen 8x (or stalls for 20 checks) d is added to u64,
+ * the FP64 defect F - K u64 becomes the FP32 right-hand side of the sweeps and d restarts
+ * at zero, while w and the momentum schedule carry on.  The solve ends when the FP64
+ * defect meets the tolerance.  With the environment variable PETTO_TRACE set, every check
+ * residual is printed to stderr.
  * w is zero at the start of every solve.  Every check_every-th sweep is a check sweep
  * (the last sweep of a paper-mode solve is one too).  Divergence guard: a non-finite
  * check residual resets u and w to zero, a residual above 10x (fixed momentum) or 100x

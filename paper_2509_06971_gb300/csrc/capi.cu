@@ -6,6 +6,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <utility>
@@ -28,6 +29,7 @@ struct petto_ctx {
     Layout L{};
     Tiling tiling{};   // tiling of the sweep kernel
     Tiling gtiling{};  // tiling of the node-gather kernels (FP64 defect of the refinement)
+    TmaMaps tma{};     // tensor maps of the TMA-staged marching kernel
     OpConst k{};
     BoxSet boxes{};
     double lam0 = 0.0, mu0 = 0.0;
@@ -50,6 +52,7 @@ struct petto_ctx {
     int64_t step = 0;
     bool have_sens = false;
     bool profiling = false;
+    bool trace = false;  // PETTO_TRACE set: print every check residual to stderr
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
     double prof_ms = 0.0;
@@ -344,7 +347,7 @@ petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, 
         }
         CK(cudaEventRecord(e0, ctx->stream));
     }
-    CK(launch_sweep(A, ctx->tiling, ctx->precision, ctx->stream));
+    CK(launch_sweep(A, ctx->tiling, ctx->precision, ctx->stream, &ctx->tma));
     if (ctx->profiling) {
         CK(cudaEventRecord(e1, ctx->stream));
         ctx->ev_pending.emplace_back(e0, e1);
@@ -355,8 +358,11 @@ petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, 
 }
 
 petto_status read_scal(petto_ctx *ctx, double *host) {
+    double ctrl[CT_N];
     CK(cudaMemcpyAsync(host, ctx->scal, sizeof(double) * SC_N, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctrl, ctx->ctrl, sizeof(double) * CT_N, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (ctrl[CT_ERR] != 0.0) return fail(ctx, PETTO_ETIMEOUT, "a bounded device-side wait ran out in a sweep");
     return PETTO_OK;
 }
 
@@ -496,6 +502,7 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
         delete ctx;
         return PETTO_EINVAL;
     }
+    ctx->trace = std::getenv("PETTO_TRACE") != nullptr;
     ctx->L = make_layout(ctx->dim, ctx->nx, ctx->ny, ctx->nz);
     ctx->tiling = choose_tiling(ctx->L, ctx->physics, ctx->precision, ctx->nrhs);
     build_opconst(ctx);
@@ -669,6 +676,18 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
         petto_destroy(ctx);
         return PETTO_ECUDA;
     }
+    if (ctx->tiling.kind == 2 || ctx->tiling.kind == 3) {
+        const int ty = ctx->tiling.kind == 3 ? 16 : 8;
+        if (!make_tma_maps(ctx->L, ty, ctx->u[0], ctx->u[1], ctx->E, ctx->tma)) {
+            if (ctx->tiling.kind == 2) {
+                march3d_tiling(ctx->L, ctx->tiling);  // same tiles, register-staged kernel
+            } else {
+                ctx->err = "tensor map creation failed";
+                petto_destroy(ctx);
+                return PETTO_ECUDA;
+            }
+        }
+    }
     petto_status st = refresh_material(ctx);
     if (st != PETTO_OK) {
         petto_destroy(ctx);
@@ -772,7 +791,7 @@ petto_status petto_residual(petto_ctx *ctx, double *res_norm2, void *R, int dtyp
     A.u_in = ctx->u[ctx->cur];
     A.u_out = nullptr;
     A.w = ctx->rbuf;
-    CK(launch_sweep(A, ctx->tiling, ctx->precision, ctx->stream));
+    CK(launch_sweep(A, ctx->tiling, ctx->precision, ctx->stream, &ctx->tma));
     ctx->launches++;
     if (res_norm2) {
         CK(cudaMemcpyAsync(res_norm2, ctx->scal + SC_RES, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -845,6 +864,13 @@ petto_status sweep_phase(petto_ctx *ctx, const petto_solve_opts *o, SolveState &
         if (st != PETTO_OK) return st;
         const double rn = std::sqrt(scal[SC_RES]);
         S.last = rn;
+        if (ctx->trace) {
+            double ctrl[CT_N];
+            cudaMemcpy(ctrl, ctx->ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost);
+            std::fprintf(stderr, "petto: sweep %lld res %.6e rel %.3e restart@%lld%s\n", (long long)S.sweeps, rn,
+                         ctx->f_norm > 0 ? rn / ctx->f_norm : 0.0, (long long)ctrl[CT_RESTART_AT],
+                         rhs ? " (correction)" : "");
+        }
         if (!check) break;
         if (!std::isfinite(rn)) {
             CK(cudaMemsetAsync(ctx->u[ctx->cur], 0, ctx->node_bytes(), ctx->stream));
@@ -898,9 +924,12 @@ petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_sol
         if (st != PETTO_OK) return st;
         conv = reached != 0;
     } else {
-        // FP32 sweeps on the state itself down to 1e-3 (or a stall), then rounds of FP64
-        // iterative refinement: defect in FP64, correction by FP32 sweeps.
-        st = sweep_phase(ctx, o, S, 1e-3 * fn, 0, 8, nullptr, &reached);
+        // FP32 sweeps on the state itself down to 1e-2, then the same iteration continued on
+        // u = u64 + d: u64 (FP64) absorbs d whenever the check residual has fallen 8x, the
+        // FP64 defect F - K u64 becomes the FP32 right-hand side of the sweeps, d restarts
+        // from zero and the increment w and the momentum schedule carry on unchanged (the
+        // APT recursion is the same in the shifted variable).
+        st = sweep_phase(ctx, o, S, 1e-2 * fn, 0, 0, nullptr, &reached);
         if (st != PETTO_OK) return st;
         const size_t nb64 = (size_t)ctx->ndofc() * ctx->L.cstride * sizeof(double);
         const int64_t nel = (int64_t)ctx->ndofc() * ctx->L.cstride;
@@ -925,6 +954,9 @@ petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_sol
             st = read_scal(ctx, scal);
             if (st != PETTO_OK) return st;
             true_res = std::sqrt(scal[SC_RES]);
+            if (ctx->trace)
+                std::fprintf(stderr, "petto: FP64 defect %.6e rel %.3e after %lld sweeps\n", true_res,
+                             fn > 0 ? true_res / fn : 0.0, (long long)S.sweeps);
             if (true_res <= o->tol * fn) {
                 conv = true;
                 break;
@@ -933,16 +965,11 @@ petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_sol
             f64_to_f32<<<grid_of(nel), 256, 0, s>>>(nel, (const double *)ctx->r64, (float *)ctx->rhs32);
             CK(cudaGetLastError());
             CK(cudaMemsetAsync(ctx->u[ctx->cur], 0, ctx->node_bytes(), s));
-            CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), s));
-            st = set_ctrl(ctx, CT_RESTART_AT, (double)S.sweeps);
-            if (st != PETTO_OK) return st;
             ctx->launches++;
-            S.best = INFINITY;
             S.improve_ref = INFINITY;
             S.since_improve = 0;
-            S.use_pt = false;
-            const double stop = std::max(1e-3 * true_res, 0.5 * o->tol * fn);
-            st = sweep_phase(ctx, o, S, stop, 0, 8, ctx->rhs32, &reached);
+            const double stop = std::max(true_res / 8.0, 0.5 * o->tol * fn);
+            st = sweep_phase(ctx, o, S, stop, 0, 20, ctx->rhs32, &reached);
             if (st != PETTO_OK) return st;
             add_f32_to_f64<<<grid_of(nel), 256, 0, s>>>(nel, (const float *)ctx->u[ctx->cur], (double *)ctx->u64);
             CK(cudaGetLastError());

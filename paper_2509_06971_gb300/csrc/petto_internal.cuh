@@ -10,6 +10,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap (type only; maps are encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -78,6 +79,7 @@ struct OpConst {
 // Device-side solve control words (doubles in the ctrl array).
 constexpr int CT_RESTART_AT = 0;  // sweep index at which the APT momentum last restarted
 constexpr int CT_DOT = 1;         // last tested <R, w> (for inspection)
+constexpr int CT_ERR = 2;         // nonzero after a bounded device-side wait ran out
 constexpr int CT_N = 4;
 
 struct SweepArgs {
@@ -219,7 +221,20 @@ cudaError_t launch_residual64(const SweepArgs &a, const Tiling &gather, cudaStre
 void march3d_tiling(const Layout &L, Tiling &t);
 cudaError_t launch_march3d(const SweepArgs &a, const Tiling &t, cudaStream_t s);
 
-cudaError_t launch_sweep(const SweepArgs &a, const Tiling &t, int precision, cudaStream_t s);
+// Tensor maps of the TMA-staged marching kernel: u (4D: x, y, z, component) for each of the
+// two ping-pong buffers, and the modulus (3D).
+struct TmaMaps {
+    bool valid = false;
+    CUtensorMap u[2];
+    CUtensorMap e;
+    const void *ubuf[2] = {nullptr, nullptr};
+};
+void march3d_tma_tiling(const Layout &L, int ty, Tiling &t);
+cudaError_t launch_march3d_tma(const SweepArgs &a, const Tiling &t, const TmaMaps &m, cudaStream_t s);
+bool make_tma_maps(const Layout &L, int ty, void *u0, void *u1, const void *E, TmaMaps &m);
+
+cudaError_t launch_sweep(const SweepArgs &a, const Tiling &t, int precision, cudaStream_t s,
+                         const TmaMaps *maps = nullptr);
 
 struct DesignArgs {
     Layout L;

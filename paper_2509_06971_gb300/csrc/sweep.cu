@@ -24,6 +24,9 @@
 // with b' = b or b / diag(K) (local pseudo-time step), u read from one buffer and written
 // to the other (ping-pong), w updated in place.  sum R^2 over free DOFs is accumulated in
 // FP64 when requested (the residual norm of Sec. 3.1, for convergence checks).
+#include <cstdlib>
+#include <cstring>
+
 #include "petto_internal.cuh"
 
 namespace petto {
@@ -468,8 +471,12 @@ Tiling gather_tiling(const Layout &L) {
 
 Tiling choose_tiling(const Layout &L, int physics, int precision, int nrhs) {
     if (L.dim == 3 && physics == 0 && precision == 0 && nrhs == 1) {
+        // z-marching kernel: TMA-staged with 32x8 owner tiles by default; PETTO_MARCH=v1
+        // selects the register-staged kernel, PETTO_MARCH=tma16 32x16 tiles
         Tiling t{};
-        march3d_tiling(L, t);
+        const char *env = std::getenv("PETTO_MARCH");
+        if (env && std::strcmp(env, "v1") == 0) march3d_tiling(L, t);
+        else march3d_tma_tiling(L, env && std::strcmp(env, "tma16") == 0 ? 16 : 8, t);
         return t;
     }
     return gather_tiling(L);
@@ -489,8 +496,12 @@ cudaError_t launch_residual64(const SweepArgs &a, const Tiling &t, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep(const SweepArgs &a, const Tiling &t, int precision, cudaStream_t s) {
+cudaError_t launch_sweep(const SweepArgs &a, const Tiling &t, int precision, cudaStream_t s, const TmaMaps *maps) {
     if (t.kind == 1) return launch_march3d(a, t, s);
+    if (t.kind == 2 || t.kind == 3) {
+        if (!maps || !maps->valid) return cudaErrorInvalidValue;
+        return launch_march3d_tma(a, t, *maps, s);
+    }
     dim3 block(t.bx, t.by, 1), grid(t.gx, t.gy, t.gz);
     if (a.L.dim == 2) {
         if (precision == 0) {
