@@ -306,6 +306,9 @@ SweepArgs base_sweep_args(petto_ctx *ctx) {
     a.red = ctx->red();
     a.ctrl = ctx->ctrl;
     a.rhs = nullptr;
+    const OpConst &k = ctx->k;
+    a.kf = OpConstF{(float)k.ce_par, (float)k.ce_perp, (float)k.cf_lam, (float)k.cf_mu, (float)k.cdiag, (float)k.ct,
+                    (float)k.src, 0.f, 0.f, 0.f};
     return a;
 }
 
@@ -332,6 +335,9 @@ petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, 
     A.a = a;
     A.b = b;
     A.s1 = s1;
+    A.kf.a = (float)a;
+    A.kf.b = (float)b;
+    A.kf.s1 = (float)s1;
     A.u_in = ctx->u[ctx->cur];
     A.u_out = ctx->u[1 - ctx->cur];
     A.w = ctx->w;
@@ -804,7 +810,7 @@ petto_status petto_residual(petto_ctx *ctx, double *res_norm2, void *R, int dtyp
 }  // extern "C"
 
 // set one device control word (stream-ordered, no host staging)
-__global__ void set_ctrl_kernel(double *ctrl, int slot, double v) { ctrl[slot] = v; }
+__global__ void set_ctrl_kernel(double *ctrl, int slot, long long v) { reinterpret_cast<long long *>(ctrl)[slot] = v; }
 
 namespace {
 
@@ -830,7 +836,7 @@ struct SolveState {
     double improve_ref = INFINITY;
 };
 
-petto_status set_ctrl(petto_ctx *ctx, int slot, double v) {
+petto_status set_ctrl(petto_ctx *ctx, int slot, long long v) {
     set_ctrl_kernel<<<1, 1, 0, ctx->stream>>>(ctx->ctrl, slot, v);
     CK(cudaGetLastError());
     ctx->launches++;
@@ -867,8 +873,10 @@ petto_status sweep_phase(petto_ctx *ctx, const petto_solve_opts *o, SolveState &
         if (ctx->trace) {
             double ctrl[CT_N];
             cudaMemcpy(ctrl, ctx->ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost);
+            long long ra = 0;
+            std::memcpy(&ra, &ctrl[CT_RESTART_AT], sizeof(ra));
             std::fprintf(stderr, "petto: sweep %lld res %.6e rel %.3e restart@%lld%s\n", (long long)S.sweeps, rn,
-                         ctx->f_norm > 0 ? rn / ctx->f_norm : 0.0, (long long)ctrl[CT_RESTART_AT],
+                         ctx->f_norm > 0 ? rn / ctx->f_norm : 0.0, ra,
                          rhs ? " (correction)" : "");
         }
         if (!check) break;
@@ -909,7 +917,7 @@ petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_sol
     if (o->n_apt < 0 || o->n_pt < 0 || o->max_sweeps < 0 || o->check_every < 0)
         return fail(ctx, PETTO_EINVAL, "negative count");
     CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
-    petto_status st = set_ctrl(ctx, CT_RESTART_AT, 0.0);
+    petto_status st = set_ctrl(ctx, CT_RESTART_AT, 0);
     if (st != PETTO_OK) return st;
     SolveState S;
     S.total = o->mode == PETTO_SOLVE_PAPER ? o->n_apt + o->n_pt : o->max_sweeps;

@@ -77,13 +77,21 @@ struct OpConst {
 };
 
 // Device-side solve control words (doubles in the ctrl array).
-constexpr int CT_RESTART_AT = 0;  // sweep index at which the APT momentum last restarted
+constexpr int CT_RESTART_AT = 0;  // sweep index (int64 bits) at which the APT momentum last restarted
 constexpr int CT_DOT = 1;         // last tested <R, w> (for inspection)
 constexpr int CT_ERR = 2;         // nonzero after a bounded device-side wait ran out
 constexpr int CT_N = 4;
 
+// FP32 copies of the constants, converted once on the host (a double-to-float conversion
+// in a kernel runs on the narrow FP64 pipe of GB300).
+struct OpConstF {
+    float ce_par, ce_perp, cf_lam, cf_mu, cdiag, ct, src;
+    float a, b, s1;
+};
+
 struct SweepArgs {
     Layout L;
+    OpConstF kf;
     int physics;              // 0 elastic, 1 thermal
     int ncomp, nrhs;
     int mode;                 // 0 APT, 1 PT, 2 residual only (writes R to w_or_r)
@@ -171,6 +179,23 @@ __device__ __forceinline__ double sum_partials(const RedBuf &rb, int64_t off, in
     for (int64_t i = block_tid(); i < n; i += block_nthreads()) acc += p[off + i];
     return block_sum(acc, sh);
 }
+
+// Momentum of the adaptive-restart schedule for this sweep: (k-1)/(k+2), k sweeps since the
+// last restart (0 for k <= 0).  Integer arithmetic until one FP32 division.
+__device__ __forceinline__ float apt_schedule(const SweepArgs &A) {
+    const long long k = A.sweep_idx - reinterpret_cast<const long long *>(A.ctrl)[CT_RESTART_AT];
+    if (k <= 0) return 0.f;
+    const int ki = k < (1 << 30) ? (int)k : (1 << 30);
+    return __fdividef((float)(ki - 1), (float)(ki + 2));
+}
+
+// Approximate reciprocal (MUFU, ~1 ulp): the local pseudo-time step only scales the update.
+__device__ __forceinline__ float fast_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 
 // atomic max for non-negative floating values through their ordered bit patterns
 __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {

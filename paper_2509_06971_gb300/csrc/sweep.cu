@@ -65,6 +65,20 @@ __device__ __forceinline__ unsigned fixed_mask(const BoxSet &bs, int i, int j, i
     return m;
 }
 
+// Sweep constants in the compute type: FP32 kernels use the host-converted FP32 copies.
+template <typename T> struct KC {
+    T ce_par, ce_perp, cf_lam, cf_mu, cdiag, ct, src, a, b, s1;
+};
+template <typename T> __device__ __forceinline__ KC<T> kconst(const SweepArgs &A);
+template <> __device__ __forceinline__ KC<float> kconst<float>(const SweepArgs &A) {
+    const OpConstF &f = A.kf;
+    return {f.ce_par, f.ce_perp, f.cf_lam, f.cf_mu, f.cdiag, f.ct, f.src, f.a, f.b, f.s1};
+}
+template <> __device__ __forceinline__ KC<double> kconst<double>(const SweepArgs &A) {
+    const OpConst &k = A.k;
+    return {k.ce_par, k.ce_perp, k.cf_lam, k.cf_mu, k.cdiag, k.ct, k.src, A.a, A.b, A.s1};
+}
+
 template <typename T> __device__ __forceinline__ T load_val(const LoadEntry &e);
 template <> __device__ __forceinline__ float load_val<float>(const LoadEntry &e) { return e.valf; }
 template <> __device__ __forceinline__ double load_val<double>(const LoadEntry &e) { return e.vald; }
@@ -73,9 +87,9 @@ template <> __device__ __forceinline__ double load_val<double>(const LoadEntry &
 // U[dy][dx][a] for offsets -1..1 around the node, Ec[cy][cx] for the 4 adjacent cells
 // (cell (i-1+cx, j-1+cy)).
 template <typename T>
-__device__ __forceinline__ void ku_elastic_2d(const T (&U)[3][3][2], const T (&Ec)[2][2], const OpConst &k,
+__device__ __forceinline__ void ku_elastic_2d(const T (&U)[3][3][2], const T (&Ec)[2][2], const KC<T> &k,
                                               T (&Ku)[2]) {
-    const T cpar = (T)k.ce_par, cperp = (T)k.ce_perp, cl = (T)k.cf_lam, cm = (T)k.cf_mu;
+    const T cpar = k.ce_par, cperp = k.ce_perp, cl = k.cf_lam, cm = k.cf_mu;
     Ku[0] = Ku[1] = T(0);
     // edges along x (b = 0) and y (b = 1)
     {
@@ -121,8 +135,8 @@ __device__ __forceinline__ void ku_elastic_2d(const T (&U)[3][3][2], const T (&E
 }
 
 template <typename T>
-__device__ __forceinline__ T ku_thermal_2d(const T (&U)[3][3], const T (&Ec)[2][2], const OpConst &k) {
-    const T ct = (T)k.ct;
+__device__ __forceinline__ T ku_thermal_2d(const T (&U)[3][3], const T (&Ec)[2][2], const KC<T> &k) {
+    const T ct = k.ct;
     const T Exm = Ec[0][0] + Ec[1][0], Exp = Ec[0][1] + Ec[1][1];
     const T Eym = Ec[0][0] + Ec[0][1], Eyp = Ec[1][0] + Ec[1][1];
     return ct * (Exm * (U[1][1] - U[1][0]) - Exp * (U[1][2] - U[1][1]) + Eym * (U[1][1] - U[0][1]) -
@@ -142,9 +156,9 @@ __device__ __forceinline__ T Eat(const T (&Ec)[2][2][2], int cx, int cy, int cz)
 }
 
 template <typename T>
-__device__ __forceinline__ void ku_elastic_3d(const T (&U)[3][3][3][3], const T (&Ec)[2][2][2], const OpConst &k,
+__device__ __forceinline__ void ku_elastic_3d(const T (&U)[3][3][3][3], const T (&Ec)[2][2][2], const KC<T> &k,
                                               T (&Ku)[3]) {
-    const T cpar = (T)k.ce_par, cperp = (T)k.ce_perp, cl = (T)k.cf_lam, cm = (T)k.cf_mu;
+    const T cpar = k.ce_par, cperp = k.ce_perp, cl = k.cf_lam, cm = k.cf_mu;
     Ku[0] = Ku[1] = Ku[2] = T(0);
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -222,8 +236,8 @@ __device__ __forceinline__ void ku_elastic_3d(const T (&U)[3][3][3][3], const T 
 }
 
 template <typename T>
-__device__ __forceinline__ T ku_thermal_3d(const T (&U)[3][3][3], const T (&Ec)[2][2][2], const OpConst &k) {
-    const T ct = (T)k.ct;
+__device__ __forceinline__ T ku_thermal_3d(const T (&U)[3][3][3], const T (&Ec)[2][2][2], const KC<T> &k) {
+    const T ct = k.ct;
     T acc = 0;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -252,17 +266,22 @@ __device__ __forceinline__ T ku_thermal_3d(const T (&U)[3][3][3], const T (&Ec)[
 // APT momentum of this sweep: fixed a, or the adaptive-restart schedule read from the
 // device control words (the same value in every thread of every block).
 template <typename T>
-__device__ __forceinline__ T apt_momentum(const SweepArgs &A) {
-    if (!A.adaptive) return (T)A.a;
-    const long long k = A.sweep_idx - (long long)A.ctrl[CT_RESTART_AT];
-    if (k <= 0) return T(0);
-    const T sched = (T)(k - 1) / (T)(k + 2);
-    return sched < (T)A.a ? sched : (T)A.a;
+__device__ __forceinline__ T apt_momentum(const SweepArgs &A, const KC<T> &k);
+template <> __device__ __forceinline__ float apt_momentum<float>(const SweepArgs &A, const KC<float> &k) {
+    return A.adaptive ? fminf(k.a, apt_schedule(A)) : k.a;
+}
+template <> __device__ __forceinline__ double apt_momentum<double>(const SweepArgs &A, const KC<double> &k) {
+    if (!A.adaptive) return k.a;
+    const long long kk = A.sweep_idx - reinterpret_cast<const long long *>(A.ctrl)[CT_RESTART_AT];
+    if (kk <= 0) return 0.0;
+    const double sched = (double)(kk - 1) / (double)(kk + 2);
+    return sched < k.a ? sched : k.a;
 }
 
 template <typename T>
 struct Upd {
     const SweepArgs &A;
+    KC<T> k;
     T a_eff;
     T res, dot;
     __device__ __forceinline__ void apply(int64_t idx_c, bool fixed, T Ku, T F, T diag, T *uo, const T *ui, T *w) {
@@ -271,14 +290,14 @@ struct Upd {
         if (A.want_res) res += R * R;
         const T u = ui[idx_c];
         if (A.mode == 0) {
-            const T step = A.local_dt ? (T)A.b / diag : (T)A.b;
+            const T step = A.local_dt ? k.b * fast_rcp(diag) : k.b;
             const T wi = w[idx_c];
             if (A.test_dot) dot += R * wi;
             const T wn = fixed ? T(0) : a_eff * wi + step * R;
             w[idx_c] = wn;
             uo[idx_c] = fixed ? T(0) : u + wn;
         } else if (A.mode == 1) {
-            const T step = A.local_dt ? (T)A.s1 / diag : (T)A.s1;
+            const T step = A.local_dt ? k.s1 * fast_rcp(diag) : k.s1;
             uo[idx_c] = fixed ? T(0) : u + step * R;
         } else {
             w[idx_c] = R;
@@ -303,7 +322,7 @@ __device__ __forceinline__ void finish_sweep(const SweepArgs &A, double res, dou
             if (A.want_res) *A.res2 = t;
             if (A.test_dot) {
                 A.ctrl[CT_DOT] = td;
-                if (td < 0.0) A.ctrl[CT_RESTART_AT] = (double)(A.sweep_idx + 1);
+                if (td < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = A.sweep_idx + 1;
             }
             *A.red.counter = 0u;
         }
@@ -320,7 +339,8 @@ __global__ void __launch_bounds__(256) sweep2d_gather(const SweepArgs A) {
     T *__restrict__ uo = static_cast<T *>(A.u_out);
     T *__restrict__ w = static_cast<T *>(A.w);
     const TE *__restrict__ E = static_cast<const TE *>(A.E);
-    Upd<T> up{A, apt_momentum<T>(A), T(0), T(0)};
+    const KC<T> kc = kconst<T>(A);
+    Upd<T> up{A, kc, apt_momentum<T>(A, kc), T(0), T(0)};
     if (i < L.NX && j < L.NY) {
         T Ec[2][2];
 #pragma unroll
@@ -328,7 +348,7 @@ __global__ void __launch_bounds__(256) sweep2d_gather(const SweepArgs A) {
 #pragma unroll
             for (int cx = 0; cx < 2; ++cx) Ec[cy][cx] = (T)__ldg(&E[L.cell(i - 1 + cx, j - 1 + cy, 0)]);
         const T S = Ec[0][0] + Ec[0][1] + Ec[1][0] + Ec[1][1];
-        const T diag = (T)A.k.cdiag * S;
+        const T diag = kc.cdiag * S;
         const unsigned fm = fixed_mask(A.boxes, i, j, 0);
         const int64_t n0 = L.node(i, j, 0);
         const int tile = blockIdx.x + gridDim.x * blockIdx.y;
@@ -346,7 +366,7 @@ __global__ void __launch_bounds__(256) sweep2d_gather(const SweepArgs A) {
                         for (int dx = 0; dx < 3; ++dx) U[dy][dx][a] = __ldg(&uc[n0 + (dy - 1) * L.SX + (dx - 1)]);
                 }
                 T Ku[2];
-                ku_elastic_2d<T>(U, Ec, A.k, Ku);
+                ku_elastic_2d<T>(U, Ec, kc, Ku);
 #pragma unroll
                 for (int a = 0; a < 2; ++a) {
                     const int c = r * 2 + a;
@@ -363,8 +383,8 @@ __global__ void __launch_bounds__(256) sweep2d_gather(const SweepArgs A) {
                 for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx) U[dy][dx] = __ldg(&uc[n0 + (dy - 1) * L.SX + (dx - 1)]);
-                const T Ku = ku_thermal_2d<T>(U, Ec, A.k);
-                T F = (T)A.k.src * (T)ncnt;
+                const T Ku = ku_thermal_2d<T>(U, Ec, kc);
+                T F = kc.src * (T)ncnt;
                 for (int l = l0; l < l1; ++l)
                     if (A.loads[l].node == n0 && A.loads[l].comp == r) F += load_val<T>(A.loads[l]);
                 const int64_t idx = (int64_t)r * L.cstride + n0;
@@ -386,7 +406,8 @@ __global__ void __launch_bounds__(128) sweep3d_gather(const SweepArgs A) {
     T *__restrict__ uo = static_cast<T *>(A.u_out);
     T *__restrict__ w = static_cast<T *>(A.w);
     const TE *__restrict__ E = static_cast<const TE *>(A.E);
-    Upd<T> up{A, apt_momentum<T>(A), T(0), T(0)};
+    const KC<T> kc = kconst<T>(A);
+    Upd<T> up{A, kc, apt_momentum<T>(A, kc), T(0), T(0)};
     const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int l0 = A.tile_ptr[tile], l1 = A.tile_ptr[tile + 1];
     if (i < L.NX && j < L.NY) {
@@ -402,7 +423,7 @@ __global__ void __launch_bounds__(128) sweep3d_gather(const SweepArgs A) {
             T S = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) S += Ec[q >> 2][(q >> 1) & 1][q & 1];
-            const T diag = (T)A.k.cdiag * S;
+            const T diag = kc.cdiag * S;
             const unsigned fm = fixed_mask(A.boxes, i, j, k);
             const int64_t n0 = L.node(i, j, k);
             const int ncnt = ((i > 0) + (i < L.nx)) * ((j > 0) + (j < L.ny)) * ((k > 0) + (k < L.nz));
@@ -421,7 +442,7 @@ __global__ void __launch_bounds__(128) sweep3d_gather(const SweepArgs A) {
                                     U[dz][dy][dx][a] = __ldg(&uc[n0 + (dz - 1) * L.SX * L.SY + (dy - 1) * L.SX + (dx - 1)]);
                     }
                     T Ku[3];
-                    ku_elastic_3d<T>(U, Ec, A.k, Ku);
+                    ku_elastic_3d<T>(U, Ec, kc, Ku);
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const int c = r * 3 + a;
@@ -440,8 +461,8 @@ __global__ void __launch_bounds__(128) sweep3d_gather(const SweepArgs A) {
 #pragma unroll
                             for (int dx = 0; dx < 3; ++dx)
                                 U[dz][dy][dx] = __ldg(&uc[n0 + (dz - 1) * L.SX * L.SY + (dy - 1) * L.SX + (dx - 1)]);
-                    const T Ku = ku_thermal_3d<T>(U, Ec, A.k);
-                    T F = (T)A.k.src * (T)ncnt;
+                    const T Ku = ku_thermal_3d<T>(U, Ec, kc);
+                    T F = kc.src * (T)ncnt;
                     for (int l = l0; l < l1; ++l)
                         if (A.loads[l].node == n0 && A.loads[l].comp == r) F += load_val<T>(A.loads[l]);
                     up.apply((int64_t)r * L.cstride + n0, fm & 1u, Ku, F, diag, uo, ui, w);
@@ -475,7 +496,8 @@ Tiling choose_tiling(const Layout &L, int physics, int precision, int nrhs) {
         // selects the register-staged kernel, PETTO_MARCH=tma16 32x16 tiles
         Tiling t{};
         const char *env = std::getenv("PETTO_MARCH");
-        if (env && std::strcmp(env, "v1") == 0) march3d_tiling(L, t);
+        // the TMA kernel addresses a node column with 32-bit offsets
+        if ((env && std::strcmp(env, "v1") == 0) || 3 * L.cstride >= (int64_t(1) << 31)) march3d_tiling(L, t);
         else march3d_tma_tiling(L, env && std::strcmp(env, "tma16") == 0 ? 16 : 8, t);
         return t;
     }
@@ -551,7 +573,7 @@ constexpr int NA_WORDS = NA_MAX_BLOCKS + 8;      // 131 136 bytes in all
 static __device__ __align__(256) double g_na_scratch[NA_WORDS];
 
 template <int DIM>
-__global__ void __launch_bounds__(NA_BLOCK) residual_norm_natural(int nx, int ny, int nz, OpConst k,
+__global__ void __launch_bounds__(NA_BLOCK) residual_norm_natural(int nx, int ny, int nz, KC<float> kf,
                                                                    const float *__restrict__ u,
                                                                    const float *__restrict__ E,
                                                                    const float *__restrict__ F,
@@ -589,7 +611,7 @@ __global__ void __launch_bounds__(NA_BLOCK) residual_norm_natural(int nx, int ny
 #pragma unroll
                 for (int cx = 0; cx < 2; ++cx) Ec[cy][cx] = eat(i - 1 + cx, j - 1 + cy, 0);
             float K2[2];
-            ku_elastic_2d<float>(U, Ec, k, K2);
+            ku_elastic_2d<float>(U, Ec, kf, K2);
             Ku[0] = K2[0];
             Ku[1] = K2[1];
         } else {
@@ -608,7 +630,7 @@ __global__ void __launch_bounds__(NA_BLOCK) residual_norm_natural(int nx, int ny
                 for (int cy = 0; cy < 2; ++cy)
 #pragma unroll
                     for (int cx = 0; cx < 2; ++cx) Ec[cz][cy][cx] = eat(i - 1 + cx, j - 1 + cy, kk - 1 + cz);
-            ku_elastic_3d<float>(U, Ec, k, Ku);
+            ku_elastic_3d<float>(U, Ec, kf, Ku);
         }
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
@@ -679,11 +701,11 @@ extern "C" petto_status petto_residual_norm_static(const petto_grid *grid, doubl
     const int d = grid->dim;
     const double hs = std::pow(grid->h, d - 2), nq = (double)(1 << d);
     const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = 1.0 / (2.0 * (1.0 + nu));
-    OpConst k{};
-    k.ce_par = 2.0 / nq * hs * (lam + 2.0 * mu);
-    k.ce_perp = 2.0 / nq * hs * mu;
-    k.cf_lam = hs * lam / nq;
-    k.cf_mu = hs * mu / nq;
+    KC<float> k{};
+    k.ce_par = (float)(2.0 / nq * hs * (lam + 2.0 * mu));
+    k.ce_perp = (float)(2.0 / nq * hs * mu);
+    k.cf_lam = (float)(hs * lam / nq);
+    k.cf_mu = (float)(hs * mu / nq);
     if (d == 2)
         residual_norm_natural<2><<<(unsigned)blocks, NA_BLOCK, 0, s>>>((int)grid->nx, (int)grid->ny, 0, k, u, E, F,
                                                                        fixed, scratch);

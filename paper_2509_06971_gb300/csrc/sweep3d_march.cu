@@ -73,15 +73,11 @@ __global__ void __launch_bounds__(MNT, 3) sweep3d_march_f32(const SweepArgs A) {
     const bool outxy = tx >= 1 && ty >= 1 && X < L.NX && Y < L.NY;
     const int zend = min(z0 + MZS, L.NZ);
 
-    const float cpar = (float)A.k.ce_par, cperp = (float)A.k.ce_perp;
-    const float cl = (float)A.k.cf_lam, cm = (float)A.k.cf_mu, cdg = (float)A.k.cdiag;
-    float fa = (float)A.a;
-    const float fb = (float)A.b, fs1 = (float)A.s1;
-    if (A.adaptive) {
-        const long long k = A.sweep_idx - (long long)A.ctrl[CT_RESTART_AT];
-        const float sched = k <= 0 ? 0.f : (float)(k - 1) / (float)(k + 2);
-        fa = fminf(fa, sched);
-    }
+    const float cpar = A.kf.ce_par, cperp = A.kf.ce_perp;
+    const float cl = A.kf.cf_lam, cm = A.kf.cf_mu, cdg = A.kf.cdiag;
+    float fa = A.kf.a;
+    const float fb = A.kf.b, fs1 = A.kf.s1;
+    if (A.adaptive) fa = fminf(fa, apt_schedule(A));
     const float *__restrict__ rhs = static_cast<const float *>(A.rhs);
 
     // supports: boxes that contain this (X, Y) column
@@ -260,7 +256,7 @@ __global__ void __launch_bounds__(MNT, 3) sweep3d_march_f32(const SweepArgs A) {
                 }
             }
             const float S8 = E0[0] + E0[1] + E0[2] + E0[3] + E1[0] + E1[1] + E1[2] + E1[3];
-            const float dinv = A.local_dt ? 1.f / (cdg * S8) : 1.f;
+            const float dinv = A.local_dt ? fast_rcp(cdg * S8) : 1.f;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const bool fixed = (fm >> c) & 1u;
@@ -306,7 +302,7 @@ __global__ void __launch_bounds__(MNT, 3) sweep3d_march_f32(const SweepArgs A) {
                 if (A.want_res) *A.res2 = t;
                 if (A.test_dot) {
                     A.ctrl[CT_DOT] = td;
-                    if (td < 0.0) A.ctrl[CT_RESTART_AT] = (double)(A.sweep_idx + 1);
+                    if (td < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = A.sweep_idx + 1;
                 }
                 *A.red.counter = 0u;
             }
@@ -405,10 +401,188 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// Per-thread state carried from plane to plane.
+struct MarchCarry {
+    float Sz[3];      // share of the z-neighbour (n + z) from this plane's owned entities
+    float Gxz[2];     // xz-face corner share for (n + x + z), sent with the next plane's x-message
+    float Gyz[2];     // yz-face corner share for (n + y + z), sent with the next plane's y-message
+    float res, dot;   // per-thread partial sums of R^2 and R.w
+};
+
+// Constants of one sweep, read once per thread.
+struct MarchConst {
+    float cpar, cperp, cl, cm, cdg, fa, fb, fs1;
+};
+
+// One owner plane zp: Ulo/Elo = plane zp / layer zp-1 (registers), the stage of plane zp+1 is
+// read from ring slot `slot` into Uhi/Ehi.  Returns false when a wait timed out.
+template <int TY>
+__device__ __forceinline__ bool march_plane(const SweepArgs &A, const MarchConst &K, int zp, int z0, int r1,
+                                            const float *su, const float *se, float4 *msg, uint64_t *bars,
+                                            int tid, int xoff, int xoffe, bool outxy, int plane32, int cs32,
+                                            float *wb, float *uob, const float *rb, unsigned boxbits, int l0, int l1,
+                                            int64_t nbase, const float (&Ulo)[4][3], const float (&Elo)[4],
+                                            float (&Uhi)[4][3], float (&Ehi)[4], MarchCarry &C, bool &bad) {
+    using G = TmaGeom<TY>;
+    const int tx = tid & 31, ty = tid >> 5;
+    const int slot = r1 & (TNS - 1);
+    const bool outp = outxy && zp >= z0;
+    const int off = zp * plane32;  // offset of (X, Y, zp) from the thread's column base
+    float wv0 = 0.f, wv1 = 0.f, wv2 = 0.f;
+    if (outp && A.mode == 0) {
+        wv0 = wb[off];
+        wv1 = wb[cs32 + off];
+        wv2 = wb[2 * cs32 + off];
+    }
+    if (!mbar_wait(smem_u32(&bars[slot]), (r1 / TNS) & 1)) bad = true;
+    {
+        const float *r0 = su + slot * (G::USLOT / 4) + ty * TBW + xoff + tx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Uhi[0][c] = r0[c * G::WY * TBW];
+            Uhi[1][c] = r0[c * G::WY * TBW + 1];
+            Uhi[2][c] = r0[c * G::WY * TBW + TBW];
+            Uhi[3][c] = r0[c * G::WY * TBW + TBW + 1];
+        }
+        const float *q0 = se + slot * (G::ESLOT / 4) + ty * TBW + xoffe + tx;
+        Ehi[0] = q0[TBW + 1];  // c(n)
+        Ehi[1] = q0[TBW];      // c(n-x)
+        Ehi[2] = q0[1];        // c(n-y)
+        Ehi[3] = q0[0];        // c(n-x-y)
+    }
+    // owned edges n->n+x, n->n+y, n->n+z
+    const float e00 = Ehi[0] + Elo[0];
+    const float Ex = e00 + Ehi[2] + Elo[2];
+    const float Ey = e00 + Ehi[1] + Elo[1];
+    const float Ez = (Ehi[0] + Ehi[1]) + (Ehi[2] + Ehi[3]);
+    float ax[3], ay[3], az[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        ax[c] = Ulo[1][c] - Ulo[0][c];
+        ay[c] = Ulo[2][c] - Ulo[0][c];
+        az[c] = Uhi[0][c] - Ulo[0][c];
+    }
+    const float exq = Ex * K.cperp, eyq = Ey * K.cperp, ezq = Ez * K.cperp;
+    const float Fx0 = Ex * K.cpar * ax[0], Fx1 = exq * ax[1], Fx2 = exq * ax[2];
+    const float Fy0 = eyq * ay[0], Fy1 = Ey * K.cpar * ay[1], Fy2 = eyq * ay[2];
+    const float Fz0 = ezq * az[0], Fz1 = ezq * az[1], Fz2 = Ez * K.cpar * az[2];
+    // owned faces (G: share of the far corner, H: share of the a-neighbour corner)
+    float Gxy0, Gxy1, Hxy0, Hxy1, Gxz0, Gxz1, Hxz0, Hxz1, Gyz0, Gyz1, Hyz0, Hyz1;
+    {
+        const float el = e00 * K.cl, em = e00 * K.cm;
+        const float SAx = ax[0] + (Ulo[3][0] - Ulo[2][0]), SAy = ax[1] + (Ulo[3][1] - Ulo[2][1]);
+        const float SBx = ay[0] + (Ulo[3][0] - Ulo[1][0]), SBy = ay[1] + (Ulo[3][1] - Ulo[1][1]);
+        const float p = em * SAy, q = el * SAx;
+        Gxy0 = fmaf(el, SBy, p);
+        Hxy0 = fmaf(el, SBy, -p);
+        Gxy1 = fmaf(em, SBx, q);
+        Hxy1 = fmaf(em, SBx, -q);
+    }
+    {
+        const float Et = Ehi[0] + Ehi[2];
+        const float el = Et * K.cl, em = Et * K.cm;
+        const float SAx = ax[0] + (Uhi[1][0] - Uhi[0][0]), SAz = ax[2] + (Uhi[1][2] - Uhi[0][2]);
+        const float SBx = az[0] + (Uhi[1][0] - Ulo[1][0]), SBz = az[2] + (Uhi[1][2] - Ulo[1][2]);
+        const float p = em * SAz, q = el * SAx;
+        Gxz0 = fmaf(el, SBz, p);
+        Hxz0 = fmaf(el, SBz, -p);
+        Gxz1 = fmaf(em, SBx, q);
+        Hxz1 = fmaf(em, SBx, -q);
+    }
+    {
+        const float Et = Ehi[0] + Ehi[1];
+        const float el = Et * K.cl, em = Et * K.cm;
+        const float SAy = ay[1] + (Uhi[2][1] - Uhi[0][1]), SAz = ay[2] + (Uhi[2][2] - Uhi[0][2]);
+        const float SBy = az[1] + (Uhi[2][1] - Ulo[2][1]), SBz = az[2] + (Uhi[2][2] - Ulo[2][2]);
+        const float p = em * SAz, q = el * SAy;
+        Gyz0 = fmaf(el, SBz, p);
+        Hyz0 = fmaf(el, SBz, -p);
+        Gyz1 = fmaf(em, SBy, q);
+        Hyz1 = fmaf(em, SBy, -q);
+    }
+    float4 *ma = msg + ((zp & 1) * 2 + 0) * G::NT;
+    float4 *mb = msg + ((zp & 1) * 2 + 1) * G::NT;
+    ma[tid] = make_float4(Fx0 + Hxy0 + Hxz0 + C.Gxz[0], Fx1 + Hxy1, Fx2 + Hxz1 + C.Gxz[1], Gxy0);
+    mb[tid] = make_float4(Fy0 - Hxy0, Fy1 - Hxy1 + Hyz0 + C.Gyz[0], Fy2 + Hyz1 + C.Gyz[1], Gxy1);
+    const float own0 = -(Fx0 + Fy0 + Fz0) - (Gxy0 + Gxz0);
+    const float own1 = -(Fx1 + Fy1 + Fz1) - (Gxy1 + Gyz0);
+    const float own2 = -(Fx2 + Fy2 + Fz2) - (Gxz1 + Gyz1);
+    if (__syncthreads_or(bad)) {
+        bad = true;
+        return false;
+    }
+    if (outp) {
+        const float4 rx = ma[tid - 1];
+        const float4 ry = mb[tid - 32];
+        const float gxy0 = ma[tid - 33].w, gxy1 = mb[tid - 33].w;
+        const float Ku0 = own0 + rx.x + ry.x + C.Sz[0] + gxy0;
+        const float Ku1 = own1 + rx.y + ry.y + C.Sz[1] + gxy1;
+        const float Ku2 = own2 + rx.z + ry.z + C.Sz[2];
+        unsigned fm = 0;
+        if (boxbits)
+            for (int q = 0; q < A.boxes.n; ++q)
+                if (((boxbits >> q) & 1u) && zp >= A.boxes.b[q].lo[2] && zp <= A.boxes.b[q].hi[2])
+                    fm |= A.boxes.b[q].mask;
+        float F0 = 0.f, F1 = 0.f, F2 = 0.f;
+        if (rb) {
+            F0 = rb[off];
+            F1 = rb[cs32 + off];
+            F2 = rb[2 * cs32 + off];
+        } else if (l0 < l1) {
+            const int64_t nidx = nbase + off;
+            for (int l = l0; l < l1; ++l) {
+                const LoadEntry &le = A.loads[l];
+                if (le.node == nidx) {
+                    if (le.comp == 0) F0 += le.valf;
+                    else if (le.comp == 1) F1 += le.valf;
+                    else F2 += le.valf;
+                }
+            }
+        }
+        float step = A.mode == 0 ? K.fb : K.fs1;
+        if (A.local_dt) {
+            const float S8 = (Elo[0] + Elo[1]) + (Elo[2] + Elo[3]) + (Ehi[0] + Ehi[1]) + (Ehi[2] + Ehi[3]);
+            step *= fast_rcp(K.cdg * S8);
+        }
+        const float R0 = (fm & 1u) ? 0.f : F0 - Ku0;
+        const float R1 = (fm & 2u) ? 0.f : F1 - Ku1;
+        const float R2 = (fm & 4u) ? 0.f : F2 - Ku2;
+        if (A.want_res) C.res += R0 * R0 + R1 * R1 + R2 * R2;
+        if (A.mode == 0) {
+            if (A.test_dot) C.dot += R0 * wv0 + R1 * wv1 + R2 * wv2;
+            const float w0 = (fm & 1u) ? 0.f : fmaf(K.fa, wv0, step * R0);
+            const float w1 = (fm & 2u) ? 0.f : fmaf(K.fa, wv1, step * R1);
+            const float w2 = (fm & 4u) ? 0.f : fmaf(K.fa, wv2, step * R2);
+            wb[off] = w0;
+            wb[cs32 + off] = w1;
+            wb[2 * cs32 + off] = w2;
+            uob[off] = (fm & 1u) ? 0.f : Ulo[0][0] + w0;
+            uob[cs32 + off] = (fm & 2u) ? 0.f : Ulo[0][1] + w1;
+            uob[2 * cs32 + off] = (fm & 4u) ? 0.f : Ulo[0][2] + w2;
+        } else if (A.mode == 1) {
+            uob[off] = (fm & 1u) ? 0.f : fmaf(step, R0, Ulo[0][0]);
+            uob[cs32 + off] = (fm & 2u) ? 0.f : fmaf(step, R1, Ulo[0][1]);
+            uob[2 * cs32 + off] = (fm & 4u) ? 0.f : fmaf(step, R2, Ulo[0][2]);
+        } else {
+            wb[off] = R0;
+            wb[cs32 + off] = R1;
+            wb[2 * cs32 + off] = R2;
+        }
+    }
+    C.Sz[0] = Fz0 - Hxz0;
+    C.Sz[1] = Fz1 - Hyz0;
+    C.Sz[2] = Fz2 - Hxz1 - Hyz1;
+    C.Gxz[0] = Gxz0;
+    C.Gxz[1] = Gxz1;
+    C.Gyz[0] = Gyz0;
+    C.Gyz[1] = Gyz1;
+    return true;
+}
+
 template <int TY>
 __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __grid_constant__ SweepArgs A,
-                                                             const __grid_constant__ CUtensorMap tmu,
-                                                             const __grid_constant__ CUtensorMap tme) {
+                                                                      const __grid_constant__ CUtensorMap tmu,
+                                                                      const __grid_constant__ CUtensorMap tme) {
     using G = TmaGeom<TY>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations at 128-byte aligned shared addresses
@@ -420,10 +594,6 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __gr
     __shared__ double shred[32];
 
     const Layout &L = A.L;
-    float *__restrict__ uo = static_cast<float *>(A.u_out);
-    float *__restrict__ w = static_cast<float *>(A.w);
-    const float *__restrict__ rhs = static_cast<const float *>(A.rhs);
-
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int x0 = blockIdx.x * 31, y0 = blockIdx.y * (TY - 1), z0 = blockIdx.z * MZS;
     const int X = x0 - 1 + tx, Y = y0 - 1 + ty;
@@ -432,15 +602,16 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __gr
     const int xs = (x0 - 1 + OX) & ~3, xoff = (x0 - 1 + OX) - xs;    // u box origin / column offset
     const int xse = (x0 - 2 + OX) & ~3, xoffe = (x0 - 2 + OX) - xse; // E box origin / column offset
 
-    const float cpar = (float)A.k.ce_par, cperp = (float)A.k.ce_perp;
-    const float cl = (float)A.k.cf_lam, cm = (float)A.k.cf_mu, cdg = (float)A.k.cdiag;
-    float fa = (float)A.a;
-    const float fb = (float)A.b, fs1 = (float)A.s1;
-    if (A.adaptive) {
-        const long long k = A.sweep_idx - (long long)A.ctrl[CT_RESTART_AT];
-        const float sched = k <= 0 ? 0.f : (float)(k - 1) / (float)(k + 2);
-        fa = fminf(fa, sched);
-    }
+    MarchConst K;
+    K.cpar = A.kf.ce_par;
+    K.cperp = A.kf.ce_perp;
+    K.cl = A.kf.cf_lam;
+    K.cm = A.kf.cf_mu;
+    K.cdg = A.kf.cdiag;
+    K.fa = A.kf.a;
+    K.fb = A.kf.b;
+    K.fs1 = A.kf.s1;
+    if (A.adaptive) K.fa = fminf(K.fa, apt_schedule(A));
     unsigned boxbits = 0;
     for (int q = 0; q < A.boxes.n; ++q) {
         const Box &b = A.boxes.b[q];
@@ -448,13 +619,17 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __gr
     }
     const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int l0 = A.tile_ptr[tile], l1 = A.tile_ptr[tile + 1];
-    const int64_t plane = L.SX * L.SY, cs = L.cstride;
+    // per-thread column bases; in-column offsets fit in 32 bits (checked on the host)
     const int64_t nbase = outxy ? L.node(X, Y, 0) : 0;
+    const int plane32 = (int)(L.SX * L.SY), cs32 = (int)L.cstride;
+    float *wb = static_cast<float *>(A.w) + nbase;
+    float *uob = A.u_out ? static_cast<float *>(A.u_out) + nbase : nullptr;
+    const float *rb = A.rhs ? static_cast<const float *>(A.rhs) + nbase : nullptr;
 
     // stage r (relative to plane z0-1) holds u plane z0-1+r and E layer z0-2+r
     auto issue = [&](int r) {
         const int p = z0 - 1 + r;
-        const int slot = r % TNS;
+        const int slot = r & (TNS - 1);
         const uint32_t bar = smem_u32(&bars[slot]);
         mbar_expect_tx(bar, (unsigned)(G::UBYTES + G::EBYTES));
         tma_load_4d(smem_u32(su + slot * (G::USLOT / 4)), &tmu, xs, y0, p + 1, 0, bar);
@@ -471,191 +646,55 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __gr
     int issued = min(TD + 1, nstage);
 
     bool bad = !mbar_wait(smem_u32(&bars[0]), 0);
-    float U0[4][3], E0[4];
+    float UA[4][3], EA[4], UB[4][3], EB[4];
     {
-        const float *u0 = su;
-        const float *e0 = se;
+        const float *r0 = su + ty * TBW + xoff + tx;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float *r0 = u0 + (c * G::WY + ty) * TBW + xoff + tx;
-            U0[0][c] = r0[0];
-            U0[1][c] = r0[1];
-            U0[2][c] = r0[TBW];
-            U0[3][c] = r0[TBW + 1];
+            UA[0][c] = r0[c * G::WY * TBW];
+            UA[1][c] = r0[c * G::WY * TBW + 1];
+            UA[2][c] = r0[c * G::WY * TBW + TBW];
+            UA[3][c] = r0[c * G::WY * TBW + TBW + 1];
         }
-        const float *q0 = e0 + ty * TBW + xoffe + tx;
-        E0[0] = q0[TBW + 1];
-        E0[1] = q0[TBW];
-        E0[2] = q0[1];
-        E0[3] = q0[0];
+        const float *q0 = se + ty * TBW + xoffe + tx;
+        EA[0] = q0[TBW + 1];
+        EA[1] = q0[TBW];
+        EA[2] = q0[1];
+        EA[3] = q0[0];
     }
     bad = __syncthreads_or(bad);
-    float Szp[3] = {0.f, 0.f, 0.f}, Gxzp[2] = {0.f, 0.f}, Gyzp[2] = {0.f, 0.f};
-    float res = 0.f, dot = 0.f;
+    MarchCarry C = {{0.f, 0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, 0.f, 0.f};
 
-    for (int zp = z0 - 1; zp < zend && !bad; ++zp) {
-        const int r1 = zp + 1 - (z0 - 1);  // stage read in this iteration
-        if (tid == 0 && issued < nstage && issued <= r1 + TD - 1 + 1) {
-            issue(issued);
-        }
+    // two planes per trip with the register sets swapping roles
+    for (int zp = z0 - 1; zp < zend && !bad; zp += 2) {
+        int r1 = zp + 1 - (z0 - 1);
+        if (tid == 0 && issued < nstage) issue(issued);
         issued = min(issued + 1, nstage);
-        const int slot = r1 % TNS;
-        const bool outp = outxy && zp >= z0;
-        const int64_t nidx = nbase + (int64_t)zp * plane;
-        float wv[3] = {0.f, 0.f, 0.f};
-        if (outp && A.mode == 0) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) wv[c] = w[c * cs + nidx];
-        }
-        if (!mbar_wait(smem_u32(&bars[slot]), (r1 / TNS) & 1)) bad = true;
-        float U1[4][3], E1[4];
-        {
-            const float *u1 = su + slot * (G::USLOT / 4);
-            const float *e1 = se + slot * (G::ESLOT / 4);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float *r0 = u1 + (c * G::WY + ty) * TBW + xoff + tx;
-                U1[0][c] = r0[0];
-                U1[1][c] = r0[1];
-                U1[2][c] = r0[TBW];
-                U1[3][c] = r0[TBW + 1];
-            }
-            const float *q0 = e1 + ty * TBW + xoffe + tx;
-            E1[0] = q0[TBW + 1];
-            E1[1] = q0[TBW];
-            E1[2] = q0[1];
-            E1[3] = q0[0];
-        }
-        const float Ex = E1[0] + E1[2] + E0[0] + E0[2];
-        const float Ey = E1[0] + E1[1] + E0[0] + E0[1];
-        const float Ez = E1[0] + E1[1] + E1[2] + E1[3];
-        float ax[3], ay[3], az[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            ax[c] = U0[1][c] - U0[0][c];
-            ay[c] = U0[2][c] - U0[0][c];
-            az[c] = U1[0][c] - U0[0][c];
-        }
-        const float exp_ = Ex * cpar, exq = Ex * cperp, eyp = Ey * cpar, eyq = Ey * cperp, ezp = Ez * cpar,
-                    ezq = Ez * cperp;
-        const float Fx[3] = {exp_ * ax[0], exq * ax[1], exq * ax[2]};
-        const float Fy[3] = {eyq * ay[0], eyp * ay[1], eyq * ay[2]};
-        const float Fz[3] = {ezq * az[0], ezq * az[1], ezp * az[2]};
-        float Gxy[2], Hxy[2], Gxz[2], Hxz[2], Gyz[2], Hyz[2];
-        {
-            const float Et = E1[0] + E0[0];
-            const float SAx = ax[0] + (U0[3][0] - U0[2][0]), SAy = ax[1] + (U0[3][1] - U0[2][1]);
-            const float SBx = ay[0] + (U0[3][0] - U0[1][0]), SBy = ay[1] + (U0[3][1] - U0[1][1]);
-            const float el = Et * cl, em = Et * cm, p = em * SAy, q = el * SAx;
-            Gxy[0] = fmaf(el, SBy, p);
-            Hxy[0] = fmaf(el, SBy, -p);
-            Gxy[1] = fmaf(em, SBx, q);
-            Hxy[1] = fmaf(em, SBx, -q);
-        }
-        {
-            const float Et = E1[0] + E1[2];
-            const float SAx = ax[0] + (U1[1][0] - U1[0][0]), SAz = ax[2] + (U1[1][2] - U1[0][2]);
-            const float SBx = az[0] + (U1[1][0] - U0[1][0]), SBz = az[2] + (U1[1][2] - U0[1][2]);
-            const float el = Et * cl, em = Et * cm, p = em * SAz, q = el * SAx;
-            Gxz[0] = fmaf(el, SBz, p);
-            Hxz[0] = fmaf(el, SBz, -p);
-            Gxz[1] = fmaf(em, SBx, q);
-            Hxz[1] = fmaf(em, SBx, -q);
-        }
-        {
-            const float Et = E1[0] + E1[1];
-            const float SAy = ay[1] + (U1[2][1] - U1[0][1]), SAz = ay[2] + (U1[2][2] - U1[0][2]);
-            const float SBy = az[1] + (U1[2][1] - U0[2][1]), SBz = az[2] + (U1[2][2] - U0[2][2]);
-            const float el = Et * cl, em = Et * cm, p = em * SAz, q = el * SAy;
-            Gyz[0] = fmaf(el, SBz, p);
-            Hyz[0] = fmaf(el, SBz, -p);
-            Gyz[1] = fmaf(em, SBy, q);
-            Hyz[1] = fmaf(em, SBy, -q);
-        }
-        const int sm = zp & 1;
-        float4 *ma = msg + (sm * 2 + 0) * G::NT;
-        float4 *mb = msg + (sm * 2 + 1) * G::NT;
-        ma[tid] = make_float4(Fx[0] + Hxy[0] + Hxz[0] + Gxzp[0], Fx[1] + Hxy[1], Fx[2] + Hxz[1] + Gxzp[1], Gxy[0]);
-        mb[tid] = make_float4(Fy[0] - Hxy[0], Fy[1] - Hxy[1] + Hyz[0] + Gyzp[0], Fy[2] + Hyz[1] + Gyzp[1], Gxy[1]);
-        const float own0 = -(Fx[0] + Fy[0] + Fz[0]) - Gxy[0] - Gxz[0];
-        const float own1 = -(Fx[1] + Fy[1] + Fz[1]) - Gxy[1] - Gyz[0];
-        const float own2 = -(Fx[2] + Fy[2] + Fz[2]) - Gxz[1] - Gyz[1];
-        const float Sz0 = Fz[0] - Hxz[0], Sz1 = Fz[1] - Hyz[0], Sz2 = Fz[2] - Hxz[1] - Hyz[1];
-        if (__syncthreads_or(bad)) {
-            bad = true;
+        if (!march_plane<TY>(A, K, zp, z0, r1, su, se, msg, bars, tid, xoff, xoffe, outxy, plane32, cs32, wb, uob, rb,
+                             boxbits, l0, l1, nbase, UA, EA, UB, EB, C, bad))
             break;
-        }
-        if (outp) {
-            const float4 rx = ma[tid - 1];
-            const float4 ry = mb[tid - 32];
-            const float gxy0 = ma[tid - 33].w, gxy1 = mb[tid - 33].w;
-            const float Ku[3] = {own0 + rx.x + ry.x + Szp[0] + gxy0, own1 + rx.y + ry.y + Szp[1] + gxy1,
-                                 own2 + rx.z + ry.z + Szp[2]};
-            unsigned fm = 0;
-            if (boxbits)
-                for (int q = 0; q < A.boxes.n; ++q)
-                    if (((boxbits >> q) & 1u) && zp >= A.boxes.b[q].lo[2] && zp <= A.boxes.b[q].hi[2])
-                        fm |= A.boxes.b[q].mask;
-            float F[3] = {0.f, 0.f, 0.f};
-            if (rhs) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) F[c] = rhs[c * cs + nidx];
-            } else {
-                for (int l = l0; l < l1; ++l) {
-                    const LoadEntry &le = A.loads[l];
-                    if (le.node == nidx) F[le.comp] += le.valf;
-                }
-            }
-            float dinv = 1.f;
-            if (A.local_dt) {
-                const float S8 = E0[0] + E0[1] + E0[2] + E0[3] + E1[0] + E1[1] + E1[2] + E1[3];
-                dinv = __frcp_rn(cdg * S8);
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const bool fixed = (fm >> c) & 1u;
-                const float R = fixed ? 0.f : F[c] - Ku[c];
-                res = fmaf(R, R, res);
-                const int64_t idx = c * cs + nidx;
-                if (A.mode == 0) {
-                    dot = fmaf(R, wv[c], dot);
-                    const float wn = fixed ? 0.f : fmaf(fa, wv[c], fb * dinv * R);
-                    w[idx] = wn;
-                    uo[idx] = fixed ? 0.f : U0[0][c] + wn;
-                } else if (A.mode == 1) {
-                    uo[idx] = fixed ? 0.f : fmaf(fs1 * dinv, R, U0[0][c]);
-                } else {
-                    w[idx] = R;
-                }
-            }
-        }
-        Szp[0] = Sz0; Szp[1] = Sz1; Szp[2] = Sz2;
-        Gxzp[0] = Gxz[0]; Gxzp[1] = Gxz[1];
-        Gyzp[0] = Gyz[0]; Gyzp[1] = Gyz[1];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            U0[0][c] = U1[0][c];
-            U0[1][c] = U1[1][c];
-            U0[2][c] = U1[2][c];
-            U0[3][c] = U1[3][c];
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) E0[q] = E1[q];
+        if (zp + 1 >= zend) break;
+        ++r1;
+        if (tid == 0 && issued < nstage) issue(issued);
+        issued = min(issued + 1, nstage);
+        if (!march_plane<TY>(A, K, zp + 1, z0, r1, su, se, msg, bars, tid, xoff, xoffe, outxy, plane32, cs32, wb, uob,
+                             rb, boxbits, l0, l1, nbase, UB, EB, UA, EA, C, bad))
+            break;
     }
 
     if (bad) {
         // record the time-out, let the copies already issued land (bounded), leave
         if (tid == 0) {
             A.ctrl[CT_ERR] = 1.0;
-            for (int r = 0; r < issued; ++r) mbar_wait(smem_u32(&bars[r % TNS]), (r / TNS) & 1);
+            for (int r = 0; r < issued; ++r) mbar_wait(smem_u32(&bars[r & (TNS - 1)]), (r / TNS) & 1);
         }
         __syncthreads();
         return;
     }
     if (A.want_res || A.test_dot) {
         const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
-        const double r = A.want_res ? block_sum((double)res, shred) : 0.0;
-        const double d = A.test_dot ? block_sum((double)dot, shred) : 0.0;
+        const double r = A.want_res ? block_sum((double)C.res, shred) : 0.0;
+        const double d = A.test_dot ? block_sum((double)C.dot, shred) : 0.0;
         if (tid == 0) A.red.partials[(int64_t)nb + tile] = d;
         if (publish_partial(r, A.red, tile, nb)) {
             const double t = A.want_res ? sum_partials(A.red, 0, nb, shred) : 0.0;
@@ -664,7 +703,7 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __gr
                 if (A.want_res) *A.res2 = t;
                 if (A.test_dot) {
                     A.ctrl[CT_DOT] = td;
-                    if (td < 0.0) A.ctrl[CT_RESTART_AT] = (double)(A.sweep_idx + 1);
+                    if (td < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = A.sweep_idx + 1;
                 }
                 *A.red.counter = 0u;
             }
