@@ -682,11 +682,11 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
         petto_destroy(ctx);
         return PETTO_ECUDA;
     }
-    if (ctx->tiling.kind == 2 || ctx->tiling.kind == 3) {
-        const int ty = ctx->tiling.kind == 3 ? 16 : 8;
-        if (!make_tma_maps(ctx->L, ty, ctx->u[0], ctx->u[1], ctx->E, ctx->tma)) {
+    if (ctx->tiling.kind == 2 || ctx->tiling.kind == 3 || ctx->tiling.kind == 4) {
+        const int ty = ctx->tiling.kind == 3 || ctx->tiling.kind == 4 ? 16 : 8;
+        if (!make_tma_maps(ctx->L, ty, ctx->u[0], ctx->u[1], ctx->w, ctx->E, ctx->tma)) {
             if (ctx->tiling.kind == 2) {
-                march3d_tiling(ctx->L, ctx->tiling);  // same tiles, register-staged kernel
+                march3d_tiling(ctx->L, ctx->tiling);  // same tile shape, register-staged kernel
             } else {
                 ctx->err = "tensor map creation failed";
                 petto_destroy(ctx);

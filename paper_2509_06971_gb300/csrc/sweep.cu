@@ -498,6 +498,7 @@ Tiling choose_tiling(const Layout &L, int physics, int precision, int nrhs) {
         const char *env = std::getenv("PETTO_MARCH");
         // the TMA kernel addresses a node column with 32-bit offsets
         if ((env && std::strcmp(env, "v1") == 0) || 3 * L.cstride >= (int64_t(1) << 31)) march3d_tiling(L, t);
+        else if (env && std::strcmp(env, "tma2") == 0) march3d_tma2_tiling(L, t);
         else march3d_tma_tiling(L, env && std::strcmp(env, "tma16") == 0 ? 16 : 8, t);
         return t;
     }
@@ -518,11 +519,17 @@ cudaError_t launch_residual64(const SweepArgs &a, const Tiling &t, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep(const SweepArgs &a, const Tiling &t, int precision, cudaStream_t s, const TmaMaps *maps) {
+cudaError_t launch_sweep(const SweepArgs &a0, const Tiling &t, int precision, cudaStream_t s, const TmaMaps *maps) {
+    SweepArgs a = a0;
+    a.zseg = t.zs;
     if (t.kind == 1) return launch_march3d(a, t, s);
     if (t.kind == 2 || t.kind == 3) {
         if (!maps || !maps->valid) return cudaErrorInvalidValue;
         return launch_march3d_tma(a, t, *maps, s);
+    }
+    if (t.kind == 4) {
+        if (!maps || !maps->valid) return cudaErrorInvalidValue;
+        return launch_march3d_tma2(a, t, *maps, s);
     }
     dim3 block(t.bx, t.by, 1), grid(t.gx, t.gy, t.gz);
     if (a.L.dim == 2) {

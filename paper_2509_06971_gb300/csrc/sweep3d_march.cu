@@ -23,7 +23,7 @@ namespace {
 
 constexpr int MX = 32;           // threads (owner columns) per tile row
 constexpr int MTY = 8;           // owner rows per tile
-constexpr int MZS = 16;          // output planes per z segment
+constexpr int MZS = 16;          // default output planes per z segment (runtime: Tiling::zs)
 constexpr int MWX = MX + 1;      // tile width in nodes / cells
 constexpr int MWY = MTY + 1;     // tile height
 constexpr int MNT = MX * MTY;    // threads per block
@@ -68,10 +68,10 @@ __global__ void __launch_bounds__(MNT, 3) sweep3d_march_f32(const SweepArgs A) {
     const float *__restrict__ E = static_cast<const float *>(A.E);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * MX + tx;
-    const int x0 = blockIdx.x * (MX - 1), y0 = blockIdx.y * (MTY - 1), z0 = blockIdx.z * MZS;
+    const int x0 = blockIdx.x * (MX - 1), y0 = blockIdx.y * (MTY - 1), z0 = blockIdx.z * A.zseg;
     const int X = x0 - 1 + tx, Y = y0 - 1 + ty;
     const bool outxy = tx >= 1 && ty >= 1 && X < L.NX && Y < L.NY;
-    const int zend = min(z0 + MZS, L.NZ);
+    const int zend = min(z0 + A.zseg, L.NZ);
 
     const float cpar = A.kf.ce_par, cperp = A.kf.ce_perp;
     const float cl = A.kf.cf_lam, cm = A.kf.cf_mu, cdg = A.kf.cdiag;
@@ -312,15 +312,35 @@ __global__ void __launch_bounds__(MNT, 3) sweep3d_march_f32(const SweepArgs A) {
 
 }  // namespace
 
+// Number of z segments: minimise (waves of resident blocks) x (planes per block, with the
+// one-plane halo), for `resident` blocks in flight on the whole GPU.
+int choose_zseg(int NZ, int columns, int resident) {
+    int best = MZS;
+    double best_cost = 1e300;
+    for (int nseg = 1; nseg <= 64; ++nseg) {
+        const int zs = (NZ + nseg - 1) / nseg;
+        const int segs = (NZ + zs - 1) / zs;
+        if (zs < 4 && nseg > 1) break;
+        const long long blocks = (long long)columns * segs;
+        const long long waves = (blocks + resident - 1) / resident;
+        const double cost = (double)waves * (zs + 1) * (1.0 + 1e-3 * nseg);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = zs;
+        }
+    }
+    return best;
+}
+
 void march3d_tiling(const Layout &L, Tiling &t) {
     t.bx = MX;
     t.by = MTY;
-    t.zs = MZS;
     t.ox = MX - 1;
     t.oy = MTY - 1;
     t.kind = 1;
     t.gx = (L.NX + t.ox - 1) / t.ox;
     t.gy = (L.NY + t.oy - 1) / t.oy;
+    t.zs = choose_zseg(L.NZ, t.gx * t.gy, 152 * 3);
     t.gz = (L.NZ + t.zs - 1) / t.zs;
 }
 
@@ -345,9 +365,10 @@ cudaError_t launch_march3d(const SweepArgs &a, const Tiling &t, cudaStream_t s) 
 namespace petto {
 namespace {
 
-constexpr int TBW = 40;        // box width (floats): covers the 33 tile columns at any offset 0..3
+constexpr int TBW = 36;        // box width (floats): covers the 33 tile columns at any offset 0..3
 constexpr int TNS = 4;         // ring slots
-constexpr int TD = 3;          // planes in flight ahead of the consumer
+constexpr int TD = 2;          // planes in flight ahead of the consumer (the slot of the plane
+                               // being updated must survive the refill issued in its iteration)
 constexpr int TWAIT = 1 << 22; // try_wait attempts before a wait is declared timed out
 
 template <int TY> struct TmaGeom {
@@ -355,7 +376,8 @@ template <int TY> struct TmaGeom {
     static constexpr int UBYTES = 3 * WY * TBW * 4, EBYTES = WY * TBW * 4;
     static constexpr int USLOT = (UBYTES + 127) / 128 * 128, ESLOT = (EBYTES + 127) / 128 * 128;
     static constexpr int MSG = 2 * 2 * NT * 16;
-    static constexpr int SMEM = TNS * (USLOT + ESLOT) + MSG + TNS * 8 + 128;  // + alignment slack
+    // per ring slot: u box, w box (same geometry), E box
+    static constexpr int SMEM = TNS * (2 * USLOT + ESLOT) + MSG + TNS * 8 + 128;  // + alignment slack
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -418,7 +440,8 @@ struct MarchConst {
 // read from ring slot `slot` into Uhi/Ehi.  Returns false when a wait timed out.
 template <int TY>
 __device__ __forceinline__ bool march_plane(const SweepArgs &A, const MarchConst &K, int zp, int z0, int r1,
-                                            const float *su, const float *se, float4 *msg, uint64_t *bars,
+                                            const float *su, const float *sw, const float *se, float4 *msg,
+                                            uint64_t *bars,
                                             int tid, int xoff, int xoffe, bool outxy, int plane32, int cs32,
                                             float *wb, float *uob, const float *rb, unsigned boxbits, int l0, int l1,
                                             int64_t nbase, const float (&Ulo)[4][3], const float (&Elo)[4],
@@ -430,9 +453,11 @@ __device__ __forceinline__ bool march_plane(const SweepArgs &A, const MarchConst
     const int off = zp * plane32;  // offset of (X, Y, zp) from the thread's column base
     float wv0 = 0.f, wv1 = 0.f, wv2 = 0.f;
     if (outp && A.mode == 0) {
-        wv0 = wb[off];
-        wv1 = wb[cs32 + off];
-        wv2 = wb[2 * cs32 + off];
+        // w of plane zp arrived with stage r1 - 1 (waited for in the previous plane)
+        const float *w0 = sw + ((r1 - 1) & (TNS - 1)) * (G::USLOT / 4) + ty * TBW + xoff + tx;
+        wv0 = w0[0];
+        wv1 = w0[G::WY * TBW];
+        wv2 = w0[2 * G::WY * TBW];
     }
     if (!mbar_wait(smem_u32(&bars[slot]), (r1 / TNS) & 1)) bad = true;
     {
@@ -582,23 +607,25 @@ __device__ __forceinline__ bool march_plane(const SweepArgs &A, const MarchConst
 template <int TY>
 __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __grid_constant__ SweepArgs A,
                                                                       const __grid_constant__ CUtensorMap tmu,
+                                                                      const __grid_constant__ CUtensorMap tmw,
                                                                       const __grid_constant__ CUtensorMap tme) {
     using G = TmaGeom<TY>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations at 128-byte aligned shared addresses
     unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-    float *su = reinterpret_cast<float *>(smem);                                  // TNS u slots
-    float *se = reinterpret_cast<float *>(smem + TNS * G::USLOT);                 // TNS E slots
-    float4 *msg = reinterpret_cast<float4 *>(smem + TNS * (G::USLOT + G::ESLOT)); // [2][2][NT]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + TNS * (G::USLOT + G::ESLOT) + G::MSG);
+    float *su = reinterpret_cast<float *>(smem);                                      // TNS u slots
+    float *sw = reinterpret_cast<float *>(smem + TNS * G::USLOT);                     // TNS w slots
+    float *se = reinterpret_cast<float *>(smem + 2 * TNS * G::USLOT);                 // TNS E slots
+    float4 *msg = reinterpret_cast<float4 *>(smem + TNS * (2 * G::USLOT + G::ESLOT)); // [2][2][NT]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + TNS * (2 * G::USLOT + G::ESLOT) + G::MSG);
     __shared__ double shred[32];
 
     const Layout &L = A.L;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-    const int x0 = blockIdx.x * 31, y0 = blockIdx.y * (TY - 1), z0 = blockIdx.z * MZS;
+    const int x0 = blockIdx.x * 31, y0 = blockIdx.y * (TY - 1), z0 = blockIdx.z * A.zseg;
     const int X = x0 - 1 + tx, Y = y0 - 1 + ty;
     const bool outxy = tx >= 1 && ty >= 1 && X < L.NX && Y < L.NY;
-    const int zend = min(z0 + MZS, L.NZ);
+    const int zend = min(z0 + A.zseg, L.NZ);
     const int xs = (x0 - 1 + OX) & ~3, xoff = (x0 - 1 + OX) - xs;    // u box origin / column offset
     const int xse = (x0 - 2 + OX) & ~3, xoffe = (x0 - 2 + OX) - xse; // E box origin / column offset
 
@@ -631,8 +658,9 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __gr
         const int p = z0 - 1 + r;
         const int slot = r & (TNS - 1);
         const uint32_t bar = smem_u32(&bars[slot]);
-        mbar_expect_tx(bar, (unsigned)(G::UBYTES + G::EBYTES));
+        mbar_expect_tx(bar, (unsigned)(2 * G::UBYTES + G::EBYTES));
         tma_load_4d(smem_u32(su + slot * (G::USLOT / 4)), &tmu, xs, y0, p + 1, 0, bar);
+        tma_load_4d(smem_u32(sw + slot * (G::USLOT / 4)), &tmw, xs, y0, p + 1, 0, bar);
         tma_load_3d(smem_u32(se + slot * (G::ESLOT / 4)), &tme, xse, y0 - 1, p, bar);
     };
     const int nstage = zend - (z0 - 1) + 1;  // stages z0-1 .. zend
@@ -670,15 +698,15 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __gr
         int r1 = zp + 1 - (z0 - 1);
         if (tid == 0 && issued < nstage) issue(issued);
         issued = min(issued + 1, nstage);
-        if (!march_plane<TY>(A, K, zp, z0, r1, su, se, msg, bars, tid, xoff, xoffe, outxy, plane32, cs32, wb, uob, rb,
-                             boxbits, l0, l1, nbase, UA, EA, UB, EB, C, bad))
+        if (!march_plane<TY>(A, K, zp, z0, r1, su, sw, se, msg, bars, tid, xoff, xoffe, outxy, plane32, cs32, wb, uob,
+                             rb, boxbits, l0, l1, nbase, UA, EA, UB, EB, C, bad))
             break;
         if (zp + 1 >= zend) break;
         ++r1;
         if (tid == 0 && issued < nstage) issue(issued);
         issued = min(issued + 1, nstage);
-        if (!march_plane<TY>(A, K, zp + 1, z0, r1, su, se, msg, bars, tid, xoff, xoffe, outxy, plane32, cs32, wb, uob,
-                             rb, boxbits, l0, l1, nbase, UB, EB, UA, EA, C, bad))
+        if (!march_plane<TY>(A, K, zp + 1, z0, r1, su, sw, se, msg, bars, tid, xoff, xoffe, outxy, plane32, cs32, wb,
+                             uob, rb, boxbits, l0, l1, nbase, UB, EB, UA, EA, C, bad))
             break;
     }
 
@@ -716,12 +744,12 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __gr
 void march3d_tma_tiling(const Layout &L, int ty, Tiling &t) {
     t.bx = 32;
     t.by = ty;
-    t.zs = MZS;
     t.ox = 31;
     t.oy = ty - 1;
     t.kind = ty == 16 ? 3 : 2;
     t.gx = (L.NX + t.ox - 1) / t.ox;
     t.gy = (L.NY + t.oy - 1) / t.oy;
+    t.zs = choose_zseg(L.NZ, t.gx * t.gy, ty == 16 ? 152 : 152 * 3);
     t.gz = (L.NZ + t.zs - 1) / t.zs;
 }
 
@@ -735,14 +763,14 @@ cudaError_t launch_march3d_tma(const SweepArgs &a, const Tiling &t, const TmaMap
             cudaFuncSetAttribute(sweep3d_march_tma<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmaGeom<16>::SMEM);
             attr = true;
         }
-        sweep3d_march_tma<16><<<grid, dim3(32, 16), TmaGeom<16>::SMEM, s>>>(a, *mu, m.e);
+        sweep3d_march_tma<16><<<grid, dim3(32, 16), TmaGeom<16>::SMEM, s>>>(a, *mu, m.w, m.e);
     } else {
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(sweep3d_march_tma<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmaGeom<8>::SMEM);
             attr = true;
         }
-        sweep3d_march_tma<8><<<grid, dim3(32, 8), TmaGeom<8>::SMEM, s>>>(a, *mu, m.e);
+        sweep3d_march_tma<8><<<grid, dim3(32, 8), TmaGeom<8>::SMEM, s>>>(a, *mu, m.w, m.e);
     }
     return cudaGetLastError();
 }
@@ -754,7 +782,7 @@ cudaError_t launch_march3d_tma(const SweepArgs &a, const Tiling &t, const TmaMap
 
 namespace petto {
 
-bool make_tma_maps(const Layout &L, int ty, void *u0, void *u1, const void *E, TmaMaps &m) {
+bool make_tma_maps(const Layout &L, int ty, void *u0, void *u1, void *w, const void *E, TmaMaps &m) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void *fn = nullptr;
@@ -778,6 +806,10 @@ bool make_tma_maps(const Layout &L, int ty, void *u0, void *u1, const void *E, T
             return false;
         m.ubuf[q] = ub[q];
     }
+    if (encode(&m.w, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, w, udim, ustr, ubox, one4, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return false;
     const cuuint64_t edim[3] = {(cuuint64_t)L.CX, (cuuint64_t)L.CY, (cuuint64_t)L.CZ};
     const cuuint64_t estr[2] = {(cuuint64_t)L.CX * 4, (cuuint64_t)(L.CX * L.CY) * 4};
     const cuuint32_t ebox[3] = {TBW, (cuuint32_t)(ty + 1), 1};
@@ -787,6 +819,411 @@ bool make_tma_maps(const Layout &L, int ty, void *u0, void *u1, const void *E, T
         return false;
     m.valid = true;
     return true;
+}
+
+}  // namespace petto
+
+// ============================================================================
+// TMA-staged marching kernel with two owner rows per thread (register blocking in y).
+// Thread (tx, ty) owns the node columns (X, YA = y0 - 1 + 2 ty) and (X, YB = YA + 1): the
+// y-share of row A for row B stays in registers, the per-plane barrier, ring wait and
+// addressing serve two nodes, and a 32 x 8 block covers 16 owner rows (15 output rows).
+// ============================================================================
+namespace petto {
+namespace {
+
+constexpr int R2TY = 8;            // threads in y (two owner rows each)
+constexpr int R2ROWS = 2 * R2TY;   // owner rows per block
+constexpr int R2WY = R2ROWS + 1;   // tile rows in the ring
+constexpr int R2NT = 32 * R2TY;
+constexpr int R2UBYTES = 3 * R2WY * TBW * 4, R2EBYTES = R2WY * TBW * 4;
+constexpr int R2USLOT = (R2UBYTES + 127) / 128 * 128, R2ESLOT = (R2EBYTES + 127) / 128 * 128;
+constexpr int R2MSG = 2 * R2NT * (3 * 16 + 16);  // per buffer: P0, P1, P2 (float4) and P3 (float, padded)
+constexpr int R2SMEM = TNS * (2 * R2USLOT + R2ESLOT) + R2MSG + TNS * 8 + 128;
+
+// Owned edge and face forces of one node from its four nodes at plane zp (n, n+x, n+y,
+// n+x+y), three at zp+1 (n, n+x, n+y) and the moduli of its four cells below / above.
+struct Owned {
+    float Fx0, Fx1, Fx2, Fy0, Fy1, Fy2, Fz0, Fz1, Fz2;
+    float Gxy0, Gxy1, Hxy0, Hxy1, Gxz0, Gxz1, Hxz0, Hxz1, Gyz0, Gyz1, Hyz0, Hyz1;
+};
+
+__device__ __forceinline__ Owned owned_forces(const MarchConst &K, const float (&l0)[3], const float (&l1)[3],
+                                              const float (&l2)[3], const float (&l3)[3], const float (&h0)[3],
+                                              const float (&h1)[3], const float (&h2)[3], const float (&Elo)[4],
+                                              const float (&Ehi)[4]) {
+    Owned o;
+    const float e00 = Ehi[0] + Elo[0];
+    const float Ex = e00 + Ehi[2] + Elo[2];
+    const float Ey = e00 + Ehi[1] + Elo[1];
+    const float Ez = (Ehi[0] + Ehi[1]) + (Ehi[2] + Ehi[3]);
+    float ax[3], ay[3], az[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        ax[c] = l1[c] - l0[c];
+        ay[c] = l2[c] - l0[c];
+        az[c] = h0[c] - l0[c];
+    }
+    const float exq = Ex * K.cperp, eyq = Ey * K.cperp, ezq = Ez * K.cperp;
+    o.Fx0 = Ex * K.cpar * ax[0];
+    o.Fx1 = exq * ax[1];
+    o.Fx2 = exq * ax[2];
+    o.Fy0 = eyq * ay[0];
+    o.Fy1 = Ey * K.cpar * ay[1];
+    o.Fy2 = eyq * ay[2];
+    o.Fz0 = ezq * az[0];
+    o.Fz1 = ezq * az[1];
+    o.Fz2 = Ez * K.cpar * az[2];
+    {
+        const float el = e00 * K.cl, em = e00 * K.cm;
+        const float SAx = ax[0] + (l3[0] - l2[0]), SAy = ax[1] + (l3[1] - l2[1]);
+        const float SBx = ay[0] + (l3[0] - l1[0]), SBy = ay[1] + (l3[1] - l1[1]);
+        const float p = em * SAy, q = el * SAx;
+        o.Gxy0 = fmaf(el, SBy, p);
+        o.Hxy0 = fmaf(el, SBy, -p);
+        o.Gxy1 = fmaf(em, SBx, q);
+        o.Hxy1 = fmaf(em, SBx, -q);
+    }
+    {
+        const float Et = Ehi[0] + Ehi[2];
+        const float el = Et * K.cl, em = Et * K.cm;
+        const float SAx = ax[0] + (h1[0] - h0[0]), SAz = ax[2] + (h1[2] - h0[2]);
+        const float SBx = az[0] + (h1[0] - l1[0]), SBz = az[2] + (h1[2] - l1[2]);
+        const float p = em * SAz, q = el * SAx;
+        o.Gxz0 = fmaf(el, SBz, p);
+        o.Hxz0 = fmaf(el, SBz, -p);
+        o.Gxz1 = fmaf(em, SBx, q);
+        o.Hxz1 = fmaf(em, SBx, -q);
+    }
+    {
+        const float Et = Ehi[0] + Ehi[1];
+        const float el = Et * K.cl, em = Et * K.cm;
+        const float SAy = ay[1] + (h2[1] - h0[1]), SAz = ay[2] + (h2[2] - h0[2]);
+        const float SBy = az[1] + (h2[1] - l2[1]), SBz = az[2] + (h2[2] - l2[2]);
+        const float p = em * SAz, q = el * SAy;
+        o.Gyz0 = fmaf(el, SBz, p);
+        o.Hyz0 = fmaf(el, SBz, -p);
+        o.Gyz1 = fmaf(em, SBy, q);
+        o.Hyz1 = fmaf(em, SBy, -q);
+    }
+    return o;
+}
+
+struct RowCarry {
+    float Sz0, Sz1, Sz2, Gxz0, Gxz1, Gyz0, Gyz1;
+};
+
+// Update of one output node from its assembled K u.
+__device__ __forceinline__ void march_update(const SweepArgs &A, const MarchConst &K, int zp, int off, int cs32,
+                                             float *wb, float *uob, const float *rb, unsigned boxbits, int l0,
+                                             int l1, int64_t nbase, float Ku0, float Ku1, float Ku2, float wv0,
+                                             float wv1, float wv2, const float (&u)[3], float S8, float &res,
+                                             float &dot) {
+    unsigned fm = 0;
+    if (boxbits)
+        for (int q = 0; q < A.boxes.n; ++q)
+            if (((boxbits >> q) & 1u) && zp >= A.boxes.b[q].lo[2] && zp <= A.boxes.b[q].hi[2]) fm |= A.boxes.b[q].mask;
+    float F0 = 0.f, F1 = 0.f, F2 = 0.f;
+    if (rb) {
+        F0 = rb[off];
+        F1 = rb[cs32 + off];
+        F2 = rb[2 * cs32 + off];
+    } else if (l0 < l1) {
+        const int64_t nidx = nbase + off;
+        for (int l = l0; l < l1; ++l) {
+            const LoadEntry &le = A.loads[l];
+            if (le.node == nidx) {
+                if (le.comp == 0) F0 += le.valf;
+                else if (le.comp == 1) F1 += le.valf;
+                else F2 += le.valf;
+            }
+        }
+    }
+    float step = A.mode == 0 ? K.fb : K.fs1;
+    if (A.local_dt) step *= fast_rcp(K.cdg * S8);
+    const float R0 = (fm & 1u) ? 0.f : F0 - Ku0;
+    const float R1 = (fm & 2u) ? 0.f : F1 - Ku1;
+    const float R2 = (fm & 4u) ? 0.f : F2 - Ku2;
+    if (A.want_res) res += R0 * R0 + R1 * R1 + R2 * R2;
+    if (A.mode == 0) {
+        if (A.test_dot) dot += R0 * wv0 + R1 * wv1 + R2 * wv2;
+        const float w0 = (fm & 1u) ? 0.f : fmaf(K.fa, wv0, step * R0);
+        const float w1 = (fm & 2u) ? 0.f : fmaf(K.fa, wv1, step * R1);
+        const float w2 = (fm & 4u) ? 0.f : fmaf(K.fa, wv2, step * R2);
+        wb[off] = w0;
+        wb[cs32 + off] = w1;
+        wb[2 * cs32 + off] = w2;
+        uob[off] = (fm & 1u) ? 0.f : u[0] + w0;
+        uob[cs32 + off] = (fm & 2u) ? 0.f : u[1] + w1;
+        uob[2 * cs32 + off] = (fm & 4u) ? 0.f : u[2] + w2;
+    } else if (A.mode == 1) {
+        uob[off] = (fm & 1u) ? 0.f : fmaf(step, R0, u[0]);
+        uob[cs32 + off] = (fm & 2u) ? 0.f : fmaf(step, R1, u[1]);
+        uob[2 * cs32 + off] = (fm & 4u) ? 0.f : fmaf(step, R2, u[2]);
+    } else {
+        wb[off] = R0;
+        wb[cs32 + off] = R1;
+        wb[2 * cs32 + off] = R2;
+    }
+}
+
+// One owner plane for both rows.  U planes: [row 0..2][col 0..1][comp], E: [row 0..2][col 0..1]
+// with row r meaning tile row 2 ty + r (node rows YA, YB, YB+1; cell rows YA-1, YA, YB).
+__device__ __forceinline__ bool march2_plane(const SweepArgs &A, const MarchConst &K, int zp, int z0, int r1,
+                                             const float *su, const float *sw, const float *se, unsigned char *msgraw,
+                                             uint64_t *bars, int tx, int ty, int xoff, int xoffe, bool outA,
+                                             bool outB, int plane32, int cs32, float *wbA, float *uobA,
+                                             const float *rbA, float *wbB, float *uobB, const float *rbB,
+                                             unsigned bbA, unsigned bbB, int l0, int l1, int64_t nbA, int64_t nbB,
+                                             const float (&Ul)[3][2][3], const float (&El)[3][2],
+                                             float (&Uh)[3][2][3], float (&Eh)[3][2], RowCarry &CA, RowCarry &CB,
+                                             float &res, float &dot, bool &bad) {
+    const int tid = ty * 32 + tx;
+    const int slot = r1 & (TNS - 1);
+    const bool pA = outA && zp >= z0, pB = outB && zp >= z0;
+    const int off = zp * plane32;
+    float wA0 = 0.f, wA1 = 0.f, wA2 = 0.f, wB0 = 0.f, wB1 = 0.f, wB2 = 0.f;
+    if (A.mode == 0 && (pA || pB)) {
+        // w of plane zp arrived with stage r1 - 1 (waited for in the previous plane)
+        const float *w0 = sw + ((r1 - 1) & (TNS - 1)) * (R2USLOT / 4) + (2 * ty) * TBW + xoff + tx;
+        wA0 = w0[0];
+        wA1 = w0[R2WY * TBW];
+        wA2 = w0[2 * R2WY * TBW];
+        wB0 = w0[TBW];
+        wB1 = w0[R2WY * TBW + TBW];
+        wB2 = w0[2 * R2WY * TBW + TBW];
+    }
+    if (!mbar_wait(smem_u32(&bars[slot]), (r1 / TNS) & 1)) bad = true;
+    {
+        const float *r0 = su + slot * (R2USLOT / 4) + (2 * ty) * TBW + xoff + tx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                Uh[r][0][c] = r0[c * R2WY * TBW + r * TBW];
+                Uh[r][1][c] = r0[c * R2WY * TBW + r * TBW + 1];
+            }
+        const float *q0 = se + slot * (R2ESLOT / 4) + (2 * ty) * TBW + xoffe + tx;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            Eh[r][0] = q0[r * TBW];      // cell (X-1, row)
+            Eh[r][1] = q0[r * TBW + 1];  // cell (X, row)
+        }
+    }
+    // owner A: nodes rows 0/1, cells rows 0 (n-y) and 1 (n); owner B: rows 1/2, cells 1/2
+    const float ElA[4] = {El[1][1], El[1][0], El[0][1], El[0][0]};
+    const float EhA[4] = {Eh[1][1], Eh[1][0], Eh[0][1], Eh[0][0]};
+    const float ElB[4] = {El[2][1], El[2][0], El[1][1], El[1][0]};
+    const float EhB[4] = {Eh[2][1], Eh[2][0], Eh[1][1], Eh[1][0]};
+    const Owned oA = owned_forces(K, Ul[0][0], Ul[0][1], Ul[1][0], Ul[1][1], Uh[0][0], Uh[0][1], Uh[1][0], ElA, EhA);
+    const Owned oB = owned_forces(K, Ul[1][0], Ul[1][1], Ul[2][0], Ul[2][1], Uh[1][0], Uh[1][1], Uh[2][0], ElB, EhB);
+    // messages: P0 = (Mx(A), Gxy(A).x), P1 = (Mx(B), Gxy(B).x), P2 = (My(B), Gxy(A).y), P3 = Gxy(B).y
+    float4 *P0 = reinterpret_cast<float4 *>(msgraw + (zp & 1) * (R2MSG / 2));
+    float4 *P1 = P0 + R2NT;
+    float4 *P2 = P1 + R2NT;
+    float *P3 = reinterpret_cast<float *>(P2 + R2NT);
+    P0[tid] = make_float4(oA.Fx0 + oA.Hxy0 + oA.Hxz0 + CA.Gxz0, oA.Fx1 + oA.Hxy1, oA.Fx2 + oA.Hxz1 + CA.Gxz1, oA.Gxy0);
+    P1[tid] = make_float4(oB.Fx0 + oB.Hxy0 + oB.Hxz0 + CB.Gxz0, oB.Fx1 + oB.Hxy1, oB.Fx2 + oB.Hxz1 + CB.Gxz1, oB.Gxy0);
+    P2[tid] = make_float4(oB.Fy0 - oB.Hxy0, oB.Fy1 - oB.Hxy1 + oB.Hyz0 + CB.Gyz0, oB.Fy2 + oB.Hyz1 + CB.Gyz1, oA.Gxy1);
+    P3[tid] = oB.Gxy1;
+    // y-share of A for B, kept in registers
+    const float MyA0 = oA.Fy0 - oA.Hxy0, MyA1 = oA.Fy1 - oA.Hxy1 + oA.Hyz0 + CA.Gyz0,
+                MyA2 = oA.Fy2 + oA.Hyz1 + CA.Gyz1;
+    if (__syncthreads_or(bad)) {
+        bad = true;
+        return false;
+    }
+    if (pA || pB) {
+        const float4 xa = P0[tid - 1];  // (x-1, A)
+        const float4 xb = P1[tid - 1];  // (x-1, B)
+        const float gB0 = xa.w, gB1 = P2[tid - 1].w;  // Gxy of (x-1, A) -> B
+        if (pA) {
+            const float4 ya = P2[tid - 32];       // My of (x, ty-1).B
+            const float gA0 = P1[tid - 33].w;     // Gxy(x-1, ty-1).B
+            const float gA1 = P3[tid - 33];
+            const float Ku0 = -(oA.Fx0 + oA.Fy0 + oA.Fz0) - (oA.Gxy0 + oA.Gxz0) + xa.x + ya.x + CA.Sz0 + gA0;
+            const float Ku1 = -(oA.Fx1 + oA.Fy1 + oA.Fz1) - (oA.Gxy1 + oA.Gyz0) + xa.y + ya.y + CA.Sz1 + gA1;
+            const float Ku2 = -(oA.Fx2 + oA.Fy2 + oA.Fz2) - (oA.Gxz1 + oA.Gyz1) + xa.z + ya.z + CA.Sz2;
+            const float S8 = (El[0][0] + El[0][1]) + (El[1][0] + El[1][1]) + (Eh[0][0] + Eh[0][1]) + (Eh[1][0] + Eh[1][1]);
+            march_update(A, K, zp, off, cs32, wbA, uobA, rbA, bbA, l0, l1, nbA, Ku0, Ku1, Ku2, wA0, wA1, wA2, Ul[0][0],
+                         S8, res, dot);
+        }
+        if (pB) {
+            const float Ku0 = -(oB.Fx0 + oB.Fy0 + oB.Fz0) - (oB.Gxy0 + oB.Gxz0) + xb.x + MyA0 + CB.Sz0 + gB0;
+            const float Ku1 = -(oB.Fx1 + oB.Fy1 + oB.Fz1) - (oB.Gxy1 + oB.Gyz0) + xb.y + MyA1 + CB.Sz1 + gB1;
+            const float Ku2 = -(oB.Fx2 + oB.Fy2 + oB.Fz2) - (oB.Gxz1 + oB.Gyz1) + xb.z + MyA2 + CB.Sz2;
+            const float S8 = (El[1][0] + El[1][1]) + (El[2][0] + El[2][1]) + (Eh[1][0] + Eh[1][1]) + (Eh[2][0] + Eh[2][1]);
+            march_update(A, K, zp, off, cs32, wbB, uobB, rbB, bbB, l0, l1, nbB, Ku0, Ku1, Ku2, wB0, wB1, wB2, Ul[1][0],
+                         S8, res, dot);
+        }
+    }
+    CA = {oA.Fz0 - oA.Hxz0, oA.Fz1 - oA.Hyz0, oA.Fz2 - oA.Hxz1 - oA.Hyz1, oA.Gxz0, oA.Gxz1, oA.Gyz0, oA.Gyz1};
+    CB = {oB.Fz0 - oB.Hxz0, oB.Fz1 - oB.Hyz0, oB.Fz2 - oB.Hxz1 - oB.Hyz1, oB.Gxz0, oB.Gxz1, oB.Gyz0, oB.Gyz1};
+    return true;
+}
+
+__global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_constant__ SweepArgs A,
+                                                              const __grid_constant__ CUtensorMap tmu,
+                                                              const __grid_constant__ CUtensorMap tmw,
+                                                              const __grid_constant__ CUtensorMap tme) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    float *su = reinterpret_cast<float *>(smem);
+    float *sw = reinterpret_cast<float *>(smem + TNS * R2USLOT);
+    float *se = reinterpret_cast<float *>(smem + 2 * TNS * R2USLOT);
+    unsigned char *msg = smem + TNS * (2 * R2USLOT + R2ESLOT);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + TNS * (2 * R2USLOT + R2ESLOT) + R2MSG);
+    __shared__ double shred[32];
+
+    const Layout &L = A.L;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int x0 = blockIdx.x * 31, y0 = blockIdx.y * (R2ROWS - 1), z0 = blockIdx.z * A.zseg;
+    const int X = x0 - 1 + tx, YA = y0 - 1 + 2 * ty, YB = YA + 1;
+    const bool outA = tx >= 1 && ty >= 1 && X < L.NX && YA < L.NY;
+    const bool outB = tx >= 1 && X < L.NX && YB < L.NY;
+    const int zend = min(z0 + A.zseg, L.NZ);
+    const int xs = (x0 - 1 + OX) & ~3, xoff = (x0 - 1 + OX) - xs;
+    const int xse = (x0 - 2 + OX) & ~3, xoffe = (x0 - 2 + OX) - xse;
+
+    MarchConst K;
+    K.cpar = A.kf.ce_par;
+    K.cperp = A.kf.ce_perp;
+    K.cl = A.kf.cf_lam;
+    K.cm = A.kf.cf_mu;
+    K.cdg = A.kf.cdiag;
+    K.fa = A.kf.a;
+    K.fb = A.kf.b;
+    K.fs1 = A.kf.s1;
+    if (A.adaptive) K.fa = fminf(K.fa, apt_schedule(A));
+    unsigned bbA = 0, bbB = 0;
+    for (int q = 0; q < A.boxes.n; ++q) {
+        const Box &b = A.boxes.b[q];
+        if (X >= b.lo[0] && X <= b.hi[0]) {
+            if (YA >= b.lo[1] && YA <= b.hi[1]) bbA |= 1u << q;
+            if (YB >= b.lo[1] && YB <= b.hi[1]) bbB |= 1u << q;
+        }
+    }
+    const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int l0 = A.tile_ptr[tile], l1 = A.tile_ptr[tile + 1];
+    const int64_t nbA = outA ? L.node(X, YA, 0) : 0, nbB = outB ? L.node(X, YB, 0) : 0;
+    const int plane32 = (int)(L.SX * L.SY), cs32 = (int)L.cstride;
+    float *w = static_cast<float *>(A.w);
+    float *uo = static_cast<float *>(A.u_out);
+    const float *rh = static_cast<const float *>(A.rhs);
+    float *wbA = w + nbA, *wbB = w + nbB;
+    float *uobA = uo ? uo + nbA : nullptr, *uobB = uo ? uo + nbB : nullptr;
+    const float *rbA = rh ? rh + nbA : nullptr, *rbB = rh ? rh + nbB : nullptr;
+
+    auto issue = [&](int r) {
+        const int p = z0 - 1 + r;
+        const int slot = r & (TNS - 1);
+        const uint32_t bar = smem_u32(&bars[slot]);
+        mbar_expect_tx(bar, (unsigned)(2 * R2UBYTES + R2EBYTES));
+        tma_load_4d(smem_u32(su + slot * (R2USLOT / 4)), &tmu, xs, y0, p + 1, 0, bar);
+        tma_load_4d(smem_u32(sw + slot * (R2USLOT / 4)), &tmw, xs, y0, p + 1, 0, bar);
+        tma_load_3d(smem_u32(se + slot * (R2ESLOT / 4)), &tme, xse, y0 - 1, p, bar);
+    };
+    const int nstage = zend - (z0 - 1) + 1;
+    if (tid == 0) {
+        for (int s = 0; s < TNS; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int r = 0; r <= TD && r < nstage; ++r) issue(r);
+    int issued = min(TD + 1, nstage);
+
+    bool bad = !mbar_wait(smem_u32(&bars[0]), 0);
+    float UA[3][2][3], EA[3][2], UB[3][2][3], EB[3][2];
+    {
+        const float *r0 = su + (2 * ty) * TBW + xoff + tx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                UA[r][0][c] = r0[c * R2WY * TBW + r * TBW];
+                UA[r][1][c] = r0[c * R2WY * TBW + r * TBW + 1];
+            }
+        const float *q0 = se + (2 * ty) * TBW + xoffe + tx;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            EA[r][0] = q0[r * TBW];
+            EA[r][1] = q0[r * TBW + 1];
+        }
+    }
+    bad = __syncthreads_or(bad);
+    RowCarry CA = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, CB = CA;
+    float res = 0.f, dot = 0.f;
+
+    for (int zp = z0 - 1; zp < zend && !bad; zp += 2) {
+        int r1 = zp + 1 - (z0 - 1);
+        if (tid == 0 && issued < nstage) issue(issued);
+        issued = min(issued + 1, nstage);
+        if (!march2_plane(A, K, zp, z0, r1, su, sw, se, msg, bars, tx, ty, xoff, xoffe, outA, outB, plane32, cs32, wbA,
+                          uobA, rbA, wbB, uobB, rbB, bbA, bbB, l0, l1, nbA, nbB, UA, EA, UB, EB, CA, CB, res, dot, bad))
+            break;
+        if (zp + 1 >= zend) break;
+        ++r1;
+        if (tid == 0 && issued < nstage) issue(issued);
+        issued = min(issued + 1, nstage);
+        if (!march2_plane(A, K, zp + 1, z0, r1, su, sw, se, msg, bars, tx, ty, xoff, xoffe, outA, outB, plane32, cs32,
+                          wbA, uobA, rbA, wbB, uobB, rbB, bbA, bbB, l0, l1, nbA, nbB, UB, EB, UA, EA, CA, CB, res, dot,
+                          bad))
+            break;
+    }
+
+    if (bad) {
+        if (tid == 0) {
+            A.ctrl[CT_ERR] = 1.0;
+            for (int r = 0; r < issued; ++r) mbar_wait(smem_u32(&bars[r & (TNS - 1)]), (r / TNS) & 1);
+        }
+        __syncthreads();
+        return;
+    }
+    if (A.want_res || A.test_dot) {
+        const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+        const double r = A.want_res ? block_sum((double)res, shred) : 0.0;
+        const double d = A.test_dot ? block_sum((double)dot, shred) : 0.0;
+        if (tid == 0) A.red.partials[(int64_t)nb + tile] = d;
+        if (publish_partial(r, A.red, tile, nb)) {
+            const double t = A.want_res ? sum_partials(A.red, 0, nb, shred) : 0.0;
+            const double td = A.test_dot ? sum_partials(A.red, nb, nb, shred) : 0.0;
+            if (tid == 0) {
+                if (A.want_res) *A.res2 = t;
+                if (A.test_dot) {
+                    A.ctrl[CT_DOT] = td;
+                    if (td < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = A.sweep_idx + 1;
+                }
+                *A.red.counter = 0u;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+void march3d_tma2_tiling(const Layout &L, Tiling &t) {
+    t.bx = 32;
+    t.by = R2TY;
+    t.ox = 31;
+    t.oy = R2ROWS - 1;
+    t.kind = 4;
+    t.gx = (L.NX + t.ox - 1) / t.ox;
+    t.gy = (L.NY + t.oy - 1) / t.oy;
+    t.zs = choose_zseg(L.NZ, t.gx * t.gy, 152 * 2);
+    t.gz = (L.NZ + t.zs - 1) / t.zs;
+}
+
+cudaError_t launch_march3d_tma2(const SweepArgs &a, const Tiling &t, const TmaMaps &m, cudaStream_t s) {
+    const CUtensorMap *mu = a.u_in == m.ubuf[0] ? &m.u[0] : (a.u_in == m.ubuf[1] ? &m.u[1] : nullptr);
+    if (!mu) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(sweep3d_march_tma2, cudaFuncAttributeMaxDynamicSharedMemorySize, R2SMEM);
+        attr = true;
+    }
+    sweep3d_march_tma2<<<dim3(t.gx, t.gy, t.gz), dim3(32, R2TY), R2SMEM, s>>>(a, *mu, m.w, m.e);
+    return cudaGetLastError();
 }
 
 }  // namespace petto

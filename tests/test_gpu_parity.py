@@ -330,10 +330,12 @@ def test_autograd_function_matches_finite_difference(P):
     prob.close()
 
 
-def test_march3d_multi_tile_and_segment(P):
-    """The z-marching FP32 kernel on a grid spanning several x/y tiles and z segments with
-    ragged tails, point loads on tile edges and supports on several faces."""
-    nx, ny, nz = 70, 22, 37
+@pytest.mark.parametrize("variant", ["tma8", "tma16", "tma2", "v1"])
+def test_march3d_multi_tile_and_segment(P, variant, monkeypatch):
+    """Every z-marching FP32 kernel variant on a grid spanning several x/y tiles and z
+    segments with ragged tails, point loads on tile edges and supports on several faces."""
+    monkeypatch.setenv("PETTO_MARCH", variant)
+    nx, ny, nz = 70, 40, 37
     base = W.cantilever3d(nx, ny, nz)
     loads = base.loads + [((31, 7, 16), 0, 0.7), ((30, 6, 15), 1, -0.4), ((62, 14, 32), 2, 0.25),
                           ((0, 0, 0), 2, 1.0), ((nx, ny, nz), 1, 0.3)]
