@@ -257,6 +257,14 @@ int64_t petto_launch_count(const petto_ctx *ctx);
 petto_status petto_profile(petto_ctx *ctx, int enable);
 petto_status petto_profile_read(petto_ctx *ctx, double *sweep_ms, int64_t *sweeps);
 
+/* Sweep-kernel autotuner: times every kernel variant and tile shape that applies to this
+ * problem (for 3D elasticity in FP32: TMA-staged marching kernels with one or two owner
+ * rows per thread, 32x16 tiles, the register-staged kernel, several z-segment lengths;
+ * otherwise the node-gather kernel's block shapes) for n APT sweeps each from the current
+ * state, restores the state, and keeps the fastest.  report (may be NULL) receives a JSON
+ * object of milliseconds per sweep for each candidate.  Uses temporary device memory. */
+petto_status petto_autotune(petto_ctx *ctx, int n, char *report, int report_len);
+
 /* Allocation-free residual norm.  The paper has no counterpart: this entry point exists
  * for callers that must not allocate GPU memory themselves -- code running under a memory
  * manager that owns every device byte (a framework's caching allocator, a fixed arena of

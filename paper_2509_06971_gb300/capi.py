@@ -96,6 +96,7 @@ _SIGS = {
     "petto_profile": (_int, [_vp, _int]),
     "petto_profile_read": (_int, [_vp, _P(_dbl), _P(_i64)]),
     "petto_residual_norm_static": (_int, [_P(petto_grid), _dbl, _vp, _vp, _vp, _vp, _P(_dbl), _vp]),
+    "petto_autotune": (_int, [_vp, _int, ctypes.c_char_p, _int]),
 }
 EXPORTED = tuple(_SIGS)
 

@@ -45,6 +45,9 @@ struct petto_ctx {
     int *tile_ptr = nullptr, *gtile_ptr = nullptr;
     LoadEntry *loads = nullptr, *gloads = nullptr;
     int n_loads = 0;
+    int ntiles_alloc = 0;
+    int64_t partial_cap = 0;
+    std::vector<std::pair<std::pair<int64_t, int>, double>> load_list;  // merged (node, component) -> value
     double *ctrl = nullptr;
     void *u64 = nullptr, *r64 = nullptr, *rhs32 = nullptr;
     int cur = 0;
@@ -405,6 +408,55 @@ petto_status drain_profile(petto_ctx *ctx) {
     return PETTO_OK;
 }
 
+
+// Switch the sweep kernel's tiling: rebuild the per-tile load table (and the tensor maps of
+// the TMA-staged kernels), growing the tile and partial-sum buffers when needed.
+petto_status set_tiling(petto_ctx *ctx, const Tiling &t) {
+    const int NX = ctx->L.NX, NY = ctx->L.NY;
+    const int nt = t.ntiles();
+    std::vector<int> tptr(nt + 1, 0);
+    std::vector<std::pair<int, LoadEntry>> tmp;
+    for (auto &kv : ctx->load_list) {
+        const int64_t n = kv.first.first;
+        const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / ((int64_t)NX * NY));
+        LoadEntry le{};
+        le.node = ctx->L.node(i, j, k);
+        le.comp = kv.first.second;
+        le.vald = kv.second;
+        le.valf = (float)kv.second;
+        tmp.emplace_back(t.tile_of(i, j, k), le);
+    }
+    std::stable_sort(tmp.begin(), tmp.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
+    std::vector<LoadEntry> ent;
+    for (auto &pr : tmp) {
+        tptr[pr.first + 1]++;
+        ent.push_back(pr.second);
+    }
+    for (int q = 0; q < nt; ++q) tptr[q + 1] += tptr[q];
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (nt > ctx->ntiles_alloc) {
+        CK(cudaFree(ctx->tile_ptr));
+        ctx->tile_ptr = nullptr;
+        CK(cudaMalloc(&ctx->tile_ptr, sizeof(int) * (nt + 1)));
+        ctx->ntiles_alloc = nt;
+    }
+    const int64_t cap = reduction_capacity(ctx->L, std::max(nt, ctx->gtiling.ntiles()), ctx->P);
+    if (cap > ctx->partial_cap) {
+        CK(cudaFree(ctx->partials));
+        ctx->partials = nullptr;
+        CK(cudaMalloc(&ctx->partials, sizeof(double) * cap));
+        ctx->partial_cap = cap;
+    }
+    CK(cudaMemcpy(ctx->tile_ptr, tptr.data(), sizeof(int) * (nt + 1), cudaMemcpyHostToDevice));
+    if (!ent.empty()) CK(cudaMemcpy(ctx->loads, ent.data(), sizeof(LoadEntry) * ent.size(), cudaMemcpyHostToDevice));
+    if (t.kind >= 2 && t.kind <= 4) {
+        const int ty = t.kind == 2 ? 8 : 16;
+        if (!make_tma_maps(ctx->L, ty, ctx->ndofc(), ctx->u[0], ctx->u[1], ctx->w, ctx->E, ctx->tma))
+            return fail(ctx, PETTO_ECUDA, "tensor map creation failed");
+    }
+    ctx->tiling = t;
+    return PETTO_OK;
+}
 }  // namespace
 
 // ==================================================================== C ABI
@@ -563,6 +615,7 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
         }
     }
     ctx->gtiling = gather_tiling(ctx->L);
+    ctx->load_list.assign(merged.begin(), merged.end());
     auto table = [&](const Tiling &t, std::vector<int> &tptr, std::vector<LoadEntry> &ent) {
         const int nt = t.ntiles();
         tptr.assign(nt + 1, 0);
@@ -639,7 +692,9 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
     alloc(&ctx->mu, (size_t)nc * ctx->tsize());
     alloc((void **)&ctx->scal, sizeof(double) * SC_N);
     alloc((void **)&ctx->counter, sizeof(unsigned) * 4);
-    alloc((void **)&ctx->partials, sizeof(double) * reduction_capacity(ctx->L, std::max(ntiles, gntiles), ctx->P));
+    ctx->partial_cap = reduction_capacity(ctx->L, std::max(ntiles, gntiles), ctx->P);
+    alloc((void **)&ctx->partials, sizeof(double) * ctx->partial_cap);
+    ctx->ntiles_alloc = ntiles;
     alloc((void **)&ctx->tile_ptr, sizeof(int) * (ntiles + 1));
     alloc((void **)&ctx->loads, sizeof(LoadEntry) * std::max(1, ctx->n_loads));
     alloc((void **)&ctx->gtile_ptr, sizeof(int) * (gntiles + 1));
@@ -684,7 +739,7 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
     }
     if (ctx->tiling.kind == 2 || ctx->tiling.kind == 3 || ctx->tiling.kind == 4) {
         const int ty = ctx->tiling.kind == 3 || ctx->tiling.kind == 4 ? 16 : 8;
-        if (!make_tma_maps(ctx->L, ty, ctx->u[0], ctx->u[1], ctx->w, ctx->E, ctx->tma)) {
+        if (!make_tma_maps(ctx->L, ty, ctx->ndofc(), ctx->u[0], ctx->u[1], ctx->w, ctx->E, ctx->tma)) {
             if (ctx->tiling.kind == 2) {
                 march3d_tiling(ctx->L, ctx->tiling);  // same tile shape, register-staged kernel
             } else {
@@ -1174,6 +1229,98 @@ petto_status petto_load(petto_ctx *ctx, const char *path) {
     ctx->step = hdr[9];
     ctx->have_sens = false;
     return refresh_material(ctx);
+}
+
+// Time each sweep-kernel variant that applies to this problem for n sweeps from the
+// current state (restored afterwards) and keep the fastest.
+petto_status petto_autotune(petto_ctx *ctx, int n, char *report, int report_len) {
+    if (!ctx || n < 1) return fail(ctx, PETTO_EINVAL, "bad arguments");
+    std::vector<std::pair<std::string, Tiling>> cand;
+    const Layout &L = ctx->L;
+    if (L.dim == 3 && ctx->physics == 0 && ctx->precision == PETTO_F32) {
+        Tiling t{};
+        const bool tma_ok = 3 * (int64_t)ctx->nrhs * L.cstride < (int64_t(1) << 31);
+        if (tma_ok) {
+            for (int zs : {0, 8, 16, 32}) {
+                march3d_tma2_tiling(L, t);
+                if (zs) {
+                    t.zs = std::min(zs, L.NZ);
+                    t.gz = (L.NZ + t.zs - 1) / t.zs;
+                }
+                cand.emplace_back("tma2/zs" + std::to_string(t.zs), t);
+                march3d_tma_tiling(L, 8, t);
+                if (zs) {
+                    t.zs = std::min(zs, L.NZ);
+                    t.gz = (L.NZ + t.zs - 1) / t.zs;
+                }
+                cand.emplace_back("tma8/zs" + std::to_string(t.zs), t);
+            }
+            march3d_tma_tiling(L, 16, t);
+            cand.emplace_back("tma16/zs" + std::to_string(t.zs), t);
+        }
+        if (ctx->nrhs == 1) {
+            march3d_tiling(L, t);
+            cand.emplace_back("v1/zs" + std::to_string(t.zs), t);
+        }
+    } else {
+        for (auto bxby : {std::make_pair(32, 8), std::make_pair(64, 4), std::make_pair(128, 2), std::make_pair(16, 16),
+                          std::make_pair(32, 4)}) {
+            Tiling t = gather_tiling(L);
+            if (L.dim == 3 && bxby.first * bxby.second > 128) continue;
+            t.bx = t.ox = bxby.first;
+            t.by = t.oy = bxby.second;
+            t.gx = (L.NX + t.ox - 1) / t.ox;
+            t.gy = (L.NY + t.oy - 1) / t.oy;
+            t.gz = (L.NZ + t.zs - 1) / t.zs;
+            cand.emplace_back("gather/" + std::to_string(t.bx) + "x" + std::to_string(t.by), t);
+        }
+    }
+    // keep the state: u (current) and w
+    void *su = nullptr, *sw = nullptr;
+    CK(cudaMalloc(&su, ctx->node_bytes()));
+    CK(cudaMalloc(&sw, ctx->node_bytes()));
+    CK(cudaMemcpyAsync(su, ctx->u[ctx->cur], ctx->node_bytes(), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(sw, ctx->w, ctx->node_bytes(), cudaMemcpyDeviceToDevice, ctx->stream));
+    const int cur0 = ctx->cur;
+    const bool prof0 = ctx->profiling;
+    std::string rep = "{";
+    double best = INFINITY;
+    Tiling best_t = ctx->tiling;
+    petto_status st = PETTO_OK;
+    for (auto &c : cand) {
+        st = set_tiling(ctx, c.second);
+        if (st != PETTO_OK) break;
+        st = petto_profile(ctx, 1);
+        if (st != PETTO_OK) break;
+        double ms = 0;
+        int64_t cnt = 0;
+        for (int t = 0; t < n + 2 && st == PETTO_OK; ++t) {
+            if (t == 2) st = petto_profile_read(ctx, &ms, &cnt);  // drop two warm-up sweeps
+            if (st == PETTO_OK) st = one_sweep(ctx, 0, 0.99, 0.5, 0.5, 1, false);
+        }
+        if (st == PETTO_OK) st = petto_profile_read(ctx, &ms, &cnt);
+        if (st != PETTO_OK) break;
+        const double per = ms / std::max<int64_t>(cnt, 1);
+        rep += (rep.size() > 1 ? ", \"" : "\"") + c.first + "\": " + std::to_string(per);
+        if (per < best) {
+            best = per;
+            best_t = c.second;
+        }
+        ctx->cur = cur0;
+        CK(cudaMemcpyAsync(ctx->u[ctx->cur], su, ctx->node_bytes(), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->w, sw, ctx->node_bytes(), cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    petto_profile(ctx, prof0 ? 1 : 0);
+    if (st == PETTO_OK) st = set_tiling(ctx, best_t);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(su);
+    cudaFree(sw);
+    rep += "}";
+    if (report && report_len > 0) {
+        std::strncpy(report, rep.c_str(), (size_t)report_len - 1);
+        report[report_len - 1] = 0;
+    }
+    return st;
 }
 
 }  // extern "C"

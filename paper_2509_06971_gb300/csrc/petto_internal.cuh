@@ -101,6 +101,7 @@ struct SweepArgs {
     int test_dot;             // this sweep tests <R, w_in> < 0 and schedules a restart
     long long sweep_idx;      // index of this sweep within the solve
     int zseg;                 // output planes per z segment of the marching kernels
+    int rhs_index;            // marching kernels: load case of this launch (one launch per case)
     double *ctrl;             // solve control words (CT_*)
     const void *rhs;          // dense right-hand side [C][cstride] replacing the loads, or null
     double a, b, s1;
@@ -260,7 +261,7 @@ void march3d_tma_tiling(const Layout &L, int ty, Tiling &t);
 void march3d_tma2_tiling(const Layout &L, Tiling &t);
 cudaError_t launch_march3d_tma2(const SweepArgs &a, const Tiling &t, const TmaMaps &m, cudaStream_t s);
 cudaError_t launch_march3d_tma(const SweepArgs &a, const Tiling &t, const TmaMaps &m, cudaStream_t s);
-bool make_tma_maps(const Layout &L, int ty, void *u0, void *u1, void *w, const void *E, TmaMaps &m);
+bool make_tma_maps(const Layout &L, int ty, int ncomp, void *u0, void *u1, void *w, const void *E, TmaMaps &m);
 
 cudaError_t launch_sweep(const SweepArgs &a, const Tiling &t, int precision, cudaStream_t s,
                          const TmaMaps *maps = nullptr);

@@ -491,15 +491,20 @@ Tiling gather_tiling(const Layout &L) {
 }
 
 Tiling choose_tiling(const Layout &L, int physics, int precision, int nrhs) {
-    if (L.dim == 3 && physics == 0 && precision == 0 && nrhs == 1) {
-        // z-marching kernel: TMA-staged with 32x8 owner tiles by default; PETTO_MARCH=v1
-        // selects the register-staged kernel, PETTO_MARCH=tma16 32x16 tiles
+    if (L.dim == 3 && physics == 0 && precision == 0) {
+        // z-marching kernel: TMA-staged with two owner rows per thread by default;
+        // PETTO_MARCH=tma8 / tma16 select one row per thread (32x8 / 32x16 tiles),
+        // PETTO_MARCH=v1 the register-staged kernel
         Tiling t{};
         const char *env = std::getenv("PETTO_MARCH");
         // the TMA kernel addresses a node column with 32-bit offsets
-        if ((env && std::strcmp(env, "v1") == 0) || 3 * L.cstride >= (int64_t(1) << 31)) march3d_tiling(L, t);
-        else if (env && std::strcmp(env, "tma2") == 0) march3d_tma2_tiling(L, t);
-        else march3d_tma_tiling(L, env && std::strcmp(env, "tma16") == 0 ? 16 : 8, t);
+        if ((env && std::strcmp(env, "v1") == 0 && nrhs == 1) || 3 * nrhs * L.cstride >= (int64_t(1) << 31)) {
+            if (nrhs != 1) return gather_tiling(L);
+            march3d_tiling(L, t);
+        }
+        else if (env && std::strcmp(env, "tma8") == 0) march3d_tma_tiling(L, 8, t);
+        else if (env && std::strcmp(env, "tma16") == 0) march3d_tma_tiling(L, 16, t);
+        else march3d_tma2_tiling(L, t);
         return t;
     }
     return gather_tiling(L);

@@ -299,10 +299,13 @@ __global__ void __launch_bounds__(MNT, 3) sweep3d_march_f32(const SweepArgs A) {
             const double t = A.want_res ? sum_partials(A.red, 0, nb, shred) : 0.0;
             const double td = A.test_dot ? sum_partials(A.red, nb, nb, shred) : 0.0;
             if (tid == 0) {
-                if (A.want_res) *A.res2 = t;
+                // one launch per load case: sums accumulate in launch order; the last case decides
+                const bool first = A.rhs_index == 0, lastc = A.rhs_index == A.nrhs - 1;
+                if (A.want_res) *A.res2 = first ? t : *A.res2 + t;
                 if (A.test_dot) {
-                    A.ctrl[CT_DOT] = td;
-                    if (td < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = A.sweep_idx + 1;
+                    const double dsum = first ? td : A.ctrl[CT_DOT] + td;
+                    A.ctrl[CT_DOT] = dsum;
+                    if (lastc && dsum < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = A.sweep_idx + 1;
                 }
                 *A.red.counter = 0u;
             }
@@ -558,9 +561,10 @@ __device__ __forceinline__ bool march_plane(const SweepArgs &A, const MarchConst
             for (int l = l0; l < l1; ++l) {
                 const LoadEntry &le = A.loads[l];
                 if (le.node == nidx) {
-                    if (le.comp == 0) F0 += le.valf;
-                    else if (le.comp == 1) F1 += le.valf;
-                    else F2 += le.valf;
+                    const int cc = le.comp - 3 * A.rhs_index;
+                    if (cc == 0) F0 += le.valf;
+                    else if (cc == 1) F1 += le.valf;
+                    else if (cc == 2) F2 += le.valf;
                 }
             }
         }
@@ -649,9 +653,11 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __gr
     // per-thread column bases; in-column offsets fit in 32 bits (checked on the host)
     const int64_t nbase = outxy ? L.node(X, Y, 0) : 0;
     const int plane32 = (int)(L.SX * L.SY), cs32 = (int)L.cstride;
-    float *wb = static_cast<float *>(A.w) + nbase;
-    float *uob = A.u_out ? static_cast<float *>(A.u_out) + nbase : nullptr;
-    const float *rb = A.rhs ? static_cast<const float *>(A.rhs) + nbase : nullptr;
+    const int c0 = 3 * A.rhs_index;  // first component of this launch's load case
+    const int64_t cbase = (int64_t)c0 * L.cstride;
+    float *wb = static_cast<float *>(A.w) + cbase + nbase;
+    float *uob = A.u_out ? static_cast<float *>(A.u_out) + cbase + nbase : nullptr;
+    const float *rb = A.rhs ? static_cast<const float *>(A.rhs) + cbase + nbase : nullptr;
 
     // stage r (relative to plane z0-1) holds u plane z0-1+r and E layer z0-2+r
     auto issue = [&](int r) {
@@ -659,8 +665,8 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __gr
         const int slot = r & (TNS - 1);
         const uint32_t bar = smem_u32(&bars[slot]);
         mbar_expect_tx(bar, (unsigned)(2 * G::UBYTES + G::EBYTES));
-        tma_load_4d(smem_u32(su + slot * (G::USLOT / 4)), &tmu, xs, y0, p + 1, 0, bar);
-        tma_load_4d(smem_u32(sw + slot * (G::USLOT / 4)), &tmw, xs, y0, p + 1, 0, bar);
+        tma_load_4d(smem_u32(su + slot * (G::USLOT / 4)), &tmu, xs, y0, p + 1, c0, bar);
+        tma_load_4d(smem_u32(sw + slot * (G::USLOT / 4)), &tmw, xs, y0, p + 1, c0, bar);
         tma_load_3d(smem_u32(se + slot * (G::ESLOT / 4)), &tme, xse, y0 - 1, p, bar);
     };
     const int nstage = zend - (z0 - 1) + 1;  // stages z0-1 .. zend
@@ -728,10 +734,13 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __gr
             const double t = A.want_res ? sum_partials(A.red, 0, nb, shred) : 0.0;
             const double td = A.test_dot ? sum_partials(A.red, nb, nb, shred) : 0.0;
             if (tid == 0) {
-                if (A.want_res) *A.res2 = t;
+                // one launch per load case: sums accumulate in launch order; the last case decides
+                const bool first = A.rhs_index == 0, lastc = A.rhs_index == A.nrhs - 1;
+                if (A.want_res) *A.res2 = first ? t : *A.res2 + t;
                 if (A.test_dot) {
-                    A.ctrl[CT_DOT] = td;
-                    if (td < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = A.sweep_idx + 1;
+                    const double dsum = first ? td : A.ctrl[CT_DOT] + td;
+                    A.ctrl[CT_DOT] = dsum;
+                    if (lastc && dsum < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = A.sweep_idx + 1;
                 }
                 *A.red.counter = 0u;
             }
@@ -753,10 +762,13 @@ void march3d_tma_tiling(const Layout &L, int ty, Tiling &t) {
     t.gz = (L.NZ + t.zs - 1) / t.zs;
 }
 
-cudaError_t launch_march3d_tma(const SweepArgs &a, const Tiling &t, const TmaMaps &m, cudaStream_t s) {
-    const CUtensorMap *mu = a.u_in == m.ubuf[0] ? &m.u[0] : (a.u_in == m.ubuf[1] ? &m.u[1] : nullptr);
+cudaError_t launch_march3d_tma(const SweepArgs &a0, const Tiling &t, const TmaMaps &m, cudaStream_t s) {
+    const CUtensorMap *mu = a0.u_in == m.ubuf[0] ? &m.u[0] : (a0.u_in == m.ubuf[1] ? &m.u[1] : nullptr);
     if (!mu) return cudaErrorInvalidValue;
     dim3 grid(t.gx, t.gy, t.gz);
+    for (int r = 0; r < a0.nrhs; ++r) {
+    SweepArgs a = a0;
+    a.rhs_index = r;
     if (t.kind == 3) {
         static bool attr = false;
         if (!attr) {
@@ -772,6 +784,7 @@ cudaError_t launch_march3d_tma(const SweepArgs &a, const Tiling &t, const TmaMap
         }
         sweep3d_march_tma<8><<<grid, dim3(32, 8), TmaGeom<8>::SMEM, s>>>(a, *mu, m.w, m.e);
     }
+    }
     return cudaGetLastError();
 }
 
@@ -782,7 +795,7 @@ cudaError_t launch_march3d_tma(const SweepArgs &a, const Tiling &t, const TmaMap
 
 namespace petto {
 
-bool make_tma_maps(const Layout &L, int ty, void *u0, void *u1, void *w, const void *E, TmaMaps &m) {
+bool make_tma_maps(const Layout &L, int ty, int ncomp, void *u0, void *u1, void *w, const void *E, TmaMaps &m) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void *fn = nullptr;
@@ -794,7 +807,7 @@ bool make_tma_maps(const Layout &L, int ty, void *u0, void *u1, void *w, const v
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
     m.valid = false;
-    const cuuint64_t udim[4] = {(cuuint64_t)L.SX, (cuuint64_t)L.SY, (cuuint64_t)L.SZ, 3};
+    const cuuint64_t udim[4] = {(cuuint64_t)L.SX, (cuuint64_t)L.SY, (cuuint64_t)L.SZ, (cuuint64_t)ncomp};
     const cuuint64_t ustr[3] = {(cuuint64_t)L.SX * 4, (cuuint64_t)(L.SX * L.SY) * 4, (cuuint64_t)L.cstride * 4};
     const cuuint32_t ubox[4] = {TBW, (cuuint32_t)(ty + 1), 1, 3};
     const cuuint32_t one4[4] = {1, 1, 1, 1};
@@ -933,9 +946,10 @@ __device__ __forceinline__ void march_update(const SweepArgs &A, const MarchCons
         for (int l = l0; l < l1; ++l) {
             const LoadEntry &le = A.loads[l];
             if (le.node == nidx) {
-                if (le.comp == 0) F0 += le.valf;
-                else if (le.comp == 1) F1 += le.valf;
-                else F2 += le.valf;
+                const int cc = le.comp - 3 * A.rhs_index;
+                if (cc == 0) F0 += le.valf;
+                else if (cc == 1) F1 += le.valf;
+                else if (cc == 2) F2 += le.valf;
             }
         }
     }
@@ -1107,9 +1121,11 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
     const int l0 = A.tile_ptr[tile], l1 = A.tile_ptr[tile + 1];
     const int64_t nbA = outA ? L.node(X, YA, 0) : 0, nbB = outB ? L.node(X, YB, 0) : 0;
     const int plane32 = (int)(L.SX * L.SY), cs32 = (int)L.cstride;
-    float *w = static_cast<float *>(A.w);
-    float *uo = static_cast<float *>(A.u_out);
-    const float *rh = static_cast<const float *>(A.rhs);
+    const int c0 = 3 * A.rhs_index;  // first component of this launch's load case
+    const int64_t cbase = (int64_t)c0 * L.cstride;
+    float *w = static_cast<float *>(A.w) + cbase;
+    float *uo = A.u_out ? static_cast<float *>(A.u_out) + cbase : nullptr;
+    const float *rh = A.rhs ? static_cast<const float *>(A.rhs) + cbase : nullptr;
     float *wbA = w + nbA, *wbB = w + nbB;
     float *uobA = uo ? uo + nbA : nullptr, *uobB = uo ? uo + nbB : nullptr;
     const float *rbA = rh ? rh + nbA : nullptr, *rbB = rh ? rh + nbB : nullptr;
@@ -1119,8 +1135,8 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
         const int slot = r & (TNS - 1);
         const uint32_t bar = smem_u32(&bars[slot]);
         mbar_expect_tx(bar, (unsigned)(2 * R2UBYTES + R2EBYTES));
-        tma_load_4d(smem_u32(su + slot * (R2USLOT / 4)), &tmu, xs, y0, p + 1, 0, bar);
-        tma_load_4d(smem_u32(sw + slot * (R2USLOT / 4)), &tmw, xs, y0, p + 1, 0, bar);
+        tma_load_4d(smem_u32(su + slot * (R2USLOT / 4)), &tmu, xs, y0, p + 1, c0, bar);
+        tma_load_4d(smem_u32(sw + slot * (R2USLOT / 4)), &tmw, xs, y0, p + 1, c0, bar);
         tma_load_3d(smem_u32(se + slot * (R2ESLOT / 4)), &tme, xse, y0 - 1, p, bar);
     };
     const int nstage = zend - (z0 - 1) + 1;
@@ -1189,10 +1205,13 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
             const double t = A.want_res ? sum_partials(A.red, 0, nb, shred) : 0.0;
             const double td = A.test_dot ? sum_partials(A.red, nb, nb, shred) : 0.0;
             if (tid == 0) {
-                if (A.want_res) *A.res2 = t;
+                // one launch per load case: sums accumulate in launch order; the last case decides
+                const bool first = A.rhs_index == 0, lastc = A.rhs_index == A.nrhs - 1;
+                if (A.want_res) *A.res2 = first ? t : *A.res2 + t;
                 if (A.test_dot) {
-                    A.ctrl[CT_DOT] = td;
-                    if (td < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = A.sweep_idx + 1;
+                    const double dsum = first ? td : A.ctrl[CT_DOT] + td;
+                    A.ctrl[CT_DOT] = dsum;
+                    if (lastc && dsum < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = A.sweep_idx + 1;
                 }
                 *A.red.counter = 0u;
             }
@@ -1222,7 +1241,11 @@ cudaError_t launch_march3d_tma2(const SweepArgs &a, const Tiling &t, const TmaMa
         cudaFuncSetAttribute(sweep3d_march_tma2, cudaFuncAttributeMaxDynamicSharedMemorySize, R2SMEM);
         attr = true;
     }
-    sweep3d_march_tma2<<<dim3(t.gx, t.gy, t.gz), dim3(32, R2TY), R2SMEM, s>>>(a, *mu, m.w, m.e);
+    for (int r = 0; r < a.nrhs; ++r) {
+        SweepArgs ar = a;
+        ar.rhs_index = r;
+        sweep3d_march_tma2<<<dim3(t.gx, t.gy, t.gz), dim3(32, R2TY), R2SMEM, s>>>(ar, *mu, m.w, m.e);
+    }
     return cudaGetLastError();
 }
 

@@ -140,6 +140,13 @@ class Problem:
         self._ck(self.lib.petto_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
 
+    def autotune(self, sweeps: int = 20) -> dict:
+        """Time the applicable sweep kernels / tile shapes and keep the fastest."""
+        import json
+        buf = ctypes.create_string_buffer(4096)
+        self._ck(self.lib.petto_autotune(self.ctx, int(sweeps), buf, len(buf)))
+        return json.loads(buf.value.decode() or "{}")
+
     def synchronize(self):
         self._ck(self.lib.petto_synchronize(self.ctx))
 

@@ -393,3 +393,75 @@ def test_paper_mode_fixed_counts(P):
              check_every=0)
     assert relmax(prob.get_state(), oracle_to_nodes(u, 2)) < 1e-12
     prob.close()
+
+
+@pytest.mark.parametrize("variant", ["tma2", "tma8"])
+def test_multi_rhs_fp32_march(P, variant, monkeypatch):
+    """FP32 multi-load-case sweeps on the marching kernels (one launch per case sharing the
+    momentum schedule) match the oracle run case by case."""
+    monkeypatch.setenv("PETTO_MARCH", variant)
+    spec, cases = W.multirhs3d(40, 18, 20, n_rhs=3, seed=3)
+    spec = spec.with_(precision="f32", storage="f32")
+    prob = P.Problem(spec, nrhs=3, load_cases=cases)
+    phi = W.random_design(spec, seed=26)
+    prob.set_design(phi)
+    rng = np.random.default_rng(4)
+    u0 = rng.standard_normal((9, spec.nnodes)).astype(np.float32)
+    prob.set_state(u0)
+    r2 = prob.sweep(0, 3, 0.9, 0.8, 0.0, True)
+    ug = prob.get_state()
+    om = oracle_materials(spec)
+    E = om.modulus(np.asarray(phi, np.float32).astype(np.float64))
+    r2o = 0.0
+    for r, case in enumerate(cases):
+        op = oracle_problem(spec, loads=case)
+        uo = nodes_to_oracle(u0[3 * r:3 * r + 3].astype(np.float64))
+        wo = np.zeros_like(uo)
+        for t in range(3):
+            rr = op.apt_sweep(E, op.load_vector(), op.fixed_mask(), 0.9, 0.8, uo, wo, local_dt=True)
+        r2o += rr
+        un = oracle_to_nodes(uo, 3)
+        for c in range(3):
+            assert rel_l2(ug[3 * r + c], un[c]) < 1e-5
+    assert abs(r2 - r2o) < 1e-4 * r2o
+    prob.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_reduced_precision_design_storage(P, storage):
+    """Design fields stored in BF16/FP16, arithmetic in FP32: the modulus equals the oracle's
+    modulus of the rounded design, and an update lands within one storage ulp of the oracle's."""
+    torch = pytest.importorskip("torch")
+    spec = W.multimat3d(20, 10, 10, storage=storage)
+    spec = spec.with_(phi0=None)
+    prob = P.Problem(spec, precision="f32", storage=storage)
+    phi = W.random_design(spec, seed=27, lo=0.05, hi=0.9)
+    tdt = torch.bfloat16 if storage == "bf16" else torch.float16
+    phir = torch.tensor(phi, dtype=torch.float64).to(tdt).to(torch.float64).numpy()
+    prob.set_design(phi)
+    assert np.array_equal(prob.get_design(), phir)
+    om = oracle_materials(spec)
+    assert relmax(prob.get_modulus(), om.modulus(phir)) < 1e-6
+    u0 = W.random_state(spec, seed=28).astype(np.float32)
+    prob.set_state(u0)
+    _, _, s = prob.sensitivity()
+    kw = dict(vol_mode=W.PROJECTED, alpha_h=0.1, kappa_1=0.0, n_bisect=60)
+    prob.design_update(**kw)
+    phi_o = phir.copy()
+    O.update(phi_o, s, spec.vol_frac, **kw)
+    ulp = 2.0 ** -8 if storage == "bf16" else 2.0 ** -11
+    assert np.abs(prob.get_design() - phi_o).max() <= ulp
+    prob.close()
+
+
+def test_autotune_keeps_state_and_picks_a_variant(P):
+    spec = W.cantilever3d(48, 24, 24)
+    prob = P.Problem(spec)
+    u0 = W.random_state(spec, seed=29).astype(np.float32)
+    prob.set_state(u0)
+    rep = prob.autotune(sweeps=4)
+    assert len(rep) >= 3 and all(v > 0 for v in rep.values())
+    assert np.array_equal(prob.get_state(dtype=np.float32), u0)
+    r = prob.solve(tol=1e-6, max_sweeps=100000)
+    assert r["converged"]
+    prob.close()
