@@ -120,9 +120,11 @@ typedef struct {
  * with b' = b, s1' = s1 (global step, the paper's form) or b' = b / diag(K),
  * s1' = s1 / diag(K) per DOF when local_dt != 0 (local pseudo-time steps).
  * momentum 0: a_k = a (the paper's fixed damping).  momentum 1 (adaptive restart, an
- * extension): a_k = min(a, (k-1)/(k+2)) with k the sweeps since the last restart; every
- * 4th sweep tests <R, w> of its input and, when negative, restarts the momentum at the
- * next sweep (decided on the device).
+ * extension): a_k = min(a, (k-1)/(k+2)) with k the sweeps since the last restart; the sweeps
+ * with (t mod check_every) % 4 == 3 test <R, w> of their input and, when negative, restart
+ * the momentum at the next sweep (decided on the device).  Whole check intervals are
+ * replayed as CUDA graphs (unless PETTO_NO_GRAPHS is set); a context created with the
+ * legacy default stream runs on a blocking stream of its own.
  * refine 1 (FP32 contexts, tolerance mode, tol < 1e-3): an FP32 state cannot represent a
  * solution much below relative residual ~1e-4 for stiff problems, so the solve sweeps the
  * FP32 state to 1e-2, then continues the same iteration on u = u64 + d with u64 in FP64:
@@ -250,12 +252,13 @@ petto_status petto_synchronize(petto_ctx *ctx);
 /* Number of kernel launches this context has issued (for launch accounting). */
 int64_t petto_launch_count(const petto_ctx *ctx);
 
-/* Sweep-kernel timing.  While enabled, every sweep launch is bracketed by a pair of CUDA
- * events on the context's stream; petto_profile_read waits for them and returns the summed
- * device time (ms) and the number of timed sweep launches since the last read, then
- * resets both.  Disabled by default. */
+/* Sweep-kernel timing.  While enabled, every sweep launch (or every graph replay of a check
+ * interval of sweeps) is bracketed by a pair of CUDA events on the context's stream;
+ * petto_profile_read waits for them and returns the summed device time (ms), the number of
+ * sweeps timed and how many of those read a dense right-hand side (refinement sweeps), then
+ * resets the counters.  Disabled by default.  Any output pointer may be NULL. */
 petto_status petto_profile(petto_ctx *ctx, int enable);
-petto_status petto_profile_read(petto_ctx *ctx, double *sweep_ms, int64_t *sweeps);
+petto_status petto_profile_read(petto_ctx *ctx, double *sweep_ms, int64_t *sweeps, int64_t *rhs_sweeps);
 
 /* Sweep-kernel autotuner: times every kernel variant and tile shape that applies to this
  * problem (for 3D elasticity in FP32: TMA-staged marching kernels with one or two owner

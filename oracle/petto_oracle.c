@@ -299,7 +299,8 @@ double or_apt_sweep(const or_grid *g, const double *E, const double *F, const ui
  * momentum 0 keeps the APT damping a fixed (the paper's form).  momentum 1 (adaptive
  * restart, an extension of the fixed damping): the APT sweep with index t (counted from 0
  * within the solve) uses a_t = min(a, (k-1)/(k+2)), k = t - t_restart (0 when k <= 0);
- * every sweep with t % 4 == 3 computes <R_t, w_t> of its input residual and increment
+ * every sweep with (t mod check_every) % 4 == 3 (t % 4 == 3 when check_every = 0) computes
+ * <R_t, w_t> of its input residual and increment
  * and, when that is negative (the last step went uphill in energy), sets t_restart = t + 1.
  * The guard factor is 10 for fixed and 100 for adaptive momentum.
  * rep: [0] sweeps, [1] APT sweeps, [2] PT sweeps, [3] last checked ||R||, [4] ||F||,
@@ -331,7 +332,7 @@ void or_solve(const or_grid *g, const double *E, const double *F, const uint8_t 
         double r2;
         if (apt) {
             double at = a, dot = 0.0;
-            const int test = momentum && (sweeps % 4 == 3);
+            const int test = momentum && (((check_every > 0 ? sweeps % check_every : sweeps) % 4) == 3);
             if (momentum) {
                 const int64_t k = sweeps - t_restart;
                 const double sched = k <= 0 ? 0.0 : (double)(k - 1) / (double)(k + 2);

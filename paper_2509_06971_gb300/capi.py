@@ -94,7 +94,7 @@ _SIGS = {
     "petto_synchronize": (_int, [_vp]),
     "petto_launch_count": (_i64, [_vp]),
     "petto_profile": (_int, [_vp, _int]),
-    "petto_profile_read": (_int, [_vp, _P(_dbl), _P(_i64)]),
+    "petto_profile_read": (_int, [_vp, _P(_dbl), _P(_i64), _P(_i64)]),
     "petto_residual_norm_static": (_int, [_P(petto_grid), _dbl, _vp, _vp, _vp, _vp, _P(_dbl), _vp]),
     "petto_autotune": (_int, [_vp, _int, ctypes.c_char_p, _int]),
 }

@@ -55,11 +55,22 @@ struct petto_ctx {
     int64_t step = 0;
     bool have_sens = false;
     bool profiling = false;
+    bool owns_stream = false;
+    bool use_graphs = true;  // replay sweep chunks between checks as CUDA graphs
+    struct GraphEntry {
+        int apt, local_dt, adaptive, cur, ce, nrhs_dummy;
+        const void *rhs;
+        double a, b, s1;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
     bool trace = false;  // PETTO_TRACE set: print every check residual to stderr
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    std::vector<int> ev_count;  // sweeps covered by each pending event pair
     double prof_ms = 0.0;
-    int64_t prof_sweeps = 0;
+    int64_t prof_sweeps = 0, prof_rhs_sweeps = 0;
+    std::vector<int> ev_rhs;  // 1 where the timed sweeps read a dense right-hand side
     std::string err;
 
     size_t tsize() const { return precision == 0 ? 4 : 8; }
@@ -68,6 +79,11 @@ struct petto_ctx {
     size_t node_bytes() const { return (size_t)ndofc() * L.cstride * tsize(); }
     RedBuf red() const { return RedBuf{partials, counter}; }
 };
+
+static void clear_graphs(petto_ctx *ctx) {
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+}
 
 namespace {
 
@@ -321,6 +337,7 @@ struct SweepCtl {
     int adaptive = 0;
     int test_dot = 0;
     long long idx = 0;
+    int base_from_ctrl = 0;
     const void *rhs = nullptr;
 };
 
@@ -334,6 +351,7 @@ petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, 
     A.adaptive = sc.adaptive;
     A.test_dot = kind == 0 && sc.adaptive ? sc.test_dot : 0;
     A.sweep_idx = sc.idx;
+    A.base_from_ctrl = sc.base_from_ctrl;
     A.rhs = sc.rhs;
     A.a = a;
     A.b = b;
@@ -345,7 +363,7 @@ petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, 
     A.u_out = ctx->u[1 - ctx->cur];
     A.w = ctx->w;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (ctx->profiling) {
+    if (ctx->profiling && !sc.base_from_ctrl) {
         for (cudaEvent_t *e : {&e0, &e1}) {
             if (!ctx->ev_free.empty()) {
                 *e = ctx->ev_free.back();
@@ -357,9 +375,11 @@ petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, 
         CK(cudaEventRecord(e0, ctx->stream));
     }
     CK(launch_sweep(A, ctx->tiling, ctx->precision, ctx->stream, &ctx->tma));
-    if (ctx->profiling) {
+    if (ctx->profiling && !sc.base_from_ctrl) {
         CK(cudaEventRecord(e1, ctx->stream));
         ctx->ev_pending.emplace_back(e0, e1);
+        ctx->ev_count.push_back(1);
+        ctx->ev_rhs.push_back(sc.rhs != nullptr);
     }
     ctx->launches++;
     ctx->cur ^= 1;
@@ -395,16 +415,21 @@ void build_opconst(petto_ctx *ctx) {
 }
 
 petto_status drain_profile(petto_ctx *ctx) {
-    for (auto &pr : ctx->ev_pending) {
+    for (size_t q = 0; q < ctx->ev_pending.size(); ++q) {
+        auto &pr = ctx->ev_pending[q];
         CK(cudaEventSynchronize(pr.second));
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
         ctx->prof_ms += ms;
-        ctx->prof_sweeps++;
+        const int cnt = q < ctx->ev_count.size() ? ctx->ev_count[q] : 1;
+        ctx->prof_sweeps += cnt;
+        if (q < ctx->ev_rhs.size() && ctx->ev_rhs[q]) ctx->prof_rhs_sweeps += cnt;
         ctx->ev_free.push_back(pr.first);
         ctx->ev_free.push_back(pr.second);
     }
     ctx->ev_pending.clear();
+    ctx->ev_count.clear();
+    ctx->ev_rhs.clear();
     return PETTO_OK;
 }
 
@@ -434,6 +459,7 @@ petto_status set_tiling(petto_ctx *ctx, const Tiling &t) {
     }
     for (int q = 0; q < nt; ++q) tptr[q + 1] += tptr[q];
     CK(cudaStreamSynchronize(ctx->stream));
+    clear_graphs(ctx);
     if (nt > ctx->ntiles_alloc) {
         CK(cudaFree(ctx->tile_ptr));
         ctx->tile_ptr = nullptr;
@@ -492,14 +518,16 @@ petto_status petto_profile(petto_ctx *ctx, int enable) {
     return PETTO_OK;
 }
 
-petto_status petto_profile_read(petto_ctx *ctx, double *sweep_ms, int64_t *sweeps) {
+petto_status petto_profile_read(petto_ctx *ctx, double *sweep_ms, int64_t *sweeps, int64_t *rhs_sweeps) {
     if (!ctx) return PETTO_EINVAL;
     petto_status st = drain_profile(ctx);
     if (st != PETTO_OK) return st;
     if (sweep_ms) *sweep_ms = ctx->prof_ms;
     if (sweeps) *sweeps = ctx->prof_sweeps;
+    if (rhs_sweeps) *rhs_sweeps = ctx->prof_rhs_sweeps;
     ctx->prof_ms = 0.0;
     ctx->prof_sweeps = 0;
+    ctx->prof_rhs_sweeps = 0;
     return PETTO_OK;
 }
 
@@ -511,11 +539,13 @@ void petto_destroy(petto_ctx *ctx) {
         cudaEventDestroy(pr.second);
     }
     for (auto e : ctx->ev_free) cudaEventDestroy(e);
+    clear_graphs(ctx);
     void *bufs[] = {ctx->u[0], ctx->u[1], ctx->w, ctx->E, ctx->phi, ctx->s, ctx->dscr, ctx->mu, ctx->rbuf,
                     ctx->stage, ctx->scal, ctx->counter, ctx->tile_ptr, ctx->loads, ctx->partials,
                     ctx->gtile_ptr, ctx->gloads, ctx->ctrl, ctx->u64, ctx->r64, ctx->rhs32};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    if (ctx->owns_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
 
@@ -553,6 +583,16 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
     ctx->precision = opt->precision;
     ctx->storage = opt->storage;
     ctx->stream = (cudaStream_t)opt->stream;
+    if (!ctx->stream) {
+        // the legacy default stream cannot be captured: use a blocking stream of our own, which
+        // still orders with work on the legacy default stream
+        if (cudaStreamCreate(&ctx->stream) != cudaSuccess) {
+            delete ctx;
+            return PETTO_ECUDA;
+        }
+        ctx->owns_stream = true;
+    }
+    ctx->use_graphs = std::getenv("PETTO_NO_GRAPHS") == nullptr;
     ctx->moduli.assign(mat->modulus, mat->modulus + mat->n_phases);
     ctx->vol.assign(vol_frac, vol_frac + mat->n_phases);
     ctx->body_source = loads ? loads->body_source : 0.0;
@@ -737,6 +777,11 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
         petto_destroy(ctx);
         return PETTO_ECUDA;
     }
+    if (ctx->dim == 3 && ctx->physics == 0 && ctx->precision == PETTO_F32 && march3d_prepare() != cudaSuccess) {
+        ctx->err = "cannot configure the marching kernels";
+        petto_destroy(ctx);
+        return PETTO_ECUDA;
+    }
     if (ctx->tiling.kind == 2 || ctx->tiling.kind == 3 || ctx->tiling.kind == 4) {
         const int ty = ctx->tiling.kind == 3 || ctx->tiling.kind == 4 ? 16 : 8;
         if (!make_tma_maps(ctx->L, ty, ctx->ndofc(), ctx->u[0], ctx->u[1], ctx->w, ctx->E, ctx->tma)) {
@@ -898,6 +943,77 @@ petto_status set_ctrl(petto_ctx *ctx, int slot, long long v) {
     return PETTO_OK;
 }
 
+// One chunk of ce sweeps (the last a check sweep) as a CUDA graph: captured once per set of
+// sweep constants and starting buffer, replayed with the chunk's first sweep index read
+// from the device control words.
+petto_status graph_chunk(petto_ctx *ctx, const petto_solve_opts *o, bool apt, int ce, long long base,
+                         const void *rhs, bool *done) {
+    *done = false;
+    const int adaptive = o->momentum ? 1 : 0;
+    petto_ctx::GraphEntry *ge = nullptr;
+    for (auto &g : ctx->graphs)
+        if (g.apt == apt && g.local_dt == o->local_dt && g.adaptive == adaptive && g.cur == ctx->cur && g.ce == ce &&
+            g.rhs == rhs && g.a == o->a && g.b == o->b && g.s1 == o->s1)
+            ge = &g;
+    if (!ge) {
+        if (ctx->graphs.size() >= 8) clear_graphs(ctx);
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        const int cur0 = ctx->cur;
+        const int64_t l0 = ctx->launches;
+        petto_status st = PETTO_OK;
+        for (int j = 0; j < ce && st == PETTO_OK; ++j) {
+            SweepCtl sc;
+            sc.adaptive = adaptive;
+            sc.test_dot = (j % 4) == 3;
+            sc.idx = j;
+            sc.base_from_ctrl = 1;
+            sc.rhs = rhs;
+            st = one_sweep(ctx, apt ? 0 : 1, o->a, o->b, o->s1, o->local_dt, j == ce - 1, sc);
+        }
+        cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
+        ctx->cur = cur0;
+        ctx->launches = l0;
+        if (st != PETTO_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        CK(ec);
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ei);
+        petto_ctx::GraphEntry g{apt ? 1 : 0, o->local_dt, adaptive, ctx->cur, ce, 0, rhs, o->a, o->b, o->s1, exec};
+        ctx->graphs.push_back(g);
+        ge = &ctx->graphs.back();
+    }
+    set_ctrl_kernel<<<1, 1, 0, ctx->stream>>>(ctx->ctrl, CT_BASE, base);
+    CK(cudaGetLastError());
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ctx->profiling) {
+        for (cudaEvent_t *e : {&e0, &e1}) {
+            if (!ctx->ev_free.empty()) {
+                *e = ctx->ev_free.back();
+                ctx->ev_free.pop_back();
+            } else {
+                CK(cudaEventCreate(e));
+            }
+        }
+        CK(cudaEventRecord(e0, ctx->stream));
+    }
+    CK(cudaGraphLaunch(ge->exec, ctx->stream));
+    if (ctx->profiling) {
+        CK(cudaEventRecord(e1, ctx->stream));
+        ctx->ev_pending.emplace_back(e0, e1);
+        ctx->ev_count.push_back(ce);
+        ctx->ev_rhs.push_back(rhs != nullptr);
+    }
+    ctx->launches += ce + 1;
+    // ce is even: the buffer roles are back where they started
+    *done = true;
+    return PETTO_OK;
+}
+
 // Sweep until a check sweep's residual is <= stop_abs, the budget ends, or (stall_checks > 0)
 // the residual has not fallen 10% over stall_checks checks.  Returns 1 when stop_abs was
 // reached, 0 otherwise.  Applies the divergence guard.
@@ -909,19 +1025,36 @@ petto_status sweep_phase(petto_ctx *ctx, const petto_solve_opts *o, SolveState &
     double scal[SC_N];
     while (S.sweeps < S.total) {
         const bool apt = !S.use_pt && (o->mode == PETTO_SOLVE_TOL || S.sweeps < n_apt);
-        const bool check = ce > 0 && (S.sweeps + 1) % ce == 0;
-        const bool final_report = (S.sweeps + 1 == S.total);
-        SweepCtl sc;
-        sc.adaptive = o->momentum ? 1 : 0;
-        sc.test_dot = (S.sweeps % 4) == 3;
-        sc.idx = S.sweeps;
-        sc.rhs = rhs;
-        petto_status st = one_sweep(ctx, apt ? 0 : 1, o->a, o->b, o->s1, o->local_dt, check || final_report, sc);
-        if (st != PETTO_OK) return st;
-        if (apt) ++S.na; else ++S.np;
-        ++S.sweeps;
-        if (!(check || final_report)) continue;
-        st = read_scal(ctx, scal);
+        // a whole check interval of one sweep kind: replay it as a graph
+        const bool same_kind = o->mode == PETTO_SOLVE_TOL || S.use_pt || S.sweeps + ce <= n_apt || S.sweeps >= n_apt;
+        if (ctx->use_graphs && ctx->stream && ce >= 4 && ce % 2 == 0 && S.sweeps % ce == 0 &&
+            S.sweeps + ce <= S.total && same_kind) {
+            bool done = false;
+            petto_status st = graph_chunk(ctx, o, apt, ce, S.sweeps, rhs, &done);
+            if (st != PETTO_OK) return st;
+            if (done) {
+                if (apt) S.na += ce; else S.np += ce;
+                S.sweeps += ce;
+                goto checked;
+            }
+        }
+        {
+            const bool check = ce > 0 && (S.sweeps + 1) % ce == 0;
+            const bool final_report = (S.sweeps + 1 == S.total);
+            SweepCtl sc;
+            sc.adaptive = o->momentum ? 1 : 0;
+            sc.test_dot = ((ce > 0 ? S.sweeps % ce : S.sweeps) % 4) == 3;
+            sc.idx = S.sweeps;
+            sc.rhs = rhs;
+            petto_status st = one_sweep(ctx, apt ? 0 : 1, o->a, o->b, o->s1, o->local_dt, check || final_report, sc);
+            if (st != PETTO_OK) return st;
+            if (apt) ++S.na; else ++S.np;
+            ++S.sweeps;
+            if (!(check || final_report)) continue;
+        }
+    checked:
+        const bool check = ce > 0 && S.sweeps % ce == 0;
+        petto_status st = read_scal(ctx, scal);
         if (st != PETTO_OK) return st;
         const double rn = std::sqrt(scal[SC_RES]);
         S.last = rn;
@@ -1295,10 +1428,10 @@ petto_status petto_autotune(petto_ctx *ctx, int n, char *report, int report_len)
         double ms = 0;
         int64_t cnt = 0;
         for (int t = 0; t < n + 2 && st == PETTO_OK; ++t) {
-            if (t == 2) st = petto_profile_read(ctx, &ms, &cnt);  // drop two warm-up sweeps
+            if (t == 2) st = petto_profile_read(ctx, &ms, &cnt, nullptr);  // drop two warm-up sweeps
             if (st == PETTO_OK) st = one_sweep(ctx, 0, 0.99, 0.5, 0.5, 1, false);
         }
-        if (st == PETTO_OK) st = petto_profile_read(ctx, &ms, &cnt);
+        if (st == PETTO_OK) st = petto_profile_read(ctx, &ms, &cnt, nullptr);
         if (st != PETTO_OK) break;
         const double per = ms / std::max<int64_t>(cnt, 1);
         rep += (rep.size() > 1 ? ", \"" : "\"") + c.first + "\": " + std::to_string(per);

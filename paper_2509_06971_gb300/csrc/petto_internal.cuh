@@ -80,7 +80,8 @@ struct OpConst {
 constexpr int CT_RESTART_AT = 0;  // sweep index (int64 bits) at which the APT momentum last restarted
 constexpr int CT_DOT = 1;         // last tested <R, w> (for inspection)
 constexpr int CT_ERR = 2;         // nonzero after a bounded device-side wait ran out
-constexpr int CT_N = 4;
+constexpr int CT_BASE = 3;        // (int64) index of the first sweep of a graph-replayed chunk
+constexpr int CT_N = 8;
 
 // FP32 copies of the constants, converted once on the host (a double-to-float conversion
 // in a kernel runs on the narrow FP64 pipe of GB300).
@@ -99,7 +100,9 @@ struct SweepArgs {
     int want_res;
     int adaptive;             // APT momentum a_k = min(a, (k-1)/(k+2)), k sweeps since the last restart
     int test_dot;             // this sweep tests <R, w_in> < 0 and schedules a restart
-    long long sweep_idx;      // index of this sweep within the solve
+    long long sweep_idx;      // index of this sweep within the solve (offset within the chunk when
+                              // base_from_ctrl: the chunk's first index is read from the device)
+    int base_from_ctrl;
     int zseg;                 // output planes per z segment of the marching kernels
     int rhs_index;            // marching kernels: load case of this launch (one launch per case)
     double *ctrl;             // solve control words (CT_*)
@@ -184,8 +187,12 @@ __device__ __forceinline__ double sum_partials(const RedBuf &rb, int64_t off, in
 
 // Momentum of the adaptive-restart schedule for this sweep: (k-1)/(k+2), k sweeps since the
 // last restart (0 for k <= 0).  Integer arithmetic until one FP32 division.
+__device__ __forceinline__ long long sweep_index(const SweepArgs &A) {
+    return A.base_from_ctrl ? reinterpret_cast<const long long *>(A.ctrl)[CT_BASE] + A.sweep_idx : A.sweep_idx;
+}
+
 __device__ __forceinline__ float apt_schedule(const SweepArgs &A) {
-    const long long k = A.sweep_idx - reinterpret_cast<const long long *>(A.ctrl)[CT_RESTART_AT];
+    const long long k = sweep_index(A) - reinterpret_cast<const long long *>(A.ctrl)[CT_RESTART_AT];
     if (k <= 0) return 0.f;
     const int ki = k < (1 << 30) ? (int)k : (1 << 30);
     return __fdividef((float)(ki - 1), (float)(ki + 2));
@@ -259,6 +266,7 @@ struct TmaMaps {
 };
 void march3d_tma_tiling(const Layout &L, int ty, Tiling &t);
 void march3d_tma2_tiling(const Layout &L, Tiling &t);
+cudaError_t march3d_prepare();
 cudaError_t launch_march3d_tma2(const SweepArgs &a, const Tiling &t, const TmaMaps &m, cudaStream_t s);
 cudaError_t launch_march3d_tma(const SweepArgs &a, const Tiling &t, const TmaMaps &m, cudaStream_t s);
 bool make_tma_maps(const Layout &L, int ty, int ncomp, void *u0, void *u1, void *w, const void *E, TmaMaps &m);

@@ -272,7 +272,7 @@ template <> __device__ __forceinline__ float apt_momentum<float>(const SweepArgs
 }
 template <> __device__ __forceinline__ double apt_momentum<double>(const SweepArgs &A, const KC<double> &k) {
     if (!A.adaptive) return k.a;
-    const long long kk = A.sweep_idx - reinterpret_cast<const long long *>(A.ctrl)[CT_RESTART_AT];
+    const long long kk = sweep_index(A) - reinterpret_cast<const long long *>(A.ctrl)[CT_RESTART_AT];
     if (kk <= 0) return 0.0;
     const double sched = (double)(kk - 1) / (double)(kk + 2);
     return sched < k.a ? sched : k.a;
@@ -322,7 +322,7 @@ __device__ __forceinline__ void finish_sweep(const SweepArgs &A, double res, dou
             if (A.want_res) *A.res2 = t;
             if (A.test_dot) {
                 A.ctrl[CT_DOT] = td;
-                if (td < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = A.sweep_idx + 1;
+                if (td < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = sweep_index(A) + 1;
             }
             *A.red.counter = 0u;
         }

@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(MNT, 3) sweep3d_march_f32(const SweepArgs A) {
                 if (A.test_dot) {
                     const double dsum = first ? td : A.ctrl[CT_DOT] + td;
                     A.ctrl[CT_DOT] = dsum;
-                    if (lastc && dsum < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = A.sweep_idx + 1;
+                    if (lastc && dsum < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = sweep_index(A) + 1;
                 }
                 *A.red.counter = 0u;
             }
@@ -740,7 +740,7 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __gr
                 if (A.test_dot) {
                     const double dsum = first ? td : A.ctrl[CT_DOT] + td;
                     A.ctrl[CT_DOT] = dsum;
-                    if (lastc && dsum < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = A.sweep_idx + 1;
+                    if (lastc && dsum < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = sweep_index(A) + 1;
                 }
                 *A.red.counter = 0u;
             }
@@ -769,21 +769,8 @@ cudaError_t launch_march3d_tma(const SweepArgs &a0, const Tiling &t, const TmaMa
     for (int r = 0; r < a0.nrhs; ++r) {
     SweepArgs a = a0;
     a.rhs_index = r;
-    if (t.kind == 3) {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(sweep3d_march_tma<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmaGeom<16>::SMEM);
-            attr = true;
-        }
-        sweep3d_march_tma<16><<<grid, dim3(32, 16), TmaGeom<16>::SMEM, s>>>(a, *mu, m.w, m.e);
-    } else {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(sweep3d_march_tma<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmaGeom<8>::SMEM);
-            attr = true;
-        }
-        sweep3d_march_tma<8><<<grid, dim3(32, 8), TmaGeom<8>::SMEM, s>>>(a, *mu, m.w, m.e);
-    }
+    if (t.kind == 3) sweep3d_march_tma<16><<<grid, dim3(32, 16), TmaGeom<16>::SMEM, s>>>(a, *mu, m.w, m.e);
+    else sweep3d_march_tma<8><<<grid, dim3(32, 8), TmaGeom<8>::SMEM, s>>>(a, *mu, m.w, m.e);
     }
     return cudaGetLastError();
 }
@@ -1211,7 +1198,7 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
                 if (A.test_dot) {
                     const double dsum = first ? td : A.ctrl[CT_DOT] + td;
                     A.ctrl[CT_DOT] = dsum;
-                    if (lastc && dsum < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = A.sweep_idx + 1;
+                    if (lastc && dsum < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = sweep_index(A) + 1;
                 }
                 *A.red.counter = 0u;
             }
@@ -1220,6 +1207,19 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
 }
 
 }  // namespace
+
+// Dynamic shared memory above 48 KB must be allowed per kernel before the first launch
+// (done when a context is created, so never inside a stream capture).
+cudaError_t march3d_prepare() {
+    cudaError_t e = cudaFuncSetAttribute(sweep3d_march_tma<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TmaGeom<8>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep3d_march_tma<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 TmaGeom<16>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep3d_march_tma2, cudaFuncAttributeMaxDynamicSharedMemorySize, R2SMEM);
+    return e;
+}
 
 void march3d_tma2_tiling(const Layout &L, Tiling &t) {
     t.bx = 32;
@@ -1236,11 +1236,6 @@ void march3d_tma2_tiling(const Layout &L, Tiling &t) {
 cudaError_t launch_march3d_tma2(const SweepArgs &a, const Tiling &t, const TmaMaps &m, cudaStream_t s) {
     const CUtensorMap *mu = a.u_in == m.ubuf[0] ? &m.u[0] : (a.u_in == m.ubuf[1] ? &m.u[1] : nullptr);
     if (!mu) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(sweep3d_march_tma2, cudaFuncAttributeMaxDynamicSharedMemorySize, R2SMEM);
-        attr = true;
-    }
     for (int r = 0; r < a.nrhs; ++r) {
         SweepArgs ar = a;
         ar.rhs_index = r;

@@ -134,11 +134,12 @@ class Problem:
     def profile(self, enable: bool = True):
         self._ck(self.lib.petto_profile(self.ctx, int(bool(enable))))
 
-    def profile_read(self):
-        """(summed sweep-kernel device milliseconds, timed sweep launches) since last read."""
-        ms, n = ctypes.c_double(0.0), ctypes.c_int64(0)
-        self._ck(self.lib.petto_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n)))
-        return ms.value, n.value
+    def profile_read(self, with_rhs: bool = False):
+        """(summed sweep device milliseconds, sweeps timed[, sweeps with a dense RHS]) since
+        the last read."""
+        ms, n, nr = ctypes.c_double(0.0), ctypes.c_int64(0), ctypes.c_int64(0)
+        self._ck(self.lib.petto_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(nr)))
+        return (ms.value, n.value, nr.value) if with_rhs else (ms.value, n.value)
 
     def autotune(self, sweeps: int = 20) -> dict:
         """Time the applicable sweep kernels / tile shapes and keep the fastest."""
