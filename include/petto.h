@@ -268,6 +268,47 @@ petto_status petto_profile_read(petto_ctx *ctx, double *sweep_ms, int64_t *sweep
  * object of milliseconds per sweep for each candidate.  Uses temporary device memory. */
 petto_status petto_autotune(petto_ctx *ctx, int n, char *report, int report_len);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent 2D problems advanced together (the paper solves one design problem at a
+ * time; batching changes how the work is scheduled on the GPU, not what each problem
+ * computes).  One kernel launch per sweep covers every problem still iterating, each
+ * chunk of check_every sweeps is replayed as one CUDA graph, and the check residuals of
+ * all problems are read with one copy.  Each problem keeps the iteration of
+ * petto_pt_solve: its own checks, momentum restarts, divergence guard, PT fallback and
+ * FP32 iterative refinement, with the same kernel arithmetic and reduction order, so it
+ * ends in the same state as when solved alone. */
+typedef struct petto_batch petto_batch;
+
+/* Borrows n contexts (they must outlive the batch): 2D, one load case (nrhs 1), and a
+ * common precision and physics, else PETTO_EUNSUPPORTED.  Contexts whose sweep tiling was
+ * changed by petto_autotune are set back to the 32 x 8 tiling the batched kernel uses.
+ * During batch calls the contexts' work runs on the first context's stream (joined to the
+ * others' streams with events).  *out is NULL on failure. */
+petto_status petto_batch_create(int n, petto_ctx *const *ctxs, petto_batch **out);
+void petto_batch_destroy(petto_batch *b);
+const char *petto_batch_last_error(const petto_batch *b);
+/* kernel launches issued by the batch and by its contexts */
+int64_t petto_batch_launch_count(const petto_batch *b);
+
+/* Solves every problem (Sec. 2.2 PT / APT relaxation).  opts [n]: mode, n_apt, n_pt,
+ * max_sweeps, check_every (even, >= 2), local_dt, momentum and refine must agree across
+ * problems (PETTO_EINVAL otherwise); a, b, s1 and tol are per problem.  reps [n] (may be
+ * NULL) receive each problem's report.  Returns PETTO_ENOTCONV when a tolerance-mode
+ * problem did not converge, PETTO_EDIVERGED when a residual stayed non-finite. */
+petto_status petto_batch_pt_solve(petto_batch *b, const petto_solve_opts *opts, petto_solve_report *reps);
+
+/* n_steps PeTTO loops (Fig. 5) on every problem: batched solve, then per problem the
+ * sensitivity, the design update and the Cahn-Hilliard steps with popts[i].  metrics
+ * (may be NULL) receives [n_steps][n][8] values laid out as for petto_step_cb (entry 6,
+ * the mean phase, is NaN). */
+petto_status petto_batch_optimize(petto_batch *b, int n_steps, const petto_solve_opts *sopts,
+                                  const petto_pf_opts *popts, double *metrics);
+
+/* Timing of the batched sweeps with CUDA events around each graph replay: enable, then
+ * read (and reset) the accumulated milliseconds and batch sweeps. */
+petto_status petto_batch_profile(petto_batch *b, int enable);
+petto_status petto_batch_profile_read(petto_batch *b, double *sweep_ms, int64_t *sweeps);
+
 /* Allocation-free residual norm.  The paper has no counterpart: this entry point exists
  * for callers that must not allocate GPU memory themselves -- code running under a memory
  * manager that owns every device byte (a framework's caching allocator, a fixed arena of

@@ -97,6 +97,14 @@ _SIGS = {
     "petto_profile_read": (_int, [_vp, _P(_dbl), _P(_i64), _P(_i64)]),
     "petto_residual_norm_static": (_int, [_P(petto_grid), _dbl, _vp, _vp, _vp, _vp, _P(_dbl), _vp]),
     "petto_autotune": (_int, [_vp, _int, ctypes.c_char_p, _int]),
+    "petto_batch_create": (_int, [_int, _P(_vp), _P(_vp)]),
+    "petto_batch_destroy": (None, [_vp]),
+    "petto_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "petto_batch_launch_count": (_i64, [_vp]),
+    "petto_batch_pt_solve": (_int, [_vp, _P(petto_solve_opts), _P(petto_solve_report)]),
+    "petto_batch_optimize": (_int, [_vp, _int, _P(petto_solve_opts), _P(petto_pf_opts), _P(_dbl)]),
+    "petto_batch_profile": (_int, [_vp, _int]),
+    "petto_batch_profile_read": (_int, [_vp, _P(_dbl), _P(_i64)]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -147,5 +155,12 @@ def status_string(s: int) -> str:
 def check(ctx, status: int, allow=(PETTO_OK,)) -> int:
     if status not in allow:
         msg = load().petto_last_error(ctx).decode() if ctx else ""
+        raise PettoError(status, msg)
+    return status
+
+
+def check_batch(batch, status: int, allow=(PETTO_OK,)) -> int:
+    if status not in allow:
+        msg = load().petto_batch_last_error(batch).decode() if batch else ""
         raise PettoError(status, msg)
     return status

@@ -4,6 +4,7 @@
 // (Sec. 2.3), design update and Cahn-Hilliard step (Sec. 2.3, 2.4).
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -1014,6 +1015,108 @@ petto_status graph_chunk(petto_ctx *ctx, const petto_solve_opts *o, bool apt, in
     return PETTO_OK;
 }
 
+// One check residual rn applied to the phase state: the divergence guard (a non-finite
+// residual zeroes u and w and falls back to PT; one above guard x the best so far zeroes w
+// and falls back to PT), the stop test and the stall test.  *ended is set when the phase
+// ends; *reached when rn <= stop_abs.  check = false (the budget's last, unchecked sweep)
+// ends the phase.
+petto_status apply_check(petto_ctx *ctx, const petto_solve_opts *o, SolveState &S, double rn, bool check,
+                         double stop_abs, int stall_checks, bool *ended, int *reached) {
+    const double guard = o->momentum ? 100.0 : 10.0;
+    *ended = false;
+    if (!check) {
+        *ended = true;
+        return PETTO_OK;
+    }
+    if (!std::isfinite(rn)) {
+        CK(cudaMemsetAsync(ctx->u[ctx->cur], 0, ctx->node_bytes(), ctx->stream));
+        CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
+        S.use_pt = true;
+        S.fell = true;
+        return PETTO_OK;
+    }
+    if (rn > guard * S.best && !S.use_pt) {
+        CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
+        S.use_pt = true;
+        S.fell = true;
+    }
+    if (rn < S.best) S.best = rn;
+    if (rn <= stop_abs) {
+        *reached = 1;
+        *ended = true;
+        return PETTO_OK;
+    }
+    if (rn < 0.9 * S.improve_ref) {
+        S.improve_ref = rn;
+        S.since_improve = 0;
+    } else if (stall_checks > 0 && ++S.since_improve >= stall_checks) {
+        *ended = true;
+    }
+    return PETTO_OK;
+}
+
+// ---- iterative refinement around FP32 sweeps (steps shared by the single and batched solves)
+
+// u64 <- u (FP32 state), allocating the FP64 state, defect and FP32 right-hand side
+petto_status refine_begin(petto_ctx *ctx) {
+    const size_t nb64 = (size_t)ctx->ndofc() * ctx->L.cstride * sizeof(double);
+    const int64_t nel = (int64_t)ctx->ndofc() * ctx->L.cstride;
+    if (!ctx->u64) CK(cudaMalloc(&ctx->u64, nb64));
+    if (!ctx->r64) CK(cudaMalloc(&ctx->r64, nb64));
+    if (!ctx->rhs32) CK(cudaMalloc(&ctx->rhs32, ctx->node_bytes()));
+    f32_to_f64<<<grid_of(nel), 256, 0, ctx->stream>>>(nel, (const float *)ctx->u[ctx->cur], (double *)ctx->u64);
+    CK(cudaGetLastError());
+    ctx->launches++;
+    return PETTO_OK;
+}
+
+// FP64 defect r64 = F - K u64 and its norm (synchronises)
+petto_status refine_defect(petto_ctx *ctx, double *norm) {
+    SweepArgs R = base_sweep_args(ctx);
+    R.mode = 2;
+    R.want_res = 1;
+    R.u_in = ctx->u64;
+    R.w = ctx->r64;
+    R.tile_ptr = ctx->gtile_ptr;
+    R.loads = ctx->gloads;
+    CK(launch_residual64(R, ctx->gtiling, ctx->stream));
+    ctx->launches++;
+    double scal[SC_N];
+    petto_status st = read_scal(ctx, scal);
+    if (st != PETTO_OK) return st;
+    *norm = std::sqrt(scal[SC_RES]);
+    return PETTO_OK;
+}
+
+// the defect becomes the FP32 right-hand side; the correction d = u restarts from zero
+petto_status refine_correction(petto_ctx *ctx) {
+    const int64_t nel = (int64_t)ctx->ndofc() * ctx->L.cstride;
+    f64_to_f32<<<grid_of(nel), 256, 0, ctx->stream>>>(nel, (const double *)ctx->r64, (float *)ctx->rhs32);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(ctx->u[ctx->cur], 0, ctx->node_bytes(), ctx->stream));
+    ctx->launches++;
+    return PETTO_OK;
+}
+
+// u64 += d
+petto_status refine_absorb(petto_ctx *ctx) {
+    const int64_t nel = (int64_t)ctx->ndofc() * ctx->L.cstride;
+    add_f32_to_f64<<<grid_of(nel), 256, 0, ctx->stream>>>(nel, (const float *)ctx->u[ctx->cur], (double *)ctx->u64);
+    CK(cudaGetLastError());
+    ctx->launches++;
+    return PETTO_OK;
+}
+
+// u <- u64 rounded to FP32, w <- 0
+petto_status refine_finish(petto_ctx *ctx) {
+    const int64_t nel = (int64_t)ctx->ndofc() * ctx->L.cstride;
+    f64_to_f32<<<grid_of(nel), 256, 0, ctx->stream>>>(nel, (const double *)ctx->u64, (float *)ctx->u[ctx->cur]);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
+    ctx->launches++;
+    return PETTO_OK;
+}
+
 // Sweep until a check sweep's residual is <= stop_abs, the budget ends, or (stall_checks > 0)
 // the residual has not fallen 10% over stall_checks checks.  Returns 1 when stop_abs was
 // reached, 0 otherwise.  Applies the divergence guard.
@@ -1021,7 +1124,6 @@ petto_status sweep_phase(petto_ctx *ctx, const petto_solve_opts *o, SolveState &
                          int stall_checks, const void *rhs, int *reached) {
     *reached = 0;
     const int ce = o->check_every;
-    const double guard = o->momentum ? 100.0 : 10.0;
     double scal[SC_N];
     while (S.sweeps < S.total) {
         const bool apt = !S.use_pt && (o->mode == PETTO_SOLVE_TOL || S.sweeps < n_apt);
@@ -1067,30 +1169,10 @@ petto_status sweep_phase(petto_ctx *ctx, const petto_solve_opts *o, SolveState &
                          ctx->f_norm > 0 ? rn / ctx->f_norm : 0.0, ra,
                          rhs ? " (correction)" : "");
         }
-        if (!check) break;
-        if (!std::isfinite(rn)) {
-            CK(cudaMemsetAsync(ctx->u[ctx->cur], 0, ctx->node_bytes(), ctx->stream));
-            CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
-            S.use_pt = true;
-            S.fell = true;
-            continue;
-        }
-        if (rn > guard * S.best && !S.use_pt) {
-            CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
-            S.use_pt = true;
-            S.fell = true;
-        }
-        if (rn < S.best) S.best = rn;
-        if (rn <= stop_abs) {
-            *reached = 1;
-            break;
-        }
-        if (rn < 0.9 * S.improve_ref) {
-            S.improve_ref = rn;
-            S.since_improve = 0;
-        } else if (stall_checks > 0 && ++S.since_improve >= stall_checks) {
-            break;
-        }
+        bool ended = false;
+        st = apply_check(ctx, o, S, rn, check, stop_abs, stall_checks, &ended, reached);
+        if (st != PETTO_OK) return st;
+        if (ended) break;
     }
     return PETTO_OK;
 }
@@ -1127,29 +1209,11 @@ petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_sol
         // APT recursion is the same in the shifted variable).
         st = sweep_phase(ctx, o, S, 1e-2 * fn, 0, 0, nullptr, &reached);
         if (st != PETTO_OK) return st;
-        const size_t nb64 = (size_t)ctx->ndofc() * ctx->L.cstride * sizeof(double);
-        const int64_t nel = (int64_t)ctx->ndofc() * ctx->L.cstride;
-        if (!ctx->u64) CK(cudaMalloc(&ctx->u64, nb64));
-        if (!ctx->r64) CK(cudaMalloc(&ctx->r64, nb64));
-        if (!ctx->rhs32) CK(cudaMalloc(&ctx->rhs32, ctx->node_bytes()));
-        cudaStream_t s = ctx->stream;
-        f32_to_f64<<<grid_of(nel), 256, 0, s>>>(nel, (const float *)ctx->u[ctx->cur], (double *)ctx->u64);
-        CK(cudaGetLastError());
-        ctx->launches++;
-        double scal[SC_N];
+        st = refine_begin(ctx);
+        if (st != PETTO_OK) return st;
         while (true) {
-            SweepArgs R = base_sweep_args(ctx);
-            R.mode = 2;
-            R.want_res = 1;
-            R.u_in = ctx->u64;
-            R.w = ctx->r64;
-            R.tile_ptr = ctx->gtile_ptr;
-            R.loads = ctx->gloads;
-            CK(launch_residual64(R, ctx->gtiling, s));
-            ctx->launches++;
-            st = read_scal(ctx, scal);
+            st = refine_defect(ctx, &true_res);
             if (st != PETTO_OK) return st;
-            true_res = std::sqrt(scal[SC_RES]);
             if (ctx->trace)
                 std::fprintf(stderr, "petto: FP64 defect %.6e rel %.3e after %lld sweeps\n", true_res,
                              fn > 0 ? true_res / fn : 0.0, (long long)S.sweeps);
@@ -1158,23 +1222,18 @@ petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_sol
                 break;
             }
             if (S.sweeps >= S.total || !std::isfinite(true_res)) break;
-            f64_to_f32<<<grid_of(nel), 256, 0, s>>>(nel, (const double *)ctx->r64, (float *)ctx->rhs32);
-            CK(cudaGetLastError());
-            CK(cudaMemsetAsync(ctx->u[ctx->cur], 0, ctx->node_bytes(), s));
-            ctx->launches++;
+            st = refine_correction(ctx);
+            if (st != PETTO_OK) return st;
             S.improve_ref = INFINITY;
             S.since_improve = 0;
             const double stop = std::max(true_res / 8.0, 0.5 * o->tol * fn);
             st = sweep_phase(ctx, o, S, stop, 0, 20, ctx->rhs32, &reached);
             if (st != PETTO_OK) return st;
-            add_f32_to_f64<<<grid_of(nel), 256, 0, s>>>(nel, (const float *)ctx->u[ctx->cur], (double *)ctx->u64);
-            CK(cudaGetLastError());
-            ctx->launches++;
+            st = refine_absorb(ctx);
+            if (st != PETTO_OK) return st;
         }
-        f64_to_f32<<<grid_of(nel), 256, 0, s>>>(nel, (const double *)ctx->u64, (float *)ctx->u[ctx->cur]);
-        CK(cudaGetLastError());
-        CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), s));
-        ctx->launches++;
+        st = refine_finish(ctx);
+        if (st != PETTO_OK) return st;
         S.last = true_res;
     }
     if (rep) {
@@ -1313,6 +1372,519 @@ petto_status petto_optimize(petto_ctx *ctx, int n_steps, const petto_solve_opts 
             const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
             const double m[8] = {(double)ctx->step, C, W, rep.rel_res, (double)rep.sweeps, secs, vol[0], lam[0]};
             cb(m, user);
+        }
+    }
+    return notconv ? PETTO_ENOTCONV : PETTO_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================ batches
+// A batch advances many independent 2D problems together: one launch of sweep2d_batch per
+// sweep covers the tiles of every problem still iterating, each chunk of check_every
+// sweeps is one CUDA graph, and all residual checks of a chunk are read with one copy.
+// Per problem, the iteration, its checks, restarts, PT fallback and FP32 refinement are
+// those of petto_pt_solve (the same helpers and the same kernel arithmetic), so a problem
+// solved in a batch ends in the same state as when solved alone.
+struct petto_batch {
+    std::vector<petto_ctx *> ctx;   // borrowed
+    cudaStream_t stream = nullptr;  // the first context's stream
+    int precision = 0, physics = 0;
+    std::vector<BatchInst> inst;    // host mirror of the device table
+    BatchInst *d_inst = nullptr;
+    std::vector<BatchTile> tiles;   // active problems' tiles first
+    BatchTile *d_tiles = nullptr;
+    int ntiles = 0;
+    int *d_nact = nullptr;          // device word: number of active tiles
+    long long *d_base = nullptr;    // device word: first sweep index of the chunk
+    double *d_res = nullptr;        // sum R^2 of each problem's last check sweep
+    std::vector<int> active;
+    int cur = 0;
+    int64_t launches = 0;
+    struct Graph {
+        int len, cur, adaptive, local_dt;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
+    cudaEvent_t ev = nullptr;
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    std::vector<int> ev_count;
+    std::vector<cudaEvent_t> ev_free;
+    double prof_ms = 0.0;
+    int64_t prof_sweeps = 0;
+    std::string err;
+};
+
+namespace {
+
+petto_status bfail(petto_batch *b, petto_status st, const std::string &msg) {
+    if (b) b->err = msg;
+    return st;
+}
+
+#define BCK(call)                                                                                      \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return bfail(b, PETTO_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+    } while (0)
+
+__global__ void set_word_kernel(long long *w, long long v) { *w = v; }
+
+// problems' contexts run on the batch stream for the duration of a batch call
+struct StreamJoin {
+    petto_batch *b;
+    std::vector<cudaStream_t> saved;
+    explicit StreamJoin(petto_batch *bb) : b(bb) {
+        for (petto_ctx *c : b->ctx) {
+            saved.push_back(c->stream);
+            if (c->stream != b->stream) {
+                cudaEventRecord(b->ev, c->stream);
+                cudaStreamWaitEvent(b->stream, b->ev, 0);
+                c->stream = b->stream;
+            }
+        }
+    }
+    ~StreamJoin() {
+        for (size_t i = 0; i < b->ctx.size(); ++i) {
+            petto_ctx *c = b->ctx[i];
+            if (saved[i] != b->stream) {
+                c->stream = saved[i];
+                cudaEventRecord(b->ev, b->stream);
+                cudaStreamWaitEvent(saved[i], b->ev, 0);
+            }
+        }
+    }
+};
+
+// re-read each problem's buffers and tiling from its context (a context may have been
+// re-tiled or used alone since the last batch call) and bring every state to u[cur]
+petto_status batch_refresh(petto_batch *b) {
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        petto_ctx *ctx = b->ctx[i];
+        const Tiling g = gather_tiling(ctx->L);
+        if (ctx->tiling.kind != 0 || ctx->tiling.bx != g.bx || ctx->tiling.by != g.by) {
+            petto_status st = set_tiling(ctx, g);
+            if (st != PETTO_OK) return bfail(b, st, ctx->err);
+        }
+        if (ctx->cur != b->cur) {
+            BCK(cudaMemcpyAsync(ctx->u[b->cur], ctx->u[ctx->cur], ctx->node_bytes(), cudaMemcpyDeviceToDevice,
+                                b->stream));
+            ctx->cur = b->cur;
+        }
+        BatchInst &I = b->inst[i];
+        I.L = ctx->L;
+        I.kf = base_sweep_args(ctx).kf;
+        I.k = ctx->k;
+        I.boxes = ctx->boxes;
+        I.u[0] = ctx->u[0];
+        I.u[1] = ctx->u[1];
+        I.w = ctx->w;
+        I.E = ctx->E;
+        I.rhs = nullptr;
+        I.tile_ptr = ctx->tile_ptr;
+        I.loads = ctx->loads;
+        I.red = ctx->red();
+        I.ctrl = ctx->ctrl;
+        I.gx = g.gx;
+        I.gy = g.gy;
+        I.res2 = b->d_res + i;
+    }
+    return PETTO_OK;
+}
+
+// rebuild the tile list (active problems first) and upload it with the problem table
+petto_status batch_upload(petto_batch *b) {
+    b->tiles.clear();
+    for (int pass = 0; pass < 2; ++pass)
+        for (size_t i = 0; i < b->inst.size(); ++i) {
+            if ((b->active[i] != 0) != (pass == 0)) continue;
+            const int nt = b->inst[i].gx * b->inst[i].gy;
+            for (int t = 0; t < nt; ++t) b->tiles.push_back(BatchTile{(int)i, t});
+        }
+    int nact = 0;
+    for (size_t i = 0; i < b->inst.size(); ++i)
+        if (b->active[i]) nact += b->inst[i].gx * b->inst[i].gy;
+    BCK(cudaMemcpyAsync(b->d_tiles, b->tiles.data(), sizeof(BatchTile) * b->tiles.size(), cudaMemcpyHostToDevice,
+                        b->stream));
+    BCK(cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(BatchInst) * b->inst.size(), cudaMemcpyHostToDevice,
+                        b->stream));
+    BCK(cudaMemcpyAsync(b->d_nact, &nact, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    // the host copies above are pageable: make sure they were taken before the mirrors change
+    BCK(cudaStreamSynchronize(b->stream));
+    return PETTO_OK;
+}
+
+BatchLaunch batch_launch(petto_batch *b, const petto_solve_opts *o, long long j, int len) {
+    BatchLaunch p{};
+    p.inst = b->d_inst;
+    p.tiles = b->d_tiles;
+    p.n_active_tiles = b->d_nact;
+    p.base = b->d_base;
+    p.sweep_idx = j;
+    p.cur = (b->cur + (int)j) & 1;
+    p.physics = b->physics;
+    p.nrhs = 1;
+    p.local_dt = o->local_dt;
+    p.want_res = j == len - 1;
+    p.test_dot = (j % 4) == 3;
+    p.adaptive = o->momentum ? 1 : 0;
+    return p;
+}
+
+// len sweeps of every active problem from u[cur]: one graph per (len, cur, momentum, step) kind
+petto_status batch_chunk(petto_batch *b, const petto_solve_opts *o, long long base, int len) {
+    set_word_kernel<<<1, 1, 0, b->stream>>>(b->d_base, base);
+    BCK(cudaGetLastError());
+    const int adaptive = o->momentum ? 1 : 0;
+    petto_batch::Graph *ge = nullptr;
+    for (auto &g : b->graphs)
+        if (g.len == len && g.cur == b->cur && g.adaptive == adaptive && g.local_dt == o->local_dt) ge = &g;
+    if (!ge) {
+        cudaGraph_t graph = nullptr;
+        BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t el = cudaSuccess;
+        for (int j = 0; j < len && el == cudaSuccess; ++j)
+            el = launch_sweep2d_batch(batch_launch(b, o, j, len), b->ntiles, b->precision, b->stream);
+        cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
+        if (el != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            BCK(el);
+        }
+        BCK(ec);
+        cudaGraphExec_t exec = nullptr;
+        cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        BCK(ei);
+        b->graphs.push_back(petto_batch::Graph{len, b->cur, adaptive, o->local_dt, exec});
+        ge = &b->graphs.back();
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (b->profiling) {
+        for (cudaEvent_t *e : {&e0, &e1}) {
+            if (!b->ev_free.empty()) {
+                *e = b->ev_free.back();
+                b->ev_free.pop_back();
+            } else {
+                BCK(cudaEventCreate(e));
+            }
+        }
+        BCK(cudaEventRecord(e0, b->stream));
+    }
+    BCK(cudaGraphLaunch(ge->exec, b->stream));
+    if (b->profiling) {
+        BCK(cudaEventRecord(e1, b->stream));
+        b->ev_pending.emplace_back(e0, e1);
+        b->ev_count.push_back(len);
+    }
+    b->launches += len + 1;
+    if (len & 1) {
+        // an odd chunk moves the active problems' state to the other buffer: move the
+        // finished ones' along so that every problem's state is in u[cur]
+        for (size_t i = 0; i < b->ctx.size(); ++i)
+            if (!b->active[i]) {
+                petto_ctx *c = b->ctx[i];
+                BCK(cudaMemcpyAsync(c->u[1 - b->cur], c->u[b->cur], c->node_bytes(), cudaMemcpyDeviceToDevice,
+                                    b->stream));
+            }
+        b->cur ^= 1;
+    }
+    for (petto_ctx *c : b->ctx) c->cur = b->cur;
+    return PETTO_OK;
+}
+
+// per-problem solve state of a batched solve
+struct BatchSolve {
+    SolveState S;
+    int phase = 0;          // 0 sweeps on the state, 1 refinement correction, 2 done
+    double stop = 0.0;      // this phase's residual target
+    int stall = 0;
+    double true_res = NAN;
+    bool conv = false;
+};
+
+}  // namespace
+
+extern "C" {
+
+petto_status petto_batch_create(int n, petto_ctx *const *ctxs, petto_batch **out) {
+    if (!out || n <= 0 || !ctxs) return PETTO_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i]) return PETTO_EINVAL;
+    const petto_ctx *c0 = ctxs[0];
+    for (int i = 0; i < n; ++i) {
+        const petto_ctx *c = ctxs[i];
+        if (c->dim != 2 || c->nrhs != 1 || c->precision != c0->precision || c->physics != c0->physics)
+            return PETTO_EUNSUPPORTED;
+    }
+    petto_batch *b = new petto_batch();
+    b->ctx.assign(ctxs, ctxs + n);
+    b->stream = c0->stream;
+    b->precision = c0->precision;
+    b->physics = c0->physics;
+    b->active.assign(n, 0);
+    auto cleanup = [&](petto_status st, const char *msg) {
+        petto_batch_destroy(b);
+        (void)msg;
+        return st;
+    };
+    if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) return cleanup(PETTO_ECUDA, "event");
+    b->inst.assign(n, BatchInst{});
+    for (int i = 0; i < n; ++i) {
+        const Tiling g = gather_tiling(ctxs[i]->L);
+        b->ntiles += g.gx * g.gy;
+    }
+    if (cudaMalloc(&b->d_inst, sizeof(BatchInst) * n) != cudaSuccess ||
+        cudaMalloc(&b->d_tiles, sizeof(BatchTile) * b->ntiles) != cudaSuccess ||
+        cudaMalloc(&b->d_nact, sizeof(int)) != cudaSuccess || cudaMalloc(&b->d_base, sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&b->d_res, sizeof(double) * n) != cudaSuccess)
+        return cleanup(PETTO_ENOMEM, "device memory");
+    if (batch_refresh(b) != PETTO_OK) return cleanup(PETTO_ECUDA, "tiling");
+    *out = b;
+    return PETTO_OK;
+}
+
+void petto_batch_destroy(petto_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto &pr : b->ev_pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (auto e : b->ev_free) cudaEventDestroy(e);
+    if (b->ev) cudaEventDestroy(b->ev);
+    void *bufs[] = {b->d_inst, b->d_tiles, b->d_nact, b->d_base, b->d_res};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    delete b;
+}
+
+const char *petto_batch_last_error(const petto_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+int64_t petto_batch_launch_count(const petto_batch *b) {
+    if (!b) return 0;
+    int64_t n = b->launches;
+    for (const petto_ctx *c : b->ctx) n += c->launches;
+    return n;
+}
+
+petto_status petto_batch_profile(petto_batch *b, int enable) {
+    if (!b) return PETTO_EINVAL;
+    b->profiling = enable != 0;
+    return PETTO_OK;
+}
+
+petto_status petto_batch_profile_read(petto_batch *b, double *sweep_ms, int64_t *sweeps) {
+    if (!b) return PETTO_EINVAL;
+    for (size_t q = 0; q < b->ev_pending.size(); ++q) {
+        auto &pr = b->ev_pending[q];
+        BCK(cudaEventSynchronize(pr.second));
+        float ms = 0.f;
+        BCK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        b->prof_ms += ms;
+        b->prof_sweeps += b->ev_count[q];
+        b->ev_free.push_back(pr.first);
+        b->ev_free.push_back(pr.second);
+    }
+    b->ev_pending.clear();
+    b->ev_count.clear();
+    if (sweep_ms) *sweep_ms = b->prof_ms;
+    if (sweeps) *sweeps = b->prof_sweeps;
+    b->prof_ms = 0.0;
+    b->prof_sweeps = 0;
+    return PETTO_OK;
+}
+
+petto_status petto_batch_pt_solve(petto_batch *b, const petto_solve_opts *opts, petto_solve_report *reps) {
+    if (!b || !opts) return bfail(b, PETTO_EINVAL, "null argument");
+    const int n = (int)b->ctx.size();
+    const petto_solve_opts &o0 = opts[0];
+    for (int i = 0; i < n; ++i) {
+        const petto_solve_opts &o = opts[i];
+        if (o.mode != o0.mode || o.n_apt != o0.n_apt || o.n_pt != o0.n_pt || o.max_sweeps != o0.max_sweeps ||
+            o.check_every != o0.check_every || o.local_dt != o0.local_dt || o.momentum != o0.momentum ||
+            o.refine != o0.refine)
+            return bfail(b, PETTO_EINVAL, "batched problems share mode, counts, check interval, step kind, momentum "
+                                          "and refinement; only a, b, s1 and tol may differ");
+    }
+    if (o0.mode != PETTO_SOLVE_PAPER && o0.mode != PETTO_SOLVE_TOL) return bfail(b, PETTO_EINVAL, "bad mode");
+    if (o0.n_apt < 0 || o0.n_pt < 0 || o0.max_sweeps < 0) return bfail(b, PETTO_EINVAL, "negative count");
+    if (o0.check_every < 2 || o0.check_every % 2) return bfail(b, PETTO_EINVAL, "check_every must be even and >= 2");
+    StreamJoin join(b);
+    petto_status st = batch_refresh(b);
+    if (st != PETTO_OK) return st;
+    const int64_t total = o0.mode == PETTO_SOLVE_PAPER ? o0.n_apt + o0.n_pt : o0.max_sweeps;
+    const bool refine = o0.mode == PETTO_SOLVE_TOL && o0.refine && b->precision == PETTO_F32;
+    std::vector<BatchSolve> BS(n);
+    for (int i = 0; i < n; ++i) {
+        petto_ctx *ctx = b->ctx[i];
+        const petto_solve_opts &o = opts[i];
+        ctx->cur = b->cur;
+        BCK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), b->stream));
+        st = set_ctrl(ctx, CT_RESTART_AT, 0);
+        if (st != PETTO_OK) return bfail(b, st, ctx->err);
+        BatchSolve &q = BS[i];
+        q.S.total = total;
+        const bool ref_i = refine && o.tol < 1e-3;
+        q.stop = ref_i ? 1e-2 * ctx->f_norm : (o.mode == PETTO_SOLVE_TOL ? o.tol * ctx->f_norm : -1.0);
+        BatchInst &I = b->inst[i];
+        I.kf.a = (float)o.a;
+        I.kf.b = (float)o.b;
+        I.kf.s1 = (float)o.s1;
+        I.a = o.a;
+        I.b = o.b;
+        I.s1 = o.s1;
+        I.rhs = nullptr;
+        I.apt_until = o.mode == PETTO_SOLVE_TOL ? LLONG_MAX : o.n_apt;
+        b->active[i] = total > 0 ? 1 : 0;
+        if (!b->active[i]) q.phase = 2;
+    }
+    st = batch_upload(b);
+    if (st != PETTO_OK) return st;
+    const int ce = o0.check_every;
+    int64_t sweeps = 0;
+    std::vector<double> res(n);
+    auto refine_of = [&](int i) { return refine && opts[i].tol < 1e-3; };
+    while (sweeps < total) {
+        bool any = false;
+        for (int i = 0; i < n; ++i) any = any || b->active[i];
+        if (!any) break;
+        const int len = (int)std::min<int64_t>(ce, total - sweeps);
+        st = batch_chunk(b, &o0, sweeps, len);
+        if (st != PETTO_OK) return st;
+        BCK(cudaMemcpyAsync(res.data(), b->d_res, sizeof(double) * n, cudaMemcpyDeviceToHost, b->stream));
+        BCK(cudaStreamSynchronize(b->stream));
+        const int64_t s0 = sweeps;
+        sweeps += len;
+        const bool check = sweeps % ce == 0;
+        bool changed = false;
+        for (int i = 0; i < n; ++i) {
+            if (!b->active[i]) continue;
+            petto_ctx *ctx = b->ctx[i];
+            const petto_solve_opts &o = opts[i];
+            BatchSolve &q = BS[i];
+            BatchInst &I = b->inst[i];
+            // sweeps of each kind in this chunk
+            const int64_t na = std::max<int64_t>(0, std::min<int64_t>(sweeps, I.apt_until) - s0);
+            q.S.na += na;
+            q.S.np += len - na;
+            q.S.sweeps = sweeps;
+            const double rn = std::sqrt(res[i]);
+            q.S.last = rn;
+            bool ended = false;
+            int reached = 0;
+            const bool was_pt = q.S.use_pt;
+            st = apply_check(ctx, &o, q.S, rn, check, q.stop, q.stall, &ended, &reached);
+            if (st != PETTO_OK) return bfail(b, st, ctx->err);
+            if (q.S.use_pt && !was_pt) {
+                I.apt_until = 0;
+                changed = true;
+            }
+            if (!ended && sweeps < total) continue;
+            // the phase has ended
+            if (!refine_of(i)) {
+                q.conv = o.mode == PETTO_SOLVE_TOL && reached != 0;
+                q.phase = 2;
+            } else {
+                st = q.phase == 0 ? refine_begin(ctx) : refine_absorb(ctx);
+                if (st != PETTO_OK) return bfail(b, st, ctx->err);
+                st = refine_defect(ctx, &q.true_res);
+                if (st != PETTO_OK) return bfail(b, st, ctx->err);
+                const double fn = ctx->f_norm;
+                if (q.true_res <= o.tol * fn || sweeps >= total || !std::isfinite(q.true_res)) {
+                    q.conv = q.true_res <= o.tol * fn;
+                    st = refine_finish(ctx);
+                    if (st != PETTO_OK) return bfail(b, st, ctx->err);
+                    q.S.last = q.true_res;
+                    q.phase = 2;
+                } else {
+                    st = refine_correction(ctx);
+                    if (st != PETTO_OK) return bfail(b, st, ctx->err);
+                    q.S.improve_ref = INFINITY;
+                    q.S.since_improve = 0;
+                    q.stop = std::max(q.true_res / 8.0, 0.5 * o.tol * fn);
+                    q.stall = 20;
+                    q.phase = 1;
+                    I.rhs = ctx->rhs32;
+                }
+            }
+            if (q.phase == 2) {
+                b->active[i] = 0;
+                I.rhs = nullptr;
+            }
+            changed = true;
+        }
+        if (changed) {
+            st = batch_upload(b);
+            if (st != PETTO_OK) return st;
+        }
+    }
+    // problems still active when the budget ran out between checks (cannot happen with an
+    // even check interval dividing the budget, kept for safety)
+    for (int i = 0; i < n; ++i)
+        if (b->active[i]) {
+            b->active[i] = 0;
+            BS[i].phase = 2;
+        }
+    bool all_conv = true, bad = false;
+    for (int i = 0; i < n; ++i) {
+        petto_ctx *ctx = b->ctx[i];
+        BatchSolve &q = BS[i];
+        const double fn = ctx->f_norm;
+        if (reps) {
+            petto_solve_report &r = reps[i];
+            r.sweeps = q.S.sweeps;
+            r.apt_sweeps = q.S.na;
+            r.pt_sweeps = q.S.np;
+            r.res_norm = q.S.last;
+            r.f_norm = fn;
+            r.rel_res = fn > 0 ? q.S.last / fn : NAN;
+            r.r_pde = q.S.last / std::pow(ctx->h, ctx->dim) / (double)ctx->L.nnodes();
+            r.converged = q.conv ? 1 : 0;
+            r.fell_back_to_pt = q.S.fell ? 1 : 0;
+        }
+        if (!std::isfinite(q.S.last)) bad = true;
+        if (o0.mode == PETTO_SOLVE_TOL && !q.conv) all_conv = false;
+    }
+    if (bad) return bfail(b, PETTO_EDIVERGED, "a residual was not finite after PT fallback");
+    if (!all_conv) return PETTO_ENOTCONV;
+    return PETTO_OK;
+}
+
+petto_status petto_batch_optimize(petto_batch *b, int n_steps, const petto_solve_opts *sopts,
+                                  const petto_pf_opts *popts, double *metrics) {
+    if (!b || !sopts || !popts || n_steps < 0) return bfail(b, PETTO_EINVAL, "bad arguments");
+    const int n = (int)b->ctx.size();
+    bool notconv = false;
+    std::vector<petto_solve_report> reps(n);
+    for (int t = 0; t < n_steps; ++t) {
+        const auto t0 = std::chrono::steady_clock::now();
+        petto_status st = petto_batch_pt_solve(b, sopts, reps.data());
+        if (st == PETTO_ENOTCONV) notconv = true;
+        else if (st != PETTO_OK) return st;
+        StreamJoin join(b);
+        for (int i = 0; i < n; ++i) {
+            petto_ctx *ctx = b->ctx[i];
+            double C = 0, W = 0, lam[MAX_PHASES] = {0};
+            st = petto_sensitivity(ctx, &C, &W, nullptr, PETTO_F64, 0);
+            if (st == PETTO_OK) st = petto_design_update(ctx, &popts[i], lam);
+            if (st == PETTO_OK) st = petto_cahn_hilliard(ctx, &popts[i]);
+            if (st != PETTO_OK) return bfail(b, st, ctx->err);
+            ctx->step++;
+            if (metrics) {
+                double *m = metrics + ((int64_t)t * n + i) * 8;
+                m[0] = (double)ctx->step;
+                m[1] = C;
+                m[2] = W;
+                m[3] = reps[i].rel_res;
+                m[4] = (double)reps[i].sweeps;
+                m[5] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                m[6] = NAN;
+                m[7] = lam[0];
+            }
         }
     }
     return notconv ? PETTO_ENOTCONV : PETTO_OK;

@@ -31,10 +31,14 @@ __device__ __forceinline__ void cell_ijk(const Layout &L, int64_t c, int &i, int
 template <typename T> __device__ __forceinline__ T clamp01(T x) { return x < T(0) ? T(0) : (x > T(1) ? T(1) : x); }
 
 template <typename T>
-__device__ __forceinline__ T interp_E(const DesignArgs &d, const T *rho) {
+__device__ __forceinline__ T interp_E(const DesignArgs &d, const T (&rho)[MAX_PHASES]) {
     if (d.interp == 0) return (T)d.e_min + pow(rho[0], (T)d.penal) * ((T)d.moduli[0] - (T)d.e_min);
     T s = 0;
-    for (int p = 0; p < d.P; ++p) s += (T)d.moduli[p] * pow(rho[p], (T)d.penal);
+#pragma unroll
+    for (int p = 0; p < MAX_PHASES; ++p) {
+        if (p >= d.P) break;
+        s += (T)d.moduli[p] * pow(rho[p], (T)d.penal);
+    }
     return s;
 }
 
@@ -51,21 +55,25 @@ __global__ void material_kernel(const DesignArgs d, const S *__restrict__ phi, T
     const int64_t nc = d.L.ncells();
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         T rho[MAX_PHASES];
-        for (int p = 0; p < d.P; ++p) rho[p] = clamp01<T>((T)Store<S>::ld(phi, (int64_t)p * nc + c));
+#pragma unroll
+        for (int p = 0; p < MAX_PHASES; ++p)
+            rho[p] = p < d.P ? clamp01<T>((T)Store<S>::ld(phi, (int64_t)p * nc + c)) : T(0);
         int i, j, k;
         cell_ijk(d.L, c, i, j, k);
         E[d.L.cell(i, j, k)] = interp_E<T>(d, rho);
     }
 }
 
-// unit-modulus cell energy e_c (twice the corner-quadrature strain energy per unit E)
-template <typename T>
-__device__ __forceinline__ T cell_energy(const SensArgs &sa, const T (&ul)[8][3]) {
-    const int d = sa.L.dim, nq = 1 << d;
-    const T hs = (T)(d == 3 ? sa.h : 1.0);  // h^(d-2)
+// unit-modulus cell energy e_c (twice the corner-quadrature strain energy per unit E);
+// DIM and PHYS are compile-time so the corner table ul stays in registers
+template <typename T, int DIM, int PHYS>
+__device__ __forceinline__ T cell_energy(T lam, T mu, T hs, const T (&ul)[8][3]) {
+    constexpr int nq = 1 << DIM;
     T edge = 0, face = 0;
-    if (sa.physics == 1) {
-        for (int b = 0; b < d; ++b)
+    if (PHYS == 1) {
+#pragma unroll
+        for (int b = 0; b < DIM; ++b)
+#pragma unroll
             for (int q = 0; q < nq; ++q)
                 if (!((q >> b) & 1)) {
                     const T t = ul[q | (1 << b)][0] - ul[q][0];
@@ -73,24 +81,30 @@ __device__ __forceinline__ T cell_energy(const SensArgs &sa, const T (&ul)[8][3]
                 }
         return T(2) * hs * edge / (T)nq;
     }
-    const T lam = (T)sa.lam, mu = (T)sa.mu;
-    for (int b = 0; b < d; ++b)
+#pragma unroll
+    for (int b = 0; b < DIM; ++b)
+#pragma unroll
         for (int q = 0; q < nq; ++q)
             if (!((q >> b) & 1)) {
-                for (int a = 0; a < d; ++a) {
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) {
                     const T t = ul[q | (1 << b)][a] - ul[q][a];
                     edge += (a == b ? lam + T(2) * mu : mu) * t * t;
                 }
             }
     // faces spanned by (a, b); in 3D two of each (third-axis bit t = 0, 1)
-    for (int a = 0; a < d; ++a)
-        for (int b = a + 1; b < d; ++b) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+        for (int b = a + 1; b < DIM; ++b) {
             const int c = 3 - a - b;
-            const int nt = d == 3 ? 2 : 1;
+            constexpr int nt = DIM == 3 ? 2 : 1;
+#pragma unroll
             for (int t = 0; t < nt; ++t) {
                 T Aa = 0, Ab = 0, Ba = 0, Bb = 0;  // sums of the two a-edges / b-edges
+#pragma unroll
                 for (int q = 0; q < nq; ++q) {
-                    if (d == 3 && (((q >> c) & 1) != t)) continue;
+                    if (DIM == 3 && (((q >> c) & 1) != t)) continue;
                     if (!((q >> a) & 1)) {
                         Aa += ul[q | (1 << a)][a] - ul[q][a];
                         Ab += ul[q | (1 << a)][b] - ul[q][b];
@@ -108,45 +122,56 @@ __device__ __forceinline__ T cell_energy(const SensArgs &sa, const T (&ul)[8][3]
     return T(2) * hs * (edge / (T)nq + face * T(4) / (T)nq);
 }
 
-template <typename T, typename S>
+// Grid-stride over cells: s_{p,c} = -(dE/dphi_p) e_c and C = sum_c E_c e_c.  Per-thread
+// sums and maxima stay in T; one FP64 block sum per thread at the end (deterministic order).
+template <typename T, typename S, int DIM, int PHYS>
 __global__ void __launch_bounds__(256) sensitivity_kernel(const SensArgs sa, const DesignArgs d,
                                                           const T *__restrict__ u, const T *__restrict__ E,
                                                           const S *__restrict__ phi, T *__restrict__ s,
                                                           double *scal, const RedBuf rb) {
     __shared__ double sh[32];
     const Layout &L = sa.L;
+    constexpr int ncomp = PHYS == 1 ? 1 : DIM;
     const int64_t nc = L.ncells();
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double comp = 0.0;
-    double smax[MAX_PHASES];
-    for (int p = 0; p < d.P; ++p) smax[p] = 0.0;
-    if (c < nc) {
+    const T lam = (T)sa.lam, mu = (T)sa.mu, hs = (T)(DIM == 3 ? sa.h : 1.0);
+    T comp = 0;
+    T smax[MAX_PHASES];
+#pragma unroll
+    for (int p = 0; p < MAX_PHASES; ++p) smax[p] = 0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         int i, j, k;
         cell_ijk(L, c, i, j, k);
-        const int nq = 1 << L.dim;
+        const int64_t n0 = L.node(i, j, DIM == 3 ? k : 0);
         T e = 0;
         for (int r = 0; r < sa.nrhs; ++r) {
             T ul[8][3];
-            for (int q = 0; q < nq; ++q) {
-                const int64_t n = L.node(i + (q & 1), j + ((q >> 1) & 1), L.dim == 3 ? k + ((q >> 2) & 1) : 0);
-                for (int a = 0; a < sa.ncomp; ++a) ul[q][a] = u[(int64_t)(r * sa.ncomp + a) * L.cstride + n];
+            const T *ur = u + (int64_t)r * ncomp * L.cstride + n0;
+#pragma unroll
+            for (int q = 0; q < (1 << DIM); ++q) {
+                const int64_t o = (q & 1) + ((q >> 1) & 1) * L.SX + (DIM == 3 ? ((q >> 2) & 1) * L.SX * L.SY : 0);
+#pragma unroll
+                for (int a = 0; a < ncomp; ++a) ul[q][a] = ur[(int64_t)a * L.cstride + o];
             }
-            e += cell_energy<T>(sa, ul);
+            e += cell_energy<T, DIM, PHYS>(lam, mu, hs, ul);
         }
         const T Ec = E[L.cell(i, j, k)];
-        comp = (double)Ec * (double)e;
-        for (int p = 0; p < d.P; ++p) {
+        comp += Ec * e;
+#pragma unroll
+        for (int p = 0; p < MAX_PHASES; ++p) {
+            if (p >= d.P) break;
             const T ph = (T)Store<S>::ld(phi, (int64_t)p * nc + c);
             const T sv = -interp_dE<T>(d, p, ph) * e;
             s[(int64_t)p * nc + c] = sv;
-            smax[p] = fabs((double)sv);
+            smax[p] = fmax(smax[p], sv < T(0) ? -sv : sv);
         }
     }
-    for (int p = 0; p < d.P; ++p) {
-        double m = warp_max(smax[p]);
-        if ((threadIdx.x & 31) == 0 && m > 0.0) atomic_max_nonneg(&scal[SC_SMAX + p], m);
+#pragma unroll
+    for (int p = 0; p < MAX_PHASES; ++p) {
+        if (p >= d.P) break;
+        const T m = warp_max(smax[p]);
+        if ((threadIdx.x & 31) == 0 && m > T(0)) atomic_max_nonneg(&scal[SC_SMAX + p], (double)m);
     }
-    const double tot = block_sum(comp, sh);
+    const double tot = block_sum((double)comp, sh);
     if (publish_partial(tot, rb, blockIdx.x, gridDim.x)) {
         const double t = sum_partials(rb, 0, gridDim.x, sh);
         if (threadIdx.x == 0) {
@@ -190,24 +215,37 @@ template <typename T, typename S>
 __global__ void upd_prepare(const UpdateArgs ua, S *__restrict__ phi, const T *__restrict__ s, T *__restrict__ dbuf,
                             const double *__restrict__ scal) {
     const int64_t nc = ua.ncell;
+    // per-phase factors hoisted out of the cell loop (phase loops unrolled: registers, not stack)
+    T scale[MAX_PHASES], shift[MAX_PHASES];
+#pragma unroll
+    for (int p = 0; p < MAX_PHASES; ++p) {
+        scale[p] = 0;
+        shift[p] = 0;
+        if (p < ua.P) {
+            const double smax = scal[SC_SMAX + p];
+            scale[p] = smax > 0.0 ? (T)(ua.alpha_h / smax) : T(0);
+            shift[p] = (T)(ua.kappa_v * (scal[SC_MEAN + p] - ua.V[p]));
+        }
+    }
+    const T k1 = (T)ua.kappa_1;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         T tot = 0;
         T ph[MAX_PHASES];
-        for (int p = 0; p < ua.P; ++p) {
-            ph[p] = (T)Store<S>::ld(phi, (int64_t)p * nc + c);
-            tot += ph[p];
-        }
-        for (int p = 0; p < ua.P; ++p) {
-            const double smax = scal[SC_SMAX + p];
-            T g = smax > 0.0 ? (T)ua.alpha_h * s[(int64_t)p * nc + c] / (T)smax : T(0);
-            g += (T)ua.kappa_1 * (tot - T(1));
-            const T dv = ph[p] - g;
-            if (ua.vol_mode == 0) {
-                dbuf[(int64_t)p * nc + c] = dv;
-            } else {
-                const T nv = dv - (T)ua.kappa_v * ((T)scal[SC_MEAN + p] - (T)ua.V[p]);
-                Store<S>::st(phi, (int64_t)p * nc + c, nv);
+#pragma unroll
+        for (int p = 0; p < MAX_PHASES; ++p) {
+            ph[p] = 0;
+            if (p < ua.P) {
+                ph[p] = (T)Store<S>::ld(phi, (int64_t)p * nc + c);
+                tot += ph[p];
             }
+        }
+#pragma unroll
+        for (int p = 0; p < MAX_PHASES; ++p) {
+            if (p >= ua.P) break;
+            const T g = scale[p] * s[(int64_t)p * nc + c] + k1 * (tot - T(1));
+            const T dv = ph[p] - g;
+            if (ua.vol_mode == 0) dbuf[(int64_t)p * nc + c] = dv;
+            else Store<S>::st(phi, (int64_t)p * nc + c, dv - shift[p]);
         }
     }
 }
@@ -229,15 +267,16 @@ __global__ void __launch_bounds__(256) bis_step(const UpdateArgs ua, const T *__
     __shared__ double sh[32];
     const int p = blockIdx.y;
     const int64_t nc = ua.ncell;
-    const double mid = 0.5 * (scal[SC_LO + p] + scal[SC_HI + p]);
-    double acc = 0.0;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
-        const double v = (double)dbuf[(int64_t)p * nc + c] - mid;
-        acc += v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
-    }
-    const double t = block_sum(acc, sh);
+    // element arithmetic in T (FP32 for the FP32 path: the FP64 pipe is narrow), FP64 block sums
+    const T mid = (T)(0.5 * (scal[SC_LO + p] + scal[SC_HI + p]));
+    T acc = 0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
+        acc += clamp01<T>(dbuf[(int64_t)p * nc + c] - mid);
+    const double t = block_sum((double)acc, sh);
     if (publish_partial(t, rb, (int64_t)p * gridDim.x + blockIdx.x, gridDim.x * gridDim.y)) {
-        for (int q = 0; q < ua.P; ++q) {
+#pragma unroll
+        for (int q = 0; q < MAX_PHASES; ++q) {
+            if (q >= ua.P) break;
             const double m = sum_partials(rb, (int64_t)q * gridDim.x, gridDim.x, sh) / (double)nc;
             if (threadIdx.x == 0) {
                 volatile double *vs = scal;
@@ -256,10 +295,9 @@ __global__ void upd_apply(const UpdateArgs ua, S *__restrict__ phi, const T *__r
     const int64_t nc = ua.ncell;
     const double lam = 0.5 * (scal[SC_LO + p] + scal[SC_HI + p]);
     if (blockIdx.x == 0 && threadIdx.x == 0) scal[SC_LAM + p] = lam;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
-        const double v = (double)dbuf[(int64_t)p * nc + c] - lam;
-        Store<S>::st(phi, (int64_t)p * nc + c, (T)(v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v)));
-    }
+    const T lamT = (T)lam;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
+        Store<S>::st(phi, (int64_t)p * nc + c, clamp01<T>(dbuf[(int64_t)p * nc + c] - lamT));
 }
 
 // -------------------------------------------------------------- Cahn-Hilliard
@@ -365,11 +403,20 @@ int64_t reduction_capacity(const Layout &L, int ntiles, int P) {
 cudaError_t launch_sensitivity(const SensArgs &sa, const DesignArgs &d, const void *u, const void *E,
                                const void *phi, void *sbuf, double *scal, RedBuf rb, cudaStream_t st) {
     const int64_t nc = sa.L.ncells();
-    const int g = (int)((nc + 255) / 256);
-    PETTO_DISPATCH_PREC(d.precision, T,
-        PETTO_DISPATCH_STORAGE(d.storage, S,
-            sensitivity_kernel<T, S><<<g, 256, 0, st>>>(sa, d, static_cast<const T *>(u), static_cast<const T *>(E),
-                                                        static_cast<const S *>(phi), static_cast<T *>(sbuf), scal, rb)))
+    const int g = grid_for(nc, 256, 152 * 8);
+#define PETTO_SENS(DIM, PHYS)                                                                                       \
+    PETTO_DISPATCH_PREC(d.precision, T,                                                                             \
+        PETTO_DISPATCH_STORAGE(d.storage, S,                                                                        \
+            sensitivity_kernel<T, S, DIM, PHYS><<<g, 256, 0, st>>>(sa, d, static_cast<const T *>(u),                \
+                                                                  static_cast<const T *>(E),                        \
+                                                                  static_cast<const S *>(phi),                      \
+                                                                  static_cast<T *>(sbuf), scal, rb)))
+    if (sa.L.dim == 3) {
+        if (sa.physics == 1) PETTO_SENS(3, 1) else PETTO_SENS(3, 0)
+    } else {
+        if (sa.physics == 1) PETTO_SENS(2, 1) else PETTO_SENS(2, 0)
+    }
+#undef PETTO_SENS
     return cudaGetLastError();
 }
 

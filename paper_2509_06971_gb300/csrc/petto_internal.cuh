@@ -120,6 +120,45 @@ struct SweepArgs {
     RedBuf red;
 };
 
+// ---------------------------------------------------------------- batches
+// One problem of a batch of 2D problems that advance together, one launch per sweep
+// (sweep2d_batch).  Device-resident; the host rewrites it between sweep chunks.
+struct BatchInst {
+    Layout L;
+    OpConstF kf;            // FP32 constants, with this problem's a, b, s1
+    OpConst k;              // FP64 constants
+    double a, b, s1;
+    BoxSet boxes;
+    void *u[2];             // state ping-pong buffers
+    void *w;                // APT increment
+    const void *E;          // cell moduli
+    const void *rhs;        // dense right-hand side (refinement correction) or null
+    const int *tile_ptr;    // per-tile CSR of loads for the 32 x 8 tiling
+    const LoadEntry *loads;
+    RedBuf red;             // this problem's partial sums and ticket counter
+    double *res2;           // receives sum R^2 on check sweeps
+    double *ctrl;           // CT_RESTART_AT, CT_DOT of this problem
+    int gx, gy;             // tiles of this problem (32 x 8 nodes each)
+    long long apt_until;    // APT while the sweep index is below this, PT from there on
+};
+
+struct BatchTile {
+    int inst;               // problem
+    int tile;               // tile index inside the problem's own tiling (x fastest)
+};
+
+struct BatchLaunch {
+    const BatchInst *inst;
+    const BatchTile *tiles;       // active problems' tiles first
+    const int *n_active_tiles;    // device word: blocks at or past it return at once
+    const long long *base;        // device word: index of the first sweep of the chunk
+    long long sweep_idx;          // this sweep's offset in the chunk
+    int cur;                      // u[cur] is read, u[1 - cur] written
+    int physics, nrhs, local_dt, want_res, test_dot, adaptive;
+};
+
+cudaError_t launch_sweep2d_batch(const BatchLaunch &p, int ntiles, int precision, cudaStream_t s);
+
 // ---------------------------------------------------------------- reductions
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -191,11 +230,13 @@ __device__ __forceinline__ long long sweep_index(const SweepArgs &A) {
     return A.base_from_ctrl ? reinterpret_cast<const long long *>(A.ctrl)[CT_BASE] + A.sweep_idx : A.sweep_idx;
 }
 
-__device__ __forceinline__ float apt_schedule(const SweepArgs &A) {
-    const long long k = sweep_index(A) - reinterpret_cast<const long long *>(A.ctrl)[CT_RESTART_AT];
+__device__ __forceinline__ float apt_schedule_k(long long k) {
     if (k <= 0) return 0.f;
     const int ki = k < (1 << 30) ? (int)k : (1 << 30);
     return __fdividef((float)(ki - 1), (float)(ki + 2));
+}
+__device__ __forceinline__ float apt_schedule(const SweepArgs &A) {
+    return apt_schedule_k(sweep_index(A) - reinterpret_cast<const long long *>(A.ctrl)[CT_RESTART_AT]);
 }
 
 // Approximate reciprocal (MUFU, ~1 ulp): the local pseudo-time step only scales the update.

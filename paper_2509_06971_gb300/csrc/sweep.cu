@@ -24,6 +24,7 @@
 // with b' = b or b / diag(K) (local pseudo-time step), u read from one buffer and written
 // to the other (ping-pong), w updated in place.  sum R^2 over free DOFs is accumulated in
 // FP64 when requested (the residual norm of Sec. 3.1, for convergence checks).
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 
@@ -263,47 +264,58 @@ __device__ __forceinline__ T ku_thermal_3d(const T (&U)[3][3][3], const T (&Ec)[
 }
 
 // ------------------------------------------------------------- update
-// APT momentum of this sweep: fixed a, or the adaptive-restart schedule read from the
-// device control words (the same value in every thread of every block).
-template <typename T>
-__device__ __forceinline__ T apt_momentum(const SweepArgs &A, const KC<T> &k);
-template <> __device__ __forceinline__ float apt_momentum<float>(const SweepArgs &A, const KC<float> &k) {
-    return A.adaptive ? fminf(k.a, apt_schedule(A)) : k.a;
+// APT momentum of a sweep k sweeps after the last restart: fixed a, or the adaptive
+// schedule min(a, (k-1)/(k+2)) (the same value in every thread of every block).
+template <typename T> __device__ __forceinline__ T momentum_k(int adaptive, T a, long long k);
+template <> __device__ __forceinline__ float momentum_k<float>(int adaptive, float a, long long k) {
+    return adaptive ? fminf(a, apt_schedule_k(k)) : a;
 }
-template <> __device__ __forceinline__ double apt_momentum<double>(const SweepArgs &A, const KC<double> &k) {
-    if (!A.adaptive) return k.a;
-    const long long kk = sweep_index(A) - reinterpret_cast<const long long *>(A.ctrl)[CT_RESTART_AT];
-    if (kk <= 0) return 0.0;
-    const double sched = (double)(kk - 1) / (double)(kk + 2);
-    return sched < k.a ? sched : k.a;
+template <> __device__ __forceinline__ double momentum_k<double>(int adaptive, double a, long long k) {
+    if (!adaptive) return a;
+    if (k <= 0) return 0.0;
+    const double sched = (double)(k - 1) / (double)(k + 2);
+    return sched < a ? sched : a;
+}
+template <typename T>
+__device__ __forceinline__ T apt_momentum(const SweepArgs &A, const KC<T> &k) {
+    return momentum_k<T>(A.adaptive, k.a,
+                         A.adaptive ? sweep_index(A) - reinterpret_cast<const long long *>(A.ctrl)[CT_RESTART_AT] : 0);
 }
 
+// The per-DOF update of one sweep (APT, PT or residual only), with the block's sums of
+// R^2 and R.w (restart test) accumulated in T.
 template <typename T>
 struct Upd {
-    const SweepArgs &A;
     KC<T> k;
     T a_eff;
+    int mode, local_dt, want_res, test_dot;
+    const T *rhs;
     T res, dot;
     __device__ __forceinline__ void apply(int64_t idx_c, bool fixed, T Ku, T F, T diag, T *uo, const T *ui, T *w) {
-        if (A.rhs) F = static_cast<const T *>(A.rhs)[idx_c];
+        if (rhs) F = rhs[idx_c];
         T R = fixed ? T(0) : F - Ku;
-        if (A.want_res) res += R * R;
+        if (want_res) res += R * R;
         const T u = ui[idx_c];
-        if (A.mode == 0) {
-            const T step = A.local_dt ? k.b * fast_rcp(diag) : k.b;
+        if (mode == 0) {
+            const T step = local_dt ? k.b * fast_rcp(diag) : k.b;
             const T wi = w[idx_c];
-            if (A.test_dot) dot += R * wi;
+            if (test_dot) dot += R * wi;
             const T wn = fixed ? T(0) : a_eff * wi + step * R;
             w[idx_c] = wn;
             uo[idx_c] = fixed ? T(0) : u + wn;
-        } else if (A.mode == 1) {
-            const T step = A.local_dt ? k.s1 * fast_rcp(diag) : k.s1;
+        } else if (mode == 1) {
+            const T step = local_dt ? k.s1 * fast_rcp(diag) : k.s1;
             uo[idx_c] = fixed ? T(0) : u + step * R;
         } else {
             w[idx_c] = R;
         }
     }
 };
+template <typename T>
+__device__ __forceinline__ Upd<T> make_upd(const SweepArgs &A, const KC<T> &kc) {
+    return Upd<T>{kc, apt_momentum<T>(A, kc), A.mode, A.local_dt, A.want_res, A.test_dot,
+                  static_cast<const T *>(A.rhs), T(0), T(0)};
+}
 
 // Block totals of sum R^2 and sum R.w, then one deterministic grid reduction: partials
 // of R^2 at [0, nb), of R.w at [nb, 2 nb); the last block writes *res2 and, on a test
@@ -330,69 +342,144 @@ __device__ __forceinline__ void finish_sweep(const SweepArgs &A, double res, dou
 }
 
 // ------------------------------------------------------------- 2D gather kernel
+// One node (i, j) of a 2D sweep: gathers the 3x3 neighbourhood and the 4 cell moduli,
+// evaluates K u and hands each DOF to the update.  Shared by the single-problem kernel and
+// the batched kernel so both run the same arithmetic.
+template <typename T, int PHYS, typename TE>
+__device__ __forceinline__ void sweep2d_node(const Layout &L, const KC<T> &kc, const BoxSet &boxes, int nrhs,
+                                             const T *__restrict__ ui, T *__restrict__ uo, T *__restrict__ w,
+                                             const TE *__restrict__ E, const int *__restrict__ tile_ptr,
+                                             const LoadEntry *__restrict__ loads, int tile, int i, int j,
+                                             Upd<T> &up) {
+    T Ec[2][2];
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+        for (int cx = 0; cx < 2; ++cx) Ec[cy][cx] = (T)__ldg(&E[L.cell(i - 1 + cx, j - 1 + cy, 0)]);
+    const T S = Ec[0][0] + Ec[0][1] + Ec[1][0] + Ec[1][1];
+    const T diag = kc.cdiag * S;
+    const unsigned fm = fixed_mask(boxes, i, j, 0);
+    const int64_t n0 = L.node(i, j, 0);
+    const int l0 = tile_ptr[tile], l1 = tile_ptr[tile + 1];
+    const int ncnt = ((i > 0) + (i < L.nx)) * ((j > 0) + (j < L.ny));
+    for (int r = 0; r < nrhs; ++r) {
+        if (PHYS == 0) {
+            T U[3][3][2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const T *uc = ui + (int64_t)(r * 2 + a) * L.cstride;
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) U[dy][dx][a] = __ldg(&uc[n0 + (dy - 1) * L.SX + (dx - 1)]);
+            }
+            T Ku[2];
+            ku_elastic_2d<T>(U, Ec, kc, Ku);
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int c = r * 2 + a;
+                T F = 0;
+                for (int l = l0; l < l1; ++l)
+                    if (loads[l].node == n0 && loads[l].comp == c) F += load_val<T>(loads[l]);
+                const int64_t idx = (int64_t)c * L.cstride + n0;
+                up.apply(idx, (fm >> a) & 1u, Ku[a], F, diag, uo, ui, w);
+            }
+        } else {
+            T U[3][3];
+            const T *uc = ui + (int64_t)r * L.cstride;
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) U[dy][dx] = __ldg(&uc[n0 + (dy - 1) * L.SX + (dx - 1)]);
+            const T Ku = ku_thermal_2d<T>(U, Ec, kc);
+            T F = kc.src * (T)ncnt;
+            for (int l = l0; l < l1; ++l)
+                if (loads[l].node == n0 && loads[l].comp == r) F += load_val<T>(loads[l]);
+            const int64_t idx = (int64_t)r * L.cstride + n0;
+            up.apply(idx, fm & 1u, Ku, F, diag, uo, ui, w);
+        }
+    }
+}
+
 template <typename T, int PHYS, typename TE = T>
 __global__ void __launch_bounds__(256) sweep2d_gather(const SweepArgs A) {
     const Layout &L = A.L;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const T *__restrict__ ui = static_cast<const T *>(A.u_in);
-    T *__restrict__ uo = static_cast<T *>(A.u_out);
-    T *__restrict__ w = static_cast<T *>(A.w);
-    const TE *__restrict__ E = static_cast<const TE *>(A.E);
     const KC<T> kc = kconst<T>(A);
-    Upd<T> up{A, kc, apt_momentum<T>(A, kc), T(0), T(0)};
-    if (i < L.NX && j < L.NY) {
-        T Ec[2][2];
-#pragma unroll
-        for (int cy = 0; cy < 2; ++cy)
-#pragma unroll
-            for (int cx = 0; cx < 2; ++cx) Ec[cy][cx] = (T)__ldg(&E[L.cell(i - 1 + cx, j - 1 + cy, 0)]);
-        const T S = Ec[0][0] + Ec[0][1] + Ec[1][0] + Ec[1][1];
-        const T diag = kc.cdiag * S;
-        const unsigned fm = fixed_mask(A.boxes, i, j, 0);
-        const int64_t n0 = L.node(i, j, 0);
-        const int tile = blockIdx.x + gridDim.x * blockIdx.y;
-        const int l0 = A.tile_ptr[tile], l1 = A.tile_ptr[tile + 1];
-        const int ncnt = ((i > 0) + (i < L.nx)) * ((j > 0) + (j < L.ny));
-        for (int r = 0; r < A.nrhs; ++r) {
-            if (PHYS == 0) {
-                T U[3][3][2];
-#pragma unroll
-                for (int a = 0; a < 2; ++a) {
-                    const T *uc = ui + (int64_t)(r * 2 + a) * L.cstride;
-#pragma unroll
-                    for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                        for (int dx = 0; dx < 3; ++dx) U[dy][dx][a] = __ldg(&uc[n0 + (dy - 1) * L.SX + (dx - 1)]);
-                }
-                T Ku[2];
-                ku_elastic_2d<T>(U, Ec, kc, Ku);
-#pragma unroll
-                for (int a = 0; a < 2; ++a) {
-                    const int c = r * 2 + a;
-                    T F = 0;
-                    for (int l = l0; l < l1; ++l)
-                        if (A.loads[l].node == n0 && A.loads[l].comp == c) F += load_val<T>(A.loads[l]);
-                    const int64_t idx = (int64_t)c * L.cstride + n0;
-                    up.apply(idx, (fm >> a) & 1u, Ku[a], F, diag, uo, ui, w);
-                }
-            } else {
-                T U[3][3];
-                const T *uc = ui + (int64_t)r * L.cstride;
-#pragma unroll
-                for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                    for (int dx = 0; dx < 3; ++dx) U[dy][dx] = __ldg(&uc[n0 + (dy - 1) * L.SX + (dx - 1)]);
-                const T Ku = ku_thermal_2d<T>(U, Ec, kc);
-                T F = kc.src * (T)ncnt;
-                for (int l = l0; l < l1; ++l)
-                    if (A.loads[l].node == n0 && A.loads[l].comp == r) F += load_val<T>(A.loads[l]);
-                const int64_t idx = (int64_t)r * L.cstride + n0;
-                up.apply(idx, fm & 1u, Ku, F, diag, uo, ui, w);
+    Upd<T> up = make_upd<T>(A, kc);
+    if (i < L.NX && j < L.NY)
+        sweep2d_node<T, PHYS, TE>(L, kc, A.boxes, A.nrhs, static_cast<const T *>(A.u_in), static_cast<T *>(A.u_out),
+                                  static_cast<T *>(A.w), static_cast<const TE *>(A.E), A.tile_ptr, A.loads,
+                                  blockIdx.x + gridDim.x * blockIdx.y, i, j, up);
+    finish_sweep(A, (double)up.res, (double)up.dot, blockIdx.x + (int64_t)gridDim.x * blockIdx.y);
+}
+
+// ------------------------------------------------------------- batched 2D kernel
+// One launch sweeps every active problem of a batch.  Block b takes tile tiles[b] (its
+// problem and the tile's index inside that problem's own 32 x 8 tiling), so each problem
+// sees exactly the blocks, the arithmetic and the reduction order of its own
+// single-problem sweep; the deterministic reduction runs per problem (its own partials,
+// ticket counter, residual slot and restart word).
+template <typename T> __device__ __forceinline__ KC<T> kconst_inst(const BatchInst &I);
+template <> __device__ __forceinline__ KC<float> kconst_inst<float>(const BatchInst &I) {
+    const OpConstF &f = I.kf;
+    return {f.ce_par, f.ce_perp, f.cf_lam, f.cf_mu, f.cdiag, f.ct, f.src, f.a, f.b, f.s1};
+}
+template <> __device__ __forceinline__ KC<double> kconst_inst<double>(const BatchInst &I) {
+    const OpConst &k = I.k;
+    return {k.ce_par, k.ce_perp, k.cf_lam, k.cf_mu, k.cdiag, k.ct, k.src, I.a, I.b, I.s1};
+}
+
+template <typename T, int PHYS>
+__device__ __forceinline__ void sweep2d_batch_tile(const BatchLaunch &P, int t, long long sidx, double *sh) {
+    const BatchTile bt = P.tiles[t];
+    const BatchInst &I = P.inst[bt.inst];
+    const Layout L = I.L;
+    const int gx = I.gx, nb = I.gx * I.gy;
+    const int i = (bt.tile % gx) * 32 + threadIdx.x;
+    const int j = (bt.tile / gx) * 8 + threadIdx.y;
+    const int mode = sidx < I.apt_until ? 0 : 1;
+    const KC<T> kc = kconst_inst<T>(I);
+    const long long since = P.adaptive ? sidx - reinterpret_cast<const long long *>(I.ctrl)[CT_RESTART_AT] : 0;
+    const int test_dot = mode == 0 && P.adaptive ? P.test_dot : 0;
+    Upd<T> up{kc, momentum_k<T>(P.adaptive, kc.a, since), mode, P.local_dt, P.want_res, test_dot,
+              static_cast<const T *>(I.rhs), T(0), T(0)};
+    if (i < L.NX && j < L.NY)
+        sweep2d_node<T, PHYS, T>(L, kc, I.boxes, P.nrhs, static_cast<const T *>(I.u[P.cur]),
+                                 static_cast<T *>(I.u[1 - P.cur]), static_cast<T *>(I.w),
+                                 static_cast<const T *>(I.E), I.tile_ptr, I.loads, bt.tile, i, j, up);
+    // per-problem deterministic reduction, as finish_sweep does for a whole grid
+    if (!P.want_res && !test_dot) return;
+    const double r = P.want_res ? block_sum((double)up.res, sh) : 0.0;
+    const double d = test_dot ? block_sum((double)up.dot, sh) : 0.0;
+    if (block_tid() == 0) I.red.partials[(int64_t)nb + bt.tile] = d;
+    if (publish_partial(r, I.red, bt.tile, nb)) {
+        const double tot = P.want_res ? sum_partials(I.red, 0, nb, sh) : 0.0;
+        const double td = test_dot ? sum_partials(I.red, nb, nb, sh) : 0.0;
+        if (block_tid() == 0) {
+            if (P.want_res) *I.res2 = tot;
+            if (test_dot) {
+                I.ctrl[CT_DOT] = td;
+                if (td < 0.0) reinterpret_cast<long long *>(I.ctrl)[CT_RESTART_AT] = sidx + 1;
             }
+            *I.red.counter = 0u;
         }
     }
-    finish_sweep(A, (double)up.res, (double)up.dot, blockIdx.x + (int64_t)gridDim.x * blockIdx.y);
+}
+
+// Persistent over the active tiles: a grid sized to the resident blocks strides through
+// them, so problems that have finished cost nothing.  The barriers inside the reduction
+// are uniform per block (one tile at a time).
+template <typename T, int PHYS>
+__global__ void __launch_bounds__(256) sweep2d_batch(const BatchLaunch P) {
+    __shared__ double sh[32];
+    const int nact = *P.n_active_tiles;
+    const long long sidx = *P.base + P.sweep_idx;
+    for (int t = blockIdx.x; t < nact; t += gridDim.x) {
+        sweep2d_batch_tile<T, PHYS>(P, t, sidx, sh);
+        __syncthreads();  // the block's shared scratch is reused by the next tile
+    }
 }
 
 // ------------------------------------------------------------- 3D gather kernel
@@ -407,7 +494,7 @@ __global__ void __launch_bounds__(128) sweep3d_gather(const SweepArgs A) {
     T *__restrict__ w = static_cast<T *>(A.w);
     const TE *__restrict__ E = static_cast<const TE *>(A.E);
     const KC<T> kc = kconst<T>(A);
-    Upd<T> up{A, kc, apt_momentum<T>(A, kc), T(0), T(0)};
+    Upd<T> up = make_upd<T>(A, kc);
     const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int l0 = A.tile_ptr[tile], l1 = A.tile_ptr[tile + 1];
     if (i < L.NX && j < L.NY) {
@@ -555,6 +642,30 @@ cudaError_t launch_sweep(const SweepArgs &a0, const Tiling &t, int precision, cu
         }
     }
     return cudaGetLastError();
+}
+
+template <typename T, int PHYS>
+static cudaError_t launch_batch_kernel(const BatchLaunch &p, int ntiles, cudaStream_t s) {
+    // resident blocks of this kernel on the whole GPU (looked up once per kernel)
+    static int resident = 0;
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep2d_batch<T, PHYS>, 256, 0);
+        if (e != cudaSuccess) return e;
+        resident = std::max(1, sms * std::max(1, per_sm));
+    }
+    const int g = std::min(ntiles, resident);
+    sweep2d_batch<T, PHYS><<<g, dim3(32, 8, 1), 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep2d_batch(const BatchLaunch &p, int ntiles, int precision, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    if (precision == 0) return p.physics == 0 ? launch_batch_kernel<float, 0>(p, ntiles, s)
+                                              : launch_batch_kernel<float, 1>(p, ntiles, s);
+    return p.physics == 0 ? launch_batch_kernel<double, 0>(p, ntiles, s) : launch_batch_kernel<double, 1>(p, ntiles, s);
 }
 
 }  // namespace petto

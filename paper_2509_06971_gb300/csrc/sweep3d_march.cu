@@ -918,16 +918,17 @@ __device__ __forceinline__ void march_update(const SweepArgs &A, const MarchCons
                                              float *wb, float *uob, const float *rb, unsigned boxbits, int l0,
                                              int l1, int64_t nbase, float Ku0, float Ku1, float Ku2, float wv0,
                                              float wv1, float wv2, const float (&u)[3], float S8, float &res,
-                                             float &dot) {
+                                             float &dot, const float (&Fpre)[3]) {
     unsigned fm = 0;
     if (boxbits)
         for (int q = 0; q < A.boxes.n; ++q)
             if (((boxbits >> q) & 1u) && zp >= A.boxes.b[q].lo[2] && zp <= A.boxes.b[q].hi[2]) fm |= A.boxes.b[q].mask;
     float F0 = 0.f, F1 = 0.f, F2 = 0.f;
     if (rb) {
-        F0 = rb[off];
-        F1 = rb[cs32 + off];
-        F2 = rb[2 * cs32 + off];
+        // dense right-hand side: prefetched into registers one plane earlier
+        F0 = Fpre[0];
+        F1 = Fpre[1];
+        F2 = Fpre[2];
     } else if (l0 < l1) {
         const int64_t nidx = nbase + off;
         for (int l = l0; l < l1; ++l) {
@@ -978,7 +979,7 @@ __device__ __forceinline__ bool march2_plane(const SweepArgs &A, const MarchCons
                                              unsigned bbA, unsigned bbB, int l0, int l1, int64_t nbA, int64_t nbB,
                                              const float (&Ul)[3][2][3], const float (&El)[3][2],
                                              float (&Uh)[3][2][3], float (&Eh)[3][2], RowCarry &CA, RowCarry &CB,
-                                             float &res, float &dot, bool &bad) {
+                                             float &res, float &dot, bool &bad, float (&FA)[3], float (&FB)[3]) {
     const int tid = ty * 32 + tx;
     const int slot = r1 & (TNS - 1);
     const bool pA = outA && zp >= z0, pB = outB && zp >= z0;
@@ -1047,7 +1048,7 @@ __device__ __forceinline__ bool march2_plane(const SweepArgs &A, const MarchCons
             const float Ku2 = -(oA.Fx2 + oA.Fy2 + oA.Fz2) - (oA.Gxz1 + oA.Gyz1) + xa.z + ya.z + CA.Sz2;
             const float S8 = (El[0][0] + El[0][1]) + (El[1][0] + El[1][1]) + (Eh[0][0] + Eh[0][1]) + (Eh[1][0] + Eh[1][1]);
             march_update(A, K, zp, off, cs32, wbA, uobA, rbA, bbA, l0, l1, nbA, Ku0, Ku1, Ku2, wA0, wA1, wA2, Ul[0][0],
-                         S8, res, dot);
+                         S8, res, dot, FA);
         }
         if (pB) {
             const float Ku0 = -(oB.Fx0 + oB.Fy0 + oB.Fz0) - (oB.Gxy0 + oB.Gxz0) + xb.x + MyA0 + CB.Sz0 + gB0;
@@ -1055,7 +1056,21 @@ __device__ __forceinline__ bool march2_plane(const SweepArgs &A, const MarchCons
             const float Ku2 = -(oB.Fx2 + oB.Fy2 + oB.Fz2) - (oB.Gxz1 + oB.Gyz1) + xb.z + MyA2 + CB.Sz2;
             const float S8 = (El[1][0] + El[1][1]) + (El[2][0] + El[2][1]) + (Eh[1][0] + Eh[1][1]) + (Eh[2][0] + Eh[2][1]);
             march_update(A, K, zp, off, cs32, wbB, uobB, rbB, bbB, l0, l1, nbB, Ku0, Ku1, Ku2, wB0, wB1, wB2, Ul[1][0],
-                         S8, res, dot);
+                         S8, res, dot, FB);
+        }
+    }
+    // dense right-hand side of the next plane, in flight while the next plane's data waits
+    if (rbA && zp + 1 < A.L.NZ) {
+        const int o2 = off + plane32;
+        if (outA) {
+            FA[0] = rbA[o2];
+            FA[1] = rbA[cs32 + o2];
+            FA[2] = rbA[2 * cs32 + o2];
+        }
+        if (outB) {
+            FB[0] = rbB[o2];
+            FB[1] = rbB[cs32 + o2];
+            FB[2] = rbB[2 * cs32 + o2];
         }
     }
     CA = {oA.Fz0 - oA.Hxz0, oA.Fz1 - oA.Hyz0, oA.Fz2 - oA.Hxz1 - oA.Hyz1, oA.Gxz0, oA.Gxz1, oA.Gyz0, oA.Gyz1};
@@ -1157,13 +1172,16 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
     bad = __syncthreads_or(bad);
     RowCarry CA = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, CB = CA;
     float res = 0.f, dot = 0.f;
+    // dense right-hand side registers; the halo plane z0 - 1 (first march step) fetches plane z0
+    float FA[3] = {0.f, 0.f, 0.f}, FB[3] = {0.f, 0.f, 0.f};
 
     for (int zp = z0 - 1; zp < zend && !bad; zp += 2) {
         int r1 = zp + 1 - (z0 - 1);
         if (tid == 0 && issued < nstage) issue(issued);
         issued = min(issued + 1, nstage);
         if (!march2_plane(A, K, zp, z0, r1, su, sw, se, msg, bars, tx, ty, xoff, xoffe, outA, outB, plane32, cs32, wbA,
-                          uobA, rbA, wbB, uobB, rbB, bbA, bbB, l0, l1, nbA, nbB, UA, EA, UB, EB, CA, CB, res, dot, bad))
+                          uobA, rbA, wbB, uobB, rbB, bbA, bbB, l0, l1, nbA, nbB, UA, EA, UB, EB, CA, CB, res, dot, bad,
+                          FA, FB))
             break;
         if (zp + 1 >= zend) break;
         ++r1;
@@ -1171,7 +1189,7 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
         issued = min(issued + 1, nstage);
         if (!march2_plane(A, K, zp + 1, z0, r1, su, sw, se, msg, bars, tx, ty, xoff, xoffe, outA, outB, plane32, cs32,
                           wbA, uobA, rbA, wbB, uobB, rbB, bbA, bbB, l0, l1, nbA, nbB, UB, EB, UA, EA, CA, CB, res, dot,
-                          bad))
+                          bad, FA, FB))
             break;
     }
 

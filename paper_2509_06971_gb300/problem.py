@@ -229,10 +229,7 @@ class Problem:
         rep = C.petto_solve_report()
         st = self._ck(self.lib.petto_pt_solve(self.ctx, ctypes.byref(o), ctypes.byref(rep)),
                       allow=(C.PETTO_OK, C.PETTO_ENOTCONV))
-        return {"sweeps": rep.sweeps, "apt_sweeps": rep.apt_sweeps, "pt_sweeps": rep.pt_sweeps,
-                "res_norm": rep.res_norm, "f_norm": rep.f_norm, "rel_res": rep.rel_res, "r_pde": rep.r_pde,
-                "converged": bool(rep.converged), "fell_back_to_pt": bool(rep.fell_back_to_pt),
-                "status": st}
+        return _report(rep, st)
 
     # --------------------------------------------------------------- design
     def sensitivity(self, out=None, want_field: bool = True):
@@ -293,6 +290,96 @@ class Problem:
 
     def load(self, path: str):
         self._ck(self.lib.petto_load(self.ctx, path.encode()))
+
+
+def _report(rep, st) -> dict:
+    return {"sweeps": rep.sweeps, "apt_sweeps": rep.apt_sweeps, "pt_sweeps": rep.pt_sweeps,
+            "res_norm": rep.res_norm, "f_norm": rep.f_norm, "rel_res": rep.rel_res, "r_pde": rep.r_pde,
+            "converged": bool(rep.converged), "fell_back_to_pt": bool(rep.fell_back_to_pt), "status": st}
+
+
+class Batch:
+    """Many 2D problems advanced together by the batched sweep (petto_batch_* in
+    include/petto.h): one kernel launch per sweep over every problem still iterating.
+    The problems stay usable on their own (design, state, sensitivity); the batch borrows
+    their contexts, so close the batch before the problems."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        self.lib = C.load()
+        n = len(self.problems)
+        arr = (ctypes.c_void_p * n)(*[p.ctx.value for p in self.problems])
+        out = ctypes.c_void_p()
+        st = self.lib.petto_batch_create(n, arr, ctypes.byref(out))
+        if st != C.PETTO_OK:
+            raise C.PettoError(st, "petto_batch_create failed")
+        self.batch = out
+
+    def close(self):
+        if getattr(self, "batch", None):
+            self.lib.petto_batch_destroy(self.batch)
+            self.batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _ck(self, st, allow=(C.PETTO_OK,)):
+        return C.check_batch(self.batch, st, allow)
+
+    def __len__(self):
+        return len(self.problems)
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.petto_batch_launch_count(self.batch))
+
+    def solve_opts(self, mode=C.PETTO_SOLVE_TOL, **kw):
+        n = len(self.problems)
+        arr = (C.petto_solve_opts * n)()
+        for i, p in enumerate(self.problems):
+            arr[i] = p.solve_opts(mode, **kw)
+        return arr
+
+    def solve(self, mode=C.PETTO_SOLVE_TOL, **kw) -> list:
+        """Solve every problem; one report dict per problem (as Problem.solve)."""
+        n = len(self.problems)
+        opts = self.solve_opts(mode, **kw)
+        reps = (C.petto_solve_report * n)()
+        st = self._ck(self.lib.petto_batch_pt_solve(self.batch, opts, reps), allow=(C.PETTO_OK, C.PETTO_ENOTCONV))
+        return [_report(reps[i], st) for i in range(n)]
+
+    def optimize(self, n_steps: int, solve_kw: dict | None = None, pf_kw: dict | None = None):
+        """n_steps PeTTO loops on every problem.  Returns (metrics [n_steps, n, 8] as in
+        Problem.optimize's rows, status)."""
+        n = len(self.problems)
+        so = self.solve_opts(**(solve_kw or {}))
+        po = (C.petto_pf_opts * n)()
+        for i, p in enumerate(self.problems):
+            po[i] = p.pf_opts(**(pf_kw or {}))
+        m = np.zeros((max(1, n_steps), n, 8), dtype=np.float64)
+        st = self._ck(self.lib.petto_batch_optimize(self.batch, int(n_steps), so, po,
+                                                    m.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                      allow=(C.PETTO_OK, C.PETTO_ENOTCONV))
+        return m[:n_steps], st
+
+    def profile(self, enable: bool = True):
+        self._ck(self.lib.petto_batch_profile(self.batch, int(bool(enable))))
+
+    def profile_read(self):
+        """(milliseconds, batch sweeps) of the timed sweep chunks since the last read."""
+        ms = ctypes.c_double(0.0)
+        n = ctypes.c_int64(0)
+        self._ck(self.lib.petto_batch_profile_read(self.batch, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
 
 class PettoCompliance:
