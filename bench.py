@@ -39,6 +39,9 @@ WORKLOADS = {
     "multimat3d_384x192x192_bf16": lambda: W.multimat3d(storage="bf16"),
     "cantilever3d_64x32x32": lambda: W.cantilever3d(64, 32, 32),
 }
+BATCH_WORKLOADS = {
+    "batch2d_48": lambda: W.batch2d(48),
+}
 DEFAULT_WORKLOAD = "cantilever3d_256x128x128"
 METRIC = "APT Gcell-sweeps/s & % HBM roofline; s/design-iter at rel.res 1e-6"
 
@@ -295,11 +298,183 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """Batched workload: 48 independent 2D problems (128x64 .. 1024x512 cells) advanced
+    together, one persistent launch per sweep.  A step is one design iteration of every
+    problem (batched solve to 1e-6, then each problem's sensitivity, update and
+    Cahn-Hilliard step).  The same design iteration run problem by problem through the
+    single-problem path is timed beside it (time-to-design comparison)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2509_06971_gb300 import problem as PR
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    specs = BATCH_WORKLOADS[args.workload]()
+    probs = [PR.Problem(s) for s in specs]
+    batch = PR.Batch(probs)
+    solve_kw = dict(tol=args.tol, max_sweeps=args.max_sweeps, check_every=50)
+    cells = np.array([s.ncells for s in specs], dtype=np.float64)
+    nodes = np.array([s.nnodes for s in specs], dtype=np.float64)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        batch.optimize(1, solve_kw=solve_kw)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(vis.split(",")[local] if vis else str(local))
+    clocks.start()
+    batch.profile(True)
+    batch.profile_read()
+    launches0 = batch.launches
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ms_rows = []
+    for _ in range(args.steps):
+        m, _ = batch.optimize(1, solve_kw=solve_kw)
+        ms_rows.append(m[0])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    launches = batch.launches - launches0
+    kern_ms, kern_n = batch.profile_read()
+    batch.profile(False)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    sweeps = np.array([r[:, 4] for r in ms_rows])          # [steps, n]
+    work = float((sweeps * cells[None, :]).sum())
+    ms_max, tot = aggregate(ms, work, dev, world)
+    value = tot / (ms_max * 1e-3) / 1e9
+    # algorithmic bytes of all batched sweeps in the timed region (state and modulus
+    # fields of each problem for each of its sweeps; refinement right-hand sides not counted)
+    per_sweep = nodes * 4 * 2 * 4 + cells * 4
+    bytes_tot = float((sweeps * per_sweep[None, :]).sum())
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = bytes_tot / (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else None
+
+    # time-to-design against the single-problem path: the same design iteration (same
+    # designs and states) run once batched and once problem by problem
+    snap = [(q.get_design(dtype=np.float32), q.get_state(dtype=np.float32)) for q in probs]
+    alone_probs = [PR.Problem(s) for s in specs]
+    for p, (ph, uh) in zip(alone_probs, snap):
+        p.set_design(ph)
+        p.set_state(uh)
+        p.optimize(1, solve_kw=solve_kw)  # warm-up (graph capture)
+        p.set_design(ph)
+        p.set_state(uh)
+    for q, (ph, uh) in zip(probs, snap):
+        q.set_design(ph)
+        q.set_state(uh)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    mb, _ = batch.optimize(1, solve_kw=solve_kw)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    batch_ms = b0.elapsed_time(b1)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    alone_sweeps = [p.optimize(1, solve_kw=solve_kw)[0][-1]["sweeps"] for p in alone_probs]
+    a1.record(stream)
+    torch.cuda.synchronize()
+    alone_ms = a0.elapsed_time(a1)
+    same_sweeps = [int(x) for x in mb[0][:, 4]] == [int(x) for x in alone_sweeps]
+    for p in alone_probs:
+        p.close()
+
+    # end to end through the public API: designs and states in from pinned host memory,
+    # one batched design iteration, designs and states back out
+    hosts = []
+    for q, s in zip(probs, specs):
+        ph = torch.empty((s.n_phases, s.ncells), dtype=torch.float32, pin_memory=True).numpy()
+        uh = torch.empty((s.ncomp, s.nnodes), dtype=torch.float32, pin_memory=True).numpy()
+        ph[:] = q.get_design(dtype=np.float32)
+        uh[:] = q.get_state(dtype=np.float32)
+        hosts.append((ph, uh))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q, (ph, uh) in zip(probs, hosts):
+        q.set_design(ph)
+        q.set_state(uh)
+    m, _ = batch.optimize(1, solve_kw=solve_kw)
+    for q, (ph, uh) in zip(probs, hosts):
+        ph[:] = q.get_design(dtype=np.float32)
+        uh[:] = q.get_state(dtype=np.float32)
+    torch.cuda.synchronize()
+    e_secs = time.perf_counter() - t0
+    e_work = float((m[0][:, 4] * cells).sum())
+    e_t, e_tot = aggregate(e_secs, e_work, dev, world)
+    hbytes = sum(ph.nbytes + uh.nbytes for ph, uh in hosts)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gcell-sweeps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "instances": len(specs), "cells": int(cells.sum()),
+                   "nodes": int(nodes.sum()), "tol": args.tol, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2" if float(per_sweep.sum()) > 129e6 else "working set fits in L2"},
+        "s_per_design_iter": ms_max * 1e-3 / args.steps,
+        "sweeps_per_design_iter": {"max": float(sweeps.max()), "mean": float(sweeps.mean())},
+        "single_problem_path": {"s_per_design_iter": alone_ms * 1e-3, "batched_s_per_design_iter": batch_ms * 1e-3,
+                                "batched_speedup": alone_ms / batch_ms, "same_sweep_counts": same_sweeps},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "batched apt sweep", "kernel_ms": kern_ms / max(kern_n, 1),
+                     "bytes_per_launch": bytes_tot / max(kern_n, 1), "peak_kind": peak_kind},
+        "e2e": {"value": e_tot / e_t / 1e9, "unit": "Gcell-sweeps/s", "h2d_bytes_per_step": hbytes,
+                "d2h_bytes_per_step": hbytes, "steps": 1},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    batch.close()
+    for q in probs:
+        q.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_sweeps_only(args):
     """N APT sweeps from a seeded state: few launches, for ncu captures of the sweep."""
     import torch
     from paper_2509_06971_gb300 import problem as PR
     torch.cuda.set_device(0)
+    if args.workload in BATCH_WORKLOADS:
+        # batched sweeps from the zero state: a tolerance no problem reaches, checks every 2
+        specs = BATCH_WORKLOADS[args.workload]()
+        probs = [PR.Problem(s) for s in specs]
+        batch = PR.Batch(probs)
+        batch.solve(tol=1e-30, max_sweeps=2, check_every=2, refine=False)
+        torch.cuda.synchronize()
+        batch.profile(True)
+        batch.profile_read()
+        batch.solve(tol=1e-30, max_sweeps=args.sweeps_only, check_every=2, refine=False)
+        ms, n = batch.profile_read()
+        nodes = sum(s.nnodes for s in specs)
+        cells = sum(s.ncells for s in specs)
+        per = ms / max(n, 1)
+        print(json.dumps({"workload": args.workload, "sweeps": n, "ms_per_sweep": per,
+                          "GBps": (nodes * 32 + cells * 4) / (per * 1e-3) / 1e9,
+                          "Gcell_sweeps_per_s": cells / (per * 1e-3) / 1e9}))
+        batch.close()
+        for p in probs:
+            p.close()
+        return 0
     spec = WORKLOADS[args.workload]()
     prob = PR.Problem(spec)
     u0 = W.random_state(spec, seed=1, scale=1e-3).astype("float32")
@@ -324,7 +499,7 @@ def main():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--max-sweeps", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -334,7 +509,12 @@ def main():
     if args.sweeps_only:
         return run_sweeps_only(args)
     if args.impl == "reference":
+        if args.workload in BATCH_WORKLOADS:
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times single-problem workloads"}))
+            return 0
         return run_reference(args)
+    if args.workload in BATCH_WORKLOADS:
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -1394,8 +1394,8 @@ struct petto_batch {
     BatchInst *d_inst = nullptr;
     std::vector<BatchTile> tiles;   // active problems' tiles first
     BatchTile *d_tiles = nullptr;
-    int ntiles = 0;
-    int *d_nact = nullptr;          // device word: number of active tiles
+    int ntiles = 0;                 // all tiles
+    int nact = 0;                   // tiles of the active problems (the launch grid)
     long long *d_base = nullptr;    // device word: first sweep index of the chunk
     double *d_res = nullptr;        // sum R^2 of each problem's last check sweep
     std::vector<int> active;
@@ -1403,6 +1403,7 @@ struct petto_batch {
     int64_t launches = 0;
     struct Graph {
         int len, cur, adaptive, local_dt;
+        int nact;  // grid the graph's launches currently have
         cudaGraphExec_t exec;
     };
     std::vector<Graph> graphs;
@@ -1503,14 +1504,13 @@ petto_status batch_upload(petto_batch *b) {
             const int nt = b->inst[i].gx * b->inst[i].gy;
             for (int t = 0; t < nt; ++t) b->tiles.push_back(BatchTile{(int)i, t});
         }
-    int nact = 0;
+    b->nact = 0;
     for (size_t i = 0; i < b->inst.size(); ++i)
-        if (b->active[i]) nact += b->inst[i].gx * b->inst[i].gy;
+        if (b->active[i]) b->nact += b->inst[i].gx * b->inst[i].gy;
     BCK(cudaMemcpyAsync(b->d_tiles, b->tiles.data(), sizeof(BatchTile) * b->tiles.size(), cudaMemcpyHostToDevice,
                         b->stream));
     BCK(cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(BatchInst) * b->inst.size(), cudaMemcpyHostToDevice,
                         b->stream));
-    BCK(cudaMemcpyAsync(b->d_nact, &nact, sizeof(int), cudaMemcpyHostToDevice, b->stream));
     // the host copies above are pageable: make sure they were taken before the mirrors change
     BCK(cudaStreamSynchronize(b->stream));
     return PETTO_OK;
@@ -1520,7 +1520,6 @@ BatchLaunch batch_launch(petto_batch *b, const petto_solve_opts *o, long long j,
     BatchLaunch p{};
     p.inst = b->d_inst;
     p.tiles = b->d_tiles;
-    p.n_active_tiles = b->d_nact;
     p.base = b->d_base;
     p.sweep_idx = j;
     p.cur = (b->cur + (int)j) & 1;
@@ -1533,7 +1532,24 @@ BatchLaunch batch_launch(petto_batch *b, const petto_solve_opts *o, long long j,
     return p;
 }
 
-// len sweeps of every active problem from u[cur]: one graph per (len, cur, momentum, step) kind
+// capture len batched sweeps from u[cur] over the active tiles
+petto_status batch_capture(petto_batch *b, const petto_solve_opts *o, int len, cudaGraph_t *graph) {
+    *graph = nullptr;
+    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t el = cudaSuccess;
+    for (int j = 0; j < len && el == cudaSuccess; ++j)
+        el = launch_sweep2d_batch(batch_launch(b, o, j, len), b->nact, b->precision, b->stream);
+    cudaError_t ec = cudaStreamEndCapture(b->stream, graph);
+    if (el != cudaSuccess || ec != cudaSuccess) {
+        if (*graph) cudaGraphDestroy(*graph);
+        *graph = nullptr;
+        BCK(el != cudaSuccess ? el : ec);
+    }
+    return PETTO_OK;
+}
+
+// len sweeps of every active problem from u[cur]: one graph per (len, cur, momentum, step)
+// kind, its launch grids updated in place when the set of active problems changes
 petto_status batch_chunk(petto_batch *b, const petto_solve_opts *o, long long base, int len) {
     set_word_kernel<<<1, 1, 0, b->stream>>>(b->d_base, base);
     BCK(cudaGetLastError());
@@ -1541,24 +1557,35 @@ petto_status batch_chunk(petto_batch *b, const petto_solve_opts *o, long long ba
     petto_batch::Graph *ge = nullptr;
     for (auto &g : b->graphs)
         if (g.len == len && g.cur == b->cur && g.adaptive == adaptive && g.local_dt == o->local_dt) ge = &g;
-    if (!ge) {
+    if (!ge || ge->nact != b->nact) {
         cudaGraph_t graph = nullptr;
-        BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t el = cudaSuccess;
-        for (int j = 0; j < len && el == cudaSuccess; ++j)
-            el = launch_sweep2d_batch(batch_launch(b, o, j, len), b->ntiles, b->precision, b->stream);
-        cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
-        if (el != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            BCK(el);
+        petto_status st = batch_capture(b, o, len, &graph);
+        if (st != PETTO_OK) return st;
+        bool updated = false;
+        if (ge) {
+            cudaGraphExecUpdateResultInfo info{};
+            updated = cudaGraphExecUpdate(ge->exec, graph, &info) == cudaSuccess;
+            if (!updated) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(ge->exec);
+                ge->exec = nullptr;
+            }
         }
-        BCK(ec);
-        cudaGraphExec_t exec = nullptr;
-        cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        if (!updated) {
+            cudaGraphExec_t exec = nullptr;
+            cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+            if (ei != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                BCK(ei);
+            }
+            if (ge) ge->exec = exec;
+            else {
+                b->graphs.push_back(petto_batch::Graph{len, b->cur, adaptive, o->local_dt, b->nact, exec});
+                ge = &b->graphs.back();
+            }
+        }
+        ge->nact = b->nact;
         cudaGraphDestroy(graph);
-        BCK(ei);
-        b->graphs.push_back(petto_batch::Graph{len, b->cur, adaptive, o->local_dt, exec});
-        ge = &b->graphs.back();
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (b->profiling) {
@@ -1638,7 +1665,7 @@ petto_status petto_batch_create(int n, petto_ctx *const *ctxs, petto_batch **out
     }
     if (cudaMalloc(&b->d_inst, sizeof(BatchInst) * n) != cudaSuccess ||
         cudaMalloc(&b->d_tiles, sizeof(BatchTile) * b->ntiles) != cudaSuccess ||
-        cudaMalloc(&b->d_nact, sizeof(int)) != cudaSuccess || cudaMalloc(&b->d_base, sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&b->d_base, sizeof(long long)) != cudaSuccess ||
         cudaMalloc(&b->d_res, sizeof(double) * n) != cudaSuccess)
         return cleanup(PETTO_ENOMEM, "device memory");
     if (batch_refresh(b) != PETTO_OK) return cleanup(PETTO_ECUDA, "tiling");
@@ -1656,7 +1683,7 @@ void petto_batch_destroy(petto_batch *b) {
     }
     for (auto e : b->ev_free) cudaEventDestroy(e);
     if (b->ev) cudaEventDestroy(b->ev);
-    void *bufs[] = {b->d_inst, b->d_tiles, b->d_nact, b->d_base, b->d_res};
+    void *bufs[] = {b->d_inst, b->d_tiles, b->d_base, b->d_res};
     for (void *p : bufs)
         if (p) cudaFree(p);
     delete b;

@@ -149,14 +149,14 @@ struct BatchTile {
 
 struct BatchLaunch {
     const BatchInst *inst;
-    const BatchTile *tiles;       // active problems' tiles first
-    const int *n_active_tiles;    // device word: blocks at or past it return at once
+    const BatchTile *tiles;       // active problems' tiles first; one block per active tile
     const long long *base;        // device word: index of the first sweep of the chunk
     long long sweep_idx;          // this sweep's offset in the chunk
     int cur;                      // u[cur] is read, u[1 - cur] written
     int physics, nrhs, local_dt, want_res, test_dot, adaptive;
 };
 
+// ntiles: the active tiles (the leading entries of p.tiles)
 cudaError_t launch_sweep2d_batch(const BatchLaunch &p, int ntiles, int precision, cudaStream_t s);
 
 // ---------------------------------------------------------------- reductions

@@ -468,18 +468,13 @@ __device__ __forceinline__ void sweep2d_batch_tile(const BatchLaunch &P, int t, 
     }
 }
 
-// Persistent over the active tiles: a grid sized to the resident blocks strides through
-// them, so problems that have finished cost nothing.  The barriers inside the reduction
-// are uniform per block (one tile at a time).
+// One block per active tile (the grid is the active tile count, set by the host whenever
+// problems finish), so finished problems cost nothing and every block's latency overlaps
+// with the other blocks resident on the SM.
 template <typename T, int PHYS>
-__global__ void __launch_bounds__(256) sweep2d_batch(const BatchLaunch P) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) sweep2d_batch(const BatchLaunch P) {
     __shared__ double sh[32];
-    const int nact = *P.n_active_tiles;
-    const long long sidx = *P.base + P.sweep_idx;
-    for (int t = blockIdx.x; t < nact; t += gridDim.x) {
-        sweep2d_batch_tile<T, PHYS>(P, t, sidx, sh);
-        __syncthreads();  // the block's shared scratch is reused by the next tile
-    }
+    sweep2d_batch_tile<T, PHYS>(P, blockIdx.x, *P.base + P.sweep_idx, sh);
 }
 
 // ------------------------------------------------------------- 3D gather kernel
@@ -646,18 +641,7 @@ cudaError_t launch_sweep(const SweepArgs &a0, const Tiling &t, int precision, cu
 
 template <typename T, int PHYS>
 static cudaError_t launch_batch_kernel(const BatchLaunch &p, int ntiles, cudaStream_t s) {
-    // resident blocks of this kernel on the whole GPU (looked up once per kernel)
-    static int resident = 0;
-    if (resident == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep2d_batch<T, PHYS>, 256, 0);
-        if (e != cudaSuccess) return e;
-        resident = std::max(1, sms * std::max(1, per_sm));
-    }
-    const int g = std::min(ntiles, resident);
-    sweep2d_batch<T, PHYS><<<g, dim3(32, 8, 1), 0, s>>>(p);
+    sweep2d_batch<T, PHYS><<<ntiles, dim3(32, 8, 1), 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -1078,6 +1078,9 @@ __device__ __forceinline__ bool march2_plane(const SweepArgs &A, const MarchCons
     return true;
 }
 
+// RHS: a dense right-hand side replaces the loads (refinement corrections); compiled
+// separately so that the plain sweep carries none of its loads or checks.
+template <bool RHS>
 __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_constant__ SweepArgs A,
                                                               const __grid_constant__ CUtensorMap tmu,
                                                               const __grid_constant__ CUtensorMap tmw,
@@ -1127,7 +1130,7 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
     const int64_t cbase = (int64_t)c0 * L.cstride;
     float *w = static_cast<float *>(A.w) + cbase;
     float *uo = A.u_out ? static_cast<float *>(A.u_out) + cbase : nullptr;
-    const float *rh = A.rhs ? static_cast<const float *>(A.rhs) + cbase : nullptr;
+    const float *rh = RHS ? static_cast<const float *>(A.rhs) + cbase : nullptr;
     float *wbA = w + nbA, *wbB = w + nbB;
     float *uobA = uo ? uo + nbA : nullptr, *uobB = uo ? uo + nbB : nullptr;
     const float *rbA = rh ? rh + nbA : nullptr, *rbB = rh ? rh + nbB : nullptr;
@@ -1235,7 +1238,9 @@ cudaError_t march3d_prepare() {
         e = cudaFuncSetAttribute(sweep3d_march_tma<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  TmaGeom<16>::SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sweep3d_march_tma2, cudaFuncAttributeMaxDynamicSharedMemorySize, R2SMEM);
+        e = cudaFuncSetAttribute(sweep3d_march_tma2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, R2SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep3d_march_tma2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, R2SMEM);
     return e;
 }
 
@@ -1257,7 +1262,8 @@ cudaError_t launch_march3d_tma2(const SweepArgs &a, const Tiling &t, const TmaMa
     for (int r = 0; r < a.nrhs; ++r) {
         SweepArgs ar = a;
         ar.rhs_index = r;
-        sweep3d_march_tma2<<<dim3(t.gx, t.gy, t.gz), dim3(32, R2TY), R2SMEM, s>>>(ar, *mu, m.w, m.e);
+        if (a.rhs) sweep3d_march_tma2<true><<<dim3(t.gx, t.gy, t.gz), dim3(32, R2TY), R2SMEM, s>>>(ar, *mu, m.w, m.e);
+        else sweep3d_march_tma2<false><<<dim3(t.gx, t.gy, t.gz), dim3(32, R2TY), R2SMEM, s>>>(ar, *mu, m.w, m.e);
     }
     return cudaGetLastError();
 }
