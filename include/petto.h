@@ -263,10 +263,18 @@ petto_status petto_profile_read(petto_ctx *ctx, double *sweep_ms, int64_t *sweep
 /* Sweep-kernel autotuner: times every kernel variant and tile shape that applies to this
  * problem (for 3D elasticity in FP32: TMA-staged marching kernels with one or two owner
  * rows per thread, 32x16 tiles, the register-staged kernel, several z-segment lengths;
- * otherwise the node-gather kernel's block shapes) for n APT sweeps each from the current
- * state, restores the state, and keeps the fastest.  report (may be NULL) receives a JSON
- * object of milliseconds per sweep for each candidate.  Uses temporary device memory. */
+ * in 2D with one load case: the y-marching kernel with several rows per warp; always the
+ * node-gather kernel's block shapes) for n APT sweeps each from the current state,
+ * restores the state, and keeps the fastest.  report (may be NULL) receives a JSON object
+ * of milliseconds per sweep for each candidate, keyed by the names petto_select_kernel
+ * takes.  Uses temporary device memory. */
 petto_status petto_autotune(petto_ctx *ctx, int n, char *report, int report_len);
+
+/* Selects the sweep kernel by the name the autotuner reports ("tma2/zs16", "march2d/ly8",
+ * "gather/32x8", ...); a kernel name alone ("tma2", "march2d", "gather") selects its first
+ * listed variant (the default parameters).  PETTO_EINVAL when no such kernel applies.
+ * Every variant computes the same sweep; they differ in tiling and summation order. */
+petto_status petto_select_kernel(petto_ctx *ctx, const char *name);
 
 /* ---------------------------------------------------------------- batches
  * Many independent 2D problems advanced together (the paper solves one design problem at a
@@ -275,13 +283,16 @@ petto_status petto_autotune(petto_ctx *ctx, int n, char *report, int report_len)
  * chunk of check_every sweeps is replayed as one CUDA graph, and the check residuals of
  * all problems are read with one copy.  Each problem keeps the iteration of
  * petto_pt_solve: its own checks, momentum restarts, divergence guard, PT fallback and
- * FP32 iterative refinement, with the same kernel arithmetic and reduction order, so it
- * ends in the same state as when solved alone. */
+ * FP32 iterative refinement, with the same kernel arithmetic and reduction order as the
+ * 2D marching kernel, so it ends in the same state as when solved alone on that kernel. */
 typedef struct petto_batch petto_batch;
 
 /* Borrows n contexts (they must outlive the batch): 2D, one load case (nrhs 1), and a
- * common precision and physics, else PETTO_EUNSUPPORTED.  Contexts whose sweep tiling was
- * changed by petto_autotune are set back to the 32 x 8 tiling the batched kernel uses.
+ * common precision and physics, else PETTO_EUNSUPPORTED.  The batched sweep is the 2D
+ * y-marching kernel: each context keeps its marching variant ("march2d/ly*", chosen by
+ * petto_select_kernel or petto_autotune), and a context on another sweep kernel is
+ * switched to the default "march2d" variant (a problem matches its solve alone bit for
+ * bit when solved alone with the same variant).
  * During batch calls the contexts' work runs on the first context's stream (joined to the
  * others' streams with events).  *out is NULL on failure. */
 petto_status petto_batch_create(int n, petto_ctx *const *ctxs, petto_batch **out);

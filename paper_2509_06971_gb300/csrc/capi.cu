@@ -81,6 +81,12 @@ struct petto_ctx {
     RedBuf red() const { return RedBuf{partials, counter}; }
 };
 
+// The 2D marching kernel: one load case, 32-bit element offsets within a field.
+static bool march2d_ok(const petto_ctx *ctx) {
+    return ctx->L.dim == 2 && ctx->nrhs == 1 && (int64_t)ctx->ncomp * ctx->L.cstride < (int64_t(1) << 31) &&
+           ctx->L.estride < (int64_t(1) << 31);
+}
+
 static void clear_graphs(petto_ctx *ctx) {
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     ctx->graphs.clear();
@@ -1462,13 +1468,16 @@ struct StreamJoin {
 // re-read each problem's buffers and tiling from its context (a context may have been
 // re-tiled or used alone since the last batch call) and bring every state to u[cur]
 petto_status batch_refresh(petto_batch *b) {
+    int ntiles = 0;
     for (size_t i = 0; i < b->ctx.size(); ++i) {
         petto_ctx *ctx = b->ctx[i];
-        const Tiling g = gather_tiling(ctx->L);
-        if (ctx->tiling.kind != 0 || ctx->tiling.bx != g.bx || ctx->tiling.by != g.by) {
-            petto_status st = set_tiling(ctx, g);
+        if (!march2d_ok(ctx)) return bfail(b, PETTO_EUNSUPPORTED, "a problem is too large for the batched sweep");
+        if (ctx->tiling.kind != 5) {
+            petto_status st = set_tiling(ctx, march2d_tiling(ctx->L));
             if (st != PETTO_OK) return bfail(b, st, ctx->err);
         }
+        const Tiling &g = ctx->tiling;
+        ntiles += g.gx * g.gy;
         if (ctx->cur != b->cur) {
             BCK(cudaMemcpyAsync(ctx->u[b->cur], ctx->u[ctx->cur], ctx->node_bytes(), cudaMemcpyDeviceToDevice,
                                 b->stream));
@@ -1490,8 +1499,19 @@ petto_status batch_refresh(petto_batch *b) {
         I.ctrl = ctx->ctrl;
         I.gx = g.gx;
         I.gy = g.gy;
+        I.ly = g.ly;
         I.res2 = b->d_res + i;
     }
+    if (ntiles > b->ntiles) {
+        BCK(cudaStreamSynchronize(b->stream));
+        // the captured chunk graphs hold the old tile list's address
+        for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+        b->graphs.clear();
+        if (b->d_tiles) BCK(cudaFree(b->d_tiles));
+        b->d_tiles = nullptr;
+        BCK(cudaMalloc(&b->d_tiles, sizeof(BatchTile) * ntiles));
+    }
+    b->ntiles = ntiles;
     return PETTO_OK;
 }
 
@@ -1659,12 +1679,7 @@ petto_status petto_batch_create(int n, petto_ctx *const *ctxs, petto_batch **out
     };
     if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) return cleanup(PETTO_ECUDA, "event");
     b->inst.assign(n, BatchInst{});
-    for (int i = 0; i < n; ++i) {
-        const Tiling g = gather_tiling(ctxs[i]->L);
-        b->ntiles += g.gx * g.gy;
-    }
     if (cudaMalloc(&b->d_inst, sizeof(BatchInst) * n) != cudaSuccess ||
-        cudaMalloc(&b->d_tiles, sizeof(BatchTile) * b->ntiles) != cudaSuccess ||
         cudaMalloc(&b->d_base, sizeof(long long)) != cudaSuccess ||
         cudaMalloc(&b->d_res, sizeof(double) * n) != cudaSuccess)
         return cleanup(PETTO_ENOMEM, "device memory");
@@ -1963,10 +1978,14 @@ petto_status petto_load(petto_ctx *ctx, const char *path) {
     return refresh_material(ctx);
 }
 
-// Time each sweep-kernel variant that applies to this problem for n sweeps from the
-// current state (restored afterwards) and keep the fastest.
-petto_status petto_autotune(petto_ctx *ctx, int n, char *report, int report_len) {
-    if (!ctx || n < 1) return fail(ctx, PETTO_EINVAL, "bad arguments");
+}  // extern "C"
+
+namespace {
+
+// The sweep-kernel variants that apply to a problem, by name: the 3D marching kernels
+// (TMA two-row, TMA one-row 32x8 / 32x16, register-staged) x z-segment lengths, the 2D
+// y-marching kernel x rows per warp, and the node-gather kernel x block shapes.
+std::vector<std::pair<std::string, Tiling>> kernel_candidates(const petto_ctx *ctx) {
     std::vector<std::pair<std::string, Tiling>> cand;
     const Layout &L = ctx->L;
     if (L.dim == 3 && ctx->physics == 0 && ctx->precision == PETTO_F32) {
@@ -1994,19 +2013,46 @@ petto_status petto_autotune(petto_ctx *ctx, int n, char *report, int report_len)
             march3d_tiling(L, t);
             cand.emplace_back("v1/zs" + std::to_string(t.zs), t);
         }
-    } else {
-        for (auto bxby : {std::make_pair(32, 8), std::make_pair(64, 4), std::make_pair(128, 2), std::make_pair(16, 16),
-                          std::make_pair(32, 4)}) {
-            Tiling t = gather_tiling(L);
-            if (L.dim == 3 && bxby.first * bxby.second > 128) continue;
-            t.bx = t.ox = bxby.first;
-            t.by = t.oy = bxby.second;
-            t.gx = (L.NX + t.ox - 1) / t.ox;
-            t.gy = (L.NY + t.oy - 1) / t.oy;
-            t.gz = (L.NZ + t.zs - 1) / t.zs;
-            cand.emplace_back("gather/" + std::to_string(t.bx) + "x" + std::to_string(t.by), t);
-        }
+        return cand;
     }
+    if (march2d_ok(ctx))
+        for (int ly : {0, 4, 8, 16}) {
+            const Tiling t = march2d_tiling(L, ly);
+            cand.emplace_back("march2d/ly" + std::to_string(t.ly), t);
+        }
+    for (auto bxby : {std::make_pair(32, 8), std::make_pair(64, 4), std::make_pair(128, 2), std::make_pair(16, 16),
+                      std::make_pair(32, 4)}) {
+        Tiling t = gather_tiling(L);
+        if (L.dim == 3 && bxby.first * bxby.second > 128) continue;
+        t.bx = t.ox = bxby.first;
+        t.by = t.oy = bxby.second;
+        t.gx = (L.NX + t.ox - 1) / t.ox;
+        t.gy = (L.NY + t.oy - 1) / t.oy;
+        t.gz = (L.NZ + t.zs - 1) / t.zs;
+        cand.emplace_back("gather/" + std::to_string(t.bx) + "x" + std::to_string(t.by), t);
+    }
+    return cand;
+}
+
+}  // namespace
+
+extern "C" {
+
+petto_status petto_select_kernel(petto_ctx *ctx, const char *name) {
+    if (!ctx || !name) return fail(ctx, PETTO_EINVAL, "null argument");
+    const std::string want(name);
+    for (auto &c : kernel_candidates(ctx)) {
+        // "march2d" or "tma2" alone: the first (default-parameter) entry of that kernel
+        if (c.first == want || c.first.compare(0, want.size() + 1, want + "/") == 0) return set_tiling(ctx, c.second);
+    }
+    return fail(ctx, PETTO_EINVAL, "no sweep kernel named " + want + " applies to this problem");
+}
+
+// Time each sweep-kernel variant that applies to this problem for n sweeps from the
+// current state (restored afterwards) and keep the fastest.
+petto_status petto_autotune(petto_ctx *ctx, int n, char *report, int report_len) {
+    if (!ctx || n < 1) return fail(ctx, PETTO_EINVAL, "bad arguments");
+    const std::vector<std::pair<std::string, Tiling>> cand = kernel_candidates(ctx);
     // keep the state: u (current) and w
     void *su = nullptr, *sw = nullptr;
     CK(cudaMalloc(&su, ctx->node_bytes()));

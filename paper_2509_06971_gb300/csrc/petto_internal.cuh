@@ -133,12 +133,13 @@ struct BatchInst {
     void *w;                // APT increment
     const void *E;          // cell moduli
     const void *rhs;        // dense right-hand side (refinement correction) or null
-    const int *tile_ptr;    // per-tile CSR of loads for the 32 x 8 tiling
+    const int *tile_ptr;    // per-tile CSR of loads for the marching tiling
     const LoadEntry *loads;
     RedBuf red;             // this problem's partial sums and ticket counter
     double *res2;           // receives sum R^2 on check sweeps
     double *ctrl;           // CT_RESTART_AT, CT_DOT of this problem
-    int gx, gy;             // tiles of this problem (32 x 8 nodes each)
+    int gx, gy;             // tiles of this problem (2D marching tiling: 30 x M2W*ly nodes)
+    int ly;                 // output rows per warp
     long long apt_until;    // APT while the sweep index is below this, PT from there on
 };
 
@@ -281,7 +282,9 @@ struct Tiling {
     int zs;            // nodes per tile in z (3D), 1 in 2D
     int gx, gy, gz;    // tiles per axis
     int ox, oy;        // output nodes per tile in x, y (== bx, by for gather kernels)
-    int kind;          // 0 = gather kernel, 1 = z-marching 3D kernel
+    int kind;          // 0 gather, 1 3D z-marching (register-staged), 2/3 3D TMA one row per
+                       // thread (32x8 / 32x16), 4 3D TMA two rows per thread, 5 2D y-marching
+    int ly;            // kind 5: output rows per warp (a block's warps take consecutive segments)
     __host__ int tile_of(int i, int j, int k) const {
         return (i / ox) + gx * ((j / oy) + gy * (k / zs));
     }
@@ -292,6 +295,10 @@ struct Tiling {
 // combination uses the node-gather kernels.
 Tiling choose_tiling(const Layout &L, int physics, int precision, int nrhs);
 Tiling gather_tiling(const Layout &L);
+// 2D y-marching tiling: blocks of 32 x M2W threads, 30 output columns per warp and ly rows
+// per warp (ly = 0: chosen from the grid size)
+Tiling march2d_tiling(const Layout &L, int ly = 0);
+constexpr int M2W = 4;  // warps per block of the 2D marching kernel
 cudaError_t launch_residual64(const SweepArgs &a, const Tiling &gather, cudaStream_t s);
 void march3d_tiling(const Layout &L, Tiling &t);
 cudaError_t launch_march3d(const SweepArgs &a, const Tiling &t, cudaStream_t s);

@@ -310,6 +310,23 @@ struct Upd {
             w[idx_c] = R;
         }
     }
+    // the same update with u and w (APT) already in registers
+    __device__ __forceinline__ void apply_v(int64_t idx_c, bool fixed, T Ku, T F, T diag, T u, T wi, T *uo, T *w) {
+        T R = fixed ? T(0) : F - Ku;
+        if (want_res) res += R * R;
+        if (mode == 0) {
+            const T step = local_dt ? k.b * fast_rcp(diag) : k.b;
+            if (test_dot) dot += R * wi;
+            const T wn = fixed ? T(0) : a_eff * wi + step * R;
+            w[idx_c] = wn;
+            uo[idx_c] = fixed ? T(0) : u + wn;
+        } else if (mode == 1) {
+            const T step = local_dt ? k.s1 * fast_rcp(diag) : k.s1;
+            uo[idx_c] = fixed ? T(0) : u + step * R;
+        } else {
+            w[idx_c] = R;
+        }
+    }
 };
 template <typename T>
 __device__ __forceinline__ Upd<T> make_upd(const SweepArgs &A, const KC<T> &kc) {
@@ -343,8 +360,8 @@ __device__ __forceinline__ void finish_sweep(const SweepArgs &A, double res, dou
 
 // ------------------------------------------------------------- 2D gather kernel
 // One node (i, j) of a 2D sweep: gathers the 3x3 neighbourhood and the 4 cell moduli,
-// evaluates K u and hands each DOF to the update.  Shared by the single-problem kernel and
-// the batched kernel so both run the same arithmetic.
+// evaluates K u and hands each DOF to the update (multi-load-case 2D sweeps and the
+// autotuner's alternative to the marching kernel below).
 template <typename T, int PHYS, typename TE>
 __device__ __forceinline__ void sweep2d_node(const Layout &L, const KC<T> &kc, const BoxSet &boxes, int nrhs,
                                              const T *__restrict__ ui, T *__restrict__ uo, T *__restrict__ w,
@@ -415,6 +432,202 @@ __global__ void __launch_bounds__(256) sweep2d_gather(const SweepArgs A) {
     finish_sweep(A, (double)up.res, (double)up.dot, blockIdx.x + (int64_t)gridDim.x * blockIdx.y);
 }
 
+// ------------------------------------------------------------- 2D y-marching kernel
+// Each warp owns 32 node columns (the lane's column i = 30 * bx - 1 + lane) and marches up
+// ly rows.  At row j a lane evaluates once the terms whose lower-left corner is its node:
+// the x-edge to (i+1, j), the y-edge to (i, j+1) and the face of cell (i, j), and
+// distributes their forces: -fx - fy - G to itself, fx + H to (i+1, j) (shuffled up one
+// lane), fy - H to (i, j+1) (kept in registers for the next row) and G to (i+1, j+1)
+// (shuffled, then kept).  Neighbour values of column i+1 and cell column i-1 come by warp
+// shuffles, the next rows by loads issued one row ahead; no shared memory, no barriers.
+// Lanes 1..30 produce output (lanes 0 and 31 are the halo), and each warp starts one row
+// early to receive the messages from below.
+template <typename T, typename TE>
+struct M2View {
+    Layout L;
+    KC<T> kc;
+    const BoxSet *boxes;
+    const T *ui;
+    T *uo;
+    T *w;
+    const TE *E;
+    const T *rhs;
+    const int *tile_ptr;
+    const LoadEntry *loads;
+    int gx, ly;
+};
+
+template <typename T, int PHYS, typename TE, int LY>
+__device__ __forceinline__ void march2d_tile(const M2View<T, TE> &V, int tile, Upd<T> &up) {
+    constexpr int C = PHYS == 0 ? 2 : 1;
+    constexpr unsigned FULL = 0xffffffffu;
+    const Layout &L = V.L;
+    const KC<T> &k = V.kc;
+    const int lane = threadIdx.x;
+    const int bxi = tile % V.gx, byi = tile / V.gx;
+    const int i = bxi * 30 - 1 + lane;
+    const int y0 = (byi * M2W + (int)threadIdx.y) * LY;
+    if (y0 >= L.NY) return;  // warp-uniform
+    const int yend = min(y0 + LY, L.NY);
+    const bool ucol = i >= -1 && i <= L.NX;      // node column inside the zero ring
+    const bool ecol = i >= -1 && i <= L.nx;      // cell column inside the zero ring
+    const bool out = lane >= 1 && lane <= 30 && i < L.NX;
+    const int l0 = V.tile_ptr[tile], l1 = V.tile_ptr[tile + 1];
+    // 32-bit offsets (a 2D field has fewer than 2^31 elements per component pair; checked
+    // when the kernel is selected)
+    const int cs = (int)L.cstride, SX = (int)L.SX, CXp = (int)L.CX;
+    const int ncol = i + OX, ecolo = i + OX;
+    // supports whose x-range holds this column; their y-ranges are tested per row
+    unsigned bbits = 0;
+    for (int q = 0; q < V.boxes->n; ++q)
+        if (i >= V.boxes->b[q].lo[0] && i <= V.boxes->b[q].hi[0]) bbits |= 1u << q;
+    auto ld_u = [&](int j, T (&v)[C]) {
+        const bool ok = ucol && j >= -1 && j <= L.NY;
+        const int n = ok ? (j + 1) * SX + ncol : 0;
+#pragma unroll
+        for (int c = 0; c < C; ++c) v[c] = ok ? __ldg(&V.ui[c * cs + n]) : T(0);
+    };
+    auto ld_e = [&](int j) -> T {
+        const bool ok = ecol && j >= -1 && j <= L.ny;
+        return ok ? (T)__ldg(&V.E[(j + 1) * CXp + ecolo]) : T(0);
+    };
+    T u0[C], u1[C], u2[C], un[C], un1[C], wv[C], fv[C], wv2[C], fv2[C];
+    ld_u(y0 - 1, u0);
+    ld_u(y0, u1);
+    ld_u(y0 + 1, u2);
+    T Eb = ld_e(y0 - 2), Ec = ld_e(y0 - 1), E2 = ld_e(y0);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        un[c] = __shfl_down_sync(FULL, u0[c], 1);
+        wv[c] = fv[c] = wv2[c] = fv2[c] = T(0);
+    }
+    T Elb = __shfl_up_sync(FULL, Eb, 1);
+    // w and the dense right-hand side of output row j, two rows ahead of their use
+    auto ld_wf = [&](int j, T (&wd)[C], T (&fd)[C]) {
+        if (!out || j >= yend) return;
+        const int n = (j + 1) * SX + ncol;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            if (up.mode == 0) wd[c] = V.w[c * cs + n];
+            if (V.rhs) fd[c] = V.rhs[c * cs + n];
+        }
+    };
+    ld_wf(y0, wv, fv);
+    ld_wf(y0 + 1, wv2, fv2);
+    T cy[C], gd[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) cy[c] = gd[c] = T(0);
+    // rows are a compile-time count: the loop unrolls fully and the row rotation below
+    // becomes register renaming, so loads stay in flight until their first real use
+#pragma unroll
+    for (int r = 0; r <= LY; ++r) {
+        const int j = y0 - 1 + r;
+        if (j >= yend) break;  // warp-uniform
+        const T El = __shfl_up_sync(FULL, Ec, 1);
+#pragma unroll
+        for (int c = 0; c < C; ++c) un1[c] = __shfl_down_sync(FULL, u1[c], 1);
+        const T Ex = Eb + Ec, Ey = El + Ec;
+        T own[C], mx[C], gn[C];
+        T cyn[C];
+        if (PHYS == 0) {
+            const T ax0 = un[0] - u0[0], ax1 = un[1] - u0[1];
+            const T ay0 = u1[0] - u0[0], ay1 = u1[1] - u0[1];
+            const T fx0 = k.ce_par * Ex * ax0, fx1 = k.ce_perp * Ex * ax1;
+            const T fy0 = k.ce_perp * Ey * ay0, fy1 = k.ce_par * Ey * ay1;
+            const T SA0 = ax0 + (un1[0] - u1[0]), SA1 = ax1 + (un1[1] - u1[1]);
+            const T SB0 = ay0 + (un1[0] - un[0]), SB1 = ay1 + (un1[1] - un[1]);
+            const T G0 = Ec * (k.cf_lam * SB1 + k.cf_mu * SA1), G1 = Ec * (k.cf_mu * SB0 + k.cf_lam * SA0);
+            const T H0 = Ec * (k.cf_lam * SB1 - k.cf_mu * SA1), H1 = Ec * (k.cf_mu * SB0 - k.cf_lam * SA0);
+            own[0] = -fx0 - fy0 - G0;
+            own[1] = -fx1 - fy1 - G1;
+            mx[0] = __shfl_up_sync(FULL, fx0 + H0, 1);
+            mx[1] = __shfl_up_sync(FULL, fx1 + H1, 1);
+            gn[0] = __shfl_up_sync(FULL, G0, 1);
+            gn[1] = __shfl_up_sync(FULL, G1, 1);
+            cyn[0] = fy0 - H0;
+            cyn[1] = fy1 - H1;
+        } else {
+            const T fx = k.ct * Ex * (un[0] - u0[0]);
+            const T fy = k.ct * Ey * (u1[0] - u0[0]);
+            own[0] = -fx - fy;
+            mx[0] = __shfl_up_sync(FULL, fx, 1);
+            gn[0] = T(0);
+            cyn[0] = fy;
+        }
+        if (j >= y0 && out) {
+            const int n = (j + 1) * SX + ncol;
+            unsigned fm = 0;
+            for (unsigned bb = bbits; bb; bb &= bb - 1) {
+                const Box &bx = V.boxes->b[__ffs(bb) - 1];
+                if (j >= bx.lo[1] && j <= bx.hi[1]) fm |= bx.mask;
+            }
+            const T diag = k.cdiag * ((Elb + Eb) + (El + Ec));
+            T F[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) F[c] = fv[c];
+            if (!V.rhs) {
+                if (PHYS == 1) F[0] = k.src * (T)(((i > 0) + (i < L.nx)) * ((j > 0) + (j < L.ny)));
+                const int64_t nl = L.node(i, j, 0);
+                for (int l = l0; l < l1; ++l) {
+                    const LoadEntry &le = V.loads[l];
+                    if (le.node == nl) {
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+                            if (le.comp == c) F[c] += load_val<T>(le);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+                up.apply_v(c * cs + n, (fm >> c) & 1u, own[c] + mx[c] + cy[c] + gd[c], F[c], diag, u0[c], wv[c], V.uo,
+                           V.w);
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            cy[c] = cyn[c];
+            gd[c] = gn[c];
+            u0[c] = u1[c];
+            u1[c] = u2[c];
+            un[c] = un1[c];
+        }
+        Eb = Ec;
+        Ec = E2;
+        Elb = El;
+        if (j + 3 <= L.NY) ld_u(j + 3, u2);
+        E2 = ld_e(j + 2);
+        if (j >= y0) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                wv[c] = wv2[c];
+                fv[c] = fv2[c];
+            }
+            ld_wf(j + 2, wv2, fv2);
+        }
+    }
+}
+
+// rows per warp: the variants compiled (a tiling's ly is one of these)
+template <typename T, int PHYS, typename TE>
+__device__ __forceinline__ void march2d_tile_ly(const M2View<T, TE> &V, int tile, Upd<T> &up) {
+    switch (V.ly) {
+        case 4: march2d_tile<T, PHYS, TE, 4>(V, tile, up); break;
+        case 16: march2d_tile<T, PHYS, TE, 16>(V, tile, up); break;
+        default: march2d_tile<T, PHYS, TE, 8>(V, tile, up); break;
+    }
+}
+
+template <typename T, int PHYS, typename TE = T>
+__global__ void __launch_bounds__(32 * M2W) sweep2d_march(const __grid_constant__ SweepArgs A) {
+    const int tile = blockIdx.x + gridDim.x * blockIdx.y;
+    const KC<T> kc = kconst<T>(A);
+    Upd<T> up = make_upd<T>(A, kc);
+    const M2View<T, TE> V{A.L, kc, &A.boxes, static_cast<const T *>(A.u_in), static_cast<T *>(A.u_out),
+                          static_cast<T *>(A.w), static_cast<const TE *>(A.E), static_cast<const T *>(A.rhs),
+                          A.tile_ptr, A.loads, (int)gridDim.x, A.zseg};
+    march2d_tile_ly<T, PHYS, TE>(V, tile, up);
+    finish_sweep(A, (double)up.res, (double)up.dot, tile);
+}
+
 // ------------------------------------------------------------- batched 2D kernel
 // One launch sweeps every active problem of a batch.  Block b takes tile tiles[b] (its
 // problem and the tile's index inside that problem's own 32 x 8 tiling), so each problem
@@ -435,20 +648,17 @@ template <typename T, int PHYS>
 __device__ __forceinline__ void sweep2d_batch_tile(const BatchLaunch &P, int t, long long sidx, double *sh) {
     const BatchTile bt = P.tiles[t];
     const BatchInst &I = P.inst[bt.inst];
-    const Layout L = I.L;
-    const int gx = I.gx, nb = I.gx * I.gy;
-    const int i = (bt.tile % gx) * 32 + threadIdx.x;
-    const int j = (bt.tile / gx) * 8 + threadIdx.y;
+    const int nb = I.gx * I.gy;
     const int mode = sidx < I.apt_until ? 0 : 1;
     const KC<T> kc = kconst_inst<T>(I);
     const long long since = P.adaptive ? sidx - reinterpret_cast<const long long *>(I.ctrl)[CT_RESTART_AT] : 0;
     const int test_dot = mode == 0 && P.adaptive ? P.test_dot : 0;
     Upd<T> up{kc, momentum_k<T>(P.adaptive, kc.a, since), mode, P.local_dt, P.want_res, test_dot,
               static_cast<const T *>(I.rhs), T(0), T(0)};
-    if (i < L.NX && j < L.NY)
-        sweep2d_node<T, PHYS, T>(L, kc, I.boxes, P.nrhs, static_cast<const T *>(I.u[P.cur]),
-                                 static_cast<T *>(I.u[1 - P.cur]), static_cast<T *>(I.w),
-                                 static_cast<const T *>(I.E), I.tile_ptr, I.loads, bt.tile, i, j, up);
+    const M2View<T, T> V{I.L, kc, &I.boxes, static_cast<const T *>(I.u[P.cur]), static_cast<T *>(I.u[1 - P.cur]),
+                         static_cast<T *>(I.w), static_cast<const T *>(I.E), static_cast<const T *>(I.rhs),
+                         I.tile_ptr, I.loads, I.gx, I.ly};
+    march2d_tile_ly<T, PHYS, T>(V, bt.tile, up);
     // per-problem deterministic reduction, as finish_sweep does for a whole grid
     if (!P.want_res && !test_dot) return;
     const double r = P.want_res ? block_sum((double)up.res, sh) : 0.0;
@@ -472,7 +682,7 @@ __device__ __forceinline__ void sweep2d_batch_tile(const BatchLaunch &P, int t, 
 // problems finish), so finished problems cost nothing and every block's latency overlaps
 // with the other blocks resident on the SM.
 template <typename T, int PHYS>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) sweep2d_batch(const BatchLaunch P) {
+__global__ void __launch_bounds__(32 * M2W, sizeof(T) == 4 ? 6 : 2) sweep2d_batch(const BatchLaunch P) {
     __shared__ double sh[32];
     sweep2d_batch_tile<T, PHYS>(P, blockIdx.x, *P.base + P.sweep_idx, sh);
 }
@@ -572,6 +782,28 @@ Tiling gather_tiling(const Layout &L) {
     return t;
 }
 
+Tiling march2d_tiling(const Layout &L, int ly) {
+    Tiling t{};
+    t.kind = 5;
+    t.bx = 32;
+    t.by = M2W;
+    t.zs = 1;
+    t.ox = 30;
+    t.gx = (L.NX + t.ox - 1) / t.ox;
+    if (ly <= 0) {
+        // the longest segment (of 16, 8, 4 rows) that still gives about 16 warps per SM;
+        // each warp recomputes one row below its segment
+        ly = 16;
+        while (ly > 4 && (int64_t)t.gx * ((L.NY + ly - 1) / ly) < 152 * 16) ly /= 2;
+    }
+    ly = ly >= 16 ? 16 : (ly >= 8 ? 8 : 4);  // the compiled variants
+    t.ly = ly;
+    t.oy = M2W * ly;
+    t.gy = (L.NY + t.oy - 1) / t.oy;
+    t.gz = 1;
+    return t;
+}
+
 Tiling choose_tiling(const Layout &L, int physics, int precision, int nrhs) {
     if (L.dim == 3 && physics == 0 && precision == 0) {
         // z-marching kernel: TMA-staged with two owner rows per thread by default;
@@ -618,6 +850,18 @@ cudaError_t launch_sweep(const SweepArgs &a0, const Tiling &t, int precision, cu
         if (!maps || !maps->valid) return cudaErrorInvalidValue;
         return launch_march3d_tma2(a, t, *maps, s);
     }
+    if (t.kind == 5) {
+        a.zseg = t.ly;
+        dim3 block(32, M2W, 1), grid(t.gx, t.gy, 1);
+        if (precision == 0) {
+            if (a.physics == 0) sweep2d_march<float, 0><<<grid, block, 0, s>>>(a);
+            else sweep2d_march<float, 1><<<grid, block, 0, s>>>(a);
+        } else {
+            if (a.physics == 0) sweep2d_march<double, 0><<<grid, block, 0, s>>>(a);
+            else sweep2d_march<double, 1><<<grid, block, 0, s>>>(a);
+        }
+        return cudaGetLastError();
+    }
     dim3 block(t.bx, t.by, 1), grid(t.gx, t.gy, t.gz);
     if (a.L.dim == 2) {
         if (precision == 0) {
@@ -641,7 +885,7 @@ cudaError_t launch_sweep(const SweepArgs &a0, const Tiling &t, int precision, cu
 
 template <typename T, int PHYS>
 static cudaError_t launch_batch_kernel(const BatchLaunch &p, int ntiles, cudaStream_t s) {
-    sweep2d_batch<T, PHYS><<<ntiles, dim3(32, 8, 1), 0, s>>>(p);
+    sweep2d_batch<T, PHYS><<<ntiles, dim3(32, M2W, 1), 0, s>>>(p);
     return cudaGetLastError();
 }
 

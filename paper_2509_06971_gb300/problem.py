@@ -148,6 +148,10 @@ class Problem:
         self._ck(self.lib.petto_autotune(self.ctx, int(sweeps), buf, len(buf)))
         return json.loads(buf.value.decode() or "{}")
 
+    def select_kernel(self, name: str):
+        """Pick the sweep kernel by autotuner name ("march2d", "gather/32x8", "tma2/zs16", ...)."""
+        self._ck(self.lib.petto_select_kernel(self.ctx, name.encode()))
+
     def synchronize(self):
         self._ck(self.lib.petto_synchronize(self.ctx))
 

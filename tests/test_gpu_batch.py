@@ -1,9 +1,11 @@
 """Batched 2D problems (petto_batch_*): one launch per sweep over every problem.
 
 Each problem of a batch runs the iteration of the single-problem solve with the same
-kernel arithmetic, tiles and reduction order, so its state, sweep counts and residuals
-must equal (bit for bit) those of the same problem solved alone; the FP64 batch is also
-held against the oracle, which shares nothing with either GPU path.
+kernel arithmetic, tiles and reduction order as the 2D marching sweep, so its state,
+sweep counts and residuals must equal (bit for bit) those of the same problem solved
+alone on that kernel; against the default (node-gather) single-problem kernel they agree
+to FP32 rounding.  The FP64 batch is also held against the oracle, which shares nothing
+with either GPU path.
 """
 import numpy as np
 import pytest
@@ -31,10 +33,12 @@ def relmax(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-def _alone(P, specs, seeds, **kw):
+def _alone(P, specs, seeds, kernel="march2d", **kw):
     out = []
     for spec, sd in zip(specs, seeds):
         p = P.Problem(spec)
+        if kernel:
+            p.select_kernel(kernel)  # the batched sweep's kernel
         p.set_design(W.random_design(spec, seed=sd))
         rep = p.solve(**kw)
         out.append((rep, p.get_state(dtype=p.np_dtype)))
@@ -145,6 +149,7 @@ def test_batch_optimize_equals_alone(P):
     hist_alone, phis = [], []
     for spec in specs:
         p = P.Problem(spec)
+        p.select_kernel("march2d")
         h, _ = p.optimize(2, solve_kw=kw)
         hist_alone.append(h)
         phis.append(p.get_design())
@@ -188,11 +193,13 @@ def test_batch_state_reused_after_alone_sweeps(P):
     ref = []
     for spec in specs:
         p = P.Problem(spec)
+        p.select_kernel("march2d")
         p.sweep(0, 3, 0.9, 0.9, 0.75, True)
         ref.append((p.solve(**kw), p.get_state(dtype=np.float32)))
         p.close()
     probs = [P.Problem(spec) for spec in specs]
     for p in probs:
+        p.select_kernel("march2d")
         p.sweep(0, 3, 0.9, 0.9, 0.75, True)
     b = P.Batch(probs)
     reps = b.solve(**kw)
@@ -202,3 +209,34 @@ def test_batch_state_reused_after_alone_sweeps(P):
     b.close()
     for p in probs:
         p.close()
+
+
+def test_batch_matches_default_single_path_within_fp32(P):
+    """Against problems solved alone on the default (node-gather) 2D kernel: the same
+    iteration in another summation order, so FP32 results agree to rounding: converged
+    fields to the solve tolerance and compliance to 1e-4."""
+    specs = small_batch(4, seed=17)
+    seeds = [80, 81, 82, 83]
+    kw = dict(tol=1e-6, check_every=20, max_sweeps=40000)
+    alone = _alone(P, specs, seeds, kernel=None, **kw)
+    reps, states, _ = _batched(P, specs, seeds, **kw)
+    for (ra, ua), rb, ub, spec, sd in zip(alone, reps, states, specs, seeds):
+        assert ra["converged"] and rb["converged"]
+        op, om = oracle_problem(spec), oracle_materials(spec)
+        E = om.modulus(np.asarray(W.random_design(spec, seed=sd), np.float32).astype(np.float64))
+        F = op.load_vector()
+        ca = float(F @ np.ascontiguousarray(np.asarray(ua, np.float64).T.reshape(-1)))
+        cb = float(F @ np.ascontiguousarray(np.asarray(ub, np.float64).T.reshape(-1)))
+        assert abs(ca - cb) / abs(ca) < 1e-4
+        assert relmax(ub, ua) < 1e-3
+
+
+def test_select_kernel_names(P):
+    from paper_2509_06971_gb300 import capi as C
+    p = P.Problem(small_batch(1)[0])
+    for name in ("march2d", "march2d/ly8", "gather", "gather/32x4"):
+        p.select_kernel(name)
+    with pytest.raises(C.PettoError) as e:
+        p.select_kernel("tma2")  # a 3D kernel
+    assert e.value.status == C.PETTO_EINVAL
+    p.close()
