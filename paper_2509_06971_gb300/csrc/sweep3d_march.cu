@@ -372,7 +372,9 @@ constexpr int TBW = 36;        // box width (floats): covers the 33 tile columns
 constexpr int TNS = 4;         // ring slots
 constexpr int TD = 2;          // planes in flight ahead of the consumer (the slot of the plane
                                // being updated must survive the refill issued in its iteration)
-constexpr int TWAIT = 1 << 22; // try_wait attempts before a wait is declared timed out
+constexpr int TWAIT = 1 << 14; // try_wait attempts before a wait is declared timed out
+constexpr unsigned TSUSPEND = 100000;  // ns a waiting thread may stay suspended per attempt
+                                       // (woken early when the phase completes): <= ~1.6 s in all
 
 template <int TY> struct TmaGeom {
     static constexpr int NT = 32 * TY, WY = TY + 1;
@@ -399,9 +401,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     for (int it = 0; it < TWAIT; ++it) {
         uint32_t ok;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(ok)
-            : "r"(bar), "r"(parity)
+            : "r"(bar), "r"(parity), "r"(TSUSPEND)
             : "memory");
         if (ok) return true;
     }
@@ -943,25 +945,39 @@ __device__ __forceinline__ void march_update(const SweepArgs &A, const MarchCons
     }
     float step = A.mode == 0 ? K.fb : K.fs1;
     if (A.local_dt) step *= fast_rcp(K.cdg * S8);
-    const float R0 = (fm & 1u) ? 0.f : F0 - Ku0;
-    const float R1 = (fm & 2u) ? 0.f : F1 - Ku1;
-    const float R2 = (fm & 4u) ? 0.f : F2 - Ku2;
+    float R0 = F0 - Ku0, R1 = F1 - Ku1, R2 = F2 - Ku2;
+    float w0, w1, w2, v0, v1, v2;  // new increment and state
+    if (A.mode == 0) {
+        w0 = fmaf(K.fa, wv0, step * R0);
+        w1 = fmaf(K.fa, wv1, step * R1);
+        w2 = fmaf(K.fa, wv2, step * R2);
+        v0 = u[0] + w0;
+        v1 = u[1] + w1;
+        v2 = u[2] + w2;
+    } else {
+        w0 = w1 = w2 = 0.f;
+        v0 = fmaf(step, R0, u[0]);
+        v1 = fmaf(step, R1, u[1]);
+        v2 = fmaf(step, R2, u[2]);
+    }
+    if (fm) {  // supported DOFs (only columns inside a support box get here)
+        if (fm & 1u) R0 = w0 = v0 = 0.f;
+        if (fm & 2u) R1 = w1 = v1 = 0.f;
+        if (fm & 4u) R2 = w2 = v2 = 0.f;
+    }
     if (A.want_res) res += R0 * R0 + R1 * R1 + R2 * R2;
     if (A.mode == 0) {
         if (A.test_dot) dot += R0 * wv0 + R1 * wv1 + R2 * wv2;
-        const float w0 = (fm & 1u) ? 0.f : fmaf(K.fa, wv0, step * R0);
-        const float w1 = (fm & 2u) ? 0.f : fmaf(K.fa, wv1, step * R1);
-        const float w2 = (fm & 4u) ? 0.f : fmaf(K.fa, wv2, step * R2);
         wb[off] = w0;
         wb[cs32 + off] = w1;
         wb[2 * cs32 + off] = w2;
-        uob[off] = (fm & 1u) ? 0.f : u[0] + w0;
-        uob[cs32 + off] = (fm & 2u) ? 0.f : u[1] + w1;
-        uob[2 * cs32 + off] = (fm & 4u) ? 0.f : u[2] + w2;
+        uob[off] = v0;
+        uob[cs32 + off] = v1;
+        uob[2 * cs32 + off] = v2;
     } else if (A.mode == 1) {
-        uob[off] = (fm & 1u) ? 0.f : fmaf(step, R0, u[0]);
-        uob[cs32 + off] = (fm & 2u) ? 0.f : fmaf(step, R1, u[1]);
-        uob[2 * cs32 + off] = (fm & 4u) ? 0.f : fmaf(step, R2, u[2]);
+        uob[off] = v0;
+        uob[cs32 + off] = v1;
+        uob[2 * cs32 + off] = v2;
     } else {
         wb[off] = R0;
         wb[cs32 + off] = R1;
