@@ -38,6 +38,7 @@ WORKLOADS = {
     "heat2d_1024x1024": lambda: W.heat2d(1024),
     "multimat3d_384x192x192_bf16": lambda: W.multimat3d(storage="bf16"),
     "cantilever3d_64x32x32": lambda: W.cantilever3d(64, 32, 32),
+    "mbb_multimat2d_512x128": lambda: W.mbb_multimat2d(512, 128),
 }
 BATCH_WORKLOADS = {
     "batch2d_48": lambda: W.batch2d(48),

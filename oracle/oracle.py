@@ -76,6 +76,7 @@ def _load():
                 "or_material": (None, [_L, _I, _P, _P, _D, _D, _I, _P]),
                 "or_sensitivity": (_D, [_L, _I, _P, _P, _D, _D, _I, _P, _P, _P]),
                 "or_update": (None, [_L, _I, _P, _P, _P, _I, _D, _D, _D, _I, _P]),
+                "or_update_b": (None, [_L, _I, _P, _P, _P, _I, _D, _D, _D, _I, _P, _P, _D, _P]),
                 "or_double_well": (_D, [_D]), "or_double_well_deriv": (_D, [_D]),
                 "or_cell_laplacian": (None, [g, _P, _P]),
                 "or_ch_step": (None, [g, _I, _D, _D, _P]),
@@ -298,15 +299,25 @@ class OracleMaterials:
         return s, C
 
 
-def update(phi, s, V, *, vol_mode=PROJECTED, alpha_h=0.1, kappa_v=0.0, kappa_1=0.0, n_bisect=60):
-    """Design update (Sec. 2.3 combined objective; Sec. 3.1 normalised step).  In place on
-    phi [P, cells]; returns lambda per phase (projected) or the pre-step mean (penalty)."""
+def update(phi, s, V, *, vol_mode=PROJECTED, alpha_h=0.1, kappa_v=0.0, kappa_1=0.0, n_bisect=60,
+           keepout=None, Vb=None, kappa_b=0.0):
+    """Design update (Sec. 2.3 combined objective; Sec. 3.1 normalised step; Sec. 3.4
+    keep-out term when ``keepout`` (bool per cell), ``Vb`` (per phase) and ``kappa_b`` are
+    given).  In place on phi [P, cells]; returns lambda per phase (projected) or the
+    pre-step mean (penalty)."""
     P, ncell = phi.shape
     s = _f64(s).reshape(P, ncell)
     Vv = _f64(V).reshape(P)
     lam = np.empty(P)
-    _load().or_update(ncell, P, _ptr(phi), _ptr(s), _ptr(Vv), int(vol_mode), float(alpha_h), float(kappa_v),
-                      float(kappa_1), int(n_bisect), _ptr(lam))
+    if keepout is None:
+        _load().or_update(ncell, P, _ptr(phi), _ptr(s), _ptr(Vv), int(vol_mode), float(alpha_h), float(kappa_v),
+                          float(kappa_1), int(n_bisect), _ptr(lam))
+    else:
+        keep = np.ascontiguousarray(np.asarray(keepout, dtype=np.uint8).reshape(ncell))
+        Vbv = _f64(Vb).reshape(P)
+        _load().or_update_b(ncell, P, _ptr(phi), _ptr(s), _ptr(Vv), int(vol_mode), float(alpha_h),
+                            float(kappa_v), float(kappa_1), int(n_bisect), keep.ctypes.data_as(ctypes.c_void_p),
+                            _ptr(Vbv), float(kappa_b), _ptr(lam))
     return lam
 
 
@@ -328,7 +339,8 @@ def design_step(prob: OracleProblem, mat: OracleMaterials, phi, u, F, fixed, V, 
     s, C = mat.sensitivity(phi, E, e)
     lam = update(phi, s, V, vol_mode=pf_kw.get("vol_mode", PROJECTED), alpha_h=pf_kw.get("alpha_h", 0.1),
                  kappa_v=pf_kw.get("kappa_v", 0.0), kappa_1=pf_kw.get("kappa_1", 0.0),
-                 n_bisect=pf_kw.get("n_bisect", 60))
+                 n_bisect=pf_kw.get("n_bisect", 60), keepout=pf_kw.get("keepout"), Vb=pf_kw.get("Vb"),
+                 kappa_b=pf_kw.get("kappa_b", 0.0))
     for _ in range(ch_steps):
         prob.ch_step(phi, pf_kw.get("gamma_g", 0.0), pf_kw.get("tau", 0.0))
     return {"compliance": C, "work": float(np.dot(F, u)), "lambda": lam, "sweeps": rep["sweeps"],

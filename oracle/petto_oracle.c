@@ -418,18 +418,30 @@ double or_sensitivity(int64_t ncell, int P, const double *phi, const double *mod
  *                            reading R7: per-cell gradient of J_v is 2 (mean - V)/N, folded
  *                            into kappa_v by the caller).
  * lambda_out[i] receives lambda_i (projected) or mean phi_i before the step (penalty). */
-void or_update(int64_t ncell, int P, double *phi, const double *s, const double *V, int vol_mode,
-               double alpha_h, double kappa_v, double kappa_1, int n_bisect, double *lambda_out) {
+/* The same update with the keep-out term of the drone problem (Sec. 3.4):
+ * J_b = sum_i (mean over Omega_b of phi_i - Vb_i)^2 for the cells with keep[c] != 0
+ * (reading R23: means over the region, as R7 reads J_v), whose per-cell gradient
+ * 2 (mean_b phi_i - Vb_i) / N_b is folded into kappa_b by the caller and added to g_i on
+ * the cells of Omega_b.  keep = NULL or kappa_b = 0 leaves the update unchanged. */
+void or_update_b(int64_t ncell, int P, double *phi, const double *s, const double *V, int vol_mode,
+                 double alpha_h, double kappa_v, double kappa_1, int n_bisect, const unsigned char *keep,
+                 const double *Vb, double kappa_b, double *lambda_out) {
     double *d = (double *)malloc(sizeof(double) * (size_t)(ncell * P));
     double *smax = (double *)calloc((size_t)P, sizeof(double));
     double *mean = (double *)calloc((size_t)P, sizeof(double));
+    double *mean_b = (double *)calloc((size_t)P, sizeof(double));
+    int64_t nb = 0;
+    if (keep)
+        for (int64_t c = 0; c < ncell; ++c) nb += keep[c] != 0;
     for (int i = 0; i < P; ++i) {
         for (int64_t c = 0; c < ncell; ++c) {
             double a = fabs(s[(int64_t)i * ncell + c]);
             if (a > smax[i]) smax[i] = a;
             mean[i] += phi[(int64_t)i * ncell + c];
+            if (keep && keep[c]) mean_b[i] += phi[(int64_t)i * ncell + c];
         }
         mean[i] /= (double)ncell;
+        if (nb > 0) mean_b[i] /= (double)nb;
     }
     for (int64_t c = 0; c < ncell; ++c) {
         double tot = 0.0;
@@ -438,6 +450,7 @@ void or_update(int64_t ncell, int P, double *phi, const double *s, const double 
             int64_t ic = (int64_t)i * ncell + c;
             double gi = smax[i] > 0.0 ? alpha_h * s[ic] / smax[i] : 0.0;
             gi += kappa_1 * (tot - 1.0);
+            if (nb > 0 && keep[c]) gi += kappa_b * (mean_b[i] - Vb[i]);
             d[ic] = phi[ic] - gi;
         }
     }
@@ -459,7 +472,12 @@ void or_update(int64_t ncell, int P, double *phi, const double *s, const double 
             lambda_out[i] = mean[i];
         }
     }
-    free(d); free(smax); free(mean);
+    free(d); free(smax); free(mean); free(mean_b);
+}
+
+void or_update(int64_t ncell, int P, double *phi, const double *s, const double *V, int vol_mode,
+               double alpha_h, double kappa_v, double kappa_1, int n_bisect, double *lambda_out) {
+    or_update_b(ncell, P, phi, s, V, vol_mode, alpha_h, kappa_v, kappa_1, n_bisect, NULL, NULL, 0.0, lambda_out);
 }
 
 /* ---------------------------------------------------------- Cahn-Hilliard

@@ -215,20 +215,23 @@ class Problem:
                                          _DT[np.dtype(dtype)], 0))
         return r.value, R
 
-    def solve_opts(self, mode=C.PETTO_SOLVE_TOL, **kw) -> C.petto_solve_opts:
-        """Defaults: the workload's constants; momentum = 1 (adaptive restart, with the
-        momentum cap a = 1 unless given), refine = 1 (FP64 refinement for FP32 states)."""
+    def solve_opts(self, mode=None, **kw) -> C.petto_solve_opts:
+        """Defaults: the workload's constants and schedule (tolerance mode unless the
+        workload is the paper's fixed-count loop); momentum from the workload (adaptive
+        restart with the momentum cap a = 1 unless given), refine = 1 (FP64 refinement
+        for FP32 states)."""
         s = self.spec
+        mode = int(kw.pop("mode", s.solve_mode if mode is None else mode))
         momentum = int(kw.get("momentum", s.momentum))
         a = float(kw.get("a", 1.0 if momentum else s.apt_a))
-        return C.petto_solve_opts(mode, int(kw.get("n_apt", 0)), int(kw.get("n_pt", 0)), a,
+        return C.petto_solve_opts(mode, int(kw.get("n_apt", s.n_apt)), int(kw.get("n_pt", s.n_pt)), a,
                                   float(kw.get("b", s.apt_b)), float(kw.get("s1", s.pt_s1)),
                                   float(kw.get("tol", s.tol)), int(kw.get("max_sweeps", s.max_sweeps)),
                                   int(kw.get("check_every", s.check_every)),
                                   int(bool(kw.get("local_dt", s.local_dt))), momentum,
                                   int(bool(kw.get("refine", True))))
 
-    def solve(self, mode=C.PETTO_SOLVE_TOL, **kw) -> dict:
+    def solve(self, mode=None, **kw) -> dict:
         o = self.solve_opts(mode, **kw)
         rep = C.petto_solve_report()
         st = self._ck(self.lib.petto_pt_solve(self.ctx, ctypes.byref(o), ctypes.byref(rep)),
@@ -346,14 +349,14 @@ class Batch:
     def launches(self) -> int:
         return int(self.lib.petto_batch_launch_count(self.batch))
 
-    def solve_opts(self, mode=C.PETTO_SOLVE_TOL, **kw):
+    def solve_opts(self, mode=None, **kw):
         n = len(self.problems)
         arr = (C.petto_solve_opts * n)()
         for i, p in enumerate(self.problems):
             arr[i] = p.solve_opts(mode, **kw)
         return arr
 
-    def solve(self, mode=C.PETTO_SOLVE_TOL, **kw) -> list:
+    def solve(self, mode=None, **kw) -> list:
         """Solve every problem; one report dict per problem (as Problem.solve)."""
         n = len(self.problems)
         opts = self.solve_opts(mode, **kw)

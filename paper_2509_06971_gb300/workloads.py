@@ -55,6 +55,9 @@ class ProblemSpec:
     max_sweeps: int = 200000
     local_dt: bool = True      # local pseudo-time steps b/diag(K), s1/diag(K) (an extension)
     momentum: int = 1          # 0: fixed APT damping a; 1: adaptive-restart momentum (an extension)
+    solve_mode: int = 1        # 1: to tolerance; 0: the paper's fixed n_apt APT then n_pt PT sweeps
+    n_apt: int = 0
+    n_pt: int = 0
     # design update and phase field (Sec. 2.3, 2.4; Sec. 3.1 weights)
     vol_mode: int = PROJECTED
     alpha_h: float = 0.1
@@ -214,6 +217,31 @@ def cantilever3d(nx: int = 256, ny: int = 128, nz: int = 128, vol: float = 0.12,
         phi0=_uniform_phi(nx * ny * nz, [vol]),
         apt_a=a, apt_b=b, pt_s1=s1, tol=1e-6, tau=tau, gamma_g=gg, design_steps=50,
         precision=precision, storage=precision)
+
+
+def mbb_multimat2d(nx: int = 512, ny: int = 128, precision: str = "f32") -> ProblemSpec:
+    """The paper's own multi-material MBB loop (Sec. 3.2): a 4 x 1 domain (nx = 4 ny cells),
+    both bottom corners on rollers (u_y = 0), a unit downward load at the top-centre node,
+    five materials E = [1.0, 0.775, 0.55, 0.325, 0.1] with V = 0.08 each plus an explicit
+    void phase (E = 1e-6, V = 0.6), E = sum_i E_i phi_i^3, every phase starting at 0.5.
+    Each loop: 20 APT then 20 PT sweeps with the paper's global steps (dt2 = dx/2,
+    theta = 1, dt1 = dx^2/4; no local steps, fixed damping), the penalty update with
+    alpha_h = 0.1, alpha_v = 1e4, alpha_1 = 1e3 (reading R7: kappa = 2 alpha / N_cells), and
+    one Cahn-Hilliard step with dt3 = 500 dx^4, gamma = 3e-5.  The paper's grid is written
+    "513 x 128"; 512 x 128 cells give its 4 : 1 aspect ratio at dx = 1/128."""
+    h_p = 1.0 / ny
+    a, b, s1 = apt_params(h_p, elastic=True, dim=2)
+    tau, gg = ch_params(h_p, 2)
+    moduli = [1e-6, 1.0, 0.775, 0.55, 0.325, 0.1]
+    fr = [0.6, 0.08, 0.08, 0.08, 0.08, 0.08]
+    n = nx * ny
+    return ProblemSpec(
+        name=f"mbb_multimat2d_{nx}x{ny}", dim=2, nx=nx, ny=ny, moduli=moduli, e_min=0.0, interp=SIMP_PAPER,
+        vol_frac=fr, boxes=[((0, 0, 0), (0, 0, 0), 0b10), ((nx, 0, 0), (nx, 0, 0), 0b10)],
+        loads=[((nx // 2, ny, 0), 1, -1.0)], phi0=np.full((len(fr), n), 0.5),
+        apt_a=a, apt_b=b, pt_s1=s1, local_dt=False, momentum=0, solve_mode=0, n_apt=20, n_pt=20,
+        check_every=0, vol_mode=PENALTY, alpha_h=0.1, kappa_v=2.0 * 1e4 / n, kappa_1=2.0 * 1e3 / n,
+        tau=tau, gamma_g=gg, design_steps=200, precision=precision, storage=precision)
 
 
 def multimat3d(nx: int = 384, ny: int = 192, nz: int = 192, storage: str = "bf16") -> ProblemSpec:

@@ -291,6 +291,33 @@ def test_design_loop_mbb_fp64(P):
     prob.close()
 
 
+def test_paper_multimat_mbb_loop_fp64(P):
+    """The paper's multi-material MBB loop (Sec. 3.2) on a 64 x 16 copy: five materials plus
+    an explicit void phase (P = 6), 20 APT + 20 PT sweeps with the paper's global steps,
+    the penalty update (kappa_v, kappa_1 of the 512 x 128 problem) and one Cahn-Hilliard
+    step per loop, against the oracle loop for loop."""
+    steps = 4
+    spec = W.mbb_multimat2d(64, 16, precision="f64")
+    n_full = 512 * 128
+    pf = dict(kappa_v=2e4 / n_full, kappa_1=2e3 / n_full)
+    prob = P.Problem(spec)
+    hist, _ = prob.optimize(steps, pf_kw=pf)
+    assert all(h["sweeps"] == 40 for h in hist)
+    op, om = oracle_problem(spec), oracle_materials(spec)
+    F, fixed = op.load_vector(), op.fixed_mask()
+    phi, u = spec.phi0.copy(), np.zeros(op.ndof)
+    for t in range(steps):
+        m = O.design_step(op, om, phi, u, F, fixed, spec.vol_frac,
+                          dict(mode=0, n_apt=20, n_pt=20, a=spec.apt_a, b=spec.apt_b, s1=spec.pt_s1,
+                               check_every=0, local_dt=False, momentum=0),
+                          dict(vol_mode=W.PENALTY, alpha_h=spec.alpha_h, gamma_g=spec.gamma_g, tau=spec.tau, **pf))
+        assert abs(hist[t]["compliance"] - m["compliance"]) <= 1e-10 * abs(m["compliance"])
+    assert relmax(prob.get_design(), phi) < 1e-10
+    # the volume penalty pulls the solid phases (starting at 0.5) toward their 0.08
+    assert (prob.get_design()[1:].mean(axis=1) < 0.2).all()
+    prob.close()
+
+
 def test_checkpoint_roundtrip(P, tmp_path):
     spec = W.mbb_halfbeam(30, 10)
     prob = P.Problem(spec)

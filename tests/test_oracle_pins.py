@@ -362,6 +362,41 @@ def test_penalty_update_is_gradient_of_volume_terms():
         assert abs(step[i, c] - fd) < 1e-9
 
 
+def test_keepout_term_is_gradient_of_void_region_constraint():
+    """The keep-out term (Sec. 3.4): penalty mode with alpha_h = 0 steps along
+    -grad(alpha_v J_v + alpha_1 J_1 + alpha_b J_b) with J_b = sum_i (mean over the region
+    of phi_i - Vb_i)^2 (reading R23), checked by central differences inside and outside
+    the region; in projected mode the term moves the region's density toward Vb."""
+    rng = np.random.default_rng(4)
+    P, N = 2, 48
+    phi = rng.uniform(0, 1, (P, N))
+    V = np.array([0.3, 0.7])
+    Vb = np.array([0.0, 1.0])
+    keep = np.zeros(N, bool)
+    keep[10:22] = True
+    av, a1, ab = 0.7, 0.3, 1.9
+    nb = keep.sum()
+
+    def J(ph):
+        return (av * np.sum((ph.mean(axis=1) - V) ** 2) + a1 * np.mean((ph.sum(axis=0) - 1) ** 2)
+                + ab * np.sum((ph[:, keep].mean(axis=1) - Vb) ** 2))
+
+    new = phi.copy()
+    O.update(new, np.zeros((P, N)), V, vol_mode=O.PENALTY, alpha_h=0.0, kappa_v=2 * av / N, kappa_1=2 * a1 / N,
+             keepout=keep, Vb=Vb, kappa_b=2 * ab / nb)
+    step = phi - new
+    for (i, c) in [(0, 3), (1, 12), (0, 21), (1, 40)]:
+        e = np.zeros_like(phi)
+        e[i, c] = 1e-6
+        fd = (J(phi + e) - J(phi - e)) / 2e-6
+        assert abs(step[i, c] - fd) < 1e-9
+    # projected mode: with a strong keep-out weight the region empties of phase 0
+    ph = np.full((1, N), 0.5)
+    O.update(ph, np.zeros((1, N)), [0.5], vol_mode=O.PROJECTED, alpha_h=0.0, keepout=keep, Vb=[0.0], kappa_b=2.0)
+    assert ph[0, keep].max() < ph[0, ~keep].min()
+    assert abs(ph.mean() - 0.5) < 1e-12
+
+
 # ------------------------------------------------------------ phase field
 
 def test_double_well():
