@@ -229,6 +229,18 @@ petto_status petto_sensitivity(petto_ctx *ctx, double *compliance, double *work,
  * mean of phi_i before the step (penalty mode).  Refreshes the modulus field. */
 petto_status petto_design_update(petto_ctx *ctx, const petto_pf_opts *opts, double *lambda);
 
+/* Keep-out region of the design update (Sec. 3.4, the drone's void region): adds
+ * alpha_b dJ_b/dphi_i with J_b = sum_i (mean over the region of phi_i - target_i)^2 to the
+ * update's gradient on the region's cells; the per-cell gradient 2 (mean - target) / N_b
+ * is folded into kappa_b (= 2 alpha_b / N_b, as kappa_v is for J_v).
+ *   box     host [lo_i, lo_j, lo_k, hi_i, hi_j, hi_k]: inclusive cell ranges (lo_k = hi_k =
+ *           0 in 2D), or NULL to remove the region
+ *   target  host [n_phases] targets (e.g. 0 for a solid phase, 1 for an explicit void)
+ *   kappa_b >= 0
+ * Copied; applies to every later petto_design_update.  PETTO_EINVAL for an empty or
+ * out-of-grid box. */
+petto_status petto_set_keepout(petto_ctx *ctx, const int64_t *box, const double *target, double kappa_b);
+
 /* opts->ch_steps explicit Cahn-Hilliard steps (Sec. 2.4); refreshes the modulus field. */
 petto_status petto_cahn_hilliard(petto_ctx *ctx, const petto_pf_opts *opts);
 

@@ -35,6 +35,11 @@ struct petto_ctx {
     BoxSet boxes{};
     double lam0 = 0.0, mu0 = 0.0;
     double f_norm = 0.0;
+    // keep-out region of the design update (Sec. 3.4 J_b)
+    int keep = 0;
+    int klo[3] = {0, 0, 0}, khi[3] = {0, 0, 0};
+    double kappa_b = 0.0;
+    double Vb[MAX_PHASES] = {0};
     // device buffers
     void *u[2] = {nullptr, nullptr};
     void *w = nullptr, *E = nullptr, *phi = nullptr, *s = nullptr, *dscr = nullptr, *mu = nullptr;
@@ -59,7 +64,7 @@ struct petto_ctx {
     bool owns_stream = false;
     bool use_graphs = true;  // replay sweep chunks between checks as CUDA graphs
     struct GraphEntry {
-        int apt, local_dt, adaptive, cur, ce, nrhs_dummy;
+        int apt, local_dt, adaptive, cur, ce, res_last;
         const void *rhs;
         double a, b, s1;
         cudaGraphExec_t exec;
@@ -954,13 +959,13 @@ petto_status set_ctrl(petto_ctx *ctx, int slot, long long v) {
 // sweep constants and starting buffer, replayed with the chunk's first sweep index read
 // from the device control words.
 petto_status graph_chunk(petto_ctx *ctx, const petto_solve_opts *o, bool apt, int ce, long long base,
-                         const void *rhs, bool *done) {
+                         const void *rhs, bool *done, bool res_last = true) {
     *done = false;
     const int adaptive = o->momentum ? 1 : 0;
     petto_ctx::GraphEntry *ge = nullptr;
     for (auto &g : ctx->graphs)
         if (g.apt == apt && g.local_dt == o->local_dt && g.adaptive == adaptive && g.cur == ctx->cur && g.ce == ce &&
-            g.rhs == rhs && g.a == o->a && g.b == o->b && g.s1 == o->s1)
+            g.res_last == (res_last ? 1 : 0) && g.rhs == rhs && g.a == o->a && g.b == o->b && g.s1 == o->s1)
             ge = &g;
     if (!ge) {
         if (ctx->graphs.size() >= 8) clear_graphs(ctx);
@@ -976,7 +981,7 @@ petto_status graph_chunk(petto_ctx *ctx, const petto_solve_opts *o, bool apt, in
             sc.idx = j;
             sc.base_from_ctrl = 1;
             sc.rhs = rhs;
-            st = one_sweep(ctx, apt ? 0 : 1, o->a, o->b, o->s1, o->local_dt, j == ce - 1, sc);
+            st = one_sweep(ctx, apt ? 0 : 1, o->a, o->b, o->s1, o->local_dt, res_last && j == ce - 1, sc);
         }
         cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
         ctx->cur = cur0;
@@ -990,7 +995,8 @@ petto_status graph_chunk(petto_ctx *ctx, const petto_solve_opts *o, bool apt, in
         cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         CK(ei);
-        petto_ctx::GraphEntry g{apt ? 1 : 0, o->local_dt, adaptive, ctx->cur, ce, 0, rhs, o->a, o->b, o->s1, exec};
+        petto_ctx::GraphEntry g{apt ? 1 : 0, o->local_dt, adaptive, ctx->cur, ce, res_last ? 1 : 0, rhs, o->a, o->b,
+                                o->s1, exec};
         ctx->graphs.push_back(g);
         ge = &ctx->graphs.back();
     }
@@ -1144,6 +1150,23 @@ petto_status sweep_phase(petto_ctx *ctx, const petto_solve_opts *o, SolveState &
                 if (apt) S.na += ce; else S.np += ce;
                 S.sweeps += ce;
                 goto checked;
+            }
+        }
+        if (ctx->use_graphs && ctx->stream && ce == 0 && S.sweeps % 4 == 0) {
+            // no checks (the paper's fixed counts): replay runs of up to 64 sweeps of one kind,
+            // keeping the budget's last sweep (which reports the residual) for the loop below
+            int64_t len = S.total - S.sweeps - 1;
+            if (o->mode == PETTO_SOLVE_PAPER && !S.use_pt && S.sweeps < n_apt) len = std::min(len, n_apt - S.sweeps);
+            len = std::min<int64_t>(len, 64) & ~int64_t(3);
+            if (len >= 4) {
+                bool done = false;
+                petto_status st = graph_chunk(ctx, o, apt, (int)len, S.sweeps, rhs, &done, false);
+                if (st != PETTO_OK) return st;
+                if (done) {
+                    if (apt) S.na += len; else S.np += len;
+                    S.sweeps += len;
+                    continue;
+                }
             }
         }
         {
@@ -1308,6 +1331,15 @@ petto_status petto_design_update(petto_ctx *ctx, const petto_pf_opts *o, double 
     ua.kappa_v = o->kappa_v;
     ua.kappa_1 = o->kappa_1;
     for (int p = 0; p < ctx->P; ++p) ua.V[p] = ctx->vol[p];
+    ua.keep = ctx->keep;
+    ua.nx = ctx->L.nx;
+    ua.ny = ctx->L.ny;
+    for (int a = 0; a < 3; ++a) {
+        ua.klo[a] = ctx->klo[a];
+        ua.khi[a] = ctx->khi[a];
+    }
+    ua.kappa_b = ctx->kappa_b;
+    for (int p = 0; p < ctx->P; ++p) ua.Vb[p] = ctx->Vb[p];
     if (o->vol_mode == PETTO_VOL_PENALTY) {
         CK(launch_mean(ctx->L, ctx->P, ctx->storage, ctx->phi, ctx->scal, ctx->red(), ctx->stream));
         ctx->launches++;
@@ -1322,6 +1354,28 @@ petto_status petto_design_update(petto_ctx *ctx, const petto_pf_opts *o, double 
         if (st != PETTO_OK) return st;
         for (int p = 0; p < ctx->P; ++p) lambda[p] = o->vol_mode == PETTO_VOL_PROJECTED ? sc[SC_LAM + p] : sc[SC_MEAN + p];
     }
+    return PETTO_OK;
+}
+
+petto_status petto_set_keepout(petto_ctx *ctx, const int64_t *box, const double *target, double kappa_b) {
+    if (!ctx) return PETTO_EINVAL;
+    if (!box) {
+        ctx->keep = 0;
+        return PETTO_OK;
+    }
+    if (!target) return fail(ctx, PETTO_EINVAL, "keep-out targets missing");
+    const int64_t n[3] = {ctx->L.nx, ctx->L.ny, ctx->dim == 3 ? ctx->L.nz : 1};
+    for (int a = 0; a < 3; ++a)
+        if (box[a] < 0 || box[3 + a] >= n[a] || box[a] > box[3 + a])
+            return fail(ctx, PETTO_EINVAL, "keep-out box outside the grid or empty");
+    if (!(kappa_b >= 0.0)) return fail(ctx, PETTO_EINVAL, "kappa_b must be >= 0");
+    for (int a = 0; a < 3; ++a) {
+        ctx->klo[a] = (int)box[a];
+        ctx->khi[a] = (int)box[3 + a];
+    }
+    for (int p = 0; p < ctx->P; ++p) ctx->Vb[p] = target[p];
+    ctx->kappa_b = kappa_b;
+    ctx->keep = 1;
     return PETTO_OK;
 }
 
@@ -1360,11 +1414,14 @@ petto_status petto_optimize(petto_ctx *ctx, int n_steps, const petto_solve_opts 
         petto_status st = petto_pt_solve(ctx, so, &rep);
         if (st == PETTO_ENOTCONV) notconv = true;
         else if (st != PETTO_OK) return st;
-        double C = 0, W = 0, lam[MAX_PHASES] = {0}, vol[MAX_PHASES] = {0};
-        st = petto_sensitivity(ctx, &C, &W, nullptr, PETTO_F64, 0);
+        // the design half without host round trips; one read of the scalars at the end
+        st = petto_sensitivity(ctx, nullptr, nullptr, nullptr, PETTO_F64, 0);
         if (st != PETTO_OK) return st;
-        st = petto_design_update(ctx, po, lam);
+        st = petto_design_update(ctx, po, nullptr);
         if (st != PETTO_OK) return st;
+        if (po->vol_mode == PETTO_VOL_PENALTY)  // keep the pre-step means (the penalty's lambda)
+            CK(cudaMemcpyAsync(ctx->scal + SC_SUM, ctx->scal + SC_MEAN, sizeof(double) * ctx->P,
+                               cudaMemcpyDeviceToDevice, ctx->stream));
         st = petto_cahn_hilliard(ctx, po);
         if (st != PETTO_OK) return st;
         ctx->step++;
@@ -1374,9 +1431,10 @@ petto_status petto_optimize(petto_ctx *ctx, int n_steps, const petto_solve_opts 
             double sc[SC_N];
             st = read_scal(ctx, sc);
             if (st != PETTO_OK) return st;
-            for (int p = 0; p < ctx->P; ++p) vol[p] = sc[SC_MEAN + p];
+            const double lam0 = po->vol_mode == PETTO_VOL_PROJECTED ? sc[SC_LAM] : sc[SC_SUM];
             const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-            const double m[8] = {(double)ctx->step, C, W, rep.rel_res, (double)rep.sweeps, secs, vol[0], lam[0]};
+            const double m[8] = {(double)ctx->step, sc[SC_C], sc[SC_W], rep.rel_res, (double)rep.sweeps, secs,
+                                 sc[SC_MEAN], lam0};
             cb(m, user);
         }
     }

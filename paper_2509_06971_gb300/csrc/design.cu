@@ -228,7 +228,20 @@ __global__ void upd_prepare(const UpdateArgs ua, S *__restrict__ phi, const T *_
         }
     }
     const T k1 = (T)ua.kappa_1;
+    // keep-out term (Sec. 3.4 J_b): kappa_b (mean over the region of phi_i - Vb_i) on its cells
+    T kb[MAX_PHASES];
+#pragma unroll
+    for (int p = 0; p < MAX_PHASES; ++p)
+        kb[p] = ua.keep && p < ua.P ? (T)(ua.kappa_b * (scal[SC_BMEAN + p] - ua.Vb[p])) : T(0);
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        bool inb = false;
+        if (ua.keep) {
+            const int i = (int)(c % ua.nx);
+            const int64_t r = c / ua.nx;
+            const int j = (int)(r % ua.ny), k = (int)(r / ua.ny);
+            inb = i >= ua.klo[0] && i <= ua.khi[0] && j >= ua.klo[1] && j <= ua.khi[1] && k >= ua.klo[2] &&
+                  k <= ua.khi[2];
+        }
         T tot = 0;
         T ph[MAX_PHASES];
 #pragma unroll
@@ -242,7 +255,8 @@ __global__ void upd_prepare(const UpdateArgs ua, S *__restrict__ phi, const T *_
 #pragma unroll
         for (int p = 0; p < MAX_PHASES; ++p) {
             if (p >= ua.P) break;
-            const T g = scale[p] * s[(int64_t)p * nc + c] + k1 * (tot - T(1));
+            T g = scale[p] * s[(int64_t)p * nc + c] + k1 * (tot - T(1));
+            if (inb) g += kb[p];
             const T dv = ph[p] - g;
             if (ua.vol_mode == 0) dbuf[(int64_t)p * nc + c] = dv;
             else Store<S>::st(phi, (int64_t)p * nc + c, dv - shift[p]);
@@ -360,6 +374,33 @@ __global__ void mean_kernel(int64_t nc, int P, const S *__restrict__ phi, double
     }
 }
 
+// mean of each phase over the keep-out cells, in FP64 with the deterministic reduction
+template <typename S>
+__global__ void box_mean_kernel(const UpdateArgs ua, const S *__restrict__ phi, double *scal, const RedBuf rb) {
+    __shared__ double sh[32];
+    const int p = blockIdx.y;
+    const int bx = ua.khi[0] - ua.klo[0] + 1, by = ua.khi[1] - ua.klo[1] + 1, bz = ua.khi[2] - ua.klo[2] + 1;
+    const int64_t nb = (int64_t)bx * by * bz;
+    double acc = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nb; t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = ua.klo[0] + (int)(t % bx);
+        const int64_t r = t / bx;
+        const int j = ua.klo[1] + (int)(r % by), k = ua.klo[2] + (int)(r / by);
+        const int64_t c = (int64_t)i + (int64_t)ua.nx * ((int64_t)j + (int64_t)ua.ny * k);
+        acc += (double)Store<S>::ld(phi, (int64_t)p * ua.ncell + c);
+    }
+    const double tot = block_sum(acc, sh);
+    if (publish_partial(tot, rb, (int64_t)p * gridDim.x + blockIdx.x, gridDim.x * gridDim.y)) {
+#pragma unroll
+        for (int q = 0; q < MAX_PHASES; ++q) {
+            if (q >= ua.P) break;
+            const double m = sum_partials(rb, (int64_t)q * gridDim.x, gridDim.x, sh);
+            if (threadIdx.x == 0) scal[SC_BMEAN + q] = m / (double)nb;
+        }
+        if (threadIdx.x == 0) *rb.counter = 0u;
+    }
+}
+
 int grid_for(int64_t n, int block, int cap = 152 * 16) {
     int64_t g = (n + block - 1) / block;
     if (g < 1) g = 1;
@@ -440,6 +481,14 @@ cudaError_t launch_mean(const Layout &L, int P, int storage, const void *phi, do
 cudaError_t launch_update(const UpdateArgs &ua, void *phi, const void *s, void *dscratch, double *scal,
                           RedBuf rb, cudaStream_t st, int64_t *launches) {
     const int g = grid_for(ua.ncell, 256);
+    if (ua.keep) {
+        const int64_t nb = (int64_t)(ua.khi[0] - ua.klo[0] + 1) * (ua.khi[1] - ua.klo[1] + 1) *
+                           (ua.khi[2] - ua.klo[2] + 1);
+        dim3 gb(grid_for(nb, 256, 152 * 4), ua.P);
+        PETTO_DISPATCH_STORAGE(ua.storage, S,
+            box_mean_kernel<S><<<gb, 256, 0, st>>>(ua, static_cast<const S *>(phi), scal, rb))
+        *launches += 1;
+    }
     PETTO_DISPATCH_PREC(ua.precision, T,
         PETTO_DISPATCH_STORAGE(ua.storage, S,
             upd_prepare<T, S><<<g, 256, 0, st>>>(ua, static_cast<S *>(phi), static_cast<const T *>(s),

@@ -340,9 +340,10 @@ struct SensArgs {
 };
 
 // scal layout (device doubles): [0] sum R^2, [1] compliance, [2] work, [8..8+P) max|s_i|,
-// [16..16+P) lo_i, [24..24+P) hi_i, [32..32+P) sums, [40..40+P) mean_i, [48..48+P) lambda_i
+// [16..16+P) lo_i, [24..24+P) hi_i, [32..32+P) sums, [40..40+P) mean_i, [48..48+P) lambda_i,
+// [56..56+P) mean of phi_i over the keep-out region
 constexpr int SC_RES = 0, SC_C = 1, SC_W = 2, SC_SMAX = 8, SC_LO = 16, SC_HI = 24, SC_SUM = 32,
-              SC_MEAN = 40, SC_LAM = 48, SC_N = 64;
+              SC_MEAN = 40, SC_LAM = 48, SC_BMEAN = 56, SC_N = 64;
 
 cudaError_t launch_sensitivity(const SensArgs &sa, const DesignArgs &d, const void *u, const void *E,
                                const void *phi, void *s, double *scal, RedBuf rb, cudaStream_t st);
@@ -358,6 +359,12 @@ struct UpdateArgs {
     int P, vol_mode, n_bisect, precision, storage;
     double alpha_h, kappa_v, kappa_1;
     double V[MAX_PHASES];
+    // keep-out region (Sec. 3.4 J_b): cells lo..hi (inclusive) of an nx x ny (x nz) grid
+    int keep;                 // 0: no keep-out term
+    int nx, ny;
+    int klo[3], khi[3];
+    double kappa_b;
+    double Vb[MAX_PHASES];
 };
 
 cudaError_t launch_update(const UpdateArgs &ua, void *phi, const void *s, void *dscratch, double *scal,

@@ -105,6 +105,8 @@ class Problem:
         self.ctx = ctx
         if spec.phi0 is not None:
             self.set_design(np.asarray(spec.phi0, dtype=np.float64))
+        if spec.keepout is not None:
+            self.set_keepout(spec.keepout, spec.keepout_target, spec.kappa_b)
 
     # --------------------------------------------------------------- lifecycle
     def close(self):
@@ -147,6 +149,17 @@ class Problem:
         buf = ctypes.create_string_buffer(4096)
         self._ck(self.lib.petto_autotune(self.ctx, int(sweeps), buf, len(buf)))
         return json.loads(buf.value.decode() or "{}")
+
+    def set_keepout(self, box, target, kappa_b: float):
+        """Keep-out region of the update (petto_set_keepout): box ((lo), (hi)) inclusive cell
+        ranges, target per phase; box None removes it."""
+        if box is None:
+            self._ck(self.lib.petto_set_keepout(self.ctx, None, None, 0.0))
+            return
+        lo, hi = (list(box[0]) + [0, 0])[:3], (list(box[1]) + [0, 0])[:3]
+        b = (ctypes.c_int64 * 6)(*(lo + hi))
+        t = (ctypes.c_double * self.P)(*[float(x) for x in target])
+        self._ck(self.lib.petto_set_keepout(self.ctx, b, t, float(kappa_b)))
 
     def select_kernel(self, name: str):
         """Pick the sweep kernel by autotuner name ("march2d", "gather/32x8", "tma2/zs16", ...)."""

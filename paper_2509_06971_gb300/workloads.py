@@ -66,6 +66,11 @@ class ProblemSpec:
     gamma_g: float = 0.0
     tau: float = 0.0
     n_bisect: int = 60
+    # keep-out region of the update (Sec. 3.4 J_b): ((lo_i, lo_j, lo_k), (hi_i, hi_j, hi_k))
+    # inclusive cell ranges, per-phase targets and kappa_b = 2 alpha_b / N_b
+    keepout: tuple | None = None
+    keepout_target: list = field(default_factory=list)
+    kappa_b: float = 0.0
     design_steps: int = 1
     precision: str = "f32"
     storage: str = "f32"
@@ -242,6 +247,81 @@ def mbb_multimat2d(nx: int = 512, ny: int = 128, precision: str = "f32") -> Prob
         apt_a=a, apt_b=b, pt_s1=s1, local_dt=False, momentum=0, solve_mode=0, n_apt=20, n_pt=20,
         check_every=0, vol_mode=PENALTY, alpha_h=0.1, kappa_v=2.0 * 1e4 / n, kappa_1=2.0 * 1e3 / n,
         tau=tau, gamma_g=gg, design_steps=200, precision=precision, storage=precision)
+
+
+def heat2d_paper(n: int = 512, precision: str = "f32") -> ProblemSpec:
+    """The paper's heat-conduction loop (Sec. 3.1): n x n cells, T = 0 on the top and left
+    sides, no flux elsewhere, uniform source f = 0.01, one conductor (kappa = 1) with an
+    explicit void phase (kappa = 1e-6), solid fraction 0.3, kappa = sum_i kappa_i phi_i^3,
+    both phases starting at 1.0.  Each loop: 500 APT then 500 PT sweeps with the paper's
+    global steps (thermal form, dt2 = dx/2, theta = 1, dt1 = dx^2/4), the penalty update with
+    alpha_h = 0.1, alpha_v = 1e5, alpha_1 = 1e4 (reading R7), one Cahn-Hilliard step with
+    dt3 = 500 dx^4.  Grid units with dx = 1/n (reading R12: the printed L = 4 is garbled)."""
+    h_p = 1.0 / n
+    a, b, s1 = apt_params(h_p, elastic=False, dim=2)
+    tau, gg = ch_params(h_p, 2)
+    fr = [0.7, 0.3]
+    nc = n * n
+    return ProblemSpec(
+        name=f"heat2d_paper_{n}", dim=2, nx=n, ny=n, physics=THERMAL, moduli=[1e-6, 1.0], e_min=0.0,
+        interp=SIMP_PAPER, vol_frac=fr, body_source=0.01,
+        boxes=[((0, 0, 0), (0, n, 0), 1), ((0, n, 0), (n, n, 0), 1)], phi0=np.full((2, nc), 1.0),
+        apt_a=a, apt_b=b, pt_s1=s1, local_dt=False, momentum=0, solve_mode=0, n_apt=500, n_pt=500,
+        check_every=0, vol_mode=PENALTY, alpha_h=0.1, kappa_v=2.0 * 1e5 / nc, kappa_1=2.0 * 1e4 / nc,
+        tau=tau, gamma_g=gg, design_steps=5000, precision=precision, storage=precision)
+
+
+def multimat3d_paper(nx: int = 256, ny: int = 17, nz: int = 85, precision: str = "f32") -> ProblemSpec:
+    """The paper's 3D multi-material cantilever loop (Sec. 3.3): 256 x 17 x 85 cells of size
+    1/128 (2 x 2/15 x 2/3), the x = L face fixed, a unit force in +z spread along the
+    horizontal centre line of the x = 0 face (nodes (0, j, nz/2), end nodes half weight;
+    reading R24), three materials E = 1.0, 0.6, 0.2 with V = 0.1 each plus a void phase
+    (E = 1e-6, V = 0.7).  Each loop: 100 APT then 100 PT sweeps with the paper's global
+    steps (dt2 = dx/2, dt1 = dx^2/6), the penalty update with the MBB weights
+    (alpha_v = 1e4, alpha_1 = 1e3), one Cahn-Hilliard step (dt3 = 500 dx^4)."""
+    h_p = 1.0 / 128.0
+    a, b, s1 = apt_params(h_p, elastic=True, dim=3)
+    tau, gg = ch_params(h_p, 3)
+    fr = [0.7, 0.1, 0.1, 0.1]
+    n = nx * ny * nz
+    kz = nz // 2
+    w = [0.5 if j in (0, ny) else 1.0 for j in range(ny + 1)]
+    tot = sum(w)
+    return ProblemSpec(
+        name=f"multimat3d_paper_{nx}x{ny}x{nz}", dim=3, nx=nx, ny=ny, nz=nz, moduli=[1e-6, 1.0, 0.6, 0.2],
+        e_min=0.0, interp=SIMP_PAPER, vol_frac=fr, boxes=[((nx, 0, 0), (nx, ny, nz), 0b111)],
+        loads=[((0, j, kz), 2, w[j] / tot) for j in range(ny + 1)], phi0=_uniform_phi(n, fr),
+        apt_a=a, apt_b=b, pt_s1=s1, local_dt=False, momentum=0, solve_mode=0, n_apt=100, n_pt=100,
+        check_every=0, vol_mode=PENALTY, alpha_h=0.1, kappa_v=2.0 * 1e4 / n, kappa_1=2.0 * 1e3 / n,
+        tau=tau, gamma_g=gg, design_steps=4000, precision=precision, storage=precision)
+
+
+def drone3d(nx: int = 128, ny: int = 64, nz: int = 128, vol: float = 0.12, precision: str = "f32") -> ProblemSpec:
+    """The drone skeleton (Sec. 3.4): a 1.0 x 0.5 x 1.0 box (y vertical) on nx x ny x nz
+    cells, rollers (u_y = 0) at the four top corners, a unit downward point load at the
+    centre of the bottom face, one solid (E = 1) with an explicit void phase (E = 1e-6),
+    solid fraction ``vol``.  A keep-out region must stay void: J_b with targets 1 (void) and
+    0 (solid); the region is proposed here (the paper's figure is missing): the central
+    quarter in x and z, the middle half in y.  Each loop: 50 APT then 50 PT sweeps with the
+    paper's global steps, the penalty update with the MBB weights (alpha_v = 1e4,
+    alpha_1 = 1e3) and alpha_b = alpha_v (reading R23), one Cahn-Hilliard step."""
+    h_p = 1.0 / nx
+    a, b, s1 = apt_params(h_p, elastic=True, dim=3)
+    tau, gg = ch_params(h_p, 3)
+    n = nx * ny * nz
+    fr = [1.0 - vol, vol]
+    lo = (3 * nx // 8, ny // 4, 3 * nz // 8)
+    hi = (5 * nx // 8 - 1, 3 * ny // 4 - 1, 5 * nz // 8 - 1)
+    nb = (hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1)
+    corners = [(0, ny, 0), (nx, ny, 0), (0, ny, nz), (nx, ny, nz)]
+    return ProblemSpec(
+        name=f"drone3d_{nx}x{ny}x{nz}", dim=3, nx=nx, ny=ny, nz=nz, moduli=[1e-6, 1.0], e_min=0.0,
+        interp=SIMP_PAPER, vol_frac=fr, boxes=[(c, c, 0b010) for c in corners],
+        loads=[((nx // 2, 0, nz // 2), 1, -1.0)], phi0=_uniform_phi(n, fr),
+        apt_a=a, apt_b=b, pt_s1=s1, local_dt=False, momentum=0, solve_mode=0, n_apt=50, n_pt=50,
+        check_every=0, vol_mode=PENALTY, alpha_h=0.1, kappa_v=2.0 * 1e4 / n, kappa_1=2.0 * 1e3 / n,
+        keepout=(lo, hi), keepout_target=[1.0, 0.0], kappa_b=2.0 * 1e4 / nb,
+        tau=tau, gamma_g=gg, design_steps=40000, precision=precision, storage=precision)
 
 
 def multimat3d(nx: int = 384, ny: int = 192, nz: int = 192, storage: str = "bf16") -> ProblemSpec:

@@ -318,6 +318,81 @@ def test_paper_multimat_mbb_loop_fp64(P):
     prob.close()
 
 
+@pytest.mark.parametrize("name", ["heat", "multimat3d"])
+def test_paper_loops_fp64(P, name):
+    """The paper's heat-conduction (Sec. 3.1) and 3D multi-material (Sec. 3.3) loops on small
+    copies with fewer sweeps per loop: fixed APT/PT counts with global steps, penalty update
+    with the full-size problems' weights, Cahn-Hilliard; against the oracle loop for loop."""
+    if name == "heat":
+        spec, full, napt = W.heat2d_paper(32, precision="f64"), W.heat2d_paper(512), 40
+    else:
+        spec, full, napt = W.multimat3d_paper(32, 6, 12, precision="f64"), W.multimat3d_paper(), 20
+    pf = dict(kappa_v=full.kappa_v, kappa_1=full.kappa_1)
+    steps = 3
+    prob = P.Problem(spec)
+    hist, _ = prob.optimize(steps, solve_kw=dict(n_apt=napt, n_pt=napt), pf_kw=pf)
+    op, om = oracle_problem(spec), oracle_materials(spec)
+    F, fixed = op.load_vector(), op.fixed_mask()
+    phi, u = spec.phi0.copy(), np.zeros(op.ndof)
+    for t in range(steps):
+        m = O.design_step(op, om, phi, u, F, fixed, spec.vol_frac,
+                          dict(mode=0, n_apt=napt, n_pt=napt, a=spec.apt_a, b=spec.apt_b, s1=spec.pt_s1,
+                               check_every=0, local_dt=False, momentum=0),
+                          dict(vol_mode=W.PENALTY, alpha_h=spec.alpha_h, gamma_g=spec.gamma_g, tau=spec.tau, **pf))
+        assert abs(hist[t]["compliance"] - m["compliance"]) <= 1e-10 * abs(m["compliance"])
+    assert relmax(prob.get_design(), phi) < 1e-10
+    prob.close()
+
+
+def _keep_mask(spec):
+    (lo, hi) = spec.keepout
+    nzc = spec.nz if spec.dim == 3 else 1
+    k, j, i = np.meshgrid(np.arange(nzc), np.arange(spec.ny), np.arange(spec.nx), indexing="ij")
+    inside = ((i >= lo[0]) & (i <= hi[0]) & (j >= lo[1]) & (j <= hi[1]) & (k >= lo[2]) & (k <= hi[2]))
+    return inside.reshape(-1)
+
+
+@pytest.mark.parametrize("vol_mode", [W.PENALTY, W.PROJECTED])
+def test_drone_keepout_loop_fp64(P, vol_mode):
+    """The drone loop (Sec. 3.4) on a 24 x 12 x 24 copy: solid + explicit void, rollers at
+    the four top corners, the keep-out term J_b in the update (penalty and projected
+    volume modes), 10 APT + 10 PT sweeps per loop, against the oracle loop for loop."""
+    steps = 3
+    n_full, nb_full = 128 * 64 * 128, 32 * 32 * 32
+    spec = W.drone3d(24, 12, 24, precision="f64").with_(kappa_b=2e4 / nb_full)  # the full problem's weights
+    pf = dict(kappa_v=2e4 / n_full, kappa_1=2e3 / n_full, vol_mode=vol_mode)
+    prob = P.Problem(spec)
+    hist, _ = prob.optimize(steps, solve_kw=dict(n_apt=10, n_pt=10), pf_kw=pf)
+    op, om = oracle_problem(spec), oracle_materials(spec)
+    F, fixed = op.load_vector(), op.fixed_mask()
+    phi, u = spec.phi0.copy(), np.zeros(op.ndof)
+    keep = _keep_mask(spec)
+    for t in range(steps):
+        m = O.design_step(op, om, phi, u, F, fixed, spec.vol_frac,
+                          dict(mode=0, n_apt=10, n_pt=10, a=spec.apt_a, b=spec.apt_b, s1=spec.pt_s1,
+                               check_every=0, local_dt=False, momentum=0),
+                          dict(alpha_h=spec.alpha_h, gamma_g=spec.gamma_g, tau=spec.tau, keepout=keep,
+                               Vb=spec.keepout_target, kappa_b=spec.kappa_b, **pf))
+        assert abs(hist[t]["compliance"] - m["compliance"]) <= 1e-10 * abs(m["compliance"])
+    g = prob.get_design()
+    assert relmax(g, phi) < 1e-10
+    # the region holds more void than the rest of the domain
+    assert g[0, keep].mean() > g[0, ~keep].mean()
+    prob.close()
+
+
+def test_keepout_argument_checks(P):
+    from paper_2509_06971_gb300 import capi as C
+    spec = W.drone3d(16, 8, 16, precision="f64")
+    prob = P.Problem(spec)
+    for box in (((0, 0, 0), (16, 3, 3)), ((3, 3, 3), (2, 4, 4)), ((-1, 0, 0), (2, 2, 2))):
+        with pytest.raises(C.PettoError) as e:
+            prob.set_keepout(box, [1.0, 0.0], 1.0)
+        assert e.value.status == C.PETTO_EINVAL
+    prob.set_keepout(None, None, 0.0)
+    prob.close()
+
+
 def test_checkpoint_roundtrip(P, tmp_path):
     spec = W.mbb_halfbeam(30, 10)
     prob = P.Problem(spec)
