@@ -37,6 +37,8 @@ WORKLOADS = {
     "cantilever2d_1024x512": lambda: W.cantilever2d(1024, 512),
     "heat2d_1024x1024": lambda: W.heat2d(1024),
     "multimat3d_384x192x192_bf16": lambda: W.multimat3d(storage="bf16"),
+    "multimat3d_384x192x192_fp16": lambda: W.multimat3d(storage="f16"),
+    "multimat3d_384x192x192_fp32": lambda: W.multimat3d(storage="f32"),
     "cantilever3d_64x32x32": lambda: W.cantilever3d(64, 32, 32),
     "mbb_multimat2d_512x128": lambda: W.mbb_multimat2d(512, 128),
     "drone3d_128x64x128": lambda: W.drone3d(128, 64, 128),
