@@ -64,3 +64,12 @@ def test_reference_arm_prints_contract_line():
               "cpu_baseline", "e2e"):
         assert k in d
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_batch_shard_covers_every_problem_once():
+    import bench
+    items = list(range(48))
+    for world in (1, 2, 3, 4, 8):
+        parts = [bench.shard(items, r, world) for r in range(world)]
+        assert sorted(x for p in parts for x in p) == items
+        assert max(len(p) for p in parts) - min(len(p) for p in parts) <= 1
