@@ -40,6 +40,7 @@ WORKLOADS = {
     "multimat3d_384x192x192_fp16": lambda: W.multimat3d(storage="f16"),
     "multimat3d_384x192x192_fp32": lambda: W.multimat3d(storage="f32"),
     "cantilever3d_64x32x32": lambda: W.cantilever3d(64, 32, 32),
+    "mbb_halfbeam_60x20": lambda: W.mbb_halfbeam(60, 20),
     "mbb_multimat2d_512x128": lambda: W.mbb_multimat2d(512, 128),
     "drone3d_128x64x128": lambda: W.drone3d(128, 64, 128),
     "heat2d_paper_512": lambda: W.heat2d_paper(512),
@@ -315,6 +316,42 @@ def run_ours(args):
     return 0
 
 
+def run_time_to_design(args):
+    """Time to design: the workload's whole design run (its design_steps loops from the
+    initial design), wall time on the device, with the final compliance and volume."""
+    import numpy as np
+    import torch
+
+    from paper_2509_06971_gb300 import problem as PR
+    torch.cuda.set_device(0)
+    spec = WORKLOADS[args.workload]()
+    steps = args.design_steps or spec.design_steps
+    prob = PR.Problem(spec)
+    solve_kw = dict(tol=spec.tol, max_sweeps=args.max_sweeps, check_every=spec.check_every)
+    warm = PR.Problem(spec)  # graph capture and first-touch outside the timed run
+    warm.optimize(1, solve_kw=solve_kw)
+    warm.close()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hist, _ = prob.optimize(steps, solve_kw=solve_kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) * 1e-3
+    sweeps = sum(h["sweeps"] for h in hist)
+    phi = prob.get_design()
+    line = {"metric": "time to design", "value": secs, "unit": "s", "higher_is_better": False,
+            "workload": args.workload, "design_steps": steps, "total_sweeps": sweeps,
+            "Gcell_sweeps_per_s": spec.ncells * sweeps / secs / 1e9,
+            "final_compliance": hist[-1]["compliance"], "final_rel_res": hist[-1]["rel_res"],
+            "final_mean_phi": [float(x) for x in phi.mean(axis=1)], "target_vol": list(spec.vol_frac),
+            "max_rel_res": max(h["rel_res"] for h in hist), "data": "synthetic"}
+    print(json.dumps(line))
+    prob.close()
+    return 0
+
+
 def shard(items, rank, world):
     """The problems of a batch that rank `rank` of `world` solves: every world-th one, so
     the ranks get mixed sizes; independent problems need no collective."""
@@ -532,9 +569,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="only run this many APT sweeps of the workload (for profiler captures)")
+    ap.add_argument("--time-to-design", action="store_true",
+                    help="time the workload's whole design run instead (one JSON line)")
+    ap.add_argument("--design-steps", type=int, default=0, help="with --time-to-design: override the step count")
     args = ap.parse_args()
     if args.sweeps_only:
         return run_sweeps_only(args)
+    if args.time_to_design:
+        return run_time_to_design(args)
     if args.impl == "reference":
         if args.workload in BATCH_WORKLOADS:
             print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times single-problem workloads"}))
