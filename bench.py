@@ -492,7 +492,7 @@ def run_batch(args):
         "sweeps_per_design_iter": {"max": float(sweeps.max()), "mean": float(sweeps.mean())},
         "single_problem_path": {"s_per_design_iter": alone_ms * 1e-3, "batched_s_per_design_iter": batch_ms * 1e-3,
                                 "batched_speedup": alone_ms / batch_ms,
-                                "kernel": "default single-problem 2D sweep (node gather)",
+                                "kernel": "default single-problem 2D sweep (y-marching from 200 K nodes, node gather below)",
                                 "sweeps_total": int(sum(alone_sweeps)), "batched_sweeps_total": int(sum(batch_sweeps))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,

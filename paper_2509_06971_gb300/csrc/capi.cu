@@ -2082,7 +2082,7 @@ std::vector<std::pair<std::string, Tiling>> kernel_candidates(const petto_ctx *c
         return cand;
     }
     if (march2d_ok(ctx))
-        for (int ly : {0, 4, 8, 16}) {
+        for (int ly : {4, 8, 16}) {
             const Tiling t = march2d_tiling(L, ly);
             cand.emplace_back("march2d/ly" + std::to_string(t.ly), t);
         }

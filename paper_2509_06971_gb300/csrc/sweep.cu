@@ -790,12 +790,10 @@ Tiling march2d_tiling(const Layout &L, int ly) {
     t.zs = 1;
     t.ox = 30;
     t.gx = (L.NX + t.ox - 1) / t.ox;
-    if (ly <= 0) {
-        // the longest segment (of 16, 8, 4 rows) that still gives about 16 warps per SM;
-        // each warp recomputes one row below its segment
-        ly = 16;
-        while (ly > 4 && (int64_t)t.gx * ((L.NY + ly - 1) / ly) < 152 * 16) ly /= 2;
-    }
+    // 4 rows per warp unless asked otherwise: the shortest segments (each warp recomputes one
+    // row below its own) measured fastest from 512^2 to 2048 x 1024 nodes, single problems
+    // and batches alike -- the kernel is bound by the latency of a warp's row chain
+    if (ly <= 0) ly = 4;
     ly = ly >= 16 ? 16 : (ly >= 8 ? 8 : 4);  // the compiled variants
     t.ly = ly;
     t.oy = M2W * ly;
@@ -805,6 +803,11 @@ Tiling march2d_tiling(const Layout &L, int ly) {
 }
 
 Tiling choose_tiling(const Layout &L, int physics, int precision, int nrhs) {
+    // 2D, one load case: the y-marching kernel from about 500 x 400 nodes (below, the node
+    // gather's extra parallelism wins); 32-bit offsets required
+    if (L.dim == 2 && nrhs == 1 && (int64_t)L.NX * L.NY >= 200000 && 2 * L.cstride < (int64_t(1) << 31) &&
+        L.estride < (int64_t(1) << 31))
+        return march2d_tiling(L);
     if (L.dim == 3 && physics == 0 && precision == 0) {
         // z-marching kernel: TMA-staged with two owner rows per thread by default;
         // PETTO_MARCH=tma8 / tma16 select one row per thread (32x8 / 32x16 tiles),
