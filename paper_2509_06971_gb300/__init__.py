@@ -2,7 +2,8 @@
 
 The numerics live in libpetto.so (hand-written CUDA for sm_103a behind the C ABI of
 include/petto.h).  ``capi`` is the ctypes binding with the C names, ``problem.Problem``
-a thin owner of one context, ``workloads`` the seeded synthetic problem instances.
+a thin owner of one context, ``problem.Batch`` of a batch of 2D contexts advanced by one
+launch per sweep, ``workloads`` the seeded synthetic problem instances.
 Nothing is loaded at import time; the first use loads (and if needed builds) the
 library and raises if that fails -- there is no CPU fallback.
 """

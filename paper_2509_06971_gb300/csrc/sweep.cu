@@ -16,8 +16,10 @@
 //                  the Lame parameters of Sec. 3.2, plane strain in 2D).
 // Heat conduction keeps only the edge terms with the scalar temperature.  K u is the
 // gradient of sum_e W_e + sum_f W_f.  The FP64 oracle evaluates the corner definition
-// literally with a cell loop; these kernels gather, per node, the forces of its incident
-// edges and faces, so the two agree only if the expansion above is right.
+// literally with a cell loop; the kernels here either gather, per node, the forces of its
+// incident edges and faces (node-gather kernels), or evaluate each edge and face once at
+// its owner node and pass the shares on (2D y-marching kernel below, 3D z-marching kernels
+// in sweep3d_march.cu), so the two agree only if the expansion above is right.
 //
 // One sweep (APT):  R = F - K u (0 on supports);  w <- a w + b' R;  u' <- u + w
 //          (PT):    u' <- u + s1' R
