@@ -254,8 +254,10 @@ def run_ours(args):
 
     peaks, peak_kind = measured_peaks()
     per_launch_ms = kern_ms / max(kern_n, 1)
-    # refinement sweeps read a dense FP32 right-hand side as well (ncomp x 4 B per node)
-    bytes_avg = sweep_bytes(spec) + (kern_rhs / max(kern_n, 1)) * spec.nnodes * spec.ncomp * 4
+    # refinement sweeps read a dense right-hand side as well (ncomp values per node; FP16 for
+    # the two-row 3D marching kernel, FP32 otherwise)
+    kname, rhs_b = prob.kernel_info()
+    bytes_avg = sweep_bytes(spec) + (kern_rhs / max(kern_n, 1)) * spec.nnodes * spec.ncomp * rhs_b
     achieved = bytes_avg / (per_launch_ms * 1e-3) / 1e9 if kern_n else None
     peak = float(peaks.get("hbm_gbs", 6800.0))
 
@@ -300,7 +302,8 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
                      "kernel": "apt sweep", "kernel_ms": per_launch_ms, "bytes_per_launch": bytes_avg,
-                     "rhs_sweep_fraction": kern_rhs / max(kern_n, 1), "peak_kind": peak_kind},
+                     "rhs_sweep_fraction": kern_rhs / max(kern_n, 1), "rhs_bytes": rhs_b,
+                     "sweep_kernel": kname, "peak_kind": peak_kind},
         "e2e": {"value": e_value, "unit": "Gcell-sweeps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e_steps},
         "gpu_launches": launches,

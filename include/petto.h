@@ -288,6 +288,13 @@ petto_status petto_autotune(petto_ctx *ctx, int n, char *report, int report_len)
  * Every variant computes the same sweep; they differ in tiling and summation order. */
 petto_status petto_select_kernel(petto_ctx *ctx, const char *name);
 
+/* The sweep kernel in use, by the name petto_select_kernel takes ("custom" if none
+ * matches), copied NUL-terminated into name (at most name_len bytes; may be NULL), and in
+ * *rhs_bytes (may be NULL) the bytes per node and component of the dense right-hand side
+ * that its refinement sweeps read: 2 for the two-row 3D marching kernel, which reads the
+ * defect as FP16 scaled by a power of two, else the size of the sweep precision. */
+petto_status petto_kernel_info(petto_ctx *ctx, char *name, int name_len, int *rhs_bytes);
+
 /* ---------------------------------------------------------------- batches
  * Many independent 2D problems advanced together (the paper solves one design problem at a
  * time; batching changes how the work is scheduled on the GPU, not what each problem

@@ -98,6 +98,7 @@ _SIGS = {
     "petto_residual_norm_static": (_int, [_P(petto_grid), _dbl, _vp, _vp, _vp, _vp, _P(_dbl), _vp]),
     "petto_autotune": (_int, [_vp, _int, ctypes.c_char_p, _int]),
     "petto_select_kernel": (_int, [_vp, ctypes.c_char_p]),
+    "petto_kernel_info": (_int, [_vp, ctypes.c_char_p, _int, _P(_int)]),
     "petto_set_keepout": (_int, [_vp, _P(_i64), _P(_dbl), _dbl]),
     "petto_batch_create": (_int, [_int, _P(_vp), _P(_vp)]),
     "petto_batch_destroy": (None, [_vp]),

@@ -56,6 +56,7 @@ struct petto_ctx {
     std::vector<std::pair<std::pair<int64_t, int>, double>> load_list;  // merged (node, component) -> value
     double *ctrl = nullptr;
     void *u64 = nullptr, *r64 = nullptr, *rhs32 = nullptr;
+    bool rhs_half = false;  // rhs32 holds the scaled FP16 copy (two-row marching kernel)
     int cur = 0;
     int64_t launches = 0;
     int64_t step = 0;
@@ -365,6 +366,7 @@ petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, 
     A.sweep_idx = sc.idx;
     A.base_from_ctrl = sc.base_from_ctrl;
     A.rhs = sc.rhs;
+    A.rhs_half = sc.rhs && sc.rhs == ctx->rhs32 && ctx->rhs_half;
     A.a = a;
     A.b = b;
     A.s1 = s1;
@@ -935,6 +937,27 @@ __global__ void f64_to_f32(int64_t n, const double *__restrict__ a, float *__res
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
         b[t] = (float)a[t];
 }
+// max |a| into *m (which starts at 0): the bit patterns of non-negative doubles order as integers
+__global__ void abs_max_f64(int64_t n, const double *__restrict__ a, double *m) {
+    double v = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        v = fmax(v, fabs(a[t]));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0 && v > 0.0)
+        atomicMax(reinterpret_cast<unsigned long long *>(m), (unsigned long long)__double_as_longlong(v));
+}
+// b = FP16(a 2^k) with 2^k the power of two taking max |a| = m into [2^14, 2^15) (all
+// entries stay below the FP16 maximum); 2^-k, the factor that restores a, goes to *inv
+__global__ void f64_to_f16_scaled(int64_t n, const double *__restrict__ a, const double *m, double *inv,
+                                  __half *__restrict__ b) {
+    int e = 0;
+    frexp(*m, &e);  // m < 2^e
+    const int k = 15 - e;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *inv = ldexp(1.0, -k);
+    const double sc = ldexp(1.0, k);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        b[t] = __float2half_rn((float)(a[t] * sc));
+}
 __global__ void add_f32_to_f64(int64_t n, const float *__restrict__ d, double *__restrict__ u) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
         u[t] += (double)d[t];
@@ -1081,7 +1104,11 @@ petto_status refine_begin(petto_ctx *ctx) {
     const size_t nb64 = (size_t)ctx->ndofc() * ctx->L.cstride * sizeof(double);
     const int64_t nel = (int64_t)ctx->ndofc() * ctx->L.cstride;
     if (!ctx->u64) CK(cudaMalloc(&ctx->u64, nb64));
-    if (!ctx->r64) CK(cudaMalloc(&ctx->r64, nb64));
+    if (!ctx->r64) {
+        CK(cudaMalloc(&ctx->r64, nb64));
+        // the defect kernel writes grid nodes only: the padding stays zero (it enters max |r|)
+        CK(cudaMemsetAsync(ctx->r64, 0, nb64, ctx->stream));
+    }
     if (!ctx->rhs32) CK(cudaMalloc(&ctx->rhs32, ctx->node_bytes()));
     f32_to_f64<<<grid_of(nel), 256, 0, ctx->stream>>>(nel, (const float *)ctx->u[ctx->cur], (double *)ctx->u64);
     CK(cudaGetLastError());
@@ -1107,10 +1134,27 @@ petto_status refine_defect(petto_ctx *ctx, double *norm) {
     return PETTO_OK;
 }
 
-// the defect becomes the FP32 right-hand side; the correction d = u restarts from zero
+// the defect becomes the right-hand side of the correction sweeps, which restart from d = 0.
+// The two-row 3D marching kernel reads it as FP16 scaled by a power of two (one TMA box per
+// stage, 6 bytes a node instead of 12); FP16 keeps 11 bits, so the correction solved to the
+// FP32 floor (about 1e-4 of its right-hand side) loses nothing the next defect does not see.
 petto_status refine_correction(petto_ctx *ctx) {
     const int64_t nel = (int64_t)ctx->ndofc() * ctx->L.cstride;
-    f64_to_f32<<<grid_of(nel), 256, 0, ctx->stream>>>(nel, (const double *)ctx->r64, (float *)ctx->rhs32);
+    ctx->rhs_half = ctx->tiling.kind == 4;
+    if (ctx->rhs_half) {
+        CK(cudaMemsetAsync(ctx->ctrl + CT_RMAX, 0, sizeof(double), ctx->stream));
+        abs_max_f64<<<grid_of(nel), 256, 0, ctx->stream>>>(nel, (const double *)ctx->r64, ctx->ctrl + CT_RMAX);
+        f64_to_f16_scaled<<<grid_of(nel), 256, 0, ctx->stream>>>(nel, (const double *)ctx->r64, ctx->ctrl + CT_RMAX,
+                                                                  ctx->ctrl + CT_RSCALE, (__half *)ctx->rhs32);
+        ctx->launches += 2;
+        if (!ctx->tma.rvalid || ctx->tma.rbuf != ctx->rhs32) {
+            if (!make_tma_rhs_map(ctx->L, ctx->ndofc(), ctx->rhs32, ctx->tma))
+                return fail(ctx, PETTO_ECUDA, "tensor map creation failed");
+            clear_graphs(ctx);
+        }
+    } else {
+        f64_to_f32<<<grid_of(nel), 256, 0, ctx->stream>>>(nel, (const double *)ctx->r64, (float *)ctx->rhs32);
+    }
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(ctx->u[ctx->cur], 0, ctx->node_bytes(), ctx->stream));
     ctx->launches++;
@@ -2112,6 +2156,27 @@ petto_status petto_select_kernel(petto_ctx *ctx, const char *name) {
         if (c.first == want || c.first.compare(0, want.size() + 1, want + "/") == 0) return set_tiling(ctx, c.second);
     }
     return fail(ctx, PETTO_EINVAL, "no sweep kernel named " + want + " applies to this problem");
+}
+
+petto_status petto_kernel_info(petto_ctx *ctx, char *name, int name_len, int *rhs_bytes) {
+    if (!ctx) return fail(ctx, PETTO_EINVAL, "null context");
+    const Tiling &t = ctx->tiling;
+    std::string nm = "custom";
+    for (auto &c : kernel_candidates(ctx)) {
+        const Tiling &q = c.second;
+        if (q.kind == t.kind && q.bx == t.bx && q.by == t.by && q.zs == t.zs && q.ox == t.ox && q.oy == t.oy &&
+            (q.kind != 5 || q.ly == t.ly)) {
+            nm = c.first;
+            break;
+        }
+    }
+    if (name && name_len > 0) {
+        std::strncpy(name, nm.c_str(), name_len - 1);
+        name[name_len - 1] = 0;
+    }
+    // refinement sweeps of the two-row 3D marching kernel read an FP16 right-hand side
+    if (rhs_bytes) *rhs_bytes = t.kind == 4 ? 2 : (ctx->precision == PETTO_F32 ? 4 : 8);
+    return PETTO_OK;
 }
 
 // Time each sweep-kernel variant that applies to this problem for n sweeps from the

@@ -81,6 +81,8 @@ constexpr int CT_RESTART_AT = 0;  // sweep index (int64 bits) at which the APT m
 constexpr int CT_DOT = 1;         // last tested <R, w> (for inspection)
 constexpr int CT_ERR = 2;         // nonzero after a bounded device-side wait ran out
 constexpr int CT_BASE = 3;        // (int64) index of the first sweep of a graph-replayed chunk
+constexpr int CT_RMAX = 4;        // max |r| of the refinement defect (scaling of its FP16 copy)
+constexpr int CT_RSCALE = 5;      // 2^-k: the FP16 right-hand side holds r 2^k
 constexpr int CT_N = 8;
 
 // FP32 copies of the constants, converted once on the host (a double-to-float conversion
@@ -107,6 +109,7 @@ struct SweepArgs {
     int rhs_index;            // marching kernels: load case of this launch (one launch per case)
     double *ctrl;             // solve control words (CT_*)
     const void *rhs;          // dense right-hand side [C][cstride] replacing the loads, or null
+    int rhs_half;             // rhs is FP16 holding r 2^k, 2^-k in ctrl[CT_RSCALE] (two-row marching kernel)
     double a, b, s1;
     OpConst k;
     BoxSet boxes;
@@ -311,7 +314,12 @@ struct TmaMaps {
     CUtensorMap w;
     CUtensorMap e;
     const void *ubuf[2] = {nullptr, nullptr};
+    // FP16 refinement right-hand side of the two-row kernel (made when refinement starts)
+    bool rvalid = false;
+    CUtensorMap r;
+    const void *rbuf = nullptr;
 };
+bool make_tma_rhs_map(const Layout &L, int ncomp, const void *rhs16, TmaMaps &m);
 void march3d_tma_tiling(const Layout &L, int ty, Tiling &t);
 void march3d_tma2_tiling(const Layout &L, Tiling &t);
 cudaError_t march3d_prepare();

@@ -373,6 +373,7 @@ constexpr int TNS = 4;         // ring slots
 constexpr int TD = 2;          // planes in flight ahead of the consumer (the slot of the plane
                                // being updated must survive the refill issued in its iteration)
 constexpr int TWAIT = 1 << 14; // try_wait attempts before a wait is declared timed out
+constexpr int RBW = 40;        // FP16 box width (halves): 33 tile columns at any offset 0..7
 constexpr unsigned TSUSPEND = 100000;  // ns a waiting thread may stay suspended per attempt
                                        // (woken early when the phase completes): <= ~1.6 s in all
 
@@ -820,6 +821,34 @@ bool make_tma_maps(const Layout &L, int ty, int ncomp, void *u0, void *u1, void 
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
     m.valid = true;
+    m.rvalid = false;
+    return true;
+}
+
+// FP16 right-hand side [C][SZ][SY][SX] of the two-row kernel: boxes of RBW halves (16-byte
+// multiples: the copy's x origin is rounded down to 8 halves) x 17 rows x 1 plane x 3 components.
+bool make_tma_rhs_map(const Layout &L, int ncomp, const void *rhs16, TmaMaps &m) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    m.rvalid = false;
+    const cuuint64_t dim[4] = {(cuuint64_t)L.SX, (cuuint64_t)L.SY, (cuuint64_t)L.SZ, (cuuint64_t)ncomp};
+    const cuuint64_t str[3] = {(cuuint64_t)L.SX * 2, (cuuint64_t)(L.SX * L.SY) * 2, (cuuint64_t)L.cstride * 2};
+    const cuuint32_t box[4] = {RBW, 17, 1, 3};
+    const cuuint32_t one4[4] = {1, 1, 1, 1};
+    if (encode(&m.r, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, const_cast<void *>(rhs16), dim, str, box, one4,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    m.rbuf = rhs16;
+    m.rvalid = true;
     return true;
 }
 
@@ -840,8 +869,13 @@ constexpr int R2WY = R2ROWS + 1;   // tile rows in the ring
 constexpr int R2NT = 32 * R2TY;
 constexpr int R2UBYTES = 3 * R2WY * TBW * 4, R2EBYTES = R2WY * TBW * 4;
 constexpr int R2USLOT = (R2UBYTES + 127) / 128 * 128, R2ESLOT = (R2EBYTES + 127) / 128 * 128;
-constexpr int R2MSG = 2 * R2NT * (3 * 16 + 16);  // per buffer: P0, P1, P2 (float4) and P3 (float, padded)
-constexpr int R2SMEM = TNS * (2 * R2USLOT + R2ESLOT) + R2MSG + TNS * 8 + 128;
+constexpr int R2RBYTES = 3 * R2WY * RBW * 2;  // FP16 right-hand side box of a stage
+constexpr int R2RSLOT = (R2RBYTES + 127) / 128 * 128;
+constexpr int R2MSG = 2 * R2NT * (3 * 16 + 4);  // per buffer: P0, P1, P2 (float4) and P3 (float)
+// ring (u, w, E and, for refinement sweeps, the FP16 right-hand side), messages, barriers
+template <bool RHS> __host__ __device__ constexpr int r2_ring() { return TNS * (2 * R2USLOT + R2ESLOT + (RHS ? R2RSLOT : 0)); }
+template <bool RHS> __host__ __device__ constexpr int r2_smem() { return r2_ring<RHS>() + R2MSG + TNS * 8 + 128; }
+static_assert(2 * (r2_smem<true>() + 1024) <= 228 * 1024, "two CTAs per SM must fit");
 
 // Owned edge and face forces of one node from its four nodes at plane zp (n, n+x, n+y,
 // n+x+y), three at zp+1 (n, n+x, n+y) and the moduli of its four cells below / above.
@@ -917,7 +951,7 @@ struct RowCarry {
 
 // Update of one output node from its assembled K u.
 __device__ __forceinline__ void march_update(const SweepArgs &A, const MarchConst &K, int zp, int off, int cs32,
-                                             float *wb, float *uob, const float *rb, unsigned boxbits, int l0,
+                                             float *wb, float *uob, bool rb, unsigned boxbits, int l0,
                                              int l1, int64_t nbase, float Ku0, float Ku1, float Ku2, float wv0,
                                              float wv1, float wv2, const float (&u)[3], float S8, float &res,
                                              float &dot, const float (&Fpre)[3]) {
@@ -927,7 +961,7 @@ __device__ __forceinline__ void march_update(const SweepArgs &A, const MarchCons
             if (((boxbits >> q) & 1u) && zp >= A.boxes.b[q].lo[2] && zp <= A.boxes.b[q].hi[2]) fm |= A.boxes.b[q].mask;
     float F0 = 0.f, F1 = 0.f, F2 = 0.f;
     if (rb) {
-        // dense right-hand side: prefetched into registers one plane earlier
+        // dense right-hand side of the refinement (read from the TMA ring by the caller)
         F0 = Fpre[0];
         F1 = Fpre[1];
         F2 = Fpre[2];
@@ -987,15 +1021,16 @@ __device__ __forceinline__ void march_update(const SweepArgs &A, const MarchCons
 
 // One owner plane for both rows.  U planes: [row 0..2][col 0..1][comp], E: [row 0..2][col 0..1]
 // with row r meaning tile row 2 ty + r (node rows YA, YB, YB+1; cell rows YA-1, YA, YB).
+template <bool RHS>
 __device__ __forceinline__ bool march2_plane(const SweepArgs &A, const MarchConst &K, int zp, int z0, int r1,
                                              const float *su, const float *sw, const float *se, unsigned char *msgraw,
                                              uint64_t *bars, int tx, int ty, int xoff, int xoffe, bool outA,
                                              bool outB, int plane32, int cs32, float *wbA, float *uobA,
-                                             const float *rbA, float *wbB, float *uobB, const float *rbB,
+                                             float *wbB, float *uobB, const __half *sr, int xoffh, float rinv,
                                              unsigned bbA, unsigned bbB, int l0, int l1, int64_t nbA, int64_t nbB,
                                              const float (&Ul)[3][2][3], const float (&El)[3][2],
                                              float (&Uh)[3][2][3], float (&Eh)[3][2], RowCarry &CA, RowCarry &CB,
-                                             float &res, float &dot, bool &bad, float (&FA)[3], float (&FB)[3]) {
+                                             float &res, float &dot, bool &bad) {
     const int tid = ty * 32 + tx;
     const int slot = r1 & (TNS - 1);
     const bool pA = outA && zp >= z0, pB = outB && zp >= z0;
@@ -1010,6 +1045,17 @@ __device__ __forceinline__ bool march2_plane(const SweepArgs &A, const MarchCons
         wB0 = w0[TBW];
         wB1 = w0[R2WY * TBW + TBW];
         wB2 = w0[2 * R2WY * TBW + TBW];
+    }
+    // refinement sweeps: the FP16 right-hand side of plane zp came with stage r1 - 1 too; both
+    // are read before this plane's barrier, after which the next refill may reuse their slot
+    float FA[3] = {0.f, 0.f, 0.f}, FB[3] = {0.f, 0.f, 0.f};
+    if (RHS && (pA || pB)) {
+        const __half *f0 = sr + ((r1 - 1) & (TNS - 1)) * (R2RSLOT / 2) + (2 * ty) * RBW + xoffh + tx;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            FA[c] = __half2float(f0[c * R2WY * RBW]) * rinv;
+            FB[c] = __half2float(f0[c * R2WY * RBW + RBW]) * rinv;
+        }
     }
     if (!mbar_wait(smem_u32(&bars[slot]), (r1 / TNS) & 1)) bad = true;
     {
@@ -1063,7 +1109,7 @@ __device__ __forceinline__ bool march2_plane(const SweepArgs &A, const MarchCons
             const float Ku1 = -(oA.Fx1 + oA.Fy1 + oA.Fz1) - (oA.Gxy1 + oA.Gyz0) + xa.y + ya.y + CA.Sz1 + gA1;
             const float Ku2 = -(oA.Fx2 + oA.Fy2 + oA.Fz2) - (oA.Gxz1 + oA.Gyz1) + xa.z + ya.z + CA.Sz2;
             const float S8 = (El[0][0] + El[0][1]) + (El[1][0] + El[1][1]) + (Eh[0][0] + Eh[0][1]) + (Eh[1][0] + Eh[1][1]);
-            march_update(A, K, zp, off, cs32, wbA, uobA, rbA, bbA, l0, l1, nbA, Ku0, Ku1, Ku2, wA0, wA1, wA2, Ul[0][0],
+            march_update(A, K, zp, off, cs32, wbA, uobA, RHS, bbA, l0, l1, nbA, Ku0, Ku1, Ku2, wA0, wA1, wA2, Ul[0][0],
                          S8, res, dot, FA);
         }
         if (pB) {
@@ -1071,22 +1117,8 @@ __device__ __forceinline__ bool march2_plane(const SweepArgs &A, const MarchCons
             const float Ku1 = -(oB.Fx1 + oB.Fy1 + oB.Fz1) - (oB.Gxy1 + oB.Gyz0) + xb.y + MyA1 + CB.Sz1 + gB1;
             const float Ku2 = -(oB.Fx2 + oB.Fy2 + oB.Fz2) - (oB.Gxz1 + oB.Gyz1) + xb.z + MyA2 + CB.Sz2;
             const float S8 = (El[1][0] + El[1][1]) + (El[2][0] + El[2][1]) + (Eh[1][0] + Eh[1][1]) + (Eh[2][0] + Eh[2][1]);
-            march_update(A, K, zp, off, cs32, wbB, uobB, rbB, bbB, l0, l1, nbB, Ku0, Ku1, Ku2, wB0, wB1, wB2, Ul[1][0],
+            march_update(A, K, zp, off, cs32, wbB, uobB, RHS, bbB, l0, l1, nbB, Ku0, Ku1, Ku2, wB0, wB1, wB2, Ul[1][0],
                          S8, res, dot, FB);
-        }
-    }
-    // dense right-hand side of the next plane, in flight while the next plane's data waits
-    if (rbA && zp + 1 < A.L.NZ) {
-        const int o2 = off + plane32;
-        if (outA) {
-            FA[0] = rbA[o2];
-            FA[1] = rbA[cs32 + o2];
-            FA[2] = rbA[2 * cs32 + o2];
-        }
-        if (outB) {
-            FB[0] = rbB[o2];
-            FB[1] = rbB[cs32 + o2];
-            FB[2] = rbB[2 * cs32 + o2];
         }
     }
     CA = {oA.Fz0 - oA.Hxz0, oA.Fz1 - oA.Hyz0, oA.Fz2 - oA.Hxz1 - oA.Hyz1, oA.Gxz0, oA.Gxz1, oA.Gyz0, oA.Gyz1};
@@ -1100,14 +1132,16 @@ template <bool RHS>
 __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_constant__ SweepArgs A,
                                                               const __grid_constant__ CUtensorMap tmu,
                                                               const __grid_constant__ CUtensorMap tmw,
-                                                              const __grid_constant__ CUtensorMap tme) {
+                                                              const __grid_constant__ CUtensorMap tme,
+                                                              const __grid_constant__ CUtensorMap tmr) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     float *su = reinterpret_cast<float *>(smem);
     float *sw = reinterpret_cast<float *>(smem + TNS * R2USLOT);
     float *se = reinterpret_cast<float *>(smem + 2 * TNS * R2USLOT);
-    unsigned char *msg = smem + TNS * (2 * R2USLOT + R2ESLOT);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + TNS * (2 * R2USLOT + R2ESLOT) + R2MSG);
+    const __half *sr = reinterpret_cast<const __half *>(smem + TNS * (2 * R2USLOT + R2ESLOT));
+    unsigned char *msg = smem + r2_ring<RHS>();
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + r2_ring<RHS>() + R2MSG);
     __shared__ double shred[32];
 
     const Layout &L = A.L;
@@ -1119,6 +1153,7 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
     const int zend = min(z0 + A.zseg, L.NZ);
     const int xs = (x0 - 1 + OX) & ~3, xoff = (x0 - 1 + OX) - xs;
     const int xse = (x0 - 2 + OX) & ~3, xoffe = (x0 - 2 + OX) - xse;
+    const int xsh = (x0 - 1 + OX) & ~7, xoffh = (x0 - 1 + OX) - xsh;  // FP16 boxes start on 8 halves
 
     MarchConst K;
     K.cpar = A.kf.ce_par;
@@ -1146,19 +1181,19 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
     const int64_t cbase = (int64_t)c0 * L.cstride;
     float *w = static_cast<float *>(A.w) + cbase;
     float *uo = A.u_out ? static_cast<float *>(A.u_out) + cbase : nullptr;
-    const float *rh = RHS ? static_cast<const float *>(A.rhs) + cbase : nullptr;
     float *wbA = w + nbA, *wbB = w + nbB;
     float *uobA = uo ? uo + nbA : nullptr, *uobB = uo ? uo + nbB : nullptr;
-    const float *rbA = rh ? rh + nbA : nullptr, *rbB = rh ? rh + nbB : nullptr;
+    const float rinv = RHS ? (float)A.ctrl[CT_RSCALE] : 0.f;  // the FP16 copy holds r 2^k
 
     auto issue = [&](int r) {
         const int p = z0 - 1 + r;
         const int slot = r & (TNS - 1);
         const uint32_t bar = smem_u32(&bars[slot]);
-        mbar_expect_tx(bar, (unsigned)(2 * R2UBYTES + R2EBYTES));
+        mbar_expect_tx(bar, (unsigned)(2 * R2UBYTES + R2EBYTES + (RHS ? R2RBYTES : 0)));
         tma_load_4d(smem_u32(su + slot * (R2USLOT / 4)), &tmu, xs, y0, p + 1, c0, bar);
         tma_load_4d(smem_u32(sw + slot * (R2USLOT / 4)), &tmw, xs, y0, p + 1, c0, bar);
         tma_load_3d(smem_u32(se + slot * (R2ESLOT / 4)), &tme, xse, y0 - 1, p, bar);
+        if (RHS) tma_load_4d(smem_u32(sr + slot * (R2RSLOT / 2)), &tmr, xsh, y0, p + 1, c0, bar);
     };
     const int nstage = zend - (z0 - 1) + 1;
     if (tid == 0) {
@@ -1191,24 +1226,22 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
     bad = __syncthreads_or(bad);
     RowCarry CA = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, CB = CA;
     float res = 0.f, dot = 0.f;
-    // dense right-hand side registers; the halo plane z0 - 1 (first march step) fetches plane z0
-    float FA[3] = {0.f, 0.f, 0.f}, FB[3] = {0.f, 0.f, 0.f};
 
     for (int zp = z0 - 1; zp < zend && !bad; zp += 2) {
         int r1 = zp + 1 - (z0 - 1);
         if (tid == 0 && issued < nstage) issue(issued);
         issued = min(issued + 1, nstage);
-        if (!march2_plane(A, K, zp, z0, r1, su, sw, se, msg, bars, tx, ty, xoff, xoffe, outA, outB, plane32, cs32, wbA,
-                          uobA, rbA, wbB, uobB, rbB, bbA, bbB, l0, l1, nbA, nbB, UA, EA, UB, EB, CA, CB, res, dot, bad,
-                          FA, FB))
+        if (!march2_plane<RHS>(A, K, zp, z0, r1, su, sw, se, msg, bars, tx, ty, xoff, xoffe, outA, outB, plane32,
+                               cs32, wbA, uobA, wbB, uobB, sr, xoffh, rinv, bbA, bbB, l0, l1, nbA, nbB, UA, EA, UB, EB,
+                               CA, CB, res, dot, bad))
             break;
         if (zp + 1 >= zend) break;
         ++r1;
         if (tid == 0 && issued < nstage) issue(issued);
         issued = min(issued + 1, nstage);
-        if (!march2_plane(A, K, zp + 1, z0, r1, su, sw, se, msg, bars, tx, ty, xoff, xoffe, outA, outB, plane32, cs32,
-                          wbA, uobA, rbA, wbB, uobB, rbB, bbA, bbB, l0, l1, nbA, nbB, UB, EB, UA, EA, CA, CB, res, dot,
-                          bad, FA, FB))
+        if (!march2_plane<RHS>(A, K, zp + 1, z0, r1, su, sw, se, msg, bars, tx, ty, xoff, xoffe, outA, outB, plane32,
+                               cs32, wbA, uobA, wbB, uobB, sr, xoffh, rinv, bbA, bbB, l0, l1, nbA, nbB, UB, EB, UA, EA,
+                               CA, CB, res, dot, bad))
             break;
     }
 
@@ -1254,9 +1287,11 @@ cudaError_t march3d_prepare() {
         e = cudaFuncSetAttribute(sweep3d_march_tma<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  TmaGeom<16>::SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sweep3d_march_tma2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, R2SMEM);
+        e = cudaFuncSetAttribute(sweep3d_march_tma2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 r2_smem<false>());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sweep3d_march_tma2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, R2SMEM);
+        e = cudaFuncSetAttribute(sweep3d_march_tma2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 r2_smem<true>());
     return e;
 }
 
@@ -1275,11 +1310,17 @@ void march3d_tma2_tiling(const Layout &L, Tiling &t) {
 cudaError_t launch_march3d_tma2(const SweepArgs &a, const Tiling &t, const TmaMaps &m, cudaStream_t s) {
     const CUtensorMap *mu = a.u_in == m.ubuf[0] ? &m.u[0] : (a.u_in == m.ubuf[1] ? &m.u[1] : nullptr);
     if (!mu) return cudaErrorInvalidValue;
+    // a dense right-hand side reaches this kernel only as the scaled FP16 copy behind m.r
+    if (a.rhs && !(a.rhs_half && m.rvalid && m.rbuf == a.rhs)) return cudaErrorInvalidValue;
     for (int r = 0; r < a.nrhs; ++r) {
         SweepArgs ar = a;
         ar.rhs_index = r;
-        if (a.rhs) sweep3d_march_tma2<true><<<dim3(t.gx, t.gy, t.gz), dim3(32, R2TY), R2SMEM, s>>>(ar, *mu, m.w, m.e);
-        else sweep3d_march_tma2<false><<<dim3(t.gx, t.gy, t.gz), dim3(32, R2TY), R2SMEM, s>>>(ar, *mu, m.w, m.e);
+        if (a.rhs)
+            sweep3d_march_tma2<true>
+                <<<dim3(t.gx, t.gy, t.gz), dim3(32, R2TY), r2_smem<true>(), s>>>(ar, *mu, m.w, m.e, m.r);
+        else
+            sweep3d_march_tma2<false>
+                <<<dim3(t.gx, t.gy, t.gz), dim3(32, R2TY), r2_smem<false>(), s>>>(ar, *mu, m.w, m.e, m.u[0]);
     }
     return cudaGetLastError();
 }

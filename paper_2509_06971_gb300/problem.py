@@ -165,6 +165,14 @@ class Problem:
         """Pick the sweep kernel by autotuner name ("march2d", "gather/32x8", "tma2/zs16", ...)."""
         self._ck(self.lib.petto_select_kernel(self.ctx, name.encode()))
 
+    def kernel_info(self):
+        """(name of the sweep kernel in use, bytes per node and component of the right-hand
+        side its refinement sweeps read)."""
+        buf = ctypes.create_string_buffer(64)
+        rb = ctypes.c_int(0)
+        self._ck(self.lib.petto_kernel_info(self.ctx, buf, 64, ctypes.byref(rb)))
+        return buf.value.decode(), rb.value
+
     def synchronize(self):
         self._ck(self.lib.petto_synchronize(self.ctx))
 

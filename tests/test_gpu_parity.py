@@ -529,6 +529,63 @@ def test_multi_rhs_fp32_march(P, variant, monkeypatch):
     prob.close()
 
 
+def test_multi_rhs_refined_solve_matches_direct(P):
+    """Three load cases solved together on the two-row marching kernel: FP32 sweeps, then
+    FP64 refinement whose sweeps read each case's defect as FP16 scaled by a power of two.
+    Each case's compliance F_r . u_r lands within 1e-4 of the oracle's direct solve."""
+    spec, cases = W.multirhs3d(40, 18, 20, n_rhs=3, seed=3)
+    spec = spec.with_(precision="f32", storage="f32")
+    prob = P.Problem(spec, nrhs=3, load_cases=cases)
+    prob.select_kernel("tma2")
+    name, rhs_bytes = prob.kernel_info()
+    assert name.startswith("tma2/") and rhs_bytes == 2
+    phi = W.random_design(spec, seed=27, lo=0.05, hi=0.95)
+    prob.set_design(phi)
+    rep = prob.solve(tol=1e-6, max_sweeps=200000)
+    assert rep["converged"] and rep["rel_res"] <= 1e-6
+    ug = np.asarray(prob.get_state(), np.float64)
+    E = oracle_materials(spec).modulus(np.asarray(phi, np.float32).astype(np.float64))
+    for r, case in enumerate(cases):
+        op = oracle_problem(spec, loads=case)
+        F = op.load_vector()
+        Co = float(F @ op.direct_solve(E, F, op.fixed_mask()))
+        Cg = float(F @ nodes_to_oracle(ug[3 * r:3 * r + 3]))
+        assert abs(Cg - Co) < 1e-4 * abs(Co)
+    prob.close()
+
+
+def test_refinement_is_scale_equivariant(P):
+    """Loads scaled by 2^-20: the FP32 sweeps, the FP64 defect and the power-of-two scaling
+    of the defect's FP16 copy all commute with the scaling, so the refined solve takes the
+    same sweeps and ends in the unscaled state times 2^-20, bit for bit."""
+    base = W.cantilever3d(40, 20, 20)
+    sc = 2.0 ** -20
+    out = []
+    for s in (1.0, sc):
+        spec = base.with_(precision="f32", storage="f32", loads=[(n, c, v * s) for n, c, v in base.loads])
+        prob = P.Problem(spec)
+        prob.select_kernel("tma2")
+        prob.set_design(W.random_design(spec, seed=15, lo=0.05, hi=0.95))
+        rep = prob.solve(tol=1e-6, max_sweeps=200000)
+        out.append((rep, prob.get_state(dtype=np.float32)))
+        prob.close()
+    (r1, u1), (r2, u2) = out
+    assert r1["converged"] and r1["sweeps"] == r2["sweeps"] and r1["rel_res"] == r2["rel_res"]
+    assert np.array_equal(u1 * np.float32(sc), u2)
+
+
+def test_kernel_info_names_the_selected_kernel(P):
+    p2 = P.Problem(W.mbb_halfbeam(24, 8))
+    p2.select_kernel("gather/32x4")
+    assert p2.kernel_info() == ("gather/32x4", 8)
+    p2.close()
+    p3 = P.Problem(W.cantilever3d(24, 12, 12))
+    for name in ("tma8/zs8", "tma2/zs8"):
+        p3.select_kernel(name)
+        assert p3.kernel_info() == (name, 2 if name.startswith("tma2") else 4)
+    p3.close()
+
+
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
 def test_reduced_precision_design_storage(P, storage):
     """Design fields stored in BF16/FP16, arithmetic in FP32: the modulus equals the oracle's
