@@ -61,6 +61,12 @@ PAPER_DERIVED_GCELL_SWEEPS = {
 }
 METRIC = "APT Gcell-sweeps/s & % HBM roofline; s/design-iter at rel.res 1e-6"
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant sweep
+# kernel from one ncu capture of the workload: the refinement sweep of the two-row marching
+# kernel, 97.6 % of the sweeps of a design iteration.  Keyed by workload and kernel name, so
+# that any other kernel reports null; to be re-captured whenever that kernel changes.
+NCU_TRAFFIC = {("cantilever3d_256x128x128", "tma2/zs12"): 171.320320e6 + 64.201984e6}
+
 
 def sweep_bytes(spec, tsize=4):
     """Algorithmic bytes of one APT sweep: read+write of u and of w (node fields, ncomp
@@ -300,7 +306,8 @@ def run_ours(args):
         "sweeps_per_design_iter": sweeps / args.steps,
         "final_rel_res": rows[-1]["rel_res"], "compliance": rows[-1]["compliance"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": NCU_TRAFFIC.get((args.workload, kname)),
                      "kernel": "apt sweep", "kernel_ms": per_launch_ms, "bytes_per_launch": bytes_avg,
                      "rhs_sweep_fraction": kern_rhs / max(kern_n, 1), "rhs_bytes": rhs_b,
                      "sweep_kernel": kname, "peak_kind": peak_kind},
