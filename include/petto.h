@@ -241,6 +241,36 @@ petto_status petto_design_update(petto_ctx *ctx, const petto_pf_opts *opts, doub
  * out-of-grid box. */
 petto_status petto_set_keepout(petto_ctx *ctx, const int64_t *box, const double *target, double kappa_b);
 
+/* ---------------------------------------------------------------- slabs
+ * A single 3D grid decomposed along z into slabs, one context each (one GPU each, or several
+ * on one GPU).  The caller creates each slab's context for the node planes it owns plus one
+ * neighbour plane on each interior side (the ghost planes; cells likewise extended), with
+ * its loads, supports and design restricted to that range, and declares the owned planes
+ * with petto_set_owned_planes: sweeps, residuals and their sums then cover the owned
+ * planes only, and the ghost planes keep what was copied into them.  Before each sweep the
+ * caller copies each interface plane from its owner into the neighbour's ghost plane
+ * (petto_get_plane / petto_set_plane, or a collective between ranks); the owned planes then
+ * take the same values as in the same sweeps of the whole grid, bit for bit (a node's update
+ * reads its 3 x 3 x 3 node neighbourhood and its 8 cells only, in the same order).  Residual
+ * sums of the slabs add up to the whole grid's.  The node gather and the two-row marching
+ * kernel take slabs; selecting another kernel on a slab context is PETTO_EUNSUPPORTED. */
+
+/* Node planes zlo..zhi (local indices, inclusive) are the ones this context's sweeps write;
+ * zlo = 0, zhi = nz cells (the last node plane) restores the whole grid.  z_global is the
+ * whole grid's index of local plane 0: the marching kernel starts its z segments on the
+ * whole grid's even planes, which makes the slab's arithmetic that of the whole grid bit for
+ * bit.  PETTO_EINVAL for an empty or out-of-grid range or a negative z_global,
+ * PETTO_EUNSUPPORTED in 2D.  Synchronises the stream. */
+petto_status petto_set_owned_planes(petto_ctx *ctx, int64_t zlo, int64_t zhi, int64_t z_global);
+
+/* Copy node plane k (local index) of the current state, every component (load cases
+ * included), out to / in from a dense [ndof components][ny+1][nx+1] array in the sweep
+ * precision (dtype must equal it).  on_device = 1: the array is device memory and the copy
+ * is ordered on the context's stream; 0: host memory, and the call returns when the copy
+ * is done.  PETTO_EINVAL for a plane outside the grid or another dtype. */
+petto_status petto_get_plane(petto_ctx *ctx, int64_t k, void *dst, int dtype, int on_device);
+petto_status petto_set_plane(petto_ctx *ctx, int64_t k, const void *src, int dtype, int on_device);
+
 /* opts->ch_steps explicit Cahn-Hilliard steps (Sec. 2.4); refreshes the modulus field. */
 petto_status petto_cahn_hilliard(petto_ctx *ctx, const petto_pf_opts *opts);
 

@@ -99,6 +99,9 @@ _SIGS = {
     "petto_autotune": (_int, [_vp, _int, ctypes.c_char_p, _int]),
     "petto_select_kernel": (_int, [_vp, ctypes.c_char_p]),
     "petto_kernel_info": (_int, [_vp, ctypes.c_char_p, _int, _P(_int)]),
+    "petto_set_owned_planes": (_int, [_vp, _i64, _i64, _i64]),
+    "petto_get_plane": (_int, [_vp, _i64, _vp, _int, _int]),
+    "petto_set_plane": (_int, [_vp, _i64, _vp, _int, _int]),
     "petto_set_keepout": (_int, [_vp, _P(_i64), _P(_dbl), _dbl]),
     "petto_batch_create": (_int, [_int, _P(_vp), _P(_vp)]),
     "petto_batch_destroy": (None, [_vp]),

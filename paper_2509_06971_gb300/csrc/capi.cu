@@ -57,6 +57,9 @@ struct petto_ctx {
     double *ctrl = nullptr;
     void *u64 = nullptr, *r64 = nullptr, *rhs32 = nullptr;
     bool rhs_half = false;  // rhs32 holds the scaled FP16 copy (two-row marching kernel)
+    int own_lo = 0, own_n = 0;  // 3D slab of a decomposed grid: node planes the sweeps write
+                                // (own_n = 0: every plane)
+    int64_t own_z0 = 0;         // plane of the whole grid that local plane 0 is
     int cur = 0;
     int64_t launches = 0;
     int64_t step = 0;
@@ -338,6 +341,8 @@ SweepArgs base_sweep_args(petto_ctx *ctx) {
     a.red = ctx->red();
     a.ctrl = ctx->ctrl;
     a.rhs = nullptr;
+    a.zlo = ctx->own_n ? ctx->own_lo : 0;
+    a.zhi = ctx->own_n ? ctx->own_lo + ctx->own_n - 1 : ctx->L.NZ - 1;
     const OpConst &k = ctx->k;
     a.kf = OpConstF{(float)k.ce_par, (float)k.ce_perp, (float)k.cf_lam, (float)k.cf_mu, (float)k.cdiag, (float)k.ct,
                     (float)k.src, 0.f, 0.f, 0.f};
@@ -450,7 +455,31 @@ petto_status drain_profile(petto_ctx *ctx) {
 
 // Switch the sweep kernel's tiling: rebuild the per-tile load table (and the tensor maps of
 // the TMA-staged kernels), growing the tile and partial-sum buffers when needed.
-petto_status set_tiling(petto_ctx *ctx, const Tiling &t) {
+// A tiling restricted to the context's output planes (a slab of a decomposed grid): z tiles
+// (gather) or z segments (marching) start at the slab's first plane.
+Tiling own_planes(const petto_ctx *ctx, Tiling t) {
+    if (!ctx->own_n) return t;
+    t.zlo = ctx->own_lo;
+    t.zn = ctx->own_n;
+    t.zb = t.zlo;
+    if (t.kind == 4) {
+        // marching segments start on even planes of the whole grid, as the whole grid's do
+        // (its segment length is even), so every plane is computed as it is there
+        if ((t.zlo + ctx->own_z0) & 1) t.zb = std::max(t.zlo - 1, 0);
+        const int span = t.zlo + t.zn - t.zb;
+        t.zs = std::min(t.zs, span);
+        if (t.zs < span && (t.zs & 1)) ++t.zs;
+        t.gz = (span + t.zs - 1) / t.zs;
+    } else {
+        t.gz = (t.zn + t.zs - 1) / t.zs;
+    }
+    return t;
+}
+
+petto_status set_tiling(petto_ctx *ctx, const Tiling &t0) {
+    if (ctx->own_n && t0.kind != 0 && t0.kind != 4)
+        return fail(ctx, PETTO_EUNSUPPORTED, "a slab context sweeps with the node-gather or two-row marching kernel");
+    const Tiling t = own_planes(ctx, t0);
     const int NX = ctx->L.NX, NY = ctx->L.NY;
     const int nt = t.ntiles();
     std::vector<int> tptr(nt + 1, 0);
@@ -463,7 +492,8 @@ petto_status set_tiling(petto_ctx *ctx, const Tiling &t) {
         le.comp = kv.first.second;
         le.vald = kv.second;
         le.valf = (float)kv.second;
-        tmp.emplace_back(t.tile_of(i, j, k), le);
+        const int tl = t.tile_of(i, j, k);
+        if (tl >= 0) tmp.emplace_back(tl, le);  // loads on planes outside a slab belong to a neighbour
     }
     std::stable_sort(tmp.begin(), tmp.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
     std::vector<LoadEntry> ent;
@@ -1430,6 +1460,87 @@ petto_status petto_set_keepout(petto_ctx *ctx, const int64_t *box, const double 
     return PETTO_OK;
 }
 
+petto_status petto_set_owned_planes(petto_ctx *ctx, int64_t zlo, int64_t zhi, int64_t z_global) {
+    if (!ctx) return PETTO_EINVAL;
+    if (ctx->dim != 3) return fail(ctx, PETTO_EUNSUPPORTED, "slabs are z ranges of a 3D grid");
+    const int NZ = ctx->L.NZ;
+    if (zlo < 0 || zhi >= NZ || zlo > zhi) return fail(ctx, PETTO_EINVAL, "owned planes outside the grid or empty");
+    if (z_global < 0) return fail(ctx, PETTO_EINVAL, "negative global plane offset");
+    ctx->own_z0 = z_global;
+    const bool whole = zlo == 0 && zhi == NZ - 1;
+    Tiling t = ctx->tiling;
+    if (!whole && t.kind != 0 && t.kind != 4) {
+        // another marching variant is selected: a slab sweeps with the node gather instead
+        t = gather_tiling(ctx->L);
+    }
+    t.zlo = 0;
+    t.zn = 0;
+    ctx->own_lo = whole ? 0 : (int)zlo;
+    ctx->own_n = whole ? 0 : (int)(zhi - zlo + 1);
+    // the node-gather tiling of the FP64 defect and residual kernels, restricted the same way
+    const Tiling g = own_planes(ctx, gather_tiling(ctx->L));
+    const int NX = ctx->L.NX, NY = ctx->L.NY, gnt = g.ntiles();
+    std::vector<int> gptr(gnt + 1, 0);
+    std::vector<std::pair<int, LoadEntry>> tmp;
+    for (auto &kv : ctx->load_list) {
+        const int64_t n = kv.first.first;
+        const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / ((int64_t)NX * NY));
+        LoadEntry le{};
+        le.node = ctx->L.node(i, j, k);
+        le.comp = kv.first.second;
+        le.vald = kv.second;
+        le.valf = (float)kv.second;
+        const int tl = g.tile_of(i, j, k);
+        if (tl >= 0) tmp.emplace_back(tl, le);
+    }
+    std::stable_sort(tmp.begin(), tmp.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
+    std::vector<LoadEntry> gent;
+    for (auto &pr : tmp) {
+        gptr[pr.first + 1]++;
+        gent.push_back(pr.second);
+    }
+    for (int q = 0; q < gnt; ++q) gptr[q + 1] += gptr[q];
+    CK(cudaStreamSynchronize(ctx->stream));
+    // fewer (or as many) tiles than the whole-grid table allocated at creation
+    CK(cudaMemcpy(ctx->gtile_ptr, gptr.data(), sizeof(int) * (gnt + 1), cudaMemcpyHostToDevice));
+    if (!gent.empty())
+        CK(cudaMemcpy(ctx->gloads, gent.data(), sizeof(LoadEntry) * gent.size(), cudaMemcpyHostToDevice));
+    ctx->gtiling = g;
+    return set_tiling(ctx, t);
+}
+
+namespace {
+// one node plane k of the current state, every component, as [C][NY][NX] at dst/src
+petto_status copy_plane(petto_ctx *ctx, int64_t k, void *dst, const void *src, int dtype, int on_device) {
+    if (!ctx || (!dst && !src)) return fail(ctx, PETTO_EINVAL, "null argument");
+    if (k < 0 || k >= ctx->L.NZ) return fail(ctx, PETTO_EINVAL, "plane outside the grid");
+    if (dtype != ctx->precision) return fail(ctx, PETTO_EINVAL, "planes are copied in the sweep precision");
+    const Layout &L = ctx->L;
+    const size_t T = ctx->tsize();
+    char *u = static_cast<char *>(ctx->u[ctx->cur]);
+    const size_t plane = (size_t)L.NX * L.NY * T;
+    for (int c = 0; c < ctx->ndofc(); ++c) {
+        char *field = u + ((int64_t)c * L.cstride + L.node(0, 0, (int)k)) * T;
+        if (dst)
+            CK(cudaMemcpy2DAsync(static_cast<char *>(dst) + c * plane, L.NX * T, field, L.SX * T, L.NX * T, L.NY,
+                                 cudaMemcpyDefault, ctx->stream));
+        else
+            CK(cudaMemcpy2DAsync(field, L.SX * T, static_cast<const char *>(src) + c * plane, L.NX * T, L.NX * T,
+                                 L.NY, cudaMemcpyDefault, ctx->stream));
+    }
+    if (!on_device) CK(cudaStreamSynchronize(ctx->stream));  // host memory is the caller's again on return
+    return PETTO_OK;
+}
+}  // namespace
+
+petto_status petto_get_plane(petto_ctx *ctx, int64_t k, void *dst, int dtype, int on_device) {
+    return copy_plane(ctx, k, dst, nullptr, dtype, on_device);
+}
+
+petto_status petto_set_plane(petto_ctx *ctx, int64_t k, const void *src, int dtype, int on_device) {
+    return copy_plane(ctx, k, nullptr, src, dtype, on_device);
+}
+
 petto_status petto_cahn_hilliard(petto_ctx *ctx, const petto_pf_opts *o) {
     if (!ctx || !o) return fail(ctx, PETTO_EINVAL, "null argument");
     if (o->ch_steps < 0) return fail(ctx, PETTO_EINVAL, "negative ch_steps");
@@ -2095,7 +2206,18 @@ namespace {
 // The sweep-kernel variants that apply to a problem, by name: the 3D marching kernels
 // (TMA two-row, TMA one-row 32x8 / 32x16, register-staged) x z-segment lengths, the 2D
 // y-marching kernel x rows per warp, and the node-gather kernel x block shapes.
+std::vector<std::pair<std::string, Tiling>> kernel_candidates_all(const petto_ctx *ctx);
+
+// the candidates a context can take: a slab of a decomposed grid only the node gather and
+// the two-row marching kernel (both write a range of planes), restricted to that range
 std::vector<std::pair<std::string, Tiling>> kernel_candidates(const petto_ctx *ctx) {
+    std::vector<std::pair<std::string, Tiling>> all = kernel_candidates_all(ctx), cand;
+    for (auto &c : all)
+        if (!ctx->own_n || c.second.kind == 0 || c.second.kind == 4) cand.push_back(c);
+    return cand;
+}
+
+std::vector<std::pair<std::string, Tiling>> kernel_candidates_all(const petto_ctx *ctx) {
     std::vector<std::pair<std::string, Tiling>> cand;
     const Layout &L = ctx->L;
     if (L.dim == 3 && ctx->physics == 0 && ctx->precision == PETTO_F32) {
@@ -2123,7 +2245,7 @@ std::vector<std::pair<std::string, Tiling>> kernel_candidates(const petto_ctx *c
             march3d_tiling(L, t);
             cand.emplace_back("v1/zs" + std::to_string(t.zs), t);
         }
-        return cand;
+        // and the node gather below (slower here, but it takes slabs of any kind)
     }
     if (march2d_ok(ctx))
         for (int ly : {4, 8, 16}) {
@@ -2163,7 +2285,7 @@ petto_status petto_kernel_info(petto_ctx *ctx, char *name, int name_len, int *rh
     const Tiling &t = ctx->tiling;
     std::string nm = "custom";
     for (auto &c : kernel_candidates(ctx)) {
-        const Tiling &q = c.second;
+        const Tiling q = own_planes(ctx, c.second);
         if (q.kind == t.kind && q.bx == t.bx && q.by == t.by && q.zs == t.zs && q.ox == t.ox && q.oy == t.oy &&
             (q.kind != 5 || q.ly == t.ly)) {
             nm = c.first;

@@ -107,6 +107,9 @@ struct SweepArgs {
     int base_from_ctrl;
     int zseg;                 // output planes per z segment of the marching kernels
     int rhs_index;            // marching kernels: load case of this launch (one launch per case)
+    int zlo, zhi;             // 3D: node planes written by the sweep (a slab of a decomposed grid;
+                              // the planes outside hold a neighbour's copied values)
+    int zb;                   // 3D: first plane of the first z tile / marching segment (<= zlo)
     double *ctrl;             // solve control words (CT_*)
     const void *rhs;          // dense right-hand side [C][cstride] replacing the loads, or null
     int rhs_half;             // rhs is FP16 holding r 2^k, 2^-k in ctrl[CT_RSCALE] (two-row marching kernel)
@@ -288,8 +291,12 @@ struct Tiling {
     int kind;          // 0 gather, 1 3D z-marching (register-staged), 2/3 3D TMA one row per
                        // thread (32x8 / 32x16), 4 3D TMA two rows per thread, 5 2D y-marching
     int ly;            // kind 5: output rows per warp (a block's warps take consecutive segments)
+    int zlo, zn;       // 3D: output node planes [zlo, zlo + zn) (zn = 0: all planes, zlo = 0)
+    int zb;            // first plane of the first z tile / segment (<= zlo)
+    // tile of node (i, j, k), or -1 for a node outside the output planes
     __host__ int tile_of(int i, int j, int k) const {
-        return (i / ox) + gx * ((j / oy) + gy * (k / zs));
+        if (zn && (k < zlo || k >= zlo + zn)) return -1;
+        return (i / ox) + gx * ((j / oy) + gy * ((k - zb) / zs));
     }
     int ntiles() const { return gx * gy * gz; }
 };

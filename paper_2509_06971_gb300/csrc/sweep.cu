@@ -695,7 +695,7 @@ __global__ void __launch_bounds__(128) sweep3d_gather(const SweepArgs A) {
     const Layout &L = A.L;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int kb = blockIdx.z * GATHER3_ZS;
+    const int kb = A.zb + blockIdx.z * GATHER3_ZS;
     const T *__restrict__ ui = static_cast<const T *>(A.u_in);
     T *__restrict__ uo = static_cast<T *>(A.u_out);
     T *__restrict__ w = static_cast<T *>(A.w);
@@ -705,8 +705,8 @@ __global__ void __launch_bounds__(128) sweep3d_gather(const SweepArgs A) {
     const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int l0 = A.tile_ptr[tile], l1 = A.tile_ptr[tile + 1];
     if (i < L.NX && j < L.NY) {
-        const int ke = min(kb + GATHER3_ZS, L.NZ);
-        for (int k = kb; k < ke; ++k) {
+        const int ke = min(kb + GATHER3_ZS, A.zhi + 1);
+        for (int k = max(kb, A.zlo); k < ke; ++k) {
             T Ec[2][2][2];
 #pragma unroll
             for (int cz = 0; cz < 2; ++cz)
@@ -831,7 +831,9 @@ Tiling choose_tiling(const Layout &L, int physics, int precision, int nrhs) {
 
 // FP64 residual R = F - K(E) u of an FP64 state with the FP32 modulus field (mode 2):
 // the defect of the iterative refinement around FP32 sweeps.
-cudaError_t launch_residual64(const SweepArgs &a, const Tiling &t, cudaStream_t s) {
+cudaError_t launch_residual64(const SweepArgs &a0, const Tiling &t, cudaStream_t s) {
+    SweepArgs a = a0;
+    a.zb = t.zn ? t.zb : 0;
     dim3 block(t.bx, t.by, 1), grid(t.gx, t.gy, t.gz);
     if (a.L.dim == 2) {
         if (a.physics == 0) sweep2d_gather<double, 0, float><<<grid, block, 0, s>>>(a);
@@ -846,6 +848,7 @@ cudaError_t launch_residual64(const SweepArgs &a, const Tiling &t, cudaStream_t 
 cudaError_t launch_sweep(const SweepArgs &a0, const Tiling &t, int precision, cudaStream_t s, const TmaMaps *maps) {
     SweepArgs a = a0;
     a.zseg = t.zs;
+    a.zb = t.zn ? t.zb : 0;
     if (t.kind == 1) return launch_march3d(a, t, s);
     if (t.kind == 2 || t.kind == 3) {
         if (!maps || !maps->valid) return cudaErrorInvalidValue;

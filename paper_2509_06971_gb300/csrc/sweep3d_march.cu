@@ -1146,11 +1146,15 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
 
     const Layout &L = A.L;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-    const int x0 = blockIdx.x * 31, y0 = blockIdx.y * (R2ROWS - 1), z0 = blockIdx.z * A.zseg;
+    const int x0 = blockIdx.x * 31, y0 = blockIdx.y * (R2ROWS - 1), z0 = A.zb + blockIdx.z * A.zseg;
     const int X = x0 - 1 + tx, YA = y0 - 1 + 2 * ty, YB = YA + 1;
     const bool outA = tx >= 1 && ty >= 1 && X < L.NX && YA < L.NY;
     const bool outB = tx >= 1 && X < L.NX && YB < L.NY;
-    const int zend = min(z0 + A.zseg, L.NZ);
+    const int zend = min(z0 + A.zseg, A.zhi + 1);
+    // first plane written: a slab's segments may start one plane below its own planes, on the
+    // parity of the whole grid's segments, so each plane is computed by the same one of the
+    // two plane steps of the loop below as in the whole grid's sweep
+    const int zo = max(z0, A.zlo);
     const int xs = (x0 - 1 + OX) & ~3, xoff = (x0 - 1 + OX) - xs;
     const int xse = (x0 - 2 + OX) & ~3, xoffe = (x0 - 2 + OX) - xse;
     const int xsh = (x0 - 1 + OX) & ~7, xoffh = (x0 - 1 + OX) - xsh;  // FP16 boxes start on 8 halves
@@ -1231,7 +1235,7 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
         int r1 = zp + 1 - (z0 - 1);
         if (tid == 0 && issued < nstage) issue(issued);
         issued = min(issued + 1, nstage);
-        if (!march2_plane<RHS>(A, K, zp, z0, r1, su, sw, se, msg, bars, tx, ty, xoff, xoffe, outA, outB, plane32,
+        if (!march2_plane<RHS>(A, K, zp, zo, r1, su, sw, se, msg, bars, tx, ty, xoff, xoffe, outA, outB, plane32,
                                cs32, wbA, uobA, wbB, uobB, sr, xoffh, rinv, bbA, bbB, l0, l1, nbA, nbB, UA, EA, UB, EB,
                                CA, CB, res, dot, bad))
             break;
@@ -1239,7 +1243,7 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
         ++r1;
         if (tid == 0 && issued < nstage) issue(issued);
         issued = min(issued + 1, nstage);
-        if (!march2_plane<RHS>(A, K, zp + 1, z0, r1, su, sw, se, msg, bars, tx, ty, xoff, xoffe, outA, outB, plane32,
+        if (!march2_plane<RHS>(A, K, zp + 1, zo, r1, su, sw, se, msg, bars, tx, ty, xoff, xoffe, outA, outB, plane32,
                                cs32, wbA, uobA, wbB, uobB, sr, xoffh, rinv, bbA, bbB, l0, l1, nbA, nbB, UB, EB, UA, EA,
                                CA, CB, res, dot, bad))
             break;
@@ -1304,6 +1308,10 @@ void march3d_tma2_tiling(const Layout &L, Tiling &t) {
     t.gx = (L.NX + t.ox - 1) / t.ox;
     t.gy = (L.NY + t.oy - 1) / t.oy;
     t.zs = choose_zseg(L.NZ, t.gx * t.gy, 152 * 2);
+    // segments of even length: every segment starts on an even plane, so the plane steps of
+    // the loop (two per iteration, compiled separately) see each plane at the same parity
+    // whatever the segmentation -- a slab of a decomposed grid then reproduces it exactly
+    if (t.zs < L.NZ && (t.zs & 1)) ++t.zs;
     t.gz = (L.NZ + t.zs - 1) / t.zs;
 }
 

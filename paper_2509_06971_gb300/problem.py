@@ -220,6 +220,41 @@ class Problem:
         self._ck(self.lib.petto_get_modulus(self.ctx, E.ctypes.data_as(ctypes.c_void_p), _DT[E.dtype], 0))
         return E
 
+    # --------------------------------------------------------------- slabs
+    def set_owned_planes(self, zlo: int, zhi: int, z_global: int = 0):
+        """Sweeps write node planes zlo..zhi only (a slab of a decomposed 3D grid whose local
+        plane 0 is plane z_global of the whole grid)."""
+        self._ck(self.lib.petto_set_owned_planes(self.ctx, int(zlo), int(zhi), int(z_global)))
+
+    def plane_shape(self):
+        s = self.spec
+        return (self.nrhs * self.ncomp, s.ny + 1, s.nx + 1)
+
+    def get_plane(self, k: int, out=None):
+        """Node plane k of the current state as [components][ny+1][nx+1] in the sweep
+        precision, into `out` (a CUDA tensor: stream-ordered device copy) or a new array."""
+        if out is None:
+            out = np.empty(self.plane_shape(), dtype=self.np_dtype)
+        if _is_cuda_tensor(out):
+            ptr, dev = out.data_ptr(), 1
+        else:
+            arr = out.numpy() if hasattr(out, "numpy") else out  # host tensors through their array view
+            if arr.dtype != self.np_dtype or not arr.flags.c_contiguous:
+                raise ValueError("plane buffers are contiguous and in the sweep precision")
+            ptr, dev = arr.ctypes.data, 0
+        self._ck(self.lib.petto_get_plane(self.ctx, int(k), ctypes.c_void_p(ptr), self.precision, dev))
+        return out
+
+    def set_plane(self, k: int, src):
+        """Write node plane k of the current state from [components][ny+1][nx+1]."""
+        if _is_cuda_tensor(src):
+            src = src.contiguous()
+            ptr, dev = src.data_ptr(), 1
+        else:
+            src = np.ascontiguousarray(src.numpy() if hasattr(src, "numpy") else src, dtype=self.np_dtype)
+            ptr, dev = src.ctypes.data, 0
+        self._ck(self.lib.petto_set_plane(self.ctx, int(k), ctypes.c_void_p(ptr), self.precision, dev))
+
     # --------------------------------------------------------------- solver
     def sweep(self, kind: int, n: int, a: float = 0.0, b: float = 0.0, s1: float = 0.0, local_dt: bool = False,
               want_res: bool = True):

@@ -1,0 +1,333 @@
+"""Decomposition of one 3D grid into z slabs: the exchange step of a state solve spread over
+several contexts (GPUs).
+
+The sweep of Sec. 2.2 updates each node from its 3 x 3 x 3 node neighbourhood and its eight
+cells, so cutting the grid along z needs, per interface and sweep, one node plane of u from
+each side.  Slab s owns node planes k0..k1 of the whole grid; its context holds those planes
+plus one ghost plane on each interior side, and the cell layers between them, with the
+loads of its own planes and the supports clipped to its range.  Before every sweep each
+interface plane goes from its owner into the neighbour's ghost plane; the sweep writes the
+owned planes only (``petto_set_owned_planes``), so the owned planes follow the whole grid's
+sweeps, and the residual sums of the slabs add up to the whole grid's.  The modulus of the
+ghost cell layers comes from the design, which every slab holds for its own range.
+
+Two drivers share this host logic:
+
+* ``SlabGrid`` keeps every slab in this process (several contexts on one GPU; planes copied
+  device to device on the shared stream);
+* ``DistributedSlabs`` gives each rank of a ``torch.distributed`` group one slab and moves
+  the planes with point-to-point messages (NCCL between GPUs, gloo between host processes)
+  and the residual with an all-reduce.
+
+Only the state solve is decomposed (sweeps, residuals, a fixed-momentum APT/PT solve); the
+design step stays with a whole-grid context.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+def slab_ranges(nz: int, n: int) -> list[tuple[int, int]]:
+    """Owned node planes (k0, k1), inclusive, of n slabs over the nz + 1 node planes of a
+    grid with nz cell layers: contiguous, in order, sizes differing by at most one."""
+    planes = nz + 1
+    if not 1 <= n <= planes:
+        raise ValueError(f"cannot cut {planes} node planes into {n} slabs")
+    base, extra = divmod(planes, n)
+    out, k = [], 0
+    for s in range(n):
+        m = base + (1 if s < extra else 0)
+        out.append((k, k + m - 1))
+        k += m
+    return out
+
+
+@dataclass(frozen=True)
+class SlabGeom:
+    """Node planes of one slab in whole-grid indices: owned k0..k1, held g0..g1 (owned plus
+    the ghost planes).  Local plane index = global - g0."""
+    k0: int
+    k1: int
+    g0: int
+    g1: int
+
+    @property
+    def zlo(self) -> int:
+        return self.k0 - self.g0
+
+    @property
+    def zhi(self) -> int:
+        return self.k1 - self.g0
+
+    @property
+    def nz(self) -> int:
+        """cell layers of the slab's grid"""
+        return self.g1 - self.g0
+
+
+def slab_geometry(nz: int, n: int) -> list[SlabGeom]:
+    return [SlabGeom(k0, k1, max(k0 - 1, 0), min(k1 + 1, nz)) for k0, k1 in slab_ranges(nz, n)]
+
+
+def slab_loads(loads, g: SlabGeom):
+    """Point loads on the slab's owned planes, in its local indices."""
+    return [((i, j, k - g.g0), c, v) for (i, j, k), c, v in loads if g.k0 <= k <= g.k1]
+
+
+def slab_boxes(boxes, g: SlabGeom):
+    """Support boxes clipped to the planes the slab holds, in its local indices."""
+    out = []
+    for lo, hi, mask in boxes:
+        klo, khi = max(lo[2], g.g0), min(hi[2], g.g1)
+        if klo <= khi:
+            out.append(((lo[0], lo[1], klo - g.g0), (hi[0], hi[1], khi - g.g0), mask))
+    return out
+
+
+def slab_cells(field, spec, g: SlabGeom) -> np.ndarray:
+    """[P][cells] of the whole grid -> the slab's cell layers g0..g1-1."""
+    f = np.asarray(field)
+    return np.ascontiguousarray(f.reshape(f.shape[0], spec.nz, spec.ny, spec.nx)[:, g.g0:g.g1].reshape(f.shape[0], -1))
+
+
+def slab_nodes(u, spec, g: SlabGeom) -> np.ndarray:
+    """[C][nodes] of the whole grid -> the slab's node planes g0..g1."""
+    a = np.asarray(u)
+    return np.ascontiguousarray(
+        a.reshape(a.shape[0], spec.nz + 1, spec.ny + 1, spec.nx + 1)[:, g.g0:g.g1 + 1].reshape(a.shape[0], -1))
+
+
+def slab_spec(spec, g: SlabGeom):
+    """The problem a slab's context solves: its planes, loads, supports and design."""
+    if spec.dim != 3:
+        raise ValueError("slabs cut a 3D grid along z")
+    phi0 = None if spec.phi0 is None else slab_cells(spec.phi0, spec, g)
+    return spec.with_(name=f"{spec.name}_z{g.k0}-{g.k1}", nz=g.nz, loads=slab_loads(spec.loads, g),
+                      boxes=slab_boxes(spec.boxes, g), phi0=phi0, keepout=None)
+
+
+def interface_copies(geom: list[SlabGeom]):
+    """The plane copies of one exchange, (src slab, src local plane, dst slab, dst local
+    plane): each interface's two owned boundary planes into the neighbours' ghost planes."""
+    out = []
+    for s in range(len(geom) - 1):
+        lo, hi = geom[s], geom[s + 1]
+        out.append((s, lo.zhi, s + 1, 0))          # lo's top owned plane -> hi's lower ghost
+        out.append((s + 1, hi.zlo, s, lo.nz))      # hi's bottom owned plane -> lo's upper ghost
+    return out
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class _SlabDriver:
+    """What both drivers do around their slabs' contexts."""
+
+    def _gather_owned(self, parts, ncomp):
+        spec = self.spec
+        out = np.empty((ncomp, spec.nz + 1, spec.ny + 1, spec.nx + 1), dtype=parts[0][1].dtype)
+        for g, u in parts:
+            ul = u.reshape(ncomp, g.nz + 1, spec.ny + 1, spec.nx + 1)
+            out[:, g.k0:g.k1 + 1] = ul[:, g.zlo:g.zhi + 1]
+        return out.reshape(ncomp, -1)
+
+    def solve(self, tol: float = 1e-6, kind: int = 0, a: float | None = None, b: float | None = None,
+              s1: float | None = None, local_dt: bool | None = None, check_every: int = 50,
+              max_sweeps: int = 200000) -> dict:
+        """Fixed-momentum APT (kind 0) or PT (kind 1) sweeps with an exchange before each,
+        until ||R|| <= tol ||F|| at a check (every check_every sweeps) or max_sweeps."""
+        spec = self.spec
+        a = spec.apt_a if a is None else a
+        b = spec.apt_b if b is None else b
+        s1 = spec.pt_s1 if s1 is None else s1
+        local_dt = spec.local_dt if local_dt is None else local_dt
+        fn = self.f_norm
+        done, r2 = 0, float("nan")
+        while done < max_sweeps:
+            n = min(check_every, max_sweeps - done)
+            r2 = self.sweep(kind, n, a, b, s1, local_dt)
+            done += n
+            if not np.isfinite(r2):
+                break
+            if fn == 0.0 or np.sqrt(r2) <= tol * fn:
+                return {"sweeps": done, "rel_res": np.sqrt(r2) / fn if fn else 0.0, "converged": True}
+        return {"sweeps": done, "rel_res": np.sqrt(r2) / fn if fn else float("nan"), "converged": False}
+
+
+class SlabGrid(_SlabDriver):
+    """Every slab of the grid in this process: n contexts on the current GPU, exchanged by
+    device-to-device plane copies on the shared stream."""
+
+    def __init__(self, spec, n_slabs: int, *, kernel: str | None = None, nrhs: int = 1, load_cases=None,
+                 **problem_kw):
+        from .problem import Problem
+        torch = _torch()
+        self.spec = spec
+        self.geom = slab_geometry(spec.nz, n_slabs)
+        self.probs = []
+        if problem_kw.get("stream") is None:
+            # one stream for every slab's context: the plane copies between contexts and the
+            # sweeps are then ordered without host synchronisation
+            self._stream = torch.cuda.Stream()
+            problem_kw["stream"] = self._stream.cuda_stream
+        for g in self.geom:
+            cases = None if load_cases is None else [slab_loads(c, g) for c in load_cases]
+            p = Problem(slab_spec(spec, g), nrhs=nrhs, load_cases=cases, **problem_kw)
+            if kernel:
+                p.select_kernel(kernel)
+            p.set_owned_planes(g.zlo, g.zhi, g.g0)
+            self.probs.append(p)
+        p0 = self.probs[0]
+        self.ncomp = p0.nrhs * p0.ncomp
+        dt = torch.float64 if p0.np_dtype == np.float64 else torch.float32
+        self._buf = torch.empty(p0.plane_shape(), dtype=dt, device="cuda")
+        # ||F|| over the free DOFs: the residual of the zero state, summed over the slabs
+        self.f_norm = float(np.sqrt(sum(p.residual(with_field=False)[0] for p in self.probs)))
+
+    def close(self):
+        for p in self.probs:
+            p.synchronize()  # the plane buffer is torch's again only once its copies are done
+        for p in self.probs:
+            p.close()
+        self.probs = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_design(self, phi):
+        for g, p in zip(self.geom, self.probs):
+            p.set_design(slab_cells(phi, self.spec, g))
+
+    def set_state(self, u, w=None):
+        for g, p in zip(self.geom, self.probs):
+            p.set_state(slab_nodes(u, self.spec, g), None if w is None else slab_nodes(w, self.spec, g))
+
+    def get_state(self, with_w: bool = False, dtype=np.float64):
+        parts = [(g, p.get_state(with_w=with_w, dtype=dtype)) for g, p in zip(self.geom, self.probs)]
+        if not with_w:
+            return self._gather_owned(parts, self.ncomp)
+        return (self._gather_owned([(g, uw[0]) for g, uw in parts], self.ncomp),
+                self._gather_owned([(g, uw[1]) for g, uw in parts], self.ncomp))
+
+    def exchange(self):
+        """Each interface plane from its owner into the neighbour's ghost plane."""
+        for src, ks, dst, kd in interface_copies(self.geom):
+            self.probs[src].get_plane(ks, self._buf)
+            self.probs[dst].set_plane(kd, self._buf)
+
+    def sweep(self, kind: int, n: int, a: float = 0.0, b: float = 0.0, s1: float = 0.0,
+              local_dt: bool = False) -> float:
+        """n sweeps of every slab, an exchange before each; ||R||^2 of the last over the grid."""
+        r2 = 0.0
+        for t in range(n):
+            self.exchange()
+            last = t == n - 1
+            vals = [p.sweep(kind, 1, a, b, s1, local_dt, want_res=last) for p in self.probs]
+            if last:
+                r2 = float(sum(vals))
+        return r2
+
+    def residual(self) -> float:
+        """||R||^2 of the current state over the whole grid."""
+        self.exchange()
+        return float(sum(p.residual(with_field=False)[0] for p in self.probs))
+
+
+class DistributedSlabs(_SlabDriver):
+    """One slab per rank of a torch.distributed group (rank r holds slab r).  Planes move
+    between neighbouring ranks as point-to-point messages; residuals are all-reduced.
+    ``make_problem(local_spec)`` builds the rank's context (default: a Problem on the
+    current GPU); plane buffers live where the backend moves data (CUDA for NCCL)."""
+
+    def __init__(self, spec, *, group=None, make_problem=None, kernel: str | None = None, device=None):
+        torch = _torch()
+        import torch.distributed as dist
+        self.dist, self.group = dist, group
+        self.rank = dist.get_rank(group)
+        self.world = dist.get_world_size(group)
+        self.spec = spec
+        self.geom = slab_geometry(spec.nz, self.world)
+        self.g = self.geom[self.rank]
+        local = slab_spec(spec, self.g)
+        if make_problem is None:
+            from .problem import Problem
+            make_problem = Problem
+        self.prob = make_problem(local)
+        if kernel:
+            self.prob.select_kernel(kernel)
+        self.prob.set_owned_planes(self.g.zlo, self.g.zhi, self.g.g0)
+        self.ncomp = self.prob.nrhs * self.prob.ncomp
+        if device is None:
+            device = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+        self.device = torch.device(device)
+        dt = torch.float64 if self.prob.np_dtype == np.float64 else torch.float32
+        shape = self.prob.plane_shape()
+        self._send = [torch.empty(shape, dtype=dt, device=self.device) for _ in range(2)]
+        self._recv = [torch.empty(shape, dtype=dt, device=self.device) for _ in range(2)]
+        self.f_norm = float(np.sqrt(self._allreduce(self.prob.residual(with_field=False)[0])))
+
+    def _global_rank(self, r):
+        return r if self.group is None else self.dist.get_global_rank(self.group, r)
+
+    def _allreduce(self, x: float) -> float:
+        t = _torch().tensor([x], dtype=_torch().float64, device=self.device)
+        self.dist.all_reduce(t, group=self.group)
+        return float(t.item())
+
+    def exchange(self):
+        """Send the owned boundary planes to the neighbours, receive their planes into the
+        ghost planes."""
+        dist, r, g = self.dist, self.rank, self.g
+        ops = []
+        if r + 1 < self.world:  # upper neighbour
+            self.prob.get_plane(g.zhi, self._send[1])
+            ops.append(dist.P2POp(dist.isend, self._send[1], self._global_rank(r + 1), self.group))
+            ops.append(dist.P2POp(dist.irecv, self._recv[1], self._global_rank(r + 1), self.group))
+        if r > 0:               # lower neighbour
+            self.prob.get_plane(g.zlo, self._send[0])
+            ops.append(dist.P2POp(dist.isend, self._send[0], self._global_rank(r - 1), self.group))
+            ops.append(dist.P2POp(dist.irecv, self._recv[0], self._global_rank(r - 1), self.group))
+        if not ops:
+            return
+        cuda = self.device.type == "cuda"
+        if cuda:
+            self.prob.synchronize()  # the planes are packed on the context's stream
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+        if cuda:
+            _torch().cuda.current_stream().synchronize()  # received before the context reads them
+        if r + 1 < self.world:
+            self.prob.set_plane(g.nz, self._recv[1])
+        if r > 0:
+            self.prob.set_plane(0, self._recv[0])
+
+    def sweep(self, kind: int, n: int, a: float = 0.0, b: float = 0.0, s1: float = 0.0,
+              local_dt: bool = False) -> float:
+        r2 = 0.0
+        for t in range(n):
+            self.exchange()
+            last = t == n - 1
+            v = self.prob.sweep(kind, 1, a, b, s1, local_dt, want_res=last)
+            if last:
+                r2 = self._allreduce(v)
+        return r2
+
+    def set_design(self, phi):
+        self.prob.set_design(slab_cells(phi, self.spec, self.g))
+
+    def set_state(self, u, w=None):
+        self.prob.set_state(slab_nodes(u, self.spec, self.g), None if w is None else slab_nodes(w, self.spec, self.g))
+
+    def get_state(self, dtype=np.float64):
+        """The whole grid's state, assembled on every rank."""
+        mine = np.asarray(self.prob.get_state(dtype=np.float64))
+        parts = [None] * self.world
+        self.dist.all_gather_object(parts, (self.rank, mine), group=self.group)
+        return self._gather_owned([(self.geom[r], u) for r, u in parts], self.ncomp).astype(dtype)

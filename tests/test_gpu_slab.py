@@ -1,0 +1,143 @@
+"""Slab decomposition on one GPU: several slab contexts of one grid, planes exchanged device
+to device before every sweep, against the same sweeps of the whole grid.  A node's update
+reads only its 3 x 3 x 3 neighbourhood and its 8 cells, in the same order in both, so the
+owned planes must match bit for bit (node-gather and two-row marching kernels, FP64 and
+FP32); the FP64 decomposed solve is also held against the oracle's direct solve."""
+import numpy as np
+import pytest
+
+from paper_2509_06971_gb300 import slab as S
+from paper_2509_06971_gb300 import workloads as W
+from tests._util import oracle_materials, oracle_problem, nodes_to_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2509_06971_gb300 import problem as PR
+    return PR
+
+
+def _spec(nx=70, ny=40, nz=37, precision="f64"):
+    """Several x/y tiles and z segments with ragged tails; loads on and next to slab
+    interfaces; supports crossing them."""
+    base = W.cantilever3d(nx, ny, nz)
+    loads = base.loads + [((31, 7, 12), 0, 0.7), ((30, 6, 13), 1, -0.4), ((62, 14, 25), 2, 0.25),
+                          ((5, 39, 19), 2, 1.0), ((nx, ny, nz), 1, 0.3)]
+    boxes = base.boxes + [((nx, 0, 10), (nx, ny, 30), 0b010), ((10, 21, 0), (40, 22, 5), 0b101)]
+    spec = base.with_(loads=loads, boxes=boxes, precision=precision, storage=precision)
+    return spec.with_(phi0=W.random_design(spec, seed=31))
+
+
+def _whole(P, spec, kernel, u0, w0, sweeps):
+    p = P.Problem(spec)
+    if kernel:
+        p.select_kernel(kernel)
+    p.set_state(u0, w0)
+    r2 = [p.sweep(kind, n, a, b, s1, True) for kind, n, a, b, s1 in sweeps]
+    u, w = p.get_state(with_w=True, dtype=p.np_dtype)
+    p.close()
+    return u, w, r2
+
+
+SWEEPS = [(0, 3, 0.9, 0.8, 0.0), (1, 2, 0.0, 0.0, 0.15), (0, 2, 0.95, 0.7, 0.0)]
+
+
+def _same(a, b, spec):
+    """Bit-for-bit equality; on failure, report the size of the gap and the planes it is on."""
+    if np.array_equal(a, b):
+        return
+    d = np.abs(np.asarray(a, np.float64) - b).reshape(a.shape[0], spec.nz + 1, spec.ny + 1, spec.nx + 1)
+    planes = np.nonzero(d.max(axis=(0, 2, 3)))[0].tolist()
+    pytest.fail(f"max |diff| {d.max():.3e} (rel {d.max() / np.abs(b).max():.3e}) on planes {planes}")
+
+
+@pytest.mark.parametrize("precision,kernel", [("f64", None), ("f32", "tma2"), ("f32", "gather/32x4")])
+@pytest.mark.parametrize("n_slabs", [2, 3])
+def test_slabs_equal_whole_grid_sweeps(P, precision, kernel, n_slabs):
+    spec = _spec(precision=precision)
+    dt = np.float64 if precision == "f64" else np.float32
+    u0 = W.random_state(spec, seed=32).astype(dt)
+    w0 = W.random_state(spec, seed=33, scale=0.1).astype(dt)
+    uw, ww, r2w = _whole(P, spec, kernel, u0, w0, SWEEPS)
+    with S.SlabGrid(spec, n_slabs, kernel=kernel) as g:
+        if kernel:
+            name = g.probs[0].kernel_info()[0]
+            assert name.startswith(kernel.split("/")[0])
+        g.set_state(u0, w0)
+        r2s = [g.sweep(kind, n, a, b, s1, True) for kind, n, a, b, s1 in SWEEPS]
+        us, ws = g.get_state(with_w=True, dtype=dt)
+    _same(us, uw, spec)
+    _same(ws, ww, spec)  # w of the last APT block
+    tol = 1e-12 if precision == "f64" else 1e-5  # sums over slabs in another order
+    for a, b in zip(r2s, r2w):
+        assert abs(a - b) <= tol * b
+
+
+def test_slab_solve_matches_direct_solve_fp64(P):
+    """A fixed-momentum APT solve over three slabs, exchange before every sweep, to
+    ||R|| <= 1e-9 ||F||: compliance within 1e-7 of the oracle's direct solve."""
+    base = W.cantilever3d(24, 12, 14, precision="f64")
+    spec = base.with_(loads=base.loads + [((12, 6, 5), 0, 0.5), ((20, 3, 9), 1, -0.3)],
+                      phi0=W.random_design(base, seed=36, lo=0.3, hi=0.95))
+    with S.SlabGrid(spec, 3) as g:
+        rep = g.solve(tol=1e-9, check_every=50, max_sweeps=20000)  # about 6 600 sweeps
+        u = g.get_state()
+    assert rep["converged"], rep
+    op, om = oracle_problem(spec), oracle_materials(spec)
+    F = op.load_vector()
+    ud = op.direct_solve(om.modulus(spec.phi0), F, op.fixed_mask())
+    Cs, Cd = float(F @ nodes_to_oracle(u)), float(F @ ud)
+    assert abs(Cs - Cd) <= 1e-7 * abs(Cd)
+
+
+def test_slab_multi_rhs_tma2_equals_whole(P):
+    spec, cases = W.multirhs3d(40, 18, 20, n_rhs=2, seed=5)
+    spec = spec.with_(precision="f32", storage="f32", phi0=W.random_design(spec, seed=34))
+    rng = np.random.default_rng(35)
+    u0 = rng.standard_normal((6, spec.nnodes)).astype(np.float32)
+    p = P.Problem(spec, nrhs=2, load_cases=cases)
+    p.select_kernel("tma2")
+    p.set_state(u0)
+    p.sweep(0, 4, 0.9, 0.8, 0.0, True)
+    uw = p.get_state(dtype=np.float32)
+    p.close()
+    with S.SlabGrid(spec, 2, kernel="tma2", nrhs=2, load_cases=cases) as g:
+        g.set_state(u0)
+        g.sweep(0, 4, 0.9, 0.8, 0.0, True)
+        us = g.get_state(dtype=np.float32)
+    _same(us, uw, spec)
+
+
+def test_slab_argument_checks(P):
+    from paper_2509_06971_gb300 import capi as C
+    p2 = P.Problem(W.mbb_halfbeam(24, 8))
+    with pytest.raises(C.PettoError) as e:
+        p2.set_owned_planes(0, 0)
+    assert e.value.status == C.PETTO_EUNSUPPORTED
+    p2.close()
+    p3 = P.Problem(W.cantilever3d(24, 12, 12).with_(precision="f32", storage="f32"))
+    for lo, hi in ((-1, 3), (4, 3), (0, 13)):
+        with pytest.raises(C.PettoError) as e:
+            p3.set_owned_planes(lo, hi)
+        assert e.value.status == C.PETTO_EINVAL
+    p3.set_owned_planes(1, 11)
+    with pytest.raises(C.PettoError) as e:
+        p3.select_kernel("tma8")  # one-row marching kernels write whole columns
+    assert e.value.status == C.PETTO_EINVAL
+    p3.select_kernel("gather")
+    assert p3.kernel_info()[0].startswith("gather/")
+    with pytest.raises(C.PettoError) as e:
+        p3.get_plane(13)
+    assert e.value.status == C.PETTO_EINVAL
+    with pytest.raises(ValueError):
+        p3.get_plane(0, out=np.empty(p3.plane_shape(), np.float64))  # not the sweep precision
+    # the whole range restores a whole-grid context; planes round-trip through the host
+    p3.set_owned_planes(0, 12)
+    pl = np.arange(np.prod(p3.plane_shape()), dtype=np.float32).reshape(p3.plane_shape())
+    p3.set_plane(5, pl)
+    assert np.array_equal(p3.get_plane(5), pl)
+    u = p3.get_state(dtype=np.float32).reshape(3, 13, 13, 25)
+    assert np.array_equal(u[:, 5], pl) and not u[:, 4].any()
+    p3.close()
