@@ -219,6 +219,8 @@ def run_ours(args):
     spec = WORKLOADS[args.workload]()
     prob = PR.Problem(spec)
     solve_kw = dict(tol=args.tol, max_sweeps=args.max_sweeps, check_every=spec.check_every)
+    if args.method == "pt":
+        solve_kw["momentum"] = 2  # the plain first-order method: PT sweeps throughout
 
     def design_iter():
         hist, _ = prob.optimize(1, solve_kw=solve_kw)
@@ -300,7 +302,8 @@ def run_ours(args):
                         if args.workload in PAPER_DERIVED_GCELL_SWEEPS else None),
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "cells": spec.ncells, "nodes": spec.nnodes,
-                   "tol": args.tol, "parallelism": f"replicas{world}",
+                   "tol": args.tol, "method": args.method, "max_sweeps": args.max_sweeps,
+                   "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2" if sweep_bytes(spec) > 129e6 else "working set fits in L2"},
         "s_per_design_iter": ms_max * 1e-3 / args.steps,
         "sweeps_per_design_iter": sweeps / args.steps,
@@ -576,6 +579,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--max-sweeps", type=int, default=20000)
+    ap.add_argument("--method", choices=["apt", "pt"], default="apt",
+                    help="pt: the same design iterations with PT sweeps only (the plain first-order method)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="only run this many APT sweeps of the workload (for profiler captures)")

@@ -122,7 +122,8 @@ typedef struct {
  * momentum 0: a_k = a (the paper's fixed damping).  momentum 1 (adaptive restart, an
  * extension): a_k = min(a, (k-1)/(k+2)) with k the sweeps since the last restart; the sweeps
  * with (t mod check_every) % 4 == 3 test <R, w> of their input and, when negative, restart
- * the momentum at the next sweep (decided on the device).  Whole check intervals are
+ * the momentum at the next sweep (decided on the device).  momentum 2: PT sweeps throughout
+ * (the plain first-order method, for comparison; not taken by batches).  Whole check intervals are
  * replayed as CUDA graphs (unless PETTO_NO_GRAPHS is set); a context created with the
  * legacy default stream runs on a blocking stream of its own.
  * refine 1 (FP32 contexts, tolerance mode, tol < 1e-3): an FP32 state cannot represent a

@@ -1014,7 +1014,7 @@ petto_status set_ctrl(petto_ctx *ctx, int slot, long long v) {
 petto_status graph_chunk(petto_ctx *ctx, const petto_solve_opts *o, bool apt, int ce, long long base,
                          const void *rhs, bool *done, bool res_last = true) {
     *done = false;
-    const int adaptive = o->momentum ? 1 : 0;
+    const int adaptive = o->momentum == 1 ? 1 : 0;
     petto_ctx::GraphEntry *ge = nullptr;
     for (auto &g : ctx->graphs)
         if (g.apt == apt && g.local_dt == o->local_dt && g.adaptive == adaptive && g.cur == ctx->cur && g.ce == ce &&
@@ -1087,7 +1087,7 @@ petto_status graph_chunk(petto_ctx *ctx, const petto_solve_opts *o, bool apt, in
 // ends the phase.
 petto_status apply_check(petto_ctx *ctx, const petto_solve_opts *o, SolveState &S, double rn, bool check,
                          double stop_abs, int stall_checks, bool *ended, int *reached) {
-    const double guard = o->momentum ? 100.0 : 10.0;
+    const double guard = o->momentum == 1 ? 100.0 : 10.0;
     *ended = false;
     if (!check) {
         *ended = true;
@@ -1254,7 +1254,7 @@ petto_status sweep_phase(petto_ctx *ctx, const petto_solve_opts *o, SolveState &
             const bool check = ce > 0 && (S.sweeps + 1) % ce == 0;
             const bool final_report = (S.sweeps + 1 == S.total);
             SweepCtl sc;
-            sc.adaptive = o->momentum ? 1 : 0;
+            sc.adaptive = o->momentum == 1 ? 1 : 0;
             sc.test_dot = ((ce > 0 ? S.sweeps % ce : S.sweeps) % 4) == 3;
             sc.idx = S.sweeps;
             sc.rhs = rhs;
@@ -1296,10 +1296,12 @@ petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_sol
     if (o->mode != PETTO_SOLVE_PAPER && o->mode != PETTO_SOLVE_TOL) return fail(ctx, PETTO_EINVAL, "bad mode");
     if (o->n_apt < 0 || o->n_pt < 0 || o->max_sweeps < 0 || o->check_every < 0)
         return fail(ctx, PETTO_EINVAL, "negative count");
+    if (o->momentum < 0 || o->momentum > 2) return fail(ctx, PETTO_EINVAL, "momentum is 0, 1 or 2");
     CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
     petto_status st = set_ctrl(ctx, CT_RESTART_AT, 0);
     if (st != PETTO_OK) return st;
     SolveState S;
+    S.use_pt = o->momentum == 2;  // the plain first-order method throughout
     S.total = o->mode == PETTO_SOLVE_PAPER ? o->n_apt + o->n_pt : o->max_sweeps;
     const double fn = ctx->f_norm;
     const bool refine = o->mode == PETTO_SOLVE_TOL && o->refine && ctx->precision == PETTO_F32 && o->tol < 1e-3;
@@ -1975,6 +1977,7 @@ petto_status petto_batch_pt_solve(petto_batch *b, const petto_solve_opts *opts, 
     if (o0.mode != PETTO_SOLVE_PAPER && o0.mode != PETTO_SOLVE_TOL) return bfail(b, PETTO_EINVAL, "bad mode");
     if (o0.n_apt < 0 || o0.n_pt < 0 || o0.max_sweeps < 0) return bfail(b, PETTO_EINVAL, "negative count");
     if (o0.check_every < 2 || o0.check_every % 2) return bfail(b, PETTO_EINVAL, "check_every must be even and >= 2");
+    if (o0.momentum < 0 || o0.momentum > 1) return bfail(b, PETTO_EINVAL, "batches take momentum 0 or 1");
     StreamJoin join(b);
     petto_status st = batch_refresh(b);
     if (st != PETTO_OK) return st;

@@ -497,6 +497,28 @@ def test_paper_mode_fixed_counts(P):
     prob.close()
 
 
+def test_pt_only_solve(P):
+    """momentum 2, the plain first-order method: every sweep of a paper-mode solve is a PT
+    sweep (the oracle's PT sweeps, 1e-12), and a tolerance solve runs PT sweeps only."""
+    spec = W.mbb_halfbeam(24, 8)
+    spec, prob, op, om, phi = _setup(P, spec, seed=26)
+    rep = prob.solve(mode=0, n_apt=12, n_pt=8, s1=0.7, local_dt=True, momentum=2, check_every=0)
+    assert rep["sweeps"] == 20 and rep["apt_sweeps"] == 0 and rep["pt_sweeps"] == 20
+    u = np.zeros(op.ndof)
+    E, F, fixed = om.modulus(phi), op.load_vector(), op.fixed_mask()
+    for _ in range(20):
+        op.pt_sweep(E, F, fixed, 0.7, u, local_dt=True)
+    assert relmax(prob.get_state(), oracle_to_nodes(u, 2)) < 1e-12
+    rel0 = rep["rel_res"]
+    rep = prob.solve(tol=1e-4, s1=0.7, momentum=2, check_every=50, max_sweeps=3000)
+    assert rep["apt_sweeps"] == 0 and rep["pt_sweeps"] == rep["sweeps"] > 0 and rep["rel_res"] < rel0
+    from paper_2509_06971_gb300 import capi as C
+    with pytest.raises(C.PettoError) as e:
+        prob.solve(tol=1e-4, momentum=3)
+    assert e.value.status == C.PETTO_EINVAL
+    prob.close()
+
+
 @pytest.mark.parametrize("variant", ["tma2", "tma8"])
 def test_multi_rhs_fp32_march(P, variant, monkeypatch):
     """FP32 multi-load-case sweeps on the marching kernels (one launch per case sharing the
