@@ -65,13 +65,14 @@ METRIC = "APT Gcell-sweeps/s & % HBM roofline; s/design-iter at rel.res 1e-6"
 # kernel from one ncu capture of the workload: the refinement sweep of the two-row marching
 # kernel, 97.6 % of the sweeps of a design iteration.  Keyed by workload and kernel name, so
 # that any other kernel reports null; to be re-captured whenever that kernel changes.
-NCU_TRAFFIC = {("cantilever3d_256x128x128", "tma2/zs12"): 171.320320e6 + 64.201984e6}
+NCU_TRAFFIC = {("cantilever3d_256x128x128", "tma2/zs12"): 171334400 + 64289792}
 
 
-def sweep_bytes(spec, tsize=4):
-    """Algorithmic bytes of one APT sweep: read+write of u and of w (node fields, ncomp
-    components each) and one read of the modulus (cell field)."""
-    return spec.nnodes * 4 * spec.ncomp * tsize + spec.ncells * tsize
+def sweep_bytes(spec, tsize=4, method="apt"):
+    """Algorithmic bytes of one sweep: read+write of u and (APT) of w, node fields of ncomp
+    components each, and one read of the modulus (cell field)."""
+    fields = 4 if method == "apt" else 2
+    return spec.nnodes * fields * spec.ncomp * tsize + spec.ncells * tsize
 
 
 def measured_peaks():
@@ -265,7 +266,7 @@ def run_ours(args):
     # refinement sweeps read a dense right-hand side as well (ncomp values per node; FP16 for
     # the two-row 3D marching kernel, FP32 otherwise)
     kname, rhs_b = prob.kernel_info()
-    bytes_avg = sweep_bytes(spec) + (kern_rhs / max(kern_n, 1)) * spec.nnodes * spec.ncomp * rhs_b
+    bytes_avg = sweep_bytes(spec, method=args.method) + (kern_rhs / max(kern_n, 1)) * spec.nnodes * spec.ncomp * rhs_b
     achieved = bytes_avg / (per_launch_ms * 1e-3) / 1e9 if kern_n else None
     peak = float(peaks.get("hbm_gbs", 6800.0))
 
@@ -310,8 +311,8 @@ def run_ours(args):
         "final_rel_res": rows[-1]["rel_res"], "compliance": rows[-1]["compliance"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
-                     "traffic": NCU_TRAFFIC.get((args.workload, kname)),
-                     "kernel": "apt sweep", "kernel_ms": per_launch_ms, "bytes_per_launch": bytes_avg,
+                     "traffic": NCU_TRAFFIC.get((args.workload, kname)) if args.method == "apt" else None,
+                     "kernel": f"{args.method} sweep", "kernel_ms": per_launch_ms, "bytes_per_launch": bytes_avg,
                      "rhs_sweep_fraction": kern_rhs / max(kern_n, 1), "rhs_bytes": rhs_b,
                      "sweep_kernel": kname, "peak_kind": peak_kind},
         "e2e": {"value": e_value, "unit": "Gcell-sweeps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
