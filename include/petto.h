@@ -254,7 +254,9 @@ petto_status petto_set_keepout(petto_ctx *ctx, const int64_t *box, const double 
  * take the same values as in the same sweeps of the whole grid, bit for bit (a node's update
  * reads its 3 x 3 x 3 node neighbourhood and its 8 cells only, in the same order).  Residual
  * sums of the slabs add up to the whole grid's.  The node gather and the two-row marching
- * kernel take slabs; selecting another kernel on a slab context is PETTO_EUNSUPPORTED. */
+ * kernel take slabs: a slab context whose kernel is another marching variant switches to
+ * the node gather, and petto_select_kernel offers it only those two (PETTO_EINVAL for the
+ * others). */
 
 /* Node planes zlo..zhi (local indices, inclusive) are the ones this context's sweeps write;
  * zlo = 0, zhi = nz cells (the last node plane) restores the whole grid.  z_global is the
