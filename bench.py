@@ -11,6 +11,13 @@ wall time on the device), with the sweep kernel's achieved HBM bandwidth against
 measured copy peak, seconds per design iteration and sweeps per iteration.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+                  [--method apt|pt] [--max-sweeps N]
+
+The roofline object names the sweep kernel in use (`sweep_kernel`), the bytes per node and
+component of the right-hand side its refinement sweeps read (`rhs_bytes`: 2 for the FP16
+copy of the two-row 3D marching kernel) and, where an ncu capture of that kernel on that
+workload exists, its DRAM bytes per launch (`traffic`).  --method pt runs the same design
+iterations with PT sweeps only (the plain first-order method) for comparison.
 
 Under torchrun (N > 1) every rank runs its own replica of the workload (independent
 problems: weak scaling, no data-path collective); the barrier and max-over-ranks time
