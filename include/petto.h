@@ -130,7 +130,8 @@ typedef struct {
  * solution much below relative residual ~1e-4 for stiff problems, so the solve sweeps the
  * FP32 state to 1e-2, then continues the same iteration on u = u64 + d with u64 in FP64:
  * whenever the check residual has fallen 8x (or stalls for 20 checks) d is added to u64,
- * the FP64 defect F - K u64 becomes the FP32 right-hand side of the sweeps and d restarts
+ * the FP64 defect F - K u64 becomes the right-hand side of the sweeps (FP32; for the two-row
+ * 3D marching kernel FP16 scaled by a power of two, see petto_kernel_info) and d restarts
  * at zero, while w and the momentum schedule carry on.  The solve ends when the FP64
  * defect meets the tolerance.  With the environment variable PETTO_TRACE set, every check
  * residual is printed to stderr.

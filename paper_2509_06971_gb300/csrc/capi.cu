@@ -1129,7 +1129,7 @@ petto_status apply_check(petto_ctx *ctx, const petto_solve_opts *o, SolveState &
 constexpr double REFINE_FROM = 1e-2;
 constexpr int REFINE_STALL = 20;
 
-// u64 <- u (FP32 state), allocating the FP64 state, defect and FP32 right-hand side
+// u64 <- u (FP32 state), allocating the FP64 state, defect and right-hand side buffer
 petto_status refine_begin(petto_ctx *ctx) {
     const size_t nb64 = (size_t)ctx->ndofc() * ctx->L.cstride * sizeof(double);
     const int64_t nel = (int64_t)ctx->ndofc() * ctx->L.cstride;
@@ -1316,7 +1316,7 @@ petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_sol
     } else {
         // FP32 sweeps on the state itself down to REFINE_FROM, then the same iteration
         // continued on u = u64 + d: u64 (FP64) absorbs d whenever the check residual has fallen 8x, the
-        // FP64 defect F - K u64 becomes the FP32 right-hand side of the sweeps, d restarts
+        // FP64 defect F - K u64 becomes the right-hand side of the sweeps, d restarts
         // from zero and the increment w and the momentum schedule carry on unchanged (the
         // APT recursion is the same in the shifted variable).
         st = sweep_phase(ctx, o, S, REFINE_FROM * fn, 0, REFINE_STALL, nullptr, &reached);
