@@ -244,7 +244,9 @@ class DistributedSlabs(_SlabDriver):
     """One slab per rank of a torch.distributed group (rank r holds slab r).  Planes move
     between neighbouring ranks as point-to-point messages; residuals are all-reduced.
     ``make_problem(local_spec)`` builds the rank's context (default: a Problem on the
-    current GPU); plane buffers live where the backend moves data (CUDA for NCCL)."""
+    current GPU, so each rank selects its GPU with torch.cuda.set_device first); plane
+    buffers live where the backend moves data (CUDA for NCCL).  Every rank constructs its
+    driver and calls the same methods in the same order (they contain collectives)."""
 
     def __init__(self, spec, *, group=None, make_problem=None, kernel: str | None = None, device=None):
         torch = _torch()
