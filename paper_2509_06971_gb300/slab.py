@@ -174,13 +174,17 @@ class SlabGrid(_SlabDriver):
             # sweeps are then ordered without host synchronisation
             self._stream = torch.cuda.Stream()
             problem_kw["stream"] = self._stream.cuda_stream
-        for g in self.geom:
-            cases = None if load_cases is None else [slab_loads(c, g) for c in load_cases]
-            p = Problem(slab_spec(spec, g), nrhs=nrhs, load_cases=cases, **problem_kw)
-            if kernel:
-                p.select_kernel(kernel)
-            p.set_owned_planes(g.zlo, g.zhi, g.g0)
-            self.probs.append(p)
+        try:
+            for g in self.geom:
+                cases = None if load_cases is None else [slab_loads(c, g) for c in load_cases]
+                p = Problem(slab_spec(spec, g), nrhs=nrhs, load_cases=cases, **problem_kw)
+                self.probs.append(p)
+                if kernel:
+                    p.select_kernel(kernel)
+                p.set_owned_planes(g.zlo, g.zhi, g.g0)
+        except Exception:
+            self.close()  # the contexts made so far
+            raise
         p0 = self.probs[0]
         self.ncomp = p0.nrhs * p0.ncomp
         dt = torch.float64 if p0.np_dtype == np.float64 else torch.float32
