@@ -1,0 +1,81 @@
+"""The benchmark's workload at full size -- the 3D cantilever 256 x 128 x 128 in FP32, on the
+sweep kernel and launch configuration that bench.py times -- against the oracle.
+
+* One APT and one PT sweep from a seeded random state and design, field by field against
+  the oracle's sweeps.  Global pseudo-time steps: the oracle's local-step form recomputes
+  diag(K) on every call, about a minute per sweep at this size; the local-step path is held
+  element by element on the smaller grids of test_gpu_parity.py.
+* The refined solve of the first design iteration (local steps, adaptive momentum, FP64
+  refinement with FP16 right-hand sides), by what holds at any size: the oracle's energy
+  of the returned state equals its work F . u (the state solves K u = F), and the GPU's
+  compliance and sensitivity field equal the oracle's for that state.
+"""
+import numpy as np
+import pytest
+
+from paper_2509_06971_gb300 import workloads as W
+from tests._util import nodes_to_oracle, oracle_materials, oracle_problem, oracle_to_nodes
+
+pytestmark = pytest.mark.gpu
+
+SIZE = (256, 128, 128)
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2509_06971_gb300 import problem as PR
+    return PR
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_fullsize_sweeps_match_oracle(P):
+    spec = W.cantilever3d(*SIZE)
+    phi = W.random_design(spec, seed=41)
+    u0 = W.random_state(spec, seed=42).astype(np.float32)
+    w0 = W.random_state(spec, seed=43, scale=0.1).astype(np.float32)
+    a, b, s1 = 0.95, 0.05, 0.1
+    prob = P.Problem(spec)
+    assert prob.kernel_info()[0].startswith("tma2/")  # the kernel the benchmark times
+    prob.set_design(phi)
+    prob.set_state(u0, w0)
+    r2a = prob.sweep(0, 1, a, b, 0.0, False)
+    r2p = prob.sweep(1, 1, 0.0, 0.0, s1, False)
+    ug, wg = prob.get_state(with_w=True)
+    prob.close()
+
+    op, om = oracle_problem(spec), oracle_materials(spec)
+    E = om.modulus(np.asarray(phi, np.float32).astype(np.float64))
+    F, fixed = op.load_vector(), op.fixed_mask()
+    uo, wo = nodes_to_oracle(u0.astype(np.float64)), nodes_to_oracle(w0.astype(np.float64))
+    r2a_o = op.apt_sweep(E, F, fixed, a, b, uo, wo)
+    r2p_o = op.pt_sweep(E, F, fixed, s1, uo)
+    un, wn = oracle_to_nodes(uo, 3), oracle_to_nodes(wo, 3)
+    for c in range(3):
+        assert rel_l2(ug[c], un[c]) < 1e-5
+        assert rel_l2(wg[c], wn[c]) < 1e-5
+    assert abs(r2a - r2a_o) < 1e-5 * r2a_o
+    assert abs(r2p - r2p_o) < 1e-5 * r2p_o
+
+
+def test_fullsize_refined_solve(P):
+    spec = W.cantilever3d(*SIZE)
+    prob = P.Problem(spec)
+    rep = prob.solve(tol=1e-6)
+    assert rep["converged"] and rep["rel_res"] <= 1e-6
+    Cg, Wg, sg = prob.sensitivity()
+    u = prob.get_state()
+    prob.close()
+
+    op, om = oracle_problem(spec), oracle_materials(spec)
+    phi = np.asarray(spec.phi0, np.float32).astype(np.float64)
+    uo = nodes_to_oracle(u)
+    so, Co = om.sensitivity(phi, om.modulus(phi), op.cell_energy(uo))
+    Wo = float(op.load_vector() @ uo)
+    assert abs(Co - Wo) < 1e-4 * Co    # energy equals work: the state solves K u = F
+    assert abs(Cg - Co) < 1e-5 * Co    # the GPU's compliance of its own state
+    assert abs(Wg - Wo) < 1e-5 * Co
+    assert rel_l2(sg, so) < 1e-5
