@@ -1,5 +1,6 @@
 """The benchmark's workload at full size -- the 3D cantilever 256 x 128 x 128 in FP32, on the
-sweep kernel and launch configuration that bench.py times -- against the oracle.
+sweep kernel and launch configuration that bench.py times -- against the oracle; and the
+2D cantilever 1024 x 512 and heat 1024 x 1024 grids on their default (y-marching) kernel.
 
 * One APT and one PT sweep from a seeded random state and design, field by field against
   the oracle's sweeps.  Global pseudo-time steps: the oracle's local-step form recomputes
@@ -19,6 +20,8 @@ from tests._util import nodes_to_oracle, oracle_materials, oracle_problem, oracl
 pytestmark = pytest.mark.gpu
 
 SIZE = (256, 128, 128)
+# the other full-size workloads: the 2D cantilever and heat grids (y-marching kernel)
+FULL_2D = {"cantilever2d_1024x512": lambda: W.cantilever2d(1024, 512), "heat2d_1024x1024": lambda: W.heat2d(1024)}
 
 
 @pytest.fixture(scope="module")
@@ -32,14 +35,20 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-def test_fullsize_sweeps_match_oracle(P):
-    spec = W.cantilever3d(*SIZE)
+def _spec(name):
+    return W.cantilever3d(*SIZE) if name == "cantilever3d" else FULL_2D[name]()
+
+
+@pytest.mark.parametrize("name,kernel", [("cantilever3d", "tma2/"), ("cantilever2d_1024x512", "march2d/"),
+                                         ("heat2d_1024x1024", "march2d/")])
+def test_fullsize_sweeps_match_oracle(P, name, kernel):
+    spec = _spec(name)
     phi = W.random_design(spec, seed=41)
     u0 = W.random_state(spec, seed=42).astype(np.float32)
     w0 = W.random_state(spec, seed=43, scale=0.1).astype(np.float32)
     a, b, s1 = 0.95, 0.05, 0.1
     prob = P.Problem(spec)
-    assert prob.kernel_info()[0].startswith("tma2/")  # the kernel the benchmark times
+    assert prob.kernel_info()[0].startswith(kernel)  # the kernel the benchmark times
     prob.set_design(phi)
     prob.set_state(u0, w0)
     r2a = prob.sweep(0, 1, a, b, 0.0, False)
@@ -53,8 +62,8 @@ def test_fullsize_sweeps_match_oracle(P):
     uo, wo = nodes_to_oracle(u0.astype(np.float64)), nodes_to_oracle(w0.astype(np.float64))
     r2a_o = op.apt_sweep(E, F, fixed, a, b, uo, wo)
     r2p_o = op.pt_sweep(E, F, fixed, s1, uo)
-    un, wn = oracle_to_nodes(uo, 3), oracle_to_nodes(wo, 3)
-    for c in range(3):
+    un, wn = oracle_to_nodes(uo, spec.ncomp), oracle_to_nodes(wo, spec.ncomp)
+    for c in range(spec.ncomp):
         assert rel_l2(ug[c], un[c]) < 1e-5
         assert rel_l2(wg[c], wn[c]) < 1e-5
     assert abs(r2a - r2a_o) < 1e-5 * r2a_o
