@@ -88,3 +88,37 @@ def test_fullsize_refined_solve(P):
     assert abs(Cg - Co) < 1e-5 * Co    # the GPU's compliance of its own state
     assert abs(Wg - Wo) < 1e-5 * Co
     assert rel_l2(sg, so) < 1e-5
+
+
+MULTIMAT = (384, 192, 192)
+
+
+def test_fullsize_multimat_bf16_modulus_and_sweep(P):
+    """The multi-material workload at full size (384 x 192 x 192, void + two solids, design
+    stored in BF16, arithmetic in FP32): the modulus equals the oracle's interpolation of
+    the stored design, and one APT sweep on that modulus matches the oracle's sweep."""
+    spec = W.multimat3d(*MULTIMAT, storage="bf16")
+    prob = P.Problem(spec)
+    prob.set_design(W.random_design(spec, seed=45, lo=0.05, hi=0.9))
+    phi_st = prob.get_design()  # the stored design, rounded to BF16
+    Eg = prob.get_modulus()
+    om = oracle_materials(spec)
+    Eo = om.modulus(phi_st)
+    assert np.abs(Eg - Eo).max() <= 1e-6 * np.abs(Eo).max()
+    u0 = W.random_state(spec, seed=46).astype(np.float32)
+    prob.set_state(u0)
+    a, b = 0.95, 0.05
+    r2 = prob.sweep(0, 1, a, b, 0.0, False)
+    ug, wg = prob.get_state(with_w=True)
+    prob.close()
+
+    op = oracle_problem(spec)
+    F, fixed = op.load_vector(), op.fixed_mask()
+    uo = nodes_to_oracle(u0.astype(np.float64))
+    wo = np.zeros_like(uo)
+    r2o = op.apt_sweep(Eg, F, fixed, a, b, uo, wo)  # on the GPU's modulus, so both sweep the same E
+    un, wn = oracle_to_nodes(uo, 3), oracle_to_nodes(wo, 3)
+    for c in range(3):
+        assert rel_l2(ug[c], un[c]) < 1e-5
+        assert rel_l2(wg[c], wn[c]) < 1e-5
+    assert abs(r2 - r2o) < 1e-5 * r2o
