@@ -122,3 +122,36 @@ def test_fullsize_multimat_bf16_modulus_and_sweep(P):
         assert rel_l2(ug[c], un[c]) < 1e-5
         assert rel_l2(wg[c], wn[c]) < 1e-5
     assert abs(r2 - r2o) < 1e-5 * r2o
+
+
+MULTIRHS = (192, 96, 96)
+
+
+def test_fullsize_multi_rhs_sweep(P):
+    """Four load cases at full size (192 x 96 x 96, one marching launch per case sharing the
+    step constants): one APT sweep of every case matches the oracle's sweep of that case."""
+    spec, cases = W.multirhs3d(*MULTIRHS, n_rhs=4)
+    phi = W.random_design(spec, seed=47)
+    u0 = np.concatenate([W.random_state(spec, seed=48 + r) for r in range(4)]).astype(np.float32)
+    prob = P.Problem(spec, nrhs=4, load_cases=cases)
+    assert prob.kernel_info()[0].startswith("tma2/")
+    prob.set_design(phi)
+    prob.set_state(u0)
+    a, b = 0.95, 0.05
+    r2 = prob.sweep(0, 1, a, b, 0.0, False)
+    ug, wg = prob.get_state(with_w=True)
+    prob.close()
+
+    om = oracle_materials(spec)
+    E = om.modulus(np.asarray(phi, np.float32).astype(np.float64))
+    r2o = 0.0
+    for r, case in enumerate(cases):
+        op = oracle_problem(spec, loads=case)
+        uo = nodes_to_oracle(u0[3 * r:3 * r + 3].astype(np.float64))
+        wo = np.zeros_like(uo)
+        r2o += op.apt_sweep(E, op.load_vector(), op.fixed_mask(), a, b, uo, wo)
+        un, wn = oracle_to_nodes(uo, 3), oracle_to_nodes(wo, 3)
+        for c in range(3):
+            assert rel_l2(ug[3 * r + c], un[c]) < 1e-5
+            assert rel_l2(wg[3 * r + c], wn[c]) < 1e-5
+    assert abs(r2 - r2o) < 1e-5 * r2o
