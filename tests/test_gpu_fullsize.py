@@ -155,3 +155,33 @@ def test_fullsize_multi_rhs_sweep(P):
             assert rel_l2(ug[3 * r + c], un[c]) < 1e-5
             assert rel_l2(wg[3 * r + c], wn[c]) < 1e-5
     assert abs(r2 - r2o) < 1e-5 * r2o
+
+
+N_BATCH = 48
+
+
+def test_fullsize_batch_paper_schedule(P):
+    """The 48-problem batch at full size (128 x 64 .. 1024 x 512 cells, one launch per sweep
+    over every problem): two APT and two PT sweeps of the paper's schedule (global steps,
+    fixed damping); the smallest and the largest problem match the oracle's sweeps."""
+    specs = W.batch2d(N_BATCH)
+    probs = [P.Problem(s) for s in specs]
+    b = P.Batch(probs)
+    kw = dict(mode=0, n_apt=2, n_pt=2, a=0.9, b=0.05, s1=0.1, local_dt=False, momentum=0, check_every=2)
+    reps = b.solve(**kw)
+    sizes = [s.ncells for s in specs]
+    picks = sorted({int(np.argmin(sizes)), int(np.argmax(sizes))})
+    states = {i: probs[i].get_state() for i in picks}
+    b.close()
+    for p in probs:
+        p.close()
+    for i in picks:
+        spec = specs[i]
+        assert reps[i]["apt_sweeps"] == 2 and reps[i]["pt_sweeps"] == 2
+        op, om = oracle_problem(spec), oracle_materials(spec)
+        u = np.zeros(op.ndof)
+        op.solve(om.modulus(np.asarray(spec.phi0, np.float32).astype(np.float64)), op.load_vector(), op.fixed_mask(),
+                 u, mode=0, n_apt=2, n_pt=2, a=0.9, b=0.05, s1=0.1, check_every=2, local_dt=False)
+        un = oracle_to_nodes(u, spec.ncomp)
+        for c in range(spec.ncomp):
+            assert rel_l2(states[i][c], un[c]) < 1e-5
