@@ -197,3 +197,18 @@ def test_distributed_slab_solve_reaches_the_direct_solution():
     assert r0["rep"]["converged"] == 1.0 and r0["rep"]["rel_res"] <= 1e-8
     assert res[1]["rep"] == r0["rep"]
     assert abs(r0["C"] - r0["Cd"]) <= 1e-6 * abs(r0["Cd"])
+
+
+def test_one_slab_is_the_whole_grid():
+    spec = W.cantilever3d(8, 4, 5)
+    (g,) = S.slab_geometry(spec.nz, 1)
+    assert (g.k0, g.k1, g.g0, g.g1, g.zlo, g.zhi, g.nz) == (0, 5, 0, 5, 0, 5, 5)
+    assert S.interface_copies([g]) == []
+    ls = S.slab_spec(spec, g)
+    assert ls.loads == spec.loads and ls.boxes == [tuple(b) for b in spec.boxes] and ls.nz == spec.nz
+
+
+def test_slab_geometry_rejects_2d():
+    spec = W.mbb_halfbeam(12, 4)
+    with pytest.raises(ValueError):
+        S.slab_spec(spec, S.SlabGeom(0, 0, 0, 1))
