@@ -188,3 +188,32 @@ def test_fullsize_batch_paper_schedule(P):
         un = oracle_to_nodes(u, spec.ncomp)
         for c in range(spec.ncomp):
             assert rel_l2(states[i][c], un[c]) < 1e-5
+
+
+PAPER_LOOPS = {
+    "heat2d_paper_512": lambda: W.heat2d_paper(512),
+    "mbb_multimat2d_512x128": lambda: W.mbb_multimat2d(512, 128),
+    "multimat3d_paper_256x17x85": lambda: W.multimat3d_paper(256, 17, 85),
+    "drone3d_128x64x128": lambda: W.drone3d(128, 64, 128),
+}
+
+
+@pytest.mark.parametrize("name", list(PAPER_LOOPS))
+def test_fullsize_paper_loop_sweeps(P, name):
+    """The paper's own loops at their full sizes (its grids, materials, global steps and
+    fixed damping): the solve's first three APT and two PT sweeps from the initial design
+    match the oracle's."""
+    spec = PAPER_LOOPS[name]()
+    prob = P.Problem(spec)
+    rep = prob.solve(mode=0, n_apt=3, n_pt=2, check_every=0)
+    assert rep["apt_sweeps"] == 3 and rep["pt_sweeps"] == 2
+    ug = prob.get_state()
+    prob.close()
+    op, om = oracle_problem(spec), oracle_materials(spec)
+    u = np.zeros(op.ndof)
+    op.solve(om.modulus(np.asarray(spec.phi0, np.float32).astype(np.float64)), op.load_vector(), op.fixed_mask(), u,
+             mode=0, n_apt=3, n_pt=2, a=spec.apt_a, b=spec.apt_b, s1=spec.pt_s1, check_every=0,
+             local_dt=spec.local_dt, momentum=0)
+    un = oracle_to_nodes(u, spec.ncomp)
+    for c in range(spec.ncomp):
+        assert rel_l2(ug[c], un[c]) < 1e-5
