@@ -26,7 +26,6 @@ use torch.distributed.  --impl reference times the FP64 CPU oracle on this host'
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
