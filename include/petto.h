@@ -211,6 +211,19 @@ petto_status petto_get_modulus(petto_ctx *ctx, void *E, int dtype, int on_device
 petto_status petto_sweep(petto_ctx *ctx, int kind, int64_t n, double a, double b, double s1, int local_dt,
                          double *res_norm2);
 
+/* Exactly n sweeps like petto_sweep with a dense right-hand side r in place of the loads:
+ * R = r - K u.  These are the correction sweeps of the FP64 iterative refinement that FP32
+ * solves use (K d = r with r the FP64 defect F - K u64; the sweep itself is Sec. 3.2's
+ * PT/APT system with r as the force).  r is FP64 in the natural layout [C][nodes] (host,
+ * or device when on_device), copied at the call; the context turns it into what its sweep
+ * kernel reads, exactly as refinement does: FP64 contexts read it as is, FP32 contexts as
+ * FP32, and the two-row marching kernels as FP16 holding r 2^k with 2^k the power of two
+ * that takes max |r| into [2^14, 2^15) (restored by 2^-k in the kernel).  u and w continue
+ * from the current state.  res_norm2 as in petto_sweep.  PETTO_EINVAL for a bad kind, n < 0
+ * or r = NULL. */
+petto_status petto_sweep_rhs(petto_ctx *ctx, int kind, int64_t n, double a, double b, double s1, int local_dt,
+                             const double *r, int on_device, double *res_norm2);
+
 /* R = F - K u on free DOFs (0 on supports) for the current state; R [C][nodes] may be
  * NULL; res_norm2 (may be NULL) receives sum R^2. */
 petto_status petto_residual(petto_ctx *ctx, double *res_norm2, void *R, int dtype, int on_device);

@@ -218,25 +218,31 @@ class OracleProblem:
         return out
 
     # sweeps -----------------------------------------------------------------
+    def inverse_diag(self, E) -> np.ndarray:
+        """1/diag(K(E)) per DOF (0 where the diagonal is 0): the local pseudo-time step scale."""
+        return self._dinv(E, True)
+
     def _dinv(self, E, local_dt):
         if not local_dt:
             return None
         d = self.diag_K(E)
         return np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0), 0.0)
 
-    def pt_sweep(self, E, F, fixed, s1, u, local_dt=False) -> float:
-        """In place on u (float64, contiguous).  Returns sum R^2 of the input state."""
+    def pt_sweep(self, E, F, fixed, s1, u, local_dt=False, dinv=None) -> float:
+        """In place on u (float64, contiguous).  Returns sum R^2 of the input state.
+        dinv: 1/diag(K) from an earlier ``inverse_diag`` call on the same E (saves the
+        recomputation of diag(K) on large grids)."""
         E, F = _f64(E), _f64(F)
         R = np.empty(self.ndof)
-        dinv = self._dinv(E, local_dt)
+        dinv = self._dinv(E, local_dt) if dinv is None or not local_dt else _f64(dinv)
         return _load().or_pt_sweep(ctypes.byref(self._g), _ptr(E), _ptr(F), _ptr(fixed), float(s1),
                                    None if dinv is None else _ptr(dinv), _ptr(u), _ptr(R))
 
-    def apt_sweep(self, E, F, fixed, a, b, u, w, local_dt=False) -> float:
-        """In place on u and w.  Returns sum R^2 of the input state."""
+    def apt_sweep(self, E, F, fixed, a, b, u, w, local_dt=False, dinv=None) -> float:
+        """In place on u and w.  Returns sum R^2 of the input state.  dinv as in pt_sweep."""
         E, F = _f64(E), _f64(F)
         R = np.empty(self.ndof)
-        dinv = self._dinv(E, local_dt)
+        dinv = self._dinv(E, local_dt) if dinv is None or not local_dt else _f64(dinv)
         return _load().or_apt_sweep(ctypes.byref(self._g), _ptr(E), _ptr(F), _ptr(fixed), float(a), float(b),
                                     None if dinv is None else _ptr(dinv), _ptr(u), _ptr(w), _ptr(R), None)
 

@@ -1129,10 +1129,9 @@ petto_status apply_check(petto_ctx *ctx, const petto_solve_opts *o, SolveState &
 constexpr double REFINE_FROM = 1e-2;
 constexpr int REFINE_STALL = 20;
 
-// u64 <- u (FP32 state), allocating the FP64 state, defect and right-hand side buffer
-petto_status refine_begin(petto_ctx *ctx) {
+// the FP64 state, defect and right-hand side buffers of the refinement
+petto_status refine_alloc(petto_ctx *ctx) {
     const size_t nb64 = (size_t)ctx->ndofc() * ctx->L.cstride * sizeof(double);
-    const int64_t nel = (int64_t)ctx->ndofc() * ctx->L.cstride;
     if (!ctx->u64) CK(cudaMalloc(&ctx->u64, nb64));
     if (!ctx->r64) {
         CK(cudaMalloc(&ctx->r64, nb64));
@@ -1140,6 +1139,14 @@ petto_status refine_begin(petto_ctx *ctx) {
         CK(cudaMemsetAsync(ctx->r64, 0, nb64, ctx->stream));
     }
     if (!ctx->rhs32) CK(cudaMalloc(&ctx->rhs32, ctx->node_bytes()));
+    return PETTO_OK;
+}
+
+// u64 <- u (FP32 state), allocating the FP64 state, defect and right-hand side buffer
+petto_status refine_begin(petto_ctx *ctx) {
+    const int64_t nel = (int64_t)ctx->ndofc() * ctx->L.cstride;
+    petto_status st = refine_alloc(ctx);
+    if (st != PETTO_OK) return st;
     f32_to_f64<<<grid_of(nel), 256, 0, ctx->stream>>>(nel, (const float *)ctx->u[ctx->cur], (double *)ctx->u64);
     CK(cudaGetLastError());
     ctx->launches++;
@@ -1168,7 +1175,8 @@ petto_status refine_defect(petto_ctx *ctx, double *norm) {
 // The two-row 3D marching kernel reads it as FP16 scaled by a power of two (one TMA box per
 // stage, 6 bytes a node instead of 12); FP16 keeps 11 bits, so the correction solved to the
 // FP32 floor (about 1e-4 of its right-hand side) loses nothing the next defect does not see.
-petto_status refine_correction(petto_ctx *ctx) {
+// r64 -> the right-hand side the sweep kernel reads (FP16 scaled or FP32, in rhs32)
+petto_status refine_rhs(petto_ctx *ctx) {
     const int64_t nel = (int64_t)ctx->ndofc() * ctx->L.cstride;
     ctx->rhs_half = ctx->tiling.kind == 4;
     if (ctx->rhs_half) {
@@ -1186,8 +1194,14 @@ petto_status refine_correction(petto_ctx *ctx) {
         f64_to_f32<<<grid_of(nel), 256, 0, ctx->stream>>>(nel, (const double *)ctx->r64, (float *)ctx->rhs32);
     }
     CK(cudaGetLastError());
-    CK(cudaMemsetAsync(ctx->u[ctx->cur], 0, ctx->node_bytes(), ctx->stream));
     ctx->launches++;
+    return PETTO_OK;
+}
+
+petto_status refine_correction(petto_ctx *ctx) {
+    petto_status st = refine_rhs(ctx);
+    if (st != PETTO_OK) return st;
+    CK(cudaMemsetAsync(ctx->u[ctx->cur], 0, ctx->node_bytes(), ctx->stream));
     return PETTO_OK;
 }
 
@@ -1361,6 +1375,49 @@ petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_sol
     }
     if (!std::isfinite(S.last)) return fail(ctx, PETTO_EDIVERGED, "residual not finite after PT fallback");
     if (o->mode == PETTO_SOLVE_TOL && !conv) return PETTO_ENOTCONV;
+    return PETTO_OK;
+}
+
+petto_status petto_sweep_rhs(petto_ctx *ctx, int kind, int64_t n, double a, double b, double s1, int local_dt,
+                             const double *r, int on_device, double *res_norm2) {
+    if (!ctx || n < 0 || !r || (kind != PETTO_SWEEP_APT && kind != PETTO_SWEEP_PT))
+        return fail(ctx, PETTO_EINVAL, "bad sweep arguments");
+    petto_status st = refine_alloc(ctx);
+    if (st != PETTO_OK) return st;
+    const int C = ctx->ndofc();
+    const int64_t nn = (int64_t)C * ctx->L.nnodes();
+    const double *src = r;
+    if (!on_device) {
+        st = ensure_stage(ctx, nn * sizeof(double));
+        if (st != PETTO_OK) return st;
+        CK(cudaMemcpyAsync(ctx->stage, r, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        src = static_cast<const double *>(ctx->stage);
+    }
+    pack_nodes<double, double><<<grid_of(nn), 256, 0, ctx->stream>>>(ctx->L, C, src, (double *)ctx->r64, 1);
+    CK(cudaGetLastError());
+    ctx->launches++;
+    const void *rhs = ctx->r64;
+    if (ctx->precision == PETTO_F32) {
+        st = refine_rhs(ctx);
+        if (st != PETTO_OK) return st;
+        rhs = ctx->rhs32;
+    }
+    SweepCtl sc;
+    sc.rhs = rhs;
+    for (int64_t t = 0; t < n; ++t) {
+        st = one_sweep(ctx, kind, a, b, s1, local_dt, res_norm2 && t == n - 1, sc);
+        if (st != PETTO_OK) return st;
+    }
+    if (res_norm2) {
+        if (n == 0) {
+            *res_norm2 = 0.0;
+            return PETTO_OK;
+        }
+        CK(cudaMemcpyAsync(res_norm2, ctx->scal + SC_RES, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    } else if (!on_device) {
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
     return PETTO_OK;
 }
 

@@ -263,6 +263,26 @@ class Problem:
                                       ctypes.byref(r) if want_res else None))
         return r.value if want_res else None
 
+    def sweep_rhs(self, kind: int, n: int, r, a: float = 0.0, b: float = 0.0, s1: float = 0.0,
+                  local_dt: bool = False, want_res: bool = True):
+        """n sweeps with the dense right-hand side r [C, nodes] (FP64, host array or CUDA
+        tensor) in place of the loads: the correction sweeps of the FP64 refinement."""
+        ptr, on_dev, keep = self._rhs_in(r)
+        res = ctypes.c_double(0.0)
+        self._ck(self.lib.petto_sweep_rhs(self.ctx, kind, int(n), float(a), float(b), float(s1),
+                                          int(bool(local_dt)), ptr, on_dev, ctypes.byref(res) if want_res else None))
+        del keep
+        return res.value if want_res else None
+
+    def _rhs_in(self, r):
+        if _is_cuda_tensor(r):
+            t = r.contiguous()
+            if t.dtype != _torch().float64:
+                raise TypeError("the right-hand side is FP64")
+            return ctypes.c_void_p(t.data_ptr()), 1, t
+        a = np.ascontiguousarray(np.asarray(r, dtype=np.float64).reshape(self.nrhs * self.ncomp, self.nnodes))
+        return a.ctypes.data_as(ctypes.c_void_p), 0, a
+
     def residual(self, with_field: bool = True, dtype=np.float64):
         r = ctypes.c_double(0.0)
         R = np.empty((self.nrhs * self.ncomp, self.nnodes), dtype=dtype) if with_field else None

@@ -483,6 +483,34 @@ def test_adaptive_momentum_solve_matches_oracle(P, dim):
     prob.close()
 
 
+@pytest.mark.parametrize("momentum,a,b,start", [(0, 1.3, 0.25, "zero"), (1, 1.0, 25.0, "zero"),
+                                                  (0, 0.9, 0.25, "nan"), (1, 1.0, 0.25, "nan")])
+def test_divergence_guard_matches_oracle(P, momentum, a, b, start):
+    """The solve's divergence guard on the GPU (host-side check of the device residual)
+    against the oracle's: an over-relaxed iteration (fixed a > 1, or a step far above the
+    stability bound) trips the guard at the same check (factor 10 fixed, 100 adaptive),
+    w is zeroed and PT carries on from the same u; a NaN in the start state zeroes u and w
+    at the first check.  Same sweep counts, same fall-back flag, same field (FP64)."""
+    spec = W.mbb_halfbeam(12, 6)
+    spec, prob, op, om, phi = _setup(P, spec, seed=25, precision="f64")
+    u0 = np.zeros((spec.ncomp, spec.nnodes))
+    if start == "nan":
+        u0[1, 40] = np.nan
+    prob.set_state(u0)
+    kw = dict(mode=1, a=a, b=b, s1=0.25, tol=1e-30, max_sweeps=90, check_every=6, local_dt=False,
+              momentum=momentum)
+    rep = prob.solve(refine=False, **kw)
+    u = nodes_to_oracle(u0)
+    ro = op.solve(om.modulus(phi), op.load_vector(), op.fixed_mask(), u, **kw)
+    assert ro["fell_back_to_pt"] and rep["fell_back_to_pt"]
+    for key in ("sweeps", "apt_sweeps", "pt_sweeps"):
+        assert rep[key] == ro[key], (key, rep[key], ro[key])
+    ug = prob.get_state()
+    assert np.all(np.isfinite(ug))
+    assert relmax(ug, oracle_to_nodes(u, spec.ncomp)) < 1e-10
+    prob.close()
+
+
 def test_paper_mode_fixed_counts(P):
     """Paper schedule (Sec. 3: n APT then n PT sweeps with the paper's global steps)."""
     spec = W.mbb_halfbeam(24, 8)

@@ -456,3 +456,156 @@ def test_design_loop_compliance_decreases():
         Cs.append(m["compliance"])
         assert abs(m["work"] - m["compliance"]) < 1e-8 * m["compliance"]
     assert Cs[-1] < Cs[0]
+
+
+def _neumann_mode(shape, ks):
+    """Eigenvector of the no-flux cell Laplacian (Sec. 2.4 boundary conditions): the tensor
+    product of cos(pi k (i + 1/2) / n) over the axes, with eigenvalue
+    -sum_a (2 - 2 cos(pi k_a / n_a))."""
+    v = np.ones(1)
+    lam = 0.0
+    for n, k in zip(shape, ks):
+        c = np.cos(math.pi * k * (np.arange(n) + 0.5) / n)
+        v = np.multiply.outer(c, v)          # slowest axis outermost: [k][j][i]
+        lam += 2.0 - 2.0 * math.cos(math.pi * k / n)
+    return v.reshape(-1), lam
+
+
+@pytest.mark.parametrize("dim,shape,modes", [
+    (2, (24, 16), [(1, 0), (3, 2), (7, 5), (0, 15)]),
+    (3, (10, 8, 6), [(1, 0, 0), (2, 3, 1), (5, 4, 3), (9, 7, 5)])])
+def test_cahn_hilliard_linear_growth_factor(dim, shape, modes):
+    """One explicit CH step (Sec. 2.4: mu = w'(phi) - gamma_g L phi, phi <- phi + tau L mu)
+    on phi = 1/2 + eps v_k, v_k an eigenvector of the no-flux Laplacian (L v_k = -lam_k v_k),
+    multiplies eps by exactly g_k = 1 - tau lam_k (w''(1/2) + gamma_g lam_k) up to O(eps^2)
+    relative, with w''(1/2) = -2 pi^2 / 64 for the paper's double well sin^2(pi phi)/64.
+    A wrong factor on gamma_g or tau, a sign slip in mu, or a mobility applied to the wrong
+    term changes g_k for some of these modes by far more than the tolerance."""
+    h_p = 1.0 / shape[1]
+    tau, gg = W.ch_params(h_p, dim)
+    p = O.OracleProblem(dim, *shape) if dim == 3 else O.OracleProblem(dim, shape[0], shape[1])
+    wpp = -2.0 * math.pi ** 2 / 64.0
+    eps = 1e-5
+    for ks in modes:
+        v, lam = _neumann_mode(shape, ks)
+        assert np.allclose(p.cell_laplacian(v), -lam * v, atol=1e-12)
+        phi = (0.5 + eps * v)[None, :].copy()
+        p.ch_step(phi, gg, tau)
+        g = 1.0 - tau * lam * (wpp + gg * lam)
+        m = np.abs(v) > 0.05
+        ratio = (phi[0, m] - 0.5) / (eps * v[m])
+        assert np.abs(ratio - g).max() < 1e-8 * max(1.0, abs(g)), (ks, g, ratio.min(), ratio.max())
+
+
+def test_ch_params_follow_the_paper_constants():
+    """The grid-unit Cahn-Hilliard constants restate the paper's (Sec. 3.1: dt3 = 500 dx^4,
+    gamma = 3e-5, D = 1): tau = D dt3 / h_p^2 = 500 h_p^2, gamma_g = gamma / h_p^2, unless tau
+    exceeds 0.9 x the explicit bound tau (w''_max lam_L + gamma_g lam_L^2) <= 2 (reading R10),
+    lam_L = 4 d the largest eigenvalue of the no-flux Laplacian's bound, w''_max = 2 pi^2/64."""
+    with open(os.path.join(GOLDEN, "paper_constants.json")) as f:
+        pc = json.load(f)["heat2d"]
+    dt3, gamma = pc["dt3_over_dx4"], pc["gamma"]
+    wpp_max = max(abs(O.double_well_deriv(x + 1e-6) - O.double_well_deriv(x - 1e-6)) / 2e-6
+                  for x in np.linspace(0, 1, 201))
+    assert abs(wpp_max - 2 * math.pi ** 2 / 64) < 1e-6
+    for dim in (2, 3):
+        for n in (8, 20, 64, 128, 512, 1024):
+            h_p = 1.0 / n
+            tau, gg = W.ch_params(h_p, dim)
+            assert gg == pytest.approx(gamma / h_p ** 2, rel=1e-15)
+            lam_l = 4.0 * dim
+            bound = 2.0 / (wpp_max * lam_l + gg * lam_l ** 2)
+            paper_tau = dt3 * h_p ** 4 / h_p ** 2
+            if paper_tau <= 0.9 * bound * (1 - 1e-9):
+                assert tau == pytest.approx(paper_tau, rel=1e-15)
+            else:
+                assert tau == pytest.approx(0.9 * bound, rel=1e-6)
+            # the explicit step is stable on the Laplacian's actual largest eigenvalue
+            assert tau * (wpp_max * lam_l + gg * lam_l ** 2) <= 1.8 + 1e-9
+    # the product tau gamma_g of the paper's constants is scale free (Sec. 3.1: 0.015)
+    tau, gg = W.ch_params(1.0 / 512, 2)
+    assert tau * gg == pytest.approx(dt3 * gamma, rel=1e-12)
+
+
+@pytest.mark.parametrize("dim,shape", [(2, (12, 6, 0)), (3, (6, 4, 3))])
+def test_local_step_params_are_inside_the_stability_bound(dim, shape):
+    """Local pseudo-time steps (reading R19) scale the step by 1/diag(K).  PT,
+    u <- u + s1 D^-1 R, is stable when s1 lam_max(D^-1 K) < 2; APT with momentum a when
+    b lam_max < 2 (1 + a).  With uniform moduli lam_max is near 2 (so b = 0.9 is stable even
+    at a = 0); for moduli drawn log-uniform in [1e-9, 1] cell by cell it reaches 2.2 (2D) and
+    2.4 (3D), still inside the PT bound for s1 = 0.75 and inside the APT bound from a = 1/4,
+    the adaptive schedule's momentum on the second sweep after a restart."""
+    a, b, s1 = W.local_step_params(64)
+    assert (b, s1) == (0.9, 0.75) and 0.0 < a < 1.0
+    p = O.OracleProblem(dim, *shape)
+
+    def lam_max(E):
+        K = p.assemble_K(E).toarray()
+        d = np.diag(K)
+        lam = np.linalg.eigvals(K / d[:, None]).real.max()
+        assert lam <= (np.abs(K).sum(axis=1) / d).max() + 1e-9   # Gershgorin
+        return lam
+
+    lam = lam_max(np.ones(p.ncells))
+    assert 2.0 <= lam < 2.1 and b * lam < 2.0
+    rng = np.random.default_rng(11)
+    for trial in range(3):
+        lam = lam_max(10.0 ** rng.uniform(-9, 0, p.ncells))
+        assert s1 * lam < 2.0 and b * lam < 2.0 * (1.0 + 0.25), lam
+
+
+def _guard_setup():
+    spec = W.mbb_halfbeam(12, 6)
+    p, mat = oracle_problem(spec), oracle_materials(spec)
+    return p, mat.modulus(spec.phi0), p.load_vector(), p.fixed_mask()
+
+
+@pytest.mark.parametrize("momentum,a,b,factor", [(0, 1.3, 0.25, 10.0), (1, 1.0, 25.0, 100.0)])
+def test_solve_guard_switches_to_pt_above_the_guard_factor(momentum, a, b, factor):
+    """Divergence guard of the tolerance-mode solve: the first check whose residual exceeds
+    factor x the best earlier check (10 with fixed damping, 100 with adaptive-restart
+    momentum) zeroes w and switches to PT for the rest of the solve; u carries on from the
+    state it reached.  Established from fresh solves cut at successive checks (each reports
+    its last checked residual), then continued against plain PT sweeps."""
+    p, E, F, fixed = _guard_setup()
+    ce = 5
+    kw = dict(mode=1, a=a, b=b, s1=0.25, tol=1e-30, check_every=ce, local_dt=False, momentum=momentum)
+    res, fell, states = [], [], []
+    for m in range(1, 13):
+        u = np.zeros(p.ndof)
+        rep = p.solve(E, F, fixed, u, max_sweeps=m * ce, **kw)
+        res.append(rep["res_norm"])
+        fell.append(rep["fell_back_to_pt"])
+        states.append(u)
+        if rep["fell_back_to_pt"]:
+            break
+    assert fell[-1], "the over-relaxed iteration must trip the guard"
+    ms = len(res)
+    for m in range(1, ms - 1):
+        assert res[m] <= factor * min(res[:m])
+    assert res[ms - 1] > factor * min(res[:ms - 1])
+    q = 7
+    u = np.zeros(p.ndof)
+    rep = p.solve(E, F, fixed, u, max_sweeps=ms * ce + q, **kw)
+    assert rep["fell_back_to_pt"] and rep["apt_sweeps"] == ms * ce and rep["pt_sweeps"] == q
+    ref = states[-1].copy()
+    for _ in range(q):
+        p.pt_sweep(E, F, fixed, 0.25, ref)
+    assert np.array_equal(u, ref)
+
+
+@pytest.mark.parametrize("momentum", [0, 1])
+def test_solve_guard_resets_a_non_finite_state(momentum):
+    """A non-finite check residual zeroes u and w and switches to PT: from a state holding a
+    NaN, the solve ends exactly where PT sweeps from zero end."""
+    p, E, F, fixed = _guard_setup()
+    ce, q = 4, 9
+    u = np.zeros(p.ndof)
+    u[np.flatnonzero(fixed == 0)[5]] = np.nan
+    rep = p.solve(E, F, fixed, u, mode=1, a=0.9, b=0.25, s1=0.25, tol=1e-30, max_sweeps=ce + q, check_every=ce,
+                  local_dt=False, momentum=momentum)
+    assert rep["fell_back_to_pt"] and rep["apt_sweeps"] == ce and rep["pt_sweeps"] == q
+    ref = np.zeros(p.ndof)
+    for _ in range(q):
+        p.pt_sweep(E, F, fixed, 0.25, ref)
+    assert np.all(np.isfinite(u)) and np.array_equal(u, ref)
