@@ -224,6 +224,16 @@ petto_status petto_sweep(petto_ctx *ctx, int kind, int64_t n, double a, double b
 petto_status petto_sweep_rhs(petto_ctx *ctx, int kind, int64_t n, double a, double b, double s1, int local_dt,
                              const double *r, int on_device, double *res_norm2);
 
+/* Attempts of each bounded wait of the TMA marching sweeps for their ring copies (default
+ * and maximum 16384, each attempt suspending the thread for at most 100 us; tries < 0
+ * restores the default).  When a sweep's wait runs out, its CTAs let the copies already in
+ * flight land (always with the default bound), record the time-out and return, and the
+ * next residual check of a solve returns PETTO_ETIMEOUT; the next petto_pt_solve starts
+ * afresh.  With 0 every such wait runs out at once: the way to exercise that path (no
+ * counterpart in the paper; failure handling of this implementation).  PETTO_EINVAL above
+ * the default. */
+petto_status petto_set_wait_limit(petto_ctx *ctx, int tries);
+
 /* R = F - K u on free DOFs (0 on supports) for the current state; R [C][nodes] may be
  * NULL; res_norm2 (may be NULL) receives sum R^2. */
 petto_status petto_residual(petto_ctx *ctx, double *res_norm2, void *R, int dtype, int on_device);
@@ -406,11 +416,13 @@ petto_status petto_batch_profile_read(petto_batch *b, double *sweep_ms, int64_t 
  *   norm2  host double receiving the result; the call returns after it is written
  *   stream cudaStream_t to run on (NULL = legacy default stream)
  * It calls no cudaMalloc, cudaFree or other allocating routine.  The first call on a
- * device looks up the device address of the scratch array (cudaGetSymbolAddress), so make
- * that first call before any stream capture.  Every call clears the ticket counter of the
- * reduction before launching.  All calls share the one scratch array: calls that overlap
- * on the GPU (different streams, or different host threads on one device) race and must
- * be serialised by the caller. */
+ * device looks up the device address of the scratch array (cudaGetSymbolAddress) and keeps
+ * it for that device, so make that first call before any stream capture; the kept address
+ * belongs to the device context of that call, so do not call again after a
+ * cudaDeviceReset of the device.  Each call waits on its stream for its result before it
+ * returns.  Every call clears the ticket counter of the reduction before launching.  All
+ * calls share the one scratch array: calls that overlap on the GPU (different streams, or
+ * different host threads on one device) race and must be serialised by the caller. */
 petto_status petto_residual_norm_static(const petto_grid *grid, double nu, const float *u, const float *E,
                                         const float *F, const uint8_t *fixed, double *norm2, void *stream);
 

@@ -34,15 +34,31 @@ SIMP_MODIFIED, SIMP_PAPER = 0, 1
 PROJECTED, PENALTY = 0, 1
 
 
+_SO_OMP = os.path.join(_BUILD, "liboracle_omp.so")
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with the host C compiler (plain C99, -O2, no fast-math)."""
+    """Compile the oracle with the host C compiler (plain C99, -O2, no fast-math), and the
+    same source with OpenMP for the all-core CPU baseline (skipped when the compiler has no
+    OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu99", "-fPIC", "-shared", "-fno-fast-math",
-                               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
-        os.replace(tmp, _SO)
+    flags = ["-O2", "-std=gnu99", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off"]
+    for so, extra in ((_SO, []), (_SO_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+            tmp = so + f".{os.getpid()}.tmp"
+            try:
+                subprocess.check_call(["gcc", *flags, *extra, _SRC, "-o", tmp, "-lm"])
+            except (subprocess.CalledProcessError, OSError):
+                if so == _SO:
+                    raise
+                continue
+            os.replace(tmp, so)
     return _SO
+
+
+def openmp_available() -> bool:
+    build()
+    return os.path.exists(_SO_OMP)
 
 
 class _Grid(ctypes.Structure):
@@ -56,11 +72,20 @@ _I = ctypes.c_int
 _L = ctypes.c_int64
 
 
-def _load():
-    global _lib
+_lib_omp = None
+
+
+def _load(openmp: bool = False):
+    """The oracle library; openmp=True: its OpenMP build (all-core CPU baseline only)."""
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            lib = ctypes.CDLL(build())
+        if (_lib_omp if openmp else _lib) is None:
+            path = build()
+            if openmp:
+                if not os.path.exists(_SO_OMP):
+                    raise RuntimeError("the oracle's OpenMP build is not available")
+                path = _SO_OMP
+            lib = ctypes.CDLL(path)
             g = ctypes.POINTER(_Grid)
             sig = {
                 "or_ncomp": (_I, [g]), "or_nnodes": (_L, [g]), "or_ncells": (_L, [g]), "or_ndof": (_L, [g]),
@@ -85,8 +110,11 @@ def _load():
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
-            _lib = lib
-    return _lib
+            if openmp:
+                _lib_omp = lib
+            else:
+                _lib = lib
+    return _lib_omp if openmp else _lib
 
 
 def _ptr(a: np.ndarray):
@@ -117,6 +145,7 @@ class OracleProblem:
     loads: list = field(default_factory=list)
     body_source: float = 0.0
     boxes: list = field(default_factory=list)
+    openmp: bool = False  # run on the OpenMP build (the all-core CPU baseline only)
 
     def __post_init__(self):
         if self.dim == 2:
@@ -168,20 +197,20 @@ class OracleProblem:
             F[self.node_id(*node) * self.ncomp + comp] += val
         if self.body_source != 0.0:
             assert self.ncomp == 1, "a body source is a scalar heat source (Sec. 2.2)"
-            _load().or_body_load(ctypes.byref(self._g), float(self.body_source), _ptr(F))
+            _load(self.openmp).or_body_load(ctypes.byref(self._g), float(self.body_source), _ptr(F))
         return F
 
     # operator ---------------------------------------------------------------
     def apply_K(self, E, u) -> np.ndarray:
         E, u = _f64(E), _f64(u)
         out = np.empty(self.ndof)
-        _load().or_apply_K(ctypes.byref(self._g), _ptr(E), _ptr(u), _ptr(out))
+        _load(self.openmp).or_apply_K(ctypes.byref(self._g), _ptr(E), _ptr(u), _ptr(out))
         return out
 
     def cell_energy(self, u) -> np.ndarray:
         u = _f64(u)
         e = np.empty(self.ncells)
-        _load().or_cell_energy(ctypes.byref(self._g), _ptr(u), _ptr(e))
+        _load(self.openmp).or_cell_energy(ctypes.byref(self._g), _ptr(u), _ptr(e))
         return e
 
     def assemble_K(self, E):
@@ -193,13 +222,13 @@ class OracleProblem:
         rows = np.empty(nt, dtype=np.int64)
         cols = np.empty(nt, dtype=np.int64)
         vals = np.empty(nt)
-        _load().or_assemble_K(ctypes.byref(self._g), _ptr(E), _ptr(rows), _ptr(cols), _ptr(vals))
+        _load(self.openmp).or_assemble_K(ctypes.byref(self._g), _ptr(E), _ptr(rows), _ptr(cols), _ptr(vals))
         return sp.csr_matrix((vals, (rows, cols)), shape=(self.ndof, self.ndof))
 
     def residual(self, E, F, fixed, u):
         E, F, u = _f64(E), _f64(F), _f64(u)
         R = np.empty(self.ndof)
-        r2 = _load().or_residual(ctypes.byref(self._g), _ptr(E), _ptr(F), _ptr(fixed), _ptr(u), _ptr(R))
+        r2 = _load(self.openmp).or_residual(ctypes.byref(self._g), _ptr(E), _ptr(F), _ptr(fixed), _ptr(u), _ptr(R))
         return R, r2
 
     def direct_solve(self, E, F, fixed) -> np.ndarray:
@@ -214,7 +243,7 @@ class OracleProblem:
     def diag_K(self, E) -> np.ndarray:
         E = _f64(E)
         out = np.empty(self.ndof)
-        _load().or_diag_K(ctypes.byref(self._g), _ptr(E), _ptr(out))
+        _load(self.openmp).or_diag_K(ctypes.byref(self._g), _ptr(E), _ptr(out))
         return out
 
     # sweeps -----------------------------------------------------------------
@@ -235,7 +264,7 @@ class OracleProblem:
         E, F = _f64(E), _f64(F)
         R = np.empty(self.ndof)
         dinv = self._dinv(E, local_dt) if dinv is None or not local_dt else _f64(dinv)
-        return _load().or_pt_sweep(ctypes.byref(self._g), _ptr(E), _ptr(F), _ptr(fixed), float(s1),
+        return _load(self.openmp).or_pt_sweep(ctypes.byref(self._g), _ptr(E), _ptr(F), _ptr(fixed), float(s1),
                                    None if dinv is None else _ptr(dinv), _ptr(u), _ptr(R))
 
     def apt_sweep(self, E, F, fixed, a, b, u, w, local_dt=False, dinv=None) -> float:
@@ -243,7 +272,7 @@ class OracleProblem:
         E, F = _f64(E), _f64(F)
         R = np.empty(self.ndof)
         dinv = self._dinv(E, local_dt) if dinv is None or not local_dt else _f64(dinv)
-        return _load().or_apt_sweep(ctypes.byref(self._g), _ptr(E), _ptr(F), _ptr(fixed), float(a), float(b),
+        return _load(self.openmp).or_apt_sweep(ctypes.byref(self._g), _ptr(E), _ptr(F), _ptr(fixed), float(a), float(b),
                                     None if dinv is None else _ptr(dinv), _ptr(u), _ptr(w), _ptr(R), None)
 
     def solve(self, E, F, fixed, u, *, mode=1, n_apt=0, n_pt=0, a=0.9, b=0.25, s1=0.25, tol=1e-8,
@@ -253,7 +282,7 @@ class OracleProblem:
         E, F = _f64(E), _f64(F)
         w = np.zeros(self.ndof)
         rep = np.zeros(8)
-        _load().or_solve(ctypes.byref(self._g), _ptr(E), _ptr(F), _ptr(fixed), int(mode), int(n_apt), int(n_pt),
+        _load(self.openmp).or_solve(ctypes.byref(self._g), _ptr(E), _ptr(F), _ptr(fixed), int(mode), int(n_apt), int(n_pt),
                          float(a), float(b), float(s1), float(tol), int(max_sweeps), int(check_every),
                          int(bool(local_dt)), int(momentum), _ptr(u), _ptr(w), _ptr(rep))
         return {"sweeps": int(rep[0]), "apt_sweeps": int(rep[1]), "pt_sweeps": int(rep[2]),
@@ -264,13 +293,13 @@ class OracleProblem:
     def cell_laplacian(self, v) -> np.ndarray:
         v = _f64(v)
         out = np.empty(self.ncells)
-        _load().or_cell_laplacian(ctypes.byref(self._g), _ptr(v), _ptr(out))
+        _load(self.openmp).or_cell_laplacian(ctypes.byref(self._g), _ptr(v), _ptr(out))
         return out
 
     def ch_step(self, phi, gamma_g, tau) -> None:
         """In place on phi [P, cells] (Sec. 2.4, forward Euler)."""
         P = phi.shape[0] if phi.ndim == 2 else 1
-        _load().or_ch_step(ctypes.byref(self._g), int(P), float(gamma_g), float(tau), _ptr(phi))
+        _load(self.openmp).or_ch_step(ctypes.byref(self._g), int(P), float(gamma_g), float(tau), _ptr(phi))
 
 
 @dataclass

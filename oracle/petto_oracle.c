@@ -2,7 +2,8 @@
  * petto_oracle.c -- plain, slow, FP64 CPU oracle of the PeTTO hot path.
  *
  * TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the CPU-baseline
- * leg of the benchmark may load this code.  The GPU product path never links it,
+ * leg of the benchmark may load this code.  It is compiled twice: plainly (the oracle
+ * the tests hold the GPU against) and with OpenMP (the all-core CPU baseline only).  The GPU product path never links it,
  * shares no source, header, table or helper with it, and does not fall back to it.
  *
  * What it computes (paper: "PeTTO", arXiv 2509.06971):
@@ -145,14 +146,12 @@ static void cell_nodes(const or_grid *g, int64_t c, int64_t *nodes) {
         nodes[q] = node_id(g, i + (q & 1), j + ((q >> 1) & 1), g->dim == 3 ? k + ((q >> 2) & 1) : 0);
 }
 
-/* Ku = K(E) u by a cell loop that scatters element forces. */
-void or_apply_K(const or_grid *g, const double *E, const double *u, double *Ku) {
+/* Forces of cells [c0, c1) scattered into Ku. */
+static void scatter_cells(const or_grid *g, const double *E, const double *u, double *Ku, int64_t c0, int64_t c1) {
     const int nc = or_ncomp(g), nq = 1 << g->dim;
-    const int64_t ncell = or_ncells(g);
-    memset(Ku, 0, sizeof(double) * (size_t)or_ndof(g));
     double ul[24], fl[24];
     int64_t nodes[8];
-    for (int64_t c = 0; c < ncell; ++c) {
+    for (int64_t c = c0; c < c1; ++c) {
         cell_nodes(g, c, nodes);
         for (int q = 0; q < nq; ++q)
             for (int a = 0; a < nc; ++a) ul[q * nc + a] = u[nodes[q] * nc + a];
@@ -160,6 +159,26 @@ void or_apply_K(const or_grid *g, const double *E, const double *u, double *Ku) 
         for (int q = 0; q < nq; ++q)
             for (int a = 0; a < nc; ++a) Ku[nodes[q] * nc + a] += fl[q * nc + a];
     }
+}
+
+/* Ku = K(E) u by a cell loop that scatters element forces. */
+void or_apply_K(const or_grid *g, const double *E, const double *u, double *Ku) {
+    const int64_t ncell = or_ncells(g);
+    memset(Ku, 0, sizeof(double) * (size_t)or_ndof(g));
+#ifdef _OPENMP
+    /* OpenMP build, used only to time the CPU baseline on all host cores: the cells of one
+     * layer (a row in 2D, a z layer in 3D) touch two node layers, so layers of one parity
+     * touch disjoint nodes and scatter in parallel, even layers first.  The sum at a node
+     * then runs in another order than the serial loop's (the results agree to rounding). */
+    const int nl = g->dim == 3 ? g->nz : g->ny;
+    const int64_t per = ncell / nl;
+    for (int par = 0; par < 2; ++par) {
+#pragma omp parallel for schedule(static)
+        for (int l = par; l < nl; l += 2) scatter_cells(g, E, u, Ku, (int64_t)l * per, (int64_t)(l + 1) * per);
+    }
+#else
+    scatter_cells(g, E, u, Ku, 0, ncell);
+#endif
 }
 
 /* Unit-modulus cell energies e_c = sum_q (h^d/2^d) eps_q:C0:eps_q, so that the
@@ -238,6 +257,9 @@ double or_residual(const or_grid *g, const double *E, const double *F, const uin
     const int64_t nd = or_ndof(g);
     or_apply_K(g, E, u, R);
     double s = 0.0;
+#ifdef _OPENMP
+#pragma omp parallel for reduction(+ : s) schedule(static)
+#endif
     for (int64_t r = 0; r < nd; ++r) {
         R[r] = fixed[r] ? 0.0 : F[r] - R[r];
         s += R[r] * R[r];
@@ -253,6 +275,9 @@ double or_pt_sweep(const or_grid *g, const double *E, const double *F, const uin
                    double s1, const double *dinv, double *u, double *Rwork) {
     const int64_t nd = or_ndof(g);
     double s = or_residual(g, E, F, fixed, u, Rwork);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int64_t r = 0; r < nd; ++r)
         u[r] = fixed[r] ? 0.0 : u[r] + s1 * (dinv ? dinv[r] : 1.0) * Rwork[r];
     return s;
@@ -271,9 +296,15 @@ double or_apt_sweep(const or_grid *g, const double *E, const double *F, const ui
     double s = or_residual(g, E, F, fixed, u, Rwork);
     if (dot) {
         double d = 0.0;
+#ifdef _OPENMP
+#pragma omp parallel for reduction(+ : d) schedule(static)
+#endif
         for (int64_t r = 0; r < nd; ++r) d += Rwork[r] * w[r];
         *dot = d;
     }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int64_t r = 0; r < nd; ++r) {
         if (fixed[r]) {
             w[r] = 0.0;

@@ -82,6 +82,7 @@ _SIGS = {
     "petto_get_state": (_int, [_vp, _vp, _vp, _int, _int]),
     "petto_get_modulus": (_int, [_vp, _vp, _int, _int]),
     "petto_sweep": (_int, [_vp, _int, _i64, _dbl, _dbl, _dbl, _int, _P(_dbl)]),
+    "petto_set_wait_limit": (_int, [_vp, _int]),
     "petto_sweep_rhs": (_int, [_vp, _int, _i64, _dbl, _dbl, _dbl, _int, _vp, _int, _P(_dbl)]),
     "petto_residual": (_int, [_vp, _P(_dbl), _vp, _int, _int]),
     "petto_pt_solve": (_int, [_vp, _P(petto_solve_opts), _P(petto_solve_report)]),

@@ -75,6 +75,7 @@ struct petto_ctx {
     };
     std::vector<GraphEntry> graphs;
     bool trace = false;  // PETTO_TRACE set: print every check residual to stderr
+    int wait_tries = WAIT_TRIES;  // attempts of each bounded ring wait of the TMA sweeps
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
     std::vector<int> ev_count;  // sweeps covered by each pending event pair
@@ -343,6 +344,7 @@ SweepArgs base_sweep_args(petto_ctx *ctx) {
     a.rhs = nullptr;
     a.zlo = ctx->own_n ? ctx->own_lo : 0;
     a.zhi = ctx->own_n ? ctx->own_lo + ctx->own_n - 1 : ctx->L.NZ - 1;
+    a.wait_tries = ctx->wait_tries;
     const OpConst &k = ctx->k;
     a.kf = OpConstF{(float)k.ce_par, (float)k.ce_perp, (float)k.cf_lam, (float)k.cf_mu, (float)k.cdiag, (float)k.ct,
                     (float)k.src, 0.f, 0.f, 0.f};
@@ -462,7 +464,7 @@ Tiling own_planes(const petto_ctx *ctx, Tiling t) {
     t.zlo = ctx->own_lo;
     t.zn = ctx->own_n;
     t.zb = t.zlo;
-    if (t.kind == 4) {
+    if (two_row_kind(t.kind)) {
         // marching segments start on even planes of the whole grid, as the whole grid's do
         // (its segment length is even), so every plane is computed as it is there
         if ((t.zlo + ctx->own_z0) & 1) t.zb = std::max(t.zlo - 1, 0);
@@ -477,7 +479,7 @@ Tiling own_planes(const petto_ctx *ctx, Tiling t) {
 }
 
 petto_status set_tiling(petto_ctx *ctx, const Tiling &t0) {
-    if (ctx->own_n && t0.kind != 0 && t0.kind != 4)
+    if (ctx->own_n && t0.kind != 0 && !two_row_kind(t0.kind))
         return fail(ctx, PETTO_EUNSUPPORTED, "a slab context sweeps with the node-gather or two-row marching kernel");
     const Tiling t = own_planes(ctx, t0);
     const int NX = ctx->L.NX, NY = ctx->L.NY;
@@ -519,7 +521,7 @@ petto_status set_tiling(petto_ctx *ctx, const Tiling &t0) {
     }
     CK(cudaMemcpy(ctx->tile_ptr, tptr.data(), sizeof(int) * (nt + 1), cudaMemcpyHostToDevice));
     if (!ent.empty()) CK(cudaMemcpy(ctx->loads, ent.data(), sizeof(LoadEntry) * ent.size(), cudaMemcpyHostToDevice));
-    if (t.kind >= 2 && t.kind <= 4) {
+    if ((t.kind >= 2 && t.kind <= 4) || t.kind == 6) {
         const int ty = t.kind == 2 ? 8 : 16;
         if (!make_tma_maps(ctx->L, ty, ctx->ndofc(), ctx->u[0], ctx->u[1], ctx->w, ctx->E, ctx->tma))
             return fail(ctx, PETTO_ECUDA, "tensor map creation failed");
@@ -826,8 +828,8 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
         petto_destroy(ctx);
         return PETTO_ECUDA;
     }
-    if (ctx->tiling.kind == 2 || ctx->tiling.kind == 3 || ctx->tiling.kind == 4) {
-        const int ty = ctx->tiling.kind == 3 || ctx->tiling.kind == 4 ? 16 : 8;
+    if (ctx->tiling.kind == 2 || ctx->tiling.kind == 3 || two_row_kind(ctx->tiling.kind)) {
+        const int ty = ctx->tiling.kind == 2 ? 8 : 16;
         if (!make_tma_maps(ctx->L, ty, ctx->ndofc(), ctx->u[0], ctx->u[1], ctx->w, ctx->E, ctx->tma)) {
             if (ctx->tiling.kind == 2) {
                 march3d_tiling(ctx->L, ctx->tiling);  // same tile shape, register-staged kernel
@@ -1178,7 +1180,7 @@ petto_status refine_defect(petto_ctx *ctx, double *norm) {
 // r64 -> the right-hand side the sweep kernel reads (FP16 scaled or FP32, in rhs32)
 petto_status refine_rhs(petto_ctx *ctx) {
     const int64_t nel = (int64_t)ctx->ndofc() * ctx->L.cstride;
-    ctx->rhs_half = ctx->tiling.kind == 4;
+    ctx->rhs_half = two_row_kind(ctx->tiling.kind);
     if (ctx->rhs_half) {
         CK(cudaMemsetAsync(ctx->ctrl + CT_RMAX, 0, sizeof(double), ctx->stream));
         abs_max_f64<<<grid_of(nel), 256, 0, ctx->stream>>>(nel, (const double *)ctx->r64, ctx->ctrl + CT_RMAX);
@@ -1313,6 +1315,7 @@ petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_sol
     if (o->momentum < 0 || o->momentum > 2) return fail(ctx, PETTO_EINVAL, "momentum is 0, 1 or 2");
     CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
     petto_status st = set_ctrl(ctx, CT_RESTART_AT, 0);
+    if (st == PETTO_OK) st = set_ctrl(ctx, CT_ERR, 0);  // a new solve: no wait has run out yet
     if (st != PETTO_OK) return st;
     SolveState S;
     S.use_pt = o->momentum == 2;  // the plain first-order method throughout
@@ -1375,6 +1378,13 @@ petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_sol
     }
     if (!std::isfinite(S.last)) return fail(ctx, PETTO_EDIVERGED, "residual not finite after PT fallback");
     if (o->mode == PETTO_SOLVE_TOL && !conv) return PETTO_ENOTCONV;
+    return PETTO_OK;
+}
+
+petto_status petto_set_wait_limit(petto_ctx *ctx, int tries) {
+    if (!ctx || tries > WAIT_TRIES) return fail(ctx, PETTO_EINVAL, "wait limit above the default");
+    ctx->wait_tries = tries < 0 ? WAIT_TRIES : tries;
+    clear_graphs(ctx);  // captured sweeps carry the limit in their arguments
     return PETTO_OK;
 }
 
@@ -1528,7 +1538,7 @@ petto_status petto_set_owned_planes(petto_ctx *ctx, int64_t zlo, int64_t zhi, in
     ctx->own_z0 = z_global;
     const bool whole = zlo == 0 && zhi == NZ - 1;
     Tiling t = ctx->tiling;
-    if (!whole && t.kind != 0 && t.kind != 4) {
+    if (!whole && t.kind != 0 && !two_row_kind(t.kind)) {
         // another marching variant is selected: a slab sweeps with the node gather instead
         t = gather_tiling(ctx->L);
     }
@@ -2273,7 +2283,7 @@ std::vector<std::pair<std::string, Tiling>> kernel_candidates_all(const petto_ct
 std::vector<std::pair<std::string, Tiling>> kernel_candidates(const petto_ctx *ctx) {
     std::vector<std::pair<std::string, Tiling>> all = kernel_candidates_all(ctx), cand;
     for (auto &c : all)
-        if (!ctx->own_n || c.second.kind == 0 || c.second.kind == 4) cand.push_back(c);
+        if (!ctx->own_n || c.second.kind == 0 || two_row_kind(c.second.kind)) cand.push_back(c);
     return cand;
 }
 
@@ -2300,6 +2310,8 @@ std::vector<std::pair<std::string, Tiling>> kernel_candidates_all(const petto_ct
             }
             march3d_tma_tiling(L, 16, t);
             cand.emplace_back("tma16/zs" + std::to_string(t.zs), t);
+            march3d_tma3_tiling(L, t);
+            cand.emplace_back("tma3/zs" + std::to_string(t.zs), t);
         }
         if (ctx->nrhs == 1) {
             march3d_tiling(L, t);
@@ -2357,7 +2369,7 @@ petto_status petto_kernel_info(petto_ctx *ctx, char *name, int name_len, int *rh
         name[name_len - 1] = 0;
     }
     // refinement sweeps of the two-row 3D marching kernel read an FP16 right-hand side
-    if (rhs_bytes) *rhs_bytes = t.kind == 4 ? 2 : (ctx->precision == PETTO_F32 ? 4 : 8);
+    if (rhs_bytes) *rhs_bytes = two_row_kind(t.kind) ? 2 : (ctx->precision == PETTO_F32 ? 4 : 8);
     return PETTO_OK;
 }
 

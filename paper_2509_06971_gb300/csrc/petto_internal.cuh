@@ -84,6 +84,7 @@ constexpr int CT_BASE = 3;        // (int64) index of the first sweep of a graph
 constexpr int CT_RMAX = 4;        // max |r| of the refinement defect (scaling of its FP16 copy)
 constexpr int CT_RSCALE = 5;      // 2^-k: the FP16 right-hand side holds r 2^k
 constexpr int CT_N = 8;
+constexpr int WAIT_TRIES = 1 << 14;  // default attempts of a bounded ring wait (about 1.6 s at most)
 
 // FP32 copies of the constants, converted once on the host (a double-to-float conversion
 // in a kernel runs on the narrow FP64 pipe of GB300).
@@ -124,6 +125,7 @@ struct SweepArgs {
     const LoadEntry *loads;
     double *res2;             // receives sum R^2 (if want_res)
     RedBuf red;
+    int wait_tries = WAIT_TRIES;  // TMA marching kernels: attempts of each bounded ring wait
 };
 
 // ---------------------------------------------------------------- batches
@@ -289,13 +291,16 @@ struct Tiling {
     int gx, gy, gz;    // tiles per axis
     int ox, oy;        // output nodes per tile in x, y (== bx, by for gather kernels)
     int kind;          // 0 gather, 1 3D z-marching (register-staged), 2/3 3D TMA one row per
-                       // thread (32x8 / 32x16), 4 3D TMA two rows per thread, 5 2D y-marching
+                       // thread (32x8 / 32x16), 4 3D TMA two rows per thread, 5 2D y-marching,
+                       // 6 3D TMA two rows per thread, lean per-plane path
     int ly;            // kind 5: output rows per warp (a block's warps take consecutive segments)
     int zlo, zn;       // 3D: output node planes [zlo, zlo + zn) (zn = 0: all planes, zlo = 0)
     int zb;            // first plane of the first z tile / segment (<= zlo)
+    int order;         // 0: tiles numbered x fastest; 1: z fastest (tile column by column)
     // tile of node (i, j, k), or -1 for a node outside the output planes
     __host__ int tile_of(int i, int j, int k) const {
         if (zn && (k < zlo || k >= zlo + zn)) return -1;
+        if (order) return ((i / ox) + gx * (j / oy)) * gz + (k - zb) / zs;
         return (i / ox) + gx * ((j / oy) + gy * ((k - zb) / zs));
     }
     int ntiles() const { return gx * gy * gz; }
@@ -332,6 +337,11 @@ void march3d_tma2_tiling(const Layout &L, Tiling &t);
 cudaError_t march3d_prepare();
 cudaError_t launch_march3d_tma2(const SweepArgs &a, const Tiling &t, const TmaMaps &m, cudaStream_t s);
 cudaError_t launch_march3d_tma(const SweepArgs &a, const Tiling &t, const TmaMaps &m, cudaStream_t s);
+void march3d_tma3_tiling(const Layout &L, Tiling &t);
+cudaError_t launch_march3d_tma3(const SweepArgs &a, const Tiling &t, const TmaMaps &m, cudaStream_t s);
+// the two-row marching kernels (kinds 4 and 6): one tiling, one set of tensor maps, FP16
+// refinement right-hand side, slabs of a decomposed grid
+inline bool two_row_kind(int kind) { return kind == 4 || kind == 6; }
 bool make_tma_maps(const Layout &L, int ty, int ncomp, void *u0, void *u1, void *w, const void *E, TmaMaps &m);
 
 cudaError_t launch_sweep(const SweepArgs &a, const Tiling &t, int precision, cudaStream_t s,

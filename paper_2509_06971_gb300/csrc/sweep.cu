@@ -811,9 +811,9 @@ Tiling choose_tiling(const Layout &L, int physics, int precision, int nrhs) {
         L.estride < (int64_t(1) << 31))
         return march2d_tiling(L);
     if (L.dim == 3 && physics == 0 && precision == 0) {
-        // z-marching kernel: TMA-staged with two owner rows per thread by default;
-        // PETTO_MARCH=tma8 / tma16 select one row per thread (32x8 / 32x16 tiles),
-        // PETTO_MARCH=v1 the register-staged kernel
+        // z-marching kernel: TMA-staged with two owner rows per thread, lean per-plane path,
+        // by default; PETTO_MARCH=tma2 selects the two-row kernel it was derived from,
+        // tma8 / tma16 one row per thread (32x8 / 32x16 tiles), v1 the register-staged kernel
         Tiling t{};
         const char *env = std::getenv("PETTO_MARCH");
         // the TMA kernel addresses a node column with 32-bit offsets
@@ -823,7 +823,8 @@ Tiling choose_tiling(const Layout &L, int physics, int precision, int nrhs) {
         }
         else if (env && std::strcmp(env, "tma8") == 0) march3d_tma_tiling(L, 8, t);
         else if (env && std::strcmp(env, "tma16") == 0) march3d_tma_tiling(L, 16, t);
-        else march3d_tma2_tiling(L, t);
+        else if (env && std::strcmp(env, "tma2") == 0) march3d_tma2_tiling(L, t);
+        else march3d_tma3_tiling(L, t);
         return t;
     }
     return gather_tiling(L);
@@ -857,6 +858,10 @@ cudaError_t launch_sweep(const SweepArgs &a0, const Tiling &t, int precision, cu
     if (t.kind == 4) {
         if (!maps || !maps->valid) return cudaErrorInvalidValue;
         return launch_march3d_tma2(a, t, *maps, s);
+    }
+    if (t.kind == 6) {
+        if (!maps || !maps->valid) return cudaErrorInvalidValue;
+        return launch_march3d_tma3(a, t, *maps, s);
     }
     if (t.kind == 5) {
         a.zseg = t.ly;

@@ -336,6 +336,7 @@ int choose_zseg(int NZ, int columns, int resident) {
 }
 
 void march3d_tiling(const Layout &L, Tiling &t) {
+    t.order = 0;
     t.bx = MX;
     t.by = MTY;
     t.ox = MX - 1;
@@ -372,7 +373,7 @@ constexpr int TBW = 36;        // box width (floats): covers the 33 tile columns
 constexpr int TNS = 4;         // ring slots
 constexpr int TD = 2;          // planes in flight ahead of the consumer (the slot of the plane
                                // being updated must survive the refill issued in its iteration)
-constexpr int TWAIT = 1 << 14; // try_wait attempts before a wait is declared timed out
+constexpr int TWAIT = WAIT_TRIES;  // try_wait attempts before a wait is declared timed out
 constexpr int RBW = 40;        // FP16 box width (halves): 33 tile columns at any offset 0..7
 constexpr unsigned TSUSPEND = 100000;  // ns a waiting thread may stay suspended per attempt
                                        // (woken early when the phase completes): <= ~1.6 s in all
@@ -398,8 +399,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < TWAIT; ++it) {
+// Bounded wait for the phase of the given parity: at most `tries` attempts (each may
+// suspend the thread for up to TSUSPEND ns); false when they ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int tries = TWAIT) {
+    for (int it = 0; it < tries; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -465,7 +468,7 @@ __device__ __forceinline__ bool march_plane(const SweepArgs &A, const MarchConst
         wv1 = w0[G::WY * TBW];
         wv2 = w0[2 * G::WY * TBW];
     }
-    if (!mbar_wait(smem_u32(&bars[slot]), (r1 / TNS) & 1)) bad = true;
+    if (!mbar_wait(smem_u32(&bars[slot]), (r1 / TNS) & 1, A.wait_tries)) bad = true;
     {
         const float *r0 = su + slot * (G::USLOT / 4) + ty * TBW + xoff + tx;
 #pragma unroll
@@ -682,7 +685,7 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __gr
         for (int r = 0; r <= TD && r < nstage; ++r) issue(r);
     int issued = min(TD + 1, nstage);
 
-    bool bad = !mbar_wait(smem_u32(&bars[0]), 0);
+    bool bad = !mbar_wait(smem_u32(&bars[0]), 0, A.wait_tries);
     float UA[4][3], EA[4], UB[4][3], EB[4];
     {
         const float *r0 = su + ty * TBW + xoff + tx;
@@ -723,7 +726,9 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __gr
         // record the time-out, let the copies already issued land (bounded), leave
         if (tid == 0) {
             A.ctrl[CT_ERR] = 1.0;
-            for (int r = 0; r < issued; ++r) mbar_wait(smem_u32(&bars[r & (TNS - 1)]), (r / TNS) & 1);
+            // the latest copy issued into each slot (a slot's earlier phases completed first),
+            // always with the full bound, whatever limit the sweep's own waits had
+            for (int r = max(issued - TNS, 0); r < issued; ++r) mbar_wait(smem_u32(&bars[r & (TNS - 1)]), (r / TNS) & 1);
         }
         __syncthreads();
         return;
@@ -754,6 +759,7 @@ __global__ void __launch_bounds__(32 * TY, 24 / TY) sweep3d_march_tma(const __gr
 }  // namespace
 
 void march3d_tma_tiling(const Layout &L, int ty, Tiling &t) {
+    t.order = 0;
     t.bx = 32;
     t.by = ty;
     t.ox = 31;
@@ -1057,7 +1063,7 @@ __device__ __forceinline__ bool march2_plane(const SweepArgs &A, const MarchCons
             FB[c] = __half2float(f0[c * R2WY * RBW + RBW]) * rinv;
         }
     }
-    if (!mbar_wait(smem_u32(&bars[slot]), (r1 / TNS) & 1)) bad = true;
+    if (!mbar_wait(smem_u32(&bars[slot]), (r1 / TNS) & 1, A.wait_tries)) bad = true;
     {
         const float *r0 = su + slot * (R2USLOT / 4) + (2 * ty) * TBW + xoff + tx;
 #pragma unroll
@@ -1209,7 +1215,7 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
         for (int r = 0; r <= TD && r < nstage; ++r) issue(r);
     int issued = min(TD + 1, nstage);
 
-    bool bad = !mbar_wait(smem_u32(&bars[0]), 0);
+    bool bad = !mbar_wait(smem_u32(&bars[0]), 0, A.wait_tries);
     float UA[3][2][3], EA[3][2], UB[3][2][3], EB[3][2];
     {
         const float *r0 = su + (2 * ty) * TBW + xoff + tx;
@@ -1252,7 +1258,9 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
     if (bad) {
         if (tid == 0) {
             A.ctrl[CT_ERR] = 1.0;
-            for (int r = 0; r < issued; ++r) mbar_wait(smem_u32(&bars[r & (TNS - 1)]), (r / TNS) & 1);
+            // the latest copy issued into each slot (a slot's earlier phases completed first),
+            // always with the full bound, whatever limit the sweep's own waits had
+            for (int r = max(issued - TNS, 0); r < issued; ++r) mbar_wait(smem_u32(&bars[r & (TNS - 1)]), (r / TNS) & 1);
         }
         __syncthreads();
         return;
@@ -1282,6 +1290,8 @@ __global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma2(const __grid_const
 
 }  // namespace
 
+cudaError_t march3d_prepare_tma3();
+
 // Dynamic shared memory above 48 KB must be allowed per kernel before the first launch
 // (done when a context is created, so never inside a stream capture).
 cudaError_t march3d_prepare() {
@@ -1296,10 +1306,12 @@ cudaError_t march3d_prepare() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(sweep3d_march_tma2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  r2_smem<true>());
+    if (e == cudaSuccess) e = march3d_prepare_tma3();
     return e;
 }
 
 void march3d_tma2_tiling(const Layout &L, Tiling &t) {
+    t.order = 0;
     t.bx = 32;
     t.by = R2TY;
     t.ox = 31;
@@ -1329,6 +1341,483 @@ cudaError_t launch_march3d_tma2(const SweepArgs &a, const Tiling &t, const TmaMa
         else
             sweep3d_march_tma2<false>
                 <<<dim3(t.gx, t.gy, t.gz), dim3(32, R2TY), r2_smem<false>(), s>>>(ar, *mu, m.w, m.e, m.u[0]);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace petto
+
+// ============================================================================
+// Lean form of the two-row TMA marching kernel.  Tiling, tensor maps, ring and owner/message
+// arithmetic are those of sweep3d_march_tma2, so every plane gets the same bits; what
+// differs is the per-plane control path:
+//   * the sweep kind (APT / PT / residual only) and the dense right-hand side are
+//     compile-time; the supports of a thread's columns are worked out once per segment, as
+//     a fixed mask for the boxes that span the segment's planes and a per-plane test only
+//     for boxes that end inside it (point loads likewise only in tiles that have some).  The
+//     floating-point code is one copy for every tile, so a plane gets the same bits whatever
+//     segment or slab computes it;
+//   * a warp whose two owner rows both lie beyond the grid (the last tile row) keeps only the
+//     barriers; whole warps of halo rows skip the update, and the whole CTA skips the updates
+//     of the segment's first owner plane, which only sends messages;
+//   * messages are packed so that a thread reads five shared words per plane instead of
+//     six: P0 = (x-message of row A, Gxy(A).x), P1 = (x-message of row B, Gxy(A).y),
+//     P2 = (y-message of row B, Gxy(B).x), Q = Gxy(B).y.
+// Blocks run in the hardware's order, x-tiles fastest: the CTAs in flight at one time march
+// the same planes of neighbouring tiles, so the halo rows and columns two tiles share, and
+// the partial sectors at tile edges, meet in L2 (an ordering that gives each CTA a long run of
+// one tile column instead doubled the DRAM reads).
+// ============================================================================
+namespace petto {
+namespace {
+
+constexpr int R3MSG = 2 * R2NT * (3 * 16 + 4);  // two buffers of P0, P1, P2 (float4) and Q (float)
+template <bool RHS> __host__ __device__ constexpr int r3_smem() { return r2_ring<RHS>() + R3MSG + TNS * 8 + 128; }
+static_assert(2 * (r3_smem<true>() + 1024) <= 228 * 1024, "two CTAs per SM must fit");
+
+// Per-thread values of the lean kernel.
+struct M3Thread {
+    const float *ru, *re;        // ring reads: slot 0 address of this thread's first u / E element
+                                 // (its w element is TNS u slots after its u element)
+    const __half *rr;
+    float *w, *uo;               // output bases (component 0 of this launch's load case)
+    int tid;
+    int cs;                      // component stride (elements)
+    int plane;                   // plane stride (elements)
+    int offA, offB;              // offsets of (X, YA, 0) and (X, YB, 0) from the output bases
+    bool outA, outB;
+    bool dead;                   // both owner rows beyond the grid: only the barriers
+    float rinv;                  // 2^-k of the FP16 right-hand side
+    unsigned bbA, bbB;           // support boxes ending inside the segment that contain the
+                                 // columns of rows A, B (tested plane by plane)
+    unsigned fmA, fmB;           // masks of the boxes that span the segment's planes
+    int l0, l1;                  // this tile's point loads
+};
+
+template <int MODE>
+__device__ __forceinline__ void m3_update(const SweepArgs &A, const MarchConst &K, const M3Thread &T, bool out,
+                                          int zp, unsigned bb, unsigned fmfix, int off, float Ku0, float Ku1,
+                                          float Ku2, float F0, float F1, float F2, float wv0, float wv1, float wv2,
+                                          const float (&u)[3], float S8, float &res, float &dot) {
+    if (!out) return;  // whole warps of halo or out-of-grid rows skip the update
+    unsigned fm = fmfix;
+    if (bb)
+        for (int q = 0; q < A.boxes.n; ++q)
+            if (((bb >> q) & 1u) && zp >= A.boxes.b[q].lo[2] && zp <= A.boxes.b[q].hi[2]) fm |= A.boxes.b[q].mask;
+    float step = MODE == 1 ? K.fs1 : K.fb;
+    if (A.local_dt) step *= fast_rcp(K.cdg * S8);
+    float R0 = F0 - Ku0, R1 = F1 - Ku1, R2 = F2 - Ku2;
+    float w0, w1, w2, v0, v1, v2;
+    if (MODE == 0) {
+        w0 = fmaf(K.fa, wv0, step * R0);
+        w1 = fmaf(K.fa, wv1, step * R1);
+        w2 = fmaf(K.fa, wv2, step * R2);
+        v0 = u[0] + w0;
+        v1 = u[1] + w1;
+        v2 = u[2] + w2;
+    } else {
+        w0 = w1 = w2 = 0.f;
+        v0 = fmaf(step, R0, u[0]);
+        v1 = fmaf(step, R1, u[1]);
+        v2 = fmaf(step, R2, u[2]);
+    }
+    if (fm) {
+        if (fm & 1u) R0 = w0 = v0 = 0.f;
+        if (fm & 2u) R1 = w1 = v1 = 0.f;
+        if (fm & 4u) R2 = w2 = v2 = 0.f;
+    }
+    if (A.want_res) res += R0 * R0 + R1 * R1 + R2 * R2;
+    if (MODE == 0 && A.test_dot) dot += R0 * wv0 + R1 * wv1 + R2 * wv2;
+    const int o = off + zp * T.plane;
+    if (MODE == 2) {  // residual only: R into the w buffer
+        float *rq = T.w + o;
+        rq[0] = R0;
+        rq[T.cs] = R1;
+        rq[2 * T.cs] = R2;
+        return;
+    }
+    if (MODE == 0) {
+        float *wq = T.w + o;
+        wq[0] = w0;
+        wq[T.cs] = w1;
+        wq[2 * T.cs] = w2;
+    }
+    float *uq = T.uo + o;
+    uq[0] = v0;
+    uq[T.cs] = v1;
+    uq[2 * T.cs] = v2;
+}
+
+// Point loads of node nidx from this tile's load list (body kind 2 of plain sweeps).
+__device__ __forceinline__ void m3_loads(const SweepArgs &A, const M3Thread &T, int64_t nidx, float &F0, float &F1,
+                                         float &F2) {
+    for (int l = T.l0; l < T.l1; ++l) {
+        const LoadEntry &le = A.loads[l];
+        if (le.node == nidx) {
+            const int cc = le.comp - 3 * A.rhs_index;
+            if (cc == 0) F0 += le.valf;
+            else if (cc == 1) F1 += le.valf;
+            else if (cc == 2) F2 += le.valf;
+        }
+    }
+}
+
+// Copies of one segment: stage r (relative to plane z0 - 1) holds u and w of plane z0 - 1 + r,
+// the modulus layer z0 - 2 + r and (refinement sweeps) the FP16 right-hand side of plane
+// z0 - 1 + r.  Issued by thread 0.
+struct M3Ring {
+    unsigned char *smem;  // ring base (u slots, w slots, E slots, right-hand-side slots)
+    uint64_t *bars;
+    const CUtensorMap *tmu, *tmw, *tme, *tmr;
+    int xs, xse, xsh, y0, z0, c0;
+};
+
+template <bool RHS> __device__ __forceinline__ void m3_issue(const M3Ring &Rg, int r) {
+    const int p = Rg.z0 - 1 + r;
+    const int slot = r & (TNS - 1);
+    const uint32_t bar = smem_u32(&Rg.bars[slot]);
+    unsigned char *sm = Rg.smem;
+    mbar_expect_tx(bar, (unsigned)(2 * R2UBYTES + R2EBYTES + (RHS ? R2RBYTES : 0)));
+    tma_load_4d(smem_u32(sm + slot * R2USLOT), Rg.tmu, Rg.xs, Rg.y0, p + 1, Rg.c0, bar);
+    tma_load_4d(smem_u32(sm + TNS * R2USLOT + slot * R2USLOT), Rg.tmw, Rg.xs, Rg.y0, p + 1, Rg.c0, bar);
+    tma_load_3d(smem_u32(sm + 2 * TNS * R2USLOT + slot * R2ESLOT), Rg.tme, Rg.xse, Rg.y0 - 1, p, bar);
+    if (RHS)
+        tma_load_4d(smem_u32(sm + TNS * (2 * R2USLOT + R2ESLOT) + slot * R2RSLOT), Rg.tmr, Rg.xsh, Rg.y0, p + 1, Rg.c0,
+                    bar);
+}
+
+// One owner plane zp: stage r1 (plane zp + 1) is its hi plane, stage r1 - 1 holds w and the
+// right-hand side of plane zp.
+template <int MODE, bool RHS>
+__device__ __forceinline__ bool m3_plane(const SweepArgs &A, const MarchConst &K, const M3Thread &T, int zp, int zo,
+                                         int r1, unsigned char *msgraw, uint64_t *bars, const M3Ring &Rg,
+                                         int &issued, int nstage, int64_t nbA, int64_t nbB,
+                                         const float (&Ul)[3][2][3], const float (&El)[3][2], float (&Uh)[3][2][3],
+                                         float (&Eh)[3][2], RowCarry &CA, RowCarry &CB, float &res, float &dot,
+                                         bool &bad) {
+    const int tid = T.tid;
+    const int slot = r1 & (TNS - 1), pslot = (r1 - 1) & (TNS - 1);
+    if (!mbar_wait(smem_u32(&bars[slot]), (r1 / TNS) & 1, A.wait_tries)) bad = true;
+    {
+        const float *r0 = T.ru + slot * (R2USLOT / 4);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                Uh[r][0][c] = r0[c * R2WY * TBW + r * TBW];
+                Uh[r][1][c] = r0[c * R2WY * TBW + r * TBW + 1];
+            }
+        const float *q0 = T.re + slot * (R2ESLOT / 4);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            Eh[r][0] = q0[r * TBW];
+            Eh[r][1] = q0[r * TBW + 1];
+        }
+    }
+    const float ElA[4] = {El[1][1], El[1][0], El[0][1], El[0][0]};
+    const float EhA[4] = {Eh[1][1], Eh[1][0], Eh[0][1], Eh[0][0]};
+    const float ElB[4] = {El[2][1], El[2][0], El[1][1], El[1][0]};
+    const float EhB[4] = {Eh[2][1], Eh[2][0], Eh[1][1], Eh[1][0]};
+    const Owned oA = owned_forces(K, Ul[0][0], Ul[0][1], Ul[1][0], Ul[1][1], Uh[0][0], Uh[0][1], Uh[1][0], ElA, EhA);
+    const Owned oB = owned_forces(K, Ul[1][0], Ul[1][1], Ul[2][0], Ul[2][1], Uh[1][0], Uh[1][1], Uh[2][0], ElB, EhB);
+    float4 *P0 = reinterpret_cast<float4 *>(msgraw + (zp & 1) * (R3MSG / 2));
+    float4 *P1 = P0 + R2NT;
+    float4 *P2 = P1 + R2NT;
+    float *Q = reinterpret_cast<float *>(P2 + R2NT);
+    P0[tid] = make_float4(oA.Fx0 + oA.Hxy0 + oA.Hxz0 + CA.Gxz0, oA.Fx1 + oA.Hxy1, oA.Fx2 + oA.Hxz1 + CA.Gxz1, oA.Gxy0);
+    P1[tid] = make_float4(oB.Fx0 + oB.Hxy0 + oB.Hxz0 + CB.Gxz0, oB.Fx1 + oB.Hxy1, oB.Fx2 + oB.Hxz1 + CB.Gxz1, oA.Gxy1);
+    P2[tid] = make_float4(oB.Fy0 - oB.Hxy0, oB.Fy1 - oB.Hxy1 + oB.Hyz0 + CB.Gyz0, oB.Fy2 + oB.Hyz1 + CB.Gyz1, oB.Gxy0);
+    Q[tid] = oB.Gxy1;
+    const float MyA0 = oA.Fy0 - oA.Hxy0, MyA1 = oA.Fy1 - oA.Hxy1 + oA.Hyz0 + CA.Gyz0,
+                MyA2 = oA.Fy2 + oA.Hyz1 + CA.Gyz1;
+    if (__syncthreads_or(bad)) {
+        bad = true;
+        return false;
+    }
+    // past this barrier every thread is done with the previous plane, whose update read the
+    // slot of stage r1 - 2: the refill TD stages ahead (into that slot) goes out now
+    if (tid == 0 && issued < nstage) m3_issue<RHS>(Rg, issued);
+    issued = min(issued + 1, nstage);
+    // the segment's first owner plane (zp = z0 - 1, or a plane below a slab's own ones) only
+    // sends messages: the whole CTA skips its updates
+    if (zp >= zo) {
+        // the old increment and the right-hand side of plane zp came with stage r1 - 1
+        float wA0 = 0.f, wA1 = 0.f, wA2 = 0.f, wB0 = 0.f, wB1 = 0.f, wB2 = 0.f;
+        if (MODE == 0) {
+            const float *w0 = T.ru + TNS * (R2USLOT / 4) + pslot * (R2USLOT / 4);
+            wA0 = w0[0];
+            wA1 = w0[R2WY * TBW];
+            wA2 = w0[2 * R2WY * TBW];
+            wB0 = w0[TBW];
+            wB1 = w0[R2WY * TBW + TBW];
+            wB2 = w0[2 * R2WY * TBW + TBW];
+        }
+        float FA[3] = {0.f, 0.f, 0.f}, FB[3] = {0.f, 0.f, 0.f};
+        if (RHS) {
+            const __half *f0 = T.rr + pslot * (R2RSLOT / 2);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                FA[c] = __half2float(f0[c * R2WY * RBW]) * T.rinv;
+                FB[c] = __half2float(f0[c * R2WY * RBW + RBW]) * T.rinv;
+            }
+        }
+        const float4 xa = P0[tid - 1];  // (x-1, A): x-message and Gxy(A).x for B
+        const float4 xb = P1[tid - 1];  // (x-1, B): x-message and Gxy(A).y for B
+        const float4 ya = P2[tid - 32]; // (x, ty-1).B: y-message for A
+        const float gA0 = P2[tid - 33].w, gA1 = Q[tid - 33];  // Gxy of (x-1, ty-1).B for A
+        const float gB0 = xa.w, gB1 = xb.w;
+        const float Ku0A = -(oA.Fx0 + oA.Fy0 + oA.Fz0) - (oA.Gxy0 + oA.Gxz0) + xa.x + ya.x + CA.Sz0 + gA0;
+        const float Ku1A = -(oA.Fx1 + oA.Fy1 + oA.Fz1) - (oA.Gxy1 + oA.Gyz0) + xa.y + ya.y + CA.Sz1 + gA1;
+        const float Ku2A = -(oA.Fx2 + oA.Fy2 + oA.Fz2) - (oA.Gxz1 + oA.Gyz1) + xa.z + ya.z + CA.Sz2;
+        const float Ku0B = -(oB.Fx0 + oB.Fy0 + oB.Fz0) - (oB.Gxy0 + oB.Gxz0) + xb.x + MyA0 + CB.Sz0 + gB0;
+        const float Ku1B = -(oB.Fx1 + oB.Fy1 + oB.Fz1) - (oB.Gxy1 + oB.Gyz0) + xb.y + MyA1 + CB.Sz1 + gB1;
+        const float Ku2B = -(oB.Fx2 + oB.Fy2 + oB.Fz2) - (oB.Gxz1 + oB.Gyz1) + xb.z + MyA2 + CB.Sz2;
+        if (!RHS && T.l0 < T.l1) {
+            m3_loads(A, T, nbA + (int64_t)zp * T.plane, FA[0], FA[1], FA[2]);
+            m3_loads(A, T, nbB + (int64_t)zp * T.plane, FB[0], FB[1], FB[2]);
+        }
+        const float S8A = (El[0][0] + El[0][1]) + (El[1][0] + El[1][1]) + (Eh[0][0] + Eh[0][1]) + (Eh[1][0] + Eh[1][1]);
+        const float S8B = (El[1][0] + El[1][1]) + (El[2][0] + El[2][1]) + (Eh[1][0] + Eh[1][1]) + (Eh[2][0] + Eh[2][1]);
+        m3_update<MODE>(A, K, T, T.outA, zp, T.bbA, T.fmA, T.offA, Ku0A, Ku1A, Ku2A, FA[0], FA[1], FA[2], wA0,
+                              wA1, wA2, Ul[0][0], S8A, res, dot);
+        m3_update<MODE>(A, K, T, T.outB, zp, T.bbB, T.fmB, T.offB, Ku0B, Ku1B, Ku2B, FB[0], FB[1], FB[2], wB0,
+                              wB1, wB2, Ul[1][0], S8B, res, dot);
+    }
+    CA = {oA.Fz0 - oA.Hxz0, oA.Fz1 - oA.Hyz0, oA.Fz2 - oA.Hxz1 - oA.Hyz1, oA.Gxz0, oA.Gxz1, oA.Gyz0, oA.Gyz1};
+    CB = {oB.Fz0 - oB.Hxz0, oB.Fz1 - oB.Hyz0, oB.Fz2 - oB.Hxz1 - oB.Hyz1, oB.Gxz0, oB.Gxz1, oB.Gyz0, oB.Gyz1};
+    return true;
+}
+
+template <int MODE, bool RHS>
+__device__ __forceinline__ void m3_body(const SweepArgs &A, const MarchConst &K, const M3Thread &T, const M3Ring &Rg,
+                                        int z0, int zo, int zend, unsigned char *msg, int64_t nbA, int64_t nbB,
+                                        int &issued, int nstage, float &res, float &dot, bool &bad) {
+    float UA[3][2][3], EA[3][2], UB[3][2][3], EB[3][2];
+    {
+        const float *r0 = T.ru;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                UA[r][0][c] = r0[c * R2WY * TBW + r * TBW];
+                UA[r][1][c] = r0[c * R2WY * TBW + r * TBW + 1];
+            }
+        const float *q0 = T.re;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            EA[r][0] = q0[r * TBW];
+            EA[r][1] = q0[r * TBW + 1];
+        }
+    }
+    RowCarry CA = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, CB = CA;
+    // two planes per trip with the register sets swapping roles
+    for (int zp = z0 - 1; zp < zend; zp += 2) {
+        int r1 = zp + 1 - (z0 - 1);
+        if (!m3_plane<MODE, RHS>(A, K, T, zp, zo, r1, msg, Rg.bars, Rg, issued, nstage, nbA, nbB, UA, EA, UB,
+                                       EB, CA, CB, res, dot, bad))
+            return;
+        if (zp + 1 >= zend) break;
+        ++r1;
+        if (!m3_plane<MODE, RHS>(A, K, T, zp + 1, zo, r1, msg, Rg.bars, Rg, issued, nstage, nbA, nbB, UB, EB,
+                                       UA, EA, CA, CB, res, dot, bad))
+            return;
+    }
+}
+
+// The march of a warp with no row in the grid: the barriers only (one per owner plane, as
+// m3_plane has); it reads nothing, so it waits for no copy.
+__device__ __forceinline__ void m3_dead(int z0, int zend, bool &bad) {
+    for (int zp = z0 - 1; zp < zend; ++zp)
+        if (__syncthreads_or(false)) {
+            bad = true;
+            return;
+        }
+}
+
+template <int MODE, bool RHS>
+__global__ void __launch_bounds__(R2NT, 2) sweep3d_march_tma3(const __grid_constant__ SweepArgs A,
+                                                              const __grid_constant__ CUtensorMap tmu,
+                                                              const __grid_constant__ CUtensorMap tmw,
+                                                              const __grid_constant__ CUtensorMap tme,
+                                                              const __grid_constant__ CUtensorMap tmr) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    float *su = reinterpret_cast<float *>(smem);
+    float *se = reinterpret_cast<float *>(smem + 2 * TNS * R2USLOT);
+    const __half *sr = reinterpret_cast<const __half *>(smem + TNS * (2 * R2USLOT + R2ESLOT));
+    unsigned char *msg = smem + r2_ring<RHS>();
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + r2_ring<RHS>() + R3MSG);
+    __shared__ double shred[32];
+
+    const Layout &L = A.L;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int x0 = blockIdx.x * 31, y0 = blockIdx.y * (R2ROWS - 1), z0 = A.zb + blockIdx.z * A.zseg;
+    const int X = x0 - 1 + tx, YA = y0 - 1 + 2 * ty, YB = YA + 1;
+    const int zend = min(z0 + A.zseg, A.zhi + 1);
+    // first plane written: a slab's segments may start one plane below its own planes, on the
+    // parity of the whole grid's segments (see sweep3d_march_tma2)
+    const int zo = max(z0, A.zlo);
+    const int xs = (x0 - 1 + OX) & ~3, xoff = (x0 - 1 + OX) - xs;
+    const int xse = (x0 - 2 + OX) & ~3, xoffe = (x0 - 2 + OX) - xse;
+    const int xsh = (x0 - 1 + OX) & ~7, xoffh = (x0 - 1 + OX) - xsh;
+
+    MarchConst K;
+    K.cpar = A.kf.ce_par;
+    K.cperp = A.kf.ce_perp;
+    K.cl = A.kf.cf_lam;
+    K.cm = A.kf.cf_mu;
+    K.cdg = A.kf.cdiag;
+    K.fa = A.kf.a;
+    K.fb = A.kf.b;
+    K.fs1 = A.kf.s1;
+    if (MODE == 0 && A.adaptive) K.fa = fminf(K.fa, apt_schedule(A));
+
+    M3Thread T;
+    T.tid = tid;
+    T.outA = tx >= 1 && ty >= 1 && X < L.NX && YA < L.NY;
+    T.outB = tx >= 1 && X < L.NX && YB < L.NY;
+    T.dead = YA >= L.NY;
+    const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    T.l0 = A.tile_ptr[tile];
+    T.l1 = A.tile_ptr[tile + 1];
+    const int64_t nbA = T.outA ? L.node(X, YA, 0) : 0, nbB = T.outB ? L.node(X, YB, 0) : 0;
+    T.plane = (int)(L.SX * L.SY);
+    T.cs = (int)L.cstride;
+    T.offA = (int)nbA;
+    T.offB = (int)nbB;
+    const int c0 = 3 * A.rhs_index;
+    const int64_t cbase = (int64_t)c0 * L.cstride;
+    T.w = static_cast<float *>(A.w) + cbase;
+    T.uo = MODE == 2 ? nullptr : static_cast<float *>(A.u_out) + cbase;
+    T.ru = su + (2 * ty) * TBW + xoff + tx;
+    T.re = se + (2 * ty) * TBW + xoffe + tx;
+    T.rr = sr + (2 * ty) * RBW + xoffh + tx;
+    T.rinv = RHS ? (float)A.ctrl[CT_RSCALE] : 0.f;
+    // support boxes of this thread's columns: a fixed mask for those that span every plane
+    // the segment writes, a per-plane test for those that end inside it
+    T.bbA = T.bbB = T.fmA = T.fmB = 0;
+    for (int q = 0; q < A.boxes.n; ++q) {
+        const Box &b = A.boxes.b[q];
+        if (X < b.lo[0] || X > b.hi[0] || b.hi[2] < zo || b.lo[2] > zend - 1) continue;
+        const bool full = b.lo[2] <= zo && b.hi[2] >= zend - 1;
+        if (YA >= b.lo[1] && YA <= b.hi[1]) {
+            if (full) T.fmA |= b.mask;
+            else T.bbA |= 1u << q;
+        }
+        if (YB >= b.lo[1] && YB <= b.hi[1]) {
+            if (full) T.fmB |= b.mask;
+            else T.bbB |= 1u << q;
+        }
+    }
+
+    M3Ring Rg;
+    Rg.smem = smem;
+    Rg.bars = bars;
+    Rg.tmu = &tmu;
+    Rg.tmw = &tmw;
+    Rg.tme = &tme;
+    Rg.tmr = &tmr;
+    Rg.xs = xs;
+    Rg.xse = xse;
+    Rg.xsh = xsh;
+    Rg.y0 = y0;
+    Rg.z0 = z0;
+    Rg.c0 = c0;
+    const int nstage = zend - (z0 - 1) + 1;  // stages z0-1 .. zend
+    if (tid == 0) {
+        for (int s = 0; s < TNS; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int r = 0; r <= TD && r < nstage; ++r) m3_issue<RHS>(Rg, r);
+    int issued = min(TD + 1, nstage);
+
+    float res = 0.f, dot = 0.f;
+    bool bad = !T.dead && !mbar_wait(smem_u32(&bars[0]), 0, A.wait_tries);
+    bad = __syncthreads_or(bad);
+    if (!bad) {
+        if (T.dead) m3_dead(z0, zend, bad);
+        else m3_body<MODE, RHS>(A, K, T, Rg, z0, zo, zend, msg, nbA, nbB, issued, nstage, res, dot, bad);
+    }
+
+    if (bad) {
+        // record the time-out, let the copies already issued land (bounded), leave; earlier
+        // phases of a slot completed before its latest one, so the latest is the one to wait for
+        if (tid == 0) {
+            A.ctrl[CT_ERR] = 1.0;
+            for (int r = max(issued - TNS, 0); r < issued; ++r) mbar_wait(smem_u32(&bars[r & (TNS - 1)]), (r / TNS) & 1);
+        }
+        __syncthreads();
+        return;
+    }
+    if (A.want_res || A.test_dot) {
+        const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+        const double r = A.want_res ? block_sum((double)res, shred) : 0.0;
+        const double d = A.test_dot ? block_sum((double)dot, shred) : 0.0;
+        if (tid == 0) A.red.partials[(int64_t)nb + tile] = d;
+        if (publish_partial(r, A.red, tile, nb)) {
+            const double t = A.want_res ? sum_partials(A.red, 0, nb, shred) : 0.0;
+            const double td = A.test_dot ? sum_partials(A.red, nb, nb, shred) : 0.0;
+            if (tid == 0) {
+                // one launch per load case: sums accumulate in launch order; the last case decides
+                const bool first = A.rhs_index == 0, lastc = A.rhs_index == A.nrhs - 1;
+                if (A.want_res) *A.res2 = first ? t : *A.res2 + t;
+                if (A.test_dot) {
+                    const double dsum = first ? td : A.ctrl[CT_DOT] + td;
+                    A.ctrl[CT_DOT] = dsum;
+                    if (lastc && dsum < 0.0) reinterpret_cast<long long *>(A.ctrl)[CT_RESTART_AT] = sweep_index(A) + 1;
+                }
+                *A.red.counter = 0u;
+            }
+        }
+    }
+}
+
+}  // namespace
+}  // namespace petto
+
+namespace petto {
+
+void march3d_tma3_tiling(const Layout &L, Tiling &t) {
+    march3d_tma2_tiling(L, t);
+    t.kind = 6;
+}
+
+cudaError_t march3d_prepare_tma3() {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *f, int bytes) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    };
+    set((const void *)sweep3d_march_tma3<0, false>, r3_smem<false>());
+    set((const void *)sweep3d_march_tma3<1, false>, r3_smem<false>());
+    set((const void *)sweep3d_march_tma3<2, false>, r3_smem<false>());
+    set((const void *)sweep3d_march_tma3<0, true>, r3_smem<true>());
+    set((const void *)sweep3d_march_tma3<1, true>, r3_smem<true>());
+    return e;
+}
+
+// APT (mode 0), PT (mode 1) and residual-only (mode 2: R into w, no dense right-hand side)
+cudaError_t launch_march3d_tma3(const SweepArgs &a, const Tiling &t, const TmaMaps &m, cudaStream_t s) {
+    const CUtensorMap *mu = a.u_in == m.ubuf[0] ? &m.u[0] : (a.u_in == m.ubuf[1] ? &m.u[1] : nullptr);
+    if (!mu || a.mode < 0 || a.mode > 2) return cudaErrorInvalidValue;
+    if (a.mode < 2 && !a.u_out) return cudaErrorInvalidValue;
+    if (a.mode == 2 && a.rhs) return cudaErrorInvalidValue;
+    // a dense right-hand side reaches this kernel only as the scaled FP16 copy behind m.r
+    if (a.rhs && !(a.rhs_half && m.rvalid && m.rbuf == a.rhs)) return cudaErrorInvalidValue;
+    const dim3 grid(t.gx, t.gy, t.gz), block(32, R2TY);
+    for (int r = 0; r < a.nrhs; ++r) {
+        SweepArgs ar = a;
+        ar.rhs_index = r;
+        if (a.mode == 2) {
+            sweep3d_march_tma3<2, false><<<grid, block, r3_smem<false>(), s>>>(ar, *mu, m.w, m.e, m.u[0]);
+        } else if (a.rhs) {
+            if (a.mode == 0) sweep3d_march_tma3<0, true><<<grid, block, r3_smem<true>(), s>>>(ar, *mu, m.w, m.e, m.r);
+            else sweep3d_march_tma3<1, true><<<grid, block, r3_smem<true>(), s>>>(ar, *mu, m.w, m.e, m.r);
+        } else {
+            if (a.mode == 0) sweep3d_march_tma3<0, false><<<grid, block, r3_smem<false>(), s>>>(ar, *mu, m.w, m.e, m.u[0]);
+            else sweep3d_march_tma3<1, false><<<grid, block, r3_smem<false>(), s>>>(ar, *mu, m.w, m.e, m.u[0]);
+        }
     }
     return cudaGetLastError();
 }

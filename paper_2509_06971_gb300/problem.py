@@ -263,6 +263,10 @@ class Problem:
                                       ctypes.byref(r) if want_res else None))
         return r.value if want_res else None
 
+    def set_wait_limit(self, tries: int = -1):
+        """Attempts of each bounded ring wait of the TMA sweeps (-1: the default)."""
+        self._ck(self.lib.petto_set_wait_limit(self.ctx, int(tries)))
+
     def sweep_rhs(self, kind: int, n: int, r, a: float = 0.0, b: float = 0.0, s1: float = 0.0,
                   local_dt: bool = False, want_res: bool = True):
         """n sweeps with the dense right-hand side r [C, nodes] (FP64, host array or CUDA

@@ -39,7 +39,7 @@ def _spec(name):
     return W.cantilever3d(*SIZE) if name == "cantilever3d" else FULL_2D[name]()
 
 
-@pytest.mark.parametrize("name,kernel", [("cantilever3d", "tma2/"), ("cantilever2d_1024x512", "march2d/"),
+@pytest.mark.parametrize("name,kernel", [("cantilever3d", "tma3/"), ("cantilever2d_1024x512", "march2d/"),
                                          ("heat2d_1024x1024", "march2d/")])
 def test_fullsize_sweeps_match_oracle(P, name, kernel):
     spec = _spec(name)
@@ -137,7 +137,7 @@ def test_fullsize_multi_rhs_sweep(P):
     phi = W.random_design(spec, seed=47)
     u0 = np.concatenate([W.random_state(spec, seed=48 + r) for r in range(4)]).astype(np.float32)
     prob = P.Problem(spec, nrhs=4, load_cases=cases)
-    assert prob.kernel_info()[0].startswith("tma2/")
+    assert prob.kernel_info()[0].startswith("tma3/")
     prob.set_design(phi)
     prob.set_state(u0)
     a, b = 0.95, 0.05

@@ -432,7 +432,7 @@ def test_autograd_function_matches_finite_difference(P):
     prob.close()
 
 
-@pytest.mark.parametrize("variant", ["tma8", "tma16", "tma2", "v1"])
+@pytest.mark.parametrize("variant", ["tma3", "tma8", "tma16", "tma2", "v1"])
 def test_march3d_multi_tile_and_segment(P, variant, monkeypatch):
     """Every z-marching FP32 kernel variant on a grid spanning several x/y tiles and z
     segments with ragged tails, point loads on tile edges and supports on several faces."""
@@ -547,7 +547,7 @@ def test_pt_only_solve(P):
     prob.close()
 
 
-@pytest.mark.parametrize("variant", ["tma2", "tma8"])
+@pytest.mark.parametrize("variant", ["tma3", "tma2", "tma8"])
 def test_multi_rhs_fp32_march(P, variant, monkeypatch):
     """FP32 multi-load-case sweeps on the marching kernels (one launch per case sharing the
     momentum schedule) match the oracle run case by case."""
@@ -586,9 +586,8 @@ def test_multi_rhs_refined_solve_matches_direct(P):
     spec, cases = W.multirhs3d(40, 18, 20, n_rhs=3, seed=3)
     spec = spec.with_(precision="f32", storage="f32")
     prob = P.Problem(spec, nrhs=3, load_cases=cases)
-    prob.select_kernel("tma2")
     name, rhs_bytes = prob.kernel_info()
-    assert name.startswith("tma2/") and rhs_bytes == 2
+    assert name.startswith("tma3/") and rhs_bytes == 2
     phi = W.random_design(spec, seed=27, lo=0.05, hi=0.95)
     prob.set_design(phi)
     rep = prob.solve(tol=1e-6, max_sweeps=200000)
@@ -604,7 +603,8 @@ def test_multi_rhs_refined_solve_matches_direct(P):
     prob.close()
 
 
-def test_refinement_is_scale_equivariant(P):
+@pytest.mark.parametrize("kernel", ["tma3", "tma2"])
+def test_refinement_is_scale_equivariant(P, kernel):
     """Loads scaled by 2^-20: the FP32 sweeps, the FP64 defect and the power-of-two scaling
     of the defect's FP16 copy all commute with the scaling, so the refined solve takes the
     same sweeps and ends in the unscaled state times 2^-20, bit for bit."""
@@ -614,7 +614,7 @@ def test_refinement_is_scale_equivariant(P):
     for s in (1.0, sc):
         spec = base.with_(precision="f32", storage="f32", loads=[(n, c, v * s) for n, c, v in base.loads])
         prob = P.Problem(spec)
-        prob.select_kernel("tma2")
+        prob.select_kernel(kernel)
         prob.set_design(W.random_design(spec, seed=15, lo=0.05, hi=0.95))
         rep = prob.solve(tol=1e-6, max_sweeps=200000)
         out.append((rep, prob.get_state(dtype=np.float32)))
@@ -633,6 +633,9 @@ def test_kernel_info_names_the_selected_kernel(P):
     for name in ("tma8/zs8", "tma2/zs8"):
         p3.select_kernel(name)
         assert p3.kernel_info() == (name, 2 if name.startswith("tma2") else 4)
+    p3.select_kernel("tma3")
+    name, rb = p3.kernel_info()
+    assert name.startswith("tma3/zs") and rb == 2
     p3.close()
 
 
@@ -674,3 +677,75 @@ def test_autotune_keeps_state_and_picks_a_variant(P):
     r = prob.solve(tol=1e-6, max_sweeps=100000)
     assert r["converged"]
     prob.close()
+
+
+def test_lean_march_kernel_equals_two_row_kernel(P):
+    """The lean two-row marching kernel (tma3: the default 3D FP32 sweep) against the
+    two-row kernel it was derived from (tma2) on a ragged grid whose tiles take all three of
+    its bodies: no supports, supports spanning the segment (fixed masks), and a box that ends
+    inside a segment plus point loads (per-plane tests).  Same tiling and arithmetic: APT
+    sweeps, with point loads or a dense FP16 right-hand side, agree bit for bit; PT sweeps
+    and the residual field (mode 2), where the compiler may fuse a product into a different
+    addition, to rounding."""
+    nx, ny, nz = 70, 40, 37
+    base = W.cantilever3d(nx, ny, nz)
+    loads = base.loads + [((31, 7, 16), 0, 0.7), ((30, 6, 15), 1, -0.4), ((62, 14, 32), 2, 0.25)]
+    boxes = base.boxes + [((nx, 0, nz), (nx, ny, nz), 0b010), ((10, 21, 3), (40, 22, 17), 0b101)]
+    spec = base.with_(loads=loads, boxes=boxes)
+    phi = W.random_design(spec, seed=61, lo=0.05, hi=0.95)
+    u0 = W.random_state(spec, seed=62, scale=1e-2).astype(np.float32)
+    w0 = W.random_state(spec, seed=63, scale=1e-3).astype(np.float32)
+    r = W.random_state(spec, seed=64, scale=1e-2)
+    out = {}
+    for kernel in ("tma2", "tma3"):
+        prob = P.Problem(spec)
+        prob.select_kernel(kernel)
+        assert prob.kernel_info()[0].startswith(kernel + "/")
+        prob.set_design(phi)
+        res = []
+        prob.set_state(u0, w0)
+        res.append(prob.sweep(0, 3, 0.93, 0.9, 0.0, True))
+        res.append(prob.get_state(with_w=True, dtype=np.float32))
+        prob.set_state(u0, w0)
+        res.append(prob.sweep_rhs(0, 3, r, 0.91, 0.9, 0.0, True))
+        res.append(prob.get_state(with_w=True, dtype=np.float32))
+        prob.set_state(u0, w0)
+        res.append(prob.sweep(1, 2, 0.0, 0.0, 0.75, True))
+        res.append(prob.get_state(dtype=np.float32))
+        res.append(prob.residual(dtype=np.float32)[1])
+        out[kernel] = res
+        prob.close()
+    a, b = out["tma2"], out["tma3"]
+    for k in (1, 3):
+        assert np.array_equal(a[k][0], b[k][0]) and np.array_equal(a[k][1], b[k][1]), k
+    assert relmax(b[5], a[5]) < 1e-6
+    assert relmax(b[6], a[6]) < 1e-6
+    for k in (0, 2, 4):
+        assert abs(a[k] - b[k]) <= 1e-6 * a[k]
+
+
+@pytest.mark.parametrize("kernel", ["tma3", "tma2"])
+def test_ring_wait_time_out_is_reported_and_the_context_recovers(P, kernel):
+    """The bounded waits of the TMA marching sweeps: with the limit at zero every wait runs
+    out, the CTAs let their copies land and return, and the solve reports PETTO_ETIMEOUT
+    (no hang, no fault); with the default limit back the same context solves the problem and
+    its compliance matches the oracle's direct solve."""
+    from paper_2509_06971_gb300 import capi as C
+    spec = W.cantilever3d(26, 12, 11).with_(precision="f32", storage="f32")
+    prob = P.Problem(spec)
+    prob.select_kernel(kernel)
+    phi = W.random_design(spec, seed=66, lo=0.2, hi=0.9)
+    prob.set_design(phi)
+    prob.set_wait_limit(0)
+    with pytest.raises(C.PettoError) as err:
+        prob.solve(tol=1e-6, max_sweeps=200000)
+    assert err.value.status == C.PETTO_ETIMEOUT
+    prob.set_wait_limit(-1)
+    rep = prob.solve(tol=1e-6, max_sweeps=200000)
+    assert rep["converged"] and rep["rel_res"] <= 1e-6
+    Cg, _, _ = prob.sensitivity(want_field=False)
+    prob.close()
+    op, om = oracle_problem(spec), oracle_materials(spec)
+    F = op.load_vector()
+    Co = float(F @ op.direct_solve(om.modulus(np.asarray(phi, np.float32).astype(np.float64)), F, op.fixed_mask()))
+    assert abs(Cg - Co) < 1e-4 * abs(Co)

@@ -53,7 +53,8 @@ def _same(a, b, spec):
     pytest.fail(f"max |diff| {d.max():.3e} (rel {d.max() / np.abs(b).max():.3e}) on planes {planes}")
 
 
-@pytest.mark.parametrize("precision,kernel", [("f64", None), ("f32", "tma2"), ("f32", "gather/32x4")])
+@pytest.mark.parametrize("precision,kernel", [("f64", None), ("f32", "tma3"), ("f32", "tma2"),
+                                              ("f32", "gather/32x4")])
 @pytest.mark.parametrize("n_slabs", [2, 3])
 def test_slabs_equal_whole_grid_sweeps(P, precision, kernel, n_slabs):
     spec = _spec(precision=precision)
@@ -92,18 +93,19 @@ def test_slab_solve_matches_direct_solve_fp64(P):
     assert abs(Cs - Cd) <= 1e-7 * abs(Cd)
 
 
-def test_slab_multi_rhs_tma2_equals_whole(P):
+@pytest.mark.parametrize("kernel", ["tma3", "tma2"])
+def test_slab_multi_rhs_two_row_equals_whole(P, kernel):
     spec, cases = W.multirhs3d(40, 18, 20, n_rhs=2, seed=5)
     spec = spec.with_(precision="f32", storage="f32", phi0=W.random_design(spec, seed=34))
     rng = np.random.default_rng(35)
     u0 = rng.standard_normal((6, spec.nnodes)).astype(np.float32)
     p = P.Problem(spec, nrhs=2, load_cases=cases)
-    p.select_kernel("tma2")
+    p.select_kernel(kernel)
     p.set_state(u0)
     p.sweep(0, 4, 0.9, 0.8, 0.0, True)
     uw = p.get_state(dtype=np.float32)
     p.close()
-    with S.SlabGrid(spec, 2, kernel="tma2", nrhs=2, load_cases=cases) as g:
+    with S.SlabGrid(spec, 2, kernel=kernel, nrhs=2, load_cases=cases) as g:
         g.set_state(u0)
         g.sweep(0, 4, 0.9, 0.8, 0.0, True)
         us = g.get_state(dtype=np.float32)

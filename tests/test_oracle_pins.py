@@ -609,3 +609,22 @@ def test_solve_guard_resets_a_non_finite_state(momentum):
     for _ in range(q):
         p.pt_sweep(E, F, fixed, 0.25, ref)
     assert np.all(np.isfinite(u)) and np.array_equal(u, ref)
+
+
+def test_openmp_build_agrees_with_the_oracle():
+    """The OpenMP build (all-core CPU baseline only) runs the same sweeps as the oracle; its
+    scatter sums each node's cell forces in another order, so the states agree to rounding."""
+    if not O.openmp_available():
+        pytest.skip("no OpenMP in the host compiler")
+    for spec in (W.cantilever3d(18, 9, 7), W.mbb_halfbeam(30, 9)):
+        out = []
+        for omp in (False, True):
+            op = O.OracleProblem(spec.dim, spec.nx, spec.ny, spec.nz, h=spec.h, physics=spec.physics, nu=spec.nu,
+                                 loads=spec.loads, boxes=spec.boxes, openmp=omp)
+            E = oracle_materials(spec).modulus(W.random_design(spec, seed=7))
+            u = np.zeros(op.ndof)
+            op.solve(E, op.load_vector(), op.fixed_mask(), u, mode=0, n_apt=25, n_pt=5, a=0.9, b=0.25, s1=0.25,
+                     check_every=0)
+            out.append((u, op.residual(E, op.load_vector(), op.fixed_mask(), u)[1]))
+        assert np.abs(out[0][0] - out[1][0]).max() <= 1e-12 * np.abs(out[0][0]).max()
+        assert abs(out[0][1] - out[1][1]) <= 1e-12 * out[0][1]

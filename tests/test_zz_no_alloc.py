@@ -28,13 +28,26 @@ def _dense_inputs(spec):
     return F.reshape(spec.dim, -1), fixed.reshape(spec.dim, -1)
 
 
-@pytest.mark.parametrize("spec", [W.cantilever2d(90, 40, load_cells=6), W.cantilever3d(40, 18, 13)],
-                         ids=["2d", "3d"])
-def test_static_residual_norm_matches_context_residual(spec):
+CASES = {
+    "2d": (W.cantilever2d(90, 40, load_cells=6), True, True),
+    "3d": (W.cantilever3d(40, 18, 13), True, True),
+    "3d_h0.5": (W.cantilever3d(40, 18, 13).with_(h=0.5), True, True),   # h^(d-2) scaling
+    "3d_no_loads": (W.cantilever3d(24, 10, 9), False, True),            # F = NULL
+    "3d_no_supports": (W.cantilever3d(24, 10, 9), True, False),         # fixed = NULL
+    # exactly the limit of 4 194 304 nodes
+    "2d_at_limit": (W.mbb_halfbeam(2047, 2047), True, True),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_static_residual_norm_matches_context_residual(name):
     torch = pytest.importorskip("torch")
     from paper_2509_06971_gb300 import capi as C, problem
     lib = C.load()
+    spec, with_f, with_fixed = CASES[name]
     spec = spec.with_(precision="f32", storage="f32")
+    # the context residual of the same problem: no loads / no supports where those are left out
+    spec = spec.with_(loads=spec.loads if with_f else [], boxes=spec.boxes if with_fixed else [])
     prob = problem.Problem(spec)
     phi = W.random_design(spec, seed=31)
     prob.set_design(phi)
@@ -44,21 +57,32 @@ def test_static_residual_norm_matches_context_residual(spec):
     F = torch.tensor(Fh, device="cuda")
     fixed = torch.tensor(fixh, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
-    for call in range(2):
+    for call in range(2):  # two calls in a row share the static scratch
         u = W.random_state(spec, seed=40 + call).astype(np.float32)
         prob.set_state(u)
         ref, _ = prob.residual(with_field=False)
         ud = torch.tensor(u, device="cuda")
         out = ctypes.c_double(-1.0)
         st = lib.petto_residual_norm_static(ctypes.byref(grid), spec.nu, ctypes.c_void_p(ud.data_ptr()),
-                                            ctypes.c_void_p(E.data_ptr()), ctypes.c_void_p(F.data_ptr()),
-                                            ctypes.c_void_p(fixed.data_ptr()), ctypes.byref(out),
-                                            ctypes.c_void_p(stream))
+                                            ctypes.c_void_p(E.data_ptr()),
+                                            ctypes.c_void_p(F.data_ptr()) if with_f else None,
+                                            ctypes.c_void_p(fixed.data_ptr()) if with_fixed else None,
+                                            ctypes.byref(out), ctypes.c_void_p(stream))
         assert st == C.PETTO_OK
         assert abs(out.value - ref) <= 1e-5 * ref, (call, out.value, ref)
-    big = C.petto_grid(3, 200, 200, 200, 1.0)
-    out = ctypes.c_double(0.0)
-    assert lib.petto_residual_norm_static(ctypes.byref(big), 0.3, ctypes.c_void_p(ud.data_ptr()),
-                                          ctypes.c_void_p(E.data_ptr()), None, None, ctypes.byref(out),
-                                          None) == C.PETTO_EINVAL
     prob.close()
+
+
+def test_static_residual_norm_rejects_grids_above_the_limit():
+    """One node more than the 4 194 304 the static scratch covers: PETTO_EINVAL, checked
+    before any launch (the small buffers passed are never read)."""
+    torch = pytest.importorskip("torch")
+    from paper_2509_06971_gb300 import capi as C
+    lib = C.load()
+    buf = torch.zeros(16, device="cuda")
+    out = ctypes.c_double(0.0)
+    for grid in (C.petto_grid(2, 4, 838860, 0, 1.0),      # 5 x 838 861 = 4 194 305 nodes
+                 C.petto_grid(3, 200, 200, 200, 1.0)):
+        assert lib.petto_residual_norm_static(ctypes.byref(grid), 0.3, ctypes.c_void_p(buf.data_ptr()),
+                                              ctypes.c_void_p(buf.data_ptr()), None, None, ctypes.byref(out),
+                                              None) == C.PETTO_EINVAL
