@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <utility>
 #include <string>
 #include <tuple>
@@ -19,6 +20,10 @@
 #include "petto_internal.cuh"
 
 using namespace petto;
+
+// Grids from this many nodes get their sweep kernel picked by the autotuner on the first
+// solve (the tuning then costs well under one solve; below it the default choice stands).
+constexpr int64_t AUTOTUNE_MIN_NODES = 1 << 20;
 
 struct petto_ctx {
     // problem
@@ -76,6 +81,7 @@ struct petto_ctx {
     std::vector<GraphEntry> graphs;
     bool trace = false;  // PETTO_TRACE set: print every check residual to stderr
     int wait_tries = WAIT_TRIES;  // attempts of each bounded ring wait of the TMA sweeps
+    bool tune_pending = false;    // the first solve picks the sweep kernel by timing (large 3D grids)
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
     std::vector<int> ev_count;  // sweeps covered by each pending event pair
@@ -649,6 +655,10 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
     ctx->trace = std::getenv("PETTO_TRACE") != nullptr;
     ctx->L = make_layout(ctx->dim, ctx->nx, ctx->ny, ctx->nz);
     ctx->tiling = choose_tiling(ctx->L, ctx->physics, ctx->precision, ctx->nrhs);
+    // large 3D elastic FP32 grids: the first solve times the applicable sweep kernels and
+    // keeps the fastest (once per grid shape in the process), unless a kernel is chosen first
+    ctx->tune_pending = ctx->dim == 3 && ctx->physics == 0 && ctx->precision == PETTO_F32 &&
+                        ctx->L.nnodes() >= AUTOTUNE_MIN_NODES && !std::getenv("PETTO_MARCH");
     build_opconst(ctx);
 
     // supports
@@ -1303,6 +1313,34 @@ petto_status sweep_phase(petto_ctx *ctx, const petto_solve_opts *o, SolveState &
     return PETTO_OK;
 }
 
+// The first solve of a large 3D grid times the applicable sweep kernels (petto_autotune) and
+// keeps the fastest; the choice is remembered per grid shape for the rest of the process.
+std::mutex g_tune_mutex;
+std::map<std::string, std::string> g_tuned;
+
+petto_status tune_first_solve(petto_ctx *ctx) {
+    if (!ctx->tune_pending) return PETTO_OK;
+    ctx->tune_pending = false;
+    const std::string key = std::to_string(ctx->dim) + ":" + std::to_string(ctx->nx) + "x" + std::to_string(ctx->ny) +
+                            "x" + std::to_string(ctx->nz) + ":r" + std::to_string(ctx->nrhs) + ":p" +
+                            std::to_string(ctx->physics) + std::to_string(ctx->precision);
+    std::string name;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) name = it->second;
+    }
+    if (!name.empty()) return petto_select_kernel(ctx, name.c_str());
+    petto_status st = petto_autotune(ctx, 10, nullptr, 0);
+    if (st != PETTO_OK) return st;
+    char nm[64];
+    st = petto_kernel_info(ctx, nm, sizeof nm, nullptr);
+    if (st != PETTO_OK) return st;
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    g_tuned[key] = nm;
+    return PETTO_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1314,7 +1352,8 @@ petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_sol
         return fail(ctx, PETTO_EINVAL, "negative count");
     if (o->momentum < 0 || o->momentum > 2) return fail(ctx, PETTO_EINVAL, "momentum is 0, 1 or 2");
     CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
-    petto_status st = set_ctrl(ctx, CT_RESTART_AT, 0);
+    petto_status st = tune_first_solve(ctx);
+    if (st == PETTO_OK) st = set_ctrl(ctx, CT_RESTART_AT, 0);
     if (st == PETTO_OK) st = set_ctrl(ctx, CT_ERR, 0);  // a new solve: no wait has run out yet
     if (st != PETTO_OK) return st;
     SolveState S;
@@ -1530,6 +1569,7 @@ petto_status petto_set_keepout(petto_ctx *ctx, const int64_t *box, const double 
 }
 
 petto_status petto_set_owned_planes(petto_ctx *ctx, int64_t zlo, int64_t zhi, int64_t z_global) {
+    if (ctx) ctx->tune_pending = false;  // a slab keeps the kernel its decomposition chose
     if (!ctx) return PETTO_EINVAL;
     if (ctx->dim != 3) return fail(ctx, PETTO_EUNSUPPORTED, "slabs are z ranges of a 3D grid");
     const int NZ = ctx->L.NZ;
@@ -2344,6 +2384,7 @@ extern "C" {
 
 petto_status petto_select_kernel(petto_ctx *ctx, const char *name) {
     if (!ctx || !name) return fail(ctx, PETTO_EINVAL, "null argument");
+    ctx->tune_pending = false;
     const std::string want(name);
     for (auto &c : kernel_candidates(ctx)) {
         // "march2d" or "tma2" alone: the first (default-parameter) entry of that kernel
@@ -2377,6 +2418,7 @@ petto_status petto_kernel_info(petto_ctx *ctx, char *name, int name_len, int *rh
 // current state (restored afterwards) and keep the fastest.
 petto_status petto_autotune(petto_ctx *ctx, int n, char *report, int report_len) {
     if (!ctx || n < 1) return fail(ctx, PETTO_EINVAL, "bad arguments");
+    ctx->tune_pending = false;
     const std::vector<std::pair<std::string, Tiling>> cand = kernel_candidates(ctx);
     // keep the state: u (current) and w
     void *su = nullptr, *sw = nullptr;
