@@ -290,6 +290,29 @@ petto_status petto_set_keepout(petto_ctx *ctx, const int64_t *box, const double 
  * PETTO_EUNSUPPORTED in 2D.  Synchronises the stream. */
 petto_status petto_set_owned_planes(petto_ctx *ctx, int64_t zlo, int64_t zhi, int64_t z_global);
 
+/* Hooks of a decomposed state solve, supplied by the caller's transport (NCCL or gloo
+ * between ranks, copies between contexts of one process).
+ *   exchange   fills this slab's ghost planes with its neighbours' interface planes and
+ *              sends its own (petto_get_plane / petto_set_plane on ctx); called before every
+ *              sweep, by every slab in the same order
+ *   allreduce  replaces values[0..n) by their sums over all slabs
+ * Each returns PETTO_OK, or a status that ends the solve with that status. */
+typedef petto_status (*petto_exchange_fn)(petto_ctx *ctx, void *user);
+typedef petto_status (*petto_allreduce_fn)(double *values, int n, void *user);
+
+/* The state solve of petto_pt_solve (Sec. 2.2 hybrid APT -> PT schedule, checks every
+ * check_every sweeps, the divergence guard) on one slab of a z-decomposed grid: before every
+ * sweep exchange(ctx, user); the check residual and ||F|| are the whole grid's (allreduce of
+ * the slabs' sums), so every slab takes the same decisions.  Adaptive-restart momentum
+ * (momentum 1) tests the whole grid's <R, w> (allreduce on every fourth sweep, which
+ * synchronises the stream) and restarts every slab together; fixed momentum (0) and PT only
+ * (2) need no such test.  FP64 refinement is not decomposed: opts->refine is ignored, so an
+ * FP32 slab solve stops at the FP32 floor (about 1e-4 of ||F||).  rep as in petto_pt_solve,
+ * with the whole grid's residuals.  Every slab calls it with the same opts.  PETTO_EINVAL
+ * for a null hook or bad options; PETTO_ENOTCONV as petto_pt_solve. */
+petto_status petto_slab_solve(petto_ctx *ctx, const petto_solve_opts *opts, petto_exchange_fn exchange,
+                              petto_allreduce_fn allreduce, void *user, petto_solve_report *rep);
+
 /* Copy node plane k (local index) of the current state, every component (load cases
  * included), out to / in from a dense [ndof components][ny+1][nx+1] array in the sweep
  * precision (dtype must equal it).  on_device = 1: the array is device memory and the copy

@@ -68,6 +68,8 @@ class petto_pf_opts(ctypes.Structure):
 
 
 petto_step_cb = ctypes.CFUNCTYPE(None, ctypes.POINTER(_dbl), _vp)
+petto_exchange_fn = ctypes.CFUNCTYPE(_int, _vp, _vp)
+petto_allreduce_fn = ctypes.CFUNCTYPE(_int, ctypes.POINTER(_dbl), _int, _vp)
 
 _P = ctypes.POINTER
 _SIGS = {
@@ -102,6 +104,8 @@ _SIGS = {
     "petto_select_kernel": (_int, [_vp, ctypes.c_char_p]),
     "petto_kernel_info": (_int, [_vp, ctypes.c_char_p, _int, _P(_int)]),
     "petto_set_owned_planes": (_int, [_vp, _i64, _i64, _i64]),
+    "petto_slab_solve": (_int, [_vp, _P(petto_solve_opts), petto_exchange_fn, petto_allreduce_fn, _vp,
+                                _P(petto_solve_report)]),
     "petto_get_plane": (_int, [_vp, _i64, _vp, _int, _int]),
     "petto_set_plane": (_int, [_vp, _i64, _vp, _int, _int]),
     "petto_set_keepout": (_int, [_vp, _P(_i64), _P(_dbl), _dbl]),

@@ -82,6 +82,7 @@ struct petto_ctx {
     bool trace = false;  // PETTO_TRACE set: print every check residual to stderr
     int wait_tries = WAIT_TRIES;  // attempts of each bounded ring wait of the TMA sweeps
     bool tune_pending = false;    // the first solve picks the sweep kernel by timing (large 3D grids)
+    long long slab_restart_at = 0;  // petto_slab_solve: the last restart of the whole grid's momentum
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
     std::vector<int> ev_count;  // sweeps covered by each pending event pair
@@ -1417,6 +1418,94 @@ petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_sol
     }
     if (!std::isfinite(S.last)) return fail(ctx, PETTO_EDIVERGED, "residual not finite after PT fallback");
     if (o->mode == PETTO_SOLVE_TOL && !conv) return PETTO_ENOTCONV;
+    return PETTO_OK;
+}
+
+petto_status petto_slab_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_exchange_fn exchange,
+                              petto_allreduce_fn allreduce, void *user, petto_solve_report *rep) {
+    if (!ctx || !o || !exchange || !allreduce) return fail(ctx, PETTO_EINVAL, "null argument");
+    if (o->mode != PETTO_SOLVE_PAPER && o->mode != PETTO_SOLVE_TOL) return fail(ctx, PETTO_EINVAL, "bad mode");
+    if (o->n_apt < 0 || o->n_pt < 0 || o->max_sweeps < 0 || o->check_every < 0)
+        return fail(ctx, PETTO_EINVAL, "negative count");
+    if (o->momentum < 0 || o->momentum > 2) return fail(ctx, PETTO_EINVAL, "momentum is 0, 1 or 2");
+    petto_status st = tune_first_solve(ctx);
+    // ||F|| of the whole grid: each slab holds the loads of its own planes
+    double fn2 = ctx->f_norm * ctx->f_norm;
+    if (st == PETTO_OK) st = allreduce(&fn2, 1, user);
+    if (st != PETTO_OK) return st;
+    const double fn = std::sqrt(fn2);
+    CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
+    st = set_ctrl(ctx, CT_RESTART_AT, 0);
+    if (st == PETTO_OK) st = set_ctrl(ctx, CT_ERR, 0);
+    if (st != PETTO_OK) return st;
+    ctx->slab_restart_at = 0;
+    SolveState S;
+    S.use_pt = o->momentum == 2;
+    S.total = o->mode == PETTO_SOLVE_PAPER ? o->n_apt + o->n_pt : o->max_sweeps;
+    const int ce = o->check_every;
+    const double stop = o->mode == PETTO_SOLVE_TOL ? o->tol * fn : -1.0;
+    int reached = 0;
+    while (S.sweeps < S.total) {
+        const bool apt = !S.use_pt && (o->mode == PETTO_SOLVE_TOL || S.sweeps < o->n_apt);
+        st = exchange(ctx, user);
+        if (st != PETTO_OK) return st;
+        const bool check = ce > 0 && (S.sweeps + 1) % ce == 0;
+        const bool final_report = S.sweeps + 1 == S.total;
+        SweepCtl sc;
+        sc.adaptive = o->momentum == 1 ? 1 : 0;
+        // the restart test of the adaptive momentum, on the whole grid's <R, w>
+        sc.test_dot = apt && sc.adaptive && ((ce > 0 ? S.sweeps % ce : S.sweeps) % 4) == 3;
+        sc.idx = S.sweeps;
+        st = one_sweep(ctx, apt ? 0 : 1, o->a, o->b, o->s1, o->local_dt, check || final_report, sc);
+        if (st != PETTO_OK) return st;
+        if (apt) ++S.na; else ++S.np;
+        ++S.sweeps;
+        if (sc.test_dot) {
+            // the kernel decided on this slab's own sum; the decision is the whole grid's
+            double ctrl[CT_N];
+            CK(cudaMemcpyAsync(ctrl, ctx->ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            double dot = ctrl[CT_DOT];
+            st = allreduce(&dot, 1, user);
+            if (st != PETTO_OK) return st;
+            long long at = 0;
+            std::memcpy(&at, &ctrl[CT_RESTART_AT], sizeof(at));
+            if (dot < 0.0) at = S.sweeps;
+            else if (at == S.sweeps) {
+                // this slab's own sum was negative but the grid's is not: undo its restart
+                at = ctx->slab_restart_at;
+            }
+            ctx->slab_restart_at = at;
+            st = set_ctrl(ctx, CT_RESTART_AT, at);
+            if (st != PETTO_OK) return st;
+        }
+        if (!(check || final_report)) continue;
+        double scal[SC_N];
+        st = read_scal(ctx, scal);
+        if (st != PETTO_OK) return st;
+        double r2 = scal[SC_RES];
+        st = allreduce(&r2, 1, user);
+        if (st != PETTO_OK) return st;
+        const double rn = std::sqrt(r2);
+        S.last = rn;
+        bool ended = false;
+        st = apply_check(ctx, o, S, rn, check, stop, 0, &ended, &reached);
+        if (st != PETTO_OK) return st;
+        if (ended) break;
+    }
+    if (rep) {
+        rep->sweeps = S.sweeps;
+        rep->apt_sweeps = S.na;
+        rep->pt_sweeps = S.np;
+        rep->res_norm = S.last;
+        rep->f_norm = fn;
+        rep->rel_res = fn > 0 ? S.last / fn : NAN;
+        rep->r_pde = NAN;
+        rep->converged = reached ? 1 : 0;
+        rep->fell_back_to_pt = S.fell ? 1 : 0;
+    }
+    if (!std::isfinite(S.last) && S.sweeps > 0) return fail(ctx, PETTO_EDIVERGED, "residual not finite after PT fallback");
+    if (o->mode == PETTO_SOLVE_TOL && !reached) return PETTO_ENOTCONV;
     return PETTO_OK;
 }
 

@@ -311,6 +311,39 @@ class Problem:
                                   int(bool(kw.get("local_dt", s.local_dt))), momentum,
                                   int(bool(kw.get("refine", True))))
 
+    def slab_solve(self, exchange, allreduce, mode=None, **kw) -> dict:
+        """The state solve of one slab of a decomposed grid (petto_slab_solve): exchange()
+        fills the ghost planes before every sweep, allreduce(list of floats) returns their sums
+        over the slabs.  Options as solve() (no FP64 refinement)."""
+        o = self.solve_opts(mode, **kw)
+        errors = []
+
+        def _ex(ctx, user):
+            try:
+                exchange()
+                return C.PETTO_OK
+            except BaseException as e:  # noqa: BLE001 -- handed back to the caller below
+                errors.append(e)
+                return C.PETTO_EINVAL
+
+        def _ar(values, n, user):
+            try:
+                out = allreduce([values[i] for i in range(n)])
+                for i in range(n):
+                    values[i] = float(out[i])
+                return C.PETTO_OK
+            except BaseException as e:  # noqa: BLE001
+                errors.append(e)
+                return C.PETTO_EINVAL
+
+        ex, ar = C.petto_exchange_fn(_ex), C.petto_allreduce_fn(_ar)
+        rep = C.petto_solve_report()
+        st = self.lib.petto_slab_solve(self.ctx, ctypes.byref(o), ex, ar, None, ctypes.byref(rep))
+        if errors:
+            raise errors[0]
+        self._ck(st, allow=(C.PETTO_OK, C.PETTO_ENOTCONV))
+        return _report(rep, st)
+
     def solve(self, mode=None, **kw) -> dict:
         o = self.solve_opts(mode, **kw)
         rep = C.petto_solve_report()

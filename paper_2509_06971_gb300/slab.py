@@ -19,8 +19,10 @@ Two drivers share this host logic:
   the planes with point-to-point messages (NCCL between GPUs, gloo between host processes)
   and the residual with an all-reduce.
 
-Only the state solve is decomposed (sweeps, residuals, a fixed-momentum APT/PT solve); the
-design step stays with a whole-grid context.
+The state solve is decomposed: sweeps, residuals, and the solve loop itself, which runs in
+the library (``petto_slab_solve``) with this module's exchange and all-reduce as its hooks
+(fixed or adaptive-restart momentum, PT; the FP64 refinement is not decomposed).  The design
+step stays with a whole-grid context.
 """
 from __future__ import annotations
 
@@ -137,25 +139,20 @@ class _SlabDriver:
 
     def solve(self, tol: float = 1e-6, kind: int = 0, a: float | None = None, b: float | None = None,
               s1: float | None = None, local_dt: bool | None = None, check_every: int = 50,
-              max_sweeps: int = 200000) -> dict:
-        """Fixed-momentum APT (kind 0) or PT (kind 1) sweeps with an exchange before each,
-        until ||R|| <= tol ||F|| at a check (every check_every sweeps) or max_sweeps."""
-        spec = self.spec
-        a = spec.apt_a if a is None else a
-        b = spec.apt_b if b is None else b
-        s1 = spec.pt_s1 if s1 is None else s1
-        local_dt = spec.local_dt if local_dt is None else local_dt
-        fn = self.f_norm
-        done, r2 = 0, float("nan")
-        while done < max_sweeps:
-            n = min(check_every, max_sweeps - done)
-            r2 = self.sweep(kind, n, a, b, s1, local_dt)
-            done += n
-            if not np.isfinite(r2):
-                break
-            if fn == 0.0 or np.sqrt(r2) <= tol * fn:
-                return {"sweeps": done, "rel_res": np.sqrt(r2) / fn if fn else 0.0, "converged": True}
-        return {"sweeps": done, "rel_res": np.sqrt(r2) / fn if fn else float("nan"), "converged": False}
+              max_sweeps: int = 200000, momentum: int | None = None) -> dict:
+        """The state solve over the slabs, one petto_slab_solve per slab (the loop runs in the
+        library; this driver supplies its exchange and all-reduce hooks): APT with fixed
+        momentum (kind 0, momentum 0), PT only (kind 1, momentum 2) or the adaptive-restart
+        momentum (momentum 1), until ||R|| <= tol ||F|| of the whole grid at a check (every
+        check_every sweeps) or max_sweeps."""
+        if momentum is None:
+            momentum = 0 if kind == 0 else 2
+        kw = dict(mode=1, tol=tol, check_every=check_every, max_sweeps=max_sweeps, momentum=momentum, refine=False)
+        # constants left out take the problem's defaults (Problem.solve_opts), as a whole-grid solve does
+        kw.update({k: v for k, v in dict(a=a, b=b, s1=s1, local_dt=local_dt).items() if v is not None})
+        rep = self._slab_solve(kw)
+        return {"sweeps": rep["sweeps"], "rel_res": rep["rel_res"], "converged": rep["converged"],
+                "fell_back_to_pt": rep["fell_back_to_pt"]}
 
 
 class SlabGrid(_SlabDriver):
@@ -243,6 +240,48 @@ class SlabGrid(_SlabDriver):
         self.exchange()
         return float(sum(p.residual(with_field=False)[0] for p in self.probs))
 
+    def _slab_solve(self, kw):
+        """One host thread per slab runs its petto_slab_solve; the hooks meet at a barrier:
+        the first slab's thread makes every interface copy (all contexts share one stream, so
+        the copies fall between the slabs' sweeps), and the sums are taken in slab order in
+        every thread, so all slabs take the same decisions."""
+        import threading
+        n = len(self.probs)
+        bar = threading.Barrier(n, timeout=600)
+        vals = [None] * n
+        reps, errs = [None] * n, []
+
+        def hooks(s):
+            def exchange():
+                bar.wait()
+                if s == 0:
+                    self.exchange()
+                bar.wait()
+
+            def allreduce(v):
+                vals[s] = list(v)
+                bar.wait()
+                out = [sum(vals[q][i] for q in range(n)) for i in range(len(v))]
+                bar.wait()
+                return out
+            return exchange, allreduce
+
+        def run(s):
+            try:
+                reps[s] = self.probs[s].slab_solve(*hooks(s), **kw)
+            except BaseException as e:  # noqa: BLE001 -- re-raised below
+                errs.append(e)
+                bar.abort()
+
+        threads = [threading.Thread(target=run, args=(s,)) for s in range(n)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        if errs:
+            raise errs[0]
+        return reps[0]
+
 
 class DistributedSlabs(_SlabDriver):
     """One slab per rank of a torch.distributed group (rank r holds slab r).  Planes move
@@ -324,6 +363,14 @@ class DistributedSlabs(_SlabDriver):
             if last:
                 r2 = self._allreduce(v)
         return r2
+
+    def _allreduce_list(self, values):
+        t = _torch().tensor(list(values), dtype=_torch().float64, device=self.device)
+        self.dist.all_reduce(t, group=self.group)
+        return t.tolist()
+
+    def _slab_solve(self, kw):
+        return self.prob.slab_solve(self.exchange, self._allreduce_list, **kw)
 
     def set_design(self, phi):
         self.prob.set_design(slab_cells(phi, self.spec, self.g))

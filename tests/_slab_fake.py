@@ -72,3 +72,32 @@ class OracleSlab:
                 g[:self.zlo] = gk[:self.zlo]
                 g[self.zhi + 1:] = gk[self.zhi + 1:]
         return r2
+
+    def slab_solve(self, exchange, allreduce, mode=1, tol=1e-6, a=None, b=None, s1=None, local_dt=None,
+                   check_every=50, max_sweeps=200000, momentum=0, refine=False, **_):
+        """The hook protocol of petto_slab_solve for the host stand-in: an exchange before every
+        sweep, the whole grid's ||F|| and check residuals through allreduce.  Fixed momentum
+        (0) or PT only (2)."""
+        if momentum not in (0, 2) or mode != 1:
+            raise NotImplementedError("the host stand-in runs fixed-momentum APT or PT to a tolerance")
+        sp = self.spec  # the constants left out are the workload's, as Problem.solve_opts takes them
+        a = sp.apt_a if a is None else a
+        b = sp.apt_b if b is None else b
+        s1 = sp.pt_s1 if s1 is None else s1
+        local_dt = sp.local_dt if local_dt is None else local_dt
+        free = self._grid(np.where(self.fixed == 0, self.F, 0.0))[self.zlo:self.zhi + 1]
+        fn = float(np.sqrt(allreduce([float((free ** 2).sum())])[0]))
+        kind = 0 if momentum == 0 else 1
+        sweeps, rn = 0, float("nan")
+        while sweeps < max_sweeps:
+            exchange()
+            check = check_every > 0 and (sweeps + 1) % check_every == 0
+            r2 = self.sweep(kind, 1, a, b, s1, local_dt)
+            sweeps += 1
+            if check or sweeps == max_sweeps:
+                rn = float(np.sqrt(allreduce([r2])[0]))
+                if not np.isfinite(rn) or rn <= tol * fn:
+                    break
+        conv = bool(np.isfinite(rn) and rn <= tol * fn)
+        return {"sweeps": sweeps, "rel_res": rn / fn if fn else float("nan"), "converged": conv,
+                "fell_back_to_pt": False}

@@ -143,3 +143,27 @@ def test_slab_argument_checks(P):
     u = p3.get_state(dtype=np.float32).reshape(3, 13, 13, 25)
     assert np.array_equal(u[:, 5], pl) and not u[:, 4].any()
     p3.close()
+
+
+@pytest.mark.parametrize("precision,kernel,n_slabs", [("f64", None, 2), ("f64", None, 3), ("f32", "tma3", 3)])
+def test_library_slab_solve_with_adaptive_momentum_equals_whole_grid(P, precision, kernel, n_slabs):
+    """petto_slab_solve (the solve loop in the library, with the driver's exchange and
+    all-reduce hooks) with the adaptive-restart momentum: its restart tests and checks use
+    the whole grid's <R, w> and ||R|| (sums over the slabs), so it takes the whole grid's
+    solve's decisions: the same sweep counts and the same field (sums in another order can
+    only move a decision that sits on a tie)."""
+    spec = _spec(precision=precision)
+    tol = 1e-9 if precision == "f64" else 1e-3
+    kw = dict(tol=tol, check_every=20, max_sweeps=60000)
+    p = P.Problem(spec)
+    if kernel:
+        p.select_kernel(kernel)
+    rep_w = p.solve(mode=1, momentum=1, refine=False, local_dt=True, **kw)
+    uw = p.get_state(dtype=p.np_dtype)
+    p.close()
+    with S.SlabGrid(spec, n_slabs, kernel=kernel) as g:
+        rep_s = g.solve(momentum=1, local_dt=True, **kw)
+        us = g.get_state(dtype=uw.dtype)
+    assert rep_w["converged"] and rep_s["converged"], (rep_w, rep_s)
+    assert rep_s["sweeps"] == rep_w["sweeps"]
+    _same(us, uw, spec)
