@@ -16,6 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def header_functions():
     src = open(os.path.join(ROOT, "include", "petto.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"typedef[^;]*;", "", src)  # function-pointer types of the hooks are not functions
     return sorted(set(re.findall(r"\b(petto_[a-z_0-9]+)\s*\(", src)))
 
 
