@@ -41,6 +41,8 @@ from paper_2509_06971_gb300 import workloads as W  # noqa: E402
 WORKLOADS = {
     "cantilever3d_256x128x128": lambda: W.cantilever3d(256, 128, 128),
     "cantilever2d_1024x512": lambda: W.cantilever2d(1024, 512),
+    # a 2D grid larger than L2 (8.4 M nodes, 302 MB per sweep): sweeps several per pass
+    "cantilever2d_4096x2048": lambda: W.cantilever2d(4096, 2048),
     "heat2d_1024x1024": lambda: W.heat2d(1024),
     "multimat3d_384x192x192_bf16": lambda: W.multimat3d(storage="bf16"),
     "multimat3d_384x192x192_fp16": lambda: W.multimat3d(storage="f16"),
@@ -71,7 +73,7 @@ METRIC = "APT Gcell-sweeps/s & % HBM roofline; s/design-iter at rel.res 1e-6"
 # kernel from one ncu capture of the workload: the refinement sweep of the lean two-row
 # marching kernel, nearly all of the sweeps of a design iteration.  Keyed by workload and
 # kernel name, so that any other kernel reports null; re-captured whenever that kernel changes.
-NCU_TRAFFIC = {("cantilever3d_256x128x128", "tma3/zs12"): 171944960 + 64017152}
+NCU_TRAFFIC = {("cantilever3d_256x128x128", "tma3/zs12"): 171960576 + 64645888}
 
 
 def sweep_bytes(spec, tsize=4, method="apt"):

@@ -49,6 +49,7 @@ struct petto_ctx {
     void *u[2] = {nullptr, nullptr};
     void *w = nullptr, *E = nullptr, *phi = nullptr, *s = nullptr, *dscr = nullptr, *mu = nullptr;
     void *rbuf = nullptr, *stage = nullptr;
+    void *w_alt = nullptr;  // second w buffer of the 2D sweeps several per launch (kind 7)
     size_t stage_bytes = 0;
     double *scal = nullptr;
     unsigned *counter = nullptr;
@@ -77,6 +78,9 @@ struct petto_ctx {
         const void *rhs;
         double a, b, s1;
         cudaGraphExec_t exec;
+        const void *w;     // the w buffer current when the chunk starts
+        int flips, swaps;  // ping-pong flips of u and swaps of w over the chunk (its launches)
+        int launches;      // kernel launches of the chunk
     };
     std::vector<GraphEntry> graphs;
     bool trace = false;  // PETTO_TRACE set: print every check residual to stderr
@@ -368,16 +372,22 @@ struct SweepCtl {
     const void *rhs = nullptr;
 };
 
-// one sweep kind (0 APT, 1 PT) from u[cur] into u[1-cur]; flips cur
+// Sweeps of one kind (0 APT, 1 PT) from u[cur] into u[1-cur] in one launch, flipping cur:
+// one sweep, or (the 2D kernel that runs several per launch, kind 7) nsw sweeps with indices
+// sc.idx .. sc.idx + nsw - 1, the last of them the one that sums R^2 / tests <R, w> (the
+// caller ends its groups on those sweeps); w then goes to the second buffer and the two
+// swap.
 petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, int local_dt, bool want_res,
-                       const SweepCtl &sc = SweepCtl()) {
+                       const SweepCtl &sc = SweepCtl(), int nsw = 1) {
+    if (nsw > 1 && (ctx->tiling.kind != 7 || nsw > ctx->tiling.ly || !ctx->w_alt))
+        return fail(ctx, PETTO_EINVAL, "several sweeps per launch need the 2D kernel that runs them");
     SweepArgs A = base_sweep_args(ctx);
     A.mode = kind;
     A.local_dt = local_dt;
     A.want_res = want_res ? 1 : 0;
     A.adaptive = sc.adaptive;
     A.test_dot = kind == 0 && sc.adaptive ? sc.test_dot : 0;
-    A.sweep_idx = sc.idx;
+    A.sweep_idx = sc.idx + nsw - 1;
     A.base_from_ctrl = sc.base_from_ctrl;
     A.rhs = sc.rhs;
     A.rhs_half = sc.rhs && sc.rhs == ctx->rhs32 && ctx->rhs_half;
@@ -390,6 +400,8 @@ petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, 
     A.u_in = ctx->u[ctx->cur];
     A.u_out = ctx->u[1 - ctx->cur];
     A.w = ctx->w;
+    A.tb_k = nsw;
+    A.w_out = nsw > 1 ? ctx->w_alt : ctx->w;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ctx->profiling && !sc.base_from_ctrl) {
         for (cudaEvent_t *e : {&e0, &e1}) {
@@ -406,12 +418,23 @@ petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, 
     if (ctx->profiling && !sc.base_from_ctrl) {
         CK(cudaEventRecord(e1, ctx->stream));
         ctx->ev_pending.emplace_back(e0, e1);
-        ctx->ev_count.push_back(1);
+        ctx->ev_count.push_back(nsw);
         ctx->ev_rhs.push_back(sc.rhs != nullptr);
     }
     ctx->launches++;
     ctx->cur ^= 1;
+    if (nsw > 1) std::swap(ctx->w, ctx->w_alt);
     return PETTO_OK;
+}
+
+// Sweeps per launch for the group starting at sweep j of a run of n (indices counted from
+// the run's start, which sits on a multiple of 4): the kernel's count, halved until the
+// group starts on a multiple of its size and fits the run.  Groups of 1, 2 or 4 aligned so
+// end every test sweep (j mod 4 = 3) and the run's last sweep.
+int sweep_group(const petto_ctx *ctx, int64_t j, int64_t n) {
+    int g = ctx->tiling.kind == 7 && ctx->w_alt ? ctx->tiling.ly : 1;
+    while (g > 1 && (j % g != 0 || j + g > n)) g >>= 1;
+    return g;
 }
 
 petto_status read_scal(petto_ctx *ctx, double *host) {
@@ -526,6 +549,13 @@ petto_status set_tiling(petto_ctx *ctx, const Tiling &t0) {
         CK(cudaMalloc(&ctx->partials, sizeof(double) * cap));
         ctx->partial_cap = cap;
     }
+    if (t.kind == 7) {
+        CK(tb2d_prepare());
+        if (!ctx->w_alt) {
+            CK(cudaMalloc(&ctx->w_alt, ctx->node_bytes()));
+            CK(cudaMemset(ctx->w_alt, 0, ctx->node_bytes()));
+        }
+    }
     CK(cudaMemcpy(ctx->tile_ptr, tptr.data(), sizeof(int) * (nt + 1), cudaMemcpyHostToDevice));
     if (!ent.empty()) CK(cudaMemcpy(ctx->loads, ent.data(), sizeof(LoadEntry) * ent.size(), cudaMemcpyHostToDevice));
     if ((t.kind >= 2 && t.kind <= 4) || t.kind == 6) {
@@ -593,7 +623,7 @@ void petto_destroy(petto_ctx *ctx) {
     }
     for (auto e : ctx->ev_free) cudaEventDestroy(e);
     clear_graphs(ctx);
-    void *bufs[] = {ctx->u[0], ctx->u[1], ctx->w, ctx->E, ctx->phi, ctx->s, ctx->dscr, ctx->mu, ctx->rbuf,
+    void *bufs[] = {ctx->u[0], ctx->u[1], ctx->w, ctx->w_alt, ctx->E, ctx->phi, ctx->s, ctx->dscr, ctx->mu, ctx->rbuf,
                     ctx->stage, ctx->scal, ctx->counter, ctx->tile_ptr, ctx->loads, ctx->partials,
                     ctx->gtile_ptr, ctx->gloads, ctx->ctrl, ctx->u64, ctx->r64, ctx->rhs32};
     for (void *b : bufs)
@@ -929,9 +959,13 @@ petto_status petto_sweep(petto_ctx *ctx, int kind, int64_t n, double a, double b
                          double *res_norm2) {
     if (!ctx || n < 0 || (kind != PETTO_SWEEP_APT && kind != PETTO_SWEEP_PT))
         return fail(ctx, PETTO_EINVAL, "bad sweep arguments");
-    for (int64_t t = 0; t < n; ++t) {
-        petto_status st = one_sweep(ctx, kind, a, b, s1, local_dt, res_norm2 && t == n - 1);
+    for (int64_t t = 0; t < n;) {
+        const int g = sweep_group(ctx, t, n);
+        SweepCtl sc;
+        sc.idx = t;
+        petto_status st = one_sweep(ctx, kind, a, b, s1, local_dt, res_norm2 && t + g == n, sc, g);
         if (st != PETTO_OK) return st;
+        t += g;
     }
     if (res_norm2) {
         if (n == 0) {
@@ -1031,26 +1065,34 @@ petto_status graph_chunk(petto_ctx *ctx, const petto_solve_opts *o, bool apt, in
     petto_ctx::GraphEntry *ge = nullptr;
     for (auto &g : ctx->graphs)
         if (g.apt == apt && g.local_dt == o->local_dt && g.adaptive == adaptive && g.cur == ctx->cur && g.ce == ce &&
-            g.res_last == (res_last ? 1 : 0) && g.rhs == rhs && g.a == o->a && g.b == o->b && g.s1 == o->s1)
+            g.res_last == (res_last ? 1 : 0) && g.rhs == rhs && g.a == o->a && g.b == o->b && g.s1 == o->s1 &&
+            g.w == ctx->w)
             ge = &g;
     if (!ge) {
         if (ctx->graphs.size() >= 8) clear_graphs(ctx);
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
         const int cur0 = ctx->cur;
+        void *const w0 = ctx->w;
         const int64_t l0 = ctx->launches;
         petto_status st = PETTO_OK;
-        for (int j = 0; j < ce && st == PETTO_OK; ++j) {
+        int flips = 0, swaps = 0;
+        for (int j = 0; j < ce && st == PETTO_OK;) {
+            const int g = sweep_group(ctx, j, ce);
             SweepCtl sc;
             sc.adaptive = adaptive;
-            sc.test_dot = (j % 4) == 3;
+            sc.test_dot = ((j + g - 1) % 4) == 3;
             sc.idx = j;
             sc.base_from_ctrl = 1;
             sc.rhs = rhs;
-            st = one_sweep(ctx, apt ? 0 : 1, o->a, o->b, o->s1, o->local_dt, res_last && j == ce - 1, sc);
+            st = one_sweep(ctx, apt ? 0 : 1, o->a, o->b, o->s1, o->local_dt, res_last && j + g == ce, sc, g);
+            ++flips;
+            if (g > 1) ++swaps;
+            j += g;
         }
         cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
         ctx->cur = cur0;
+        if (ctx->w != w0) std::swap(ctx->w, ctx->w_alt);
         ctx->launches = l0;
         if (st != PETTO_OK) {
             if (graph) cudaGraphDestroy(graph);
@@ -1062,7 +1104,7 @@ petto_status graph_chunk(petto_ctx *ctx, const petto_solve_opts *o, bool apt, in
         cudaGraphDestroy(graph);
         CK(ei);
         petto_ctx::GraphEntry g{apt ? 1 : 0, o->local_dt, adaptive, ctx->cur, ce, res_last ? 1 : 0, rhs, o->a, o->b,
-                                o->s1, exec};
+                                o->s1, exec, w0, flips, swaps, flips};
         ctx->graphs.push_back(g);
         ge = &ctx->graphs.back();
     }
@@ -1087,8 +1129,10 @@ petto_status graph_chunk(petto_ctx *ctx, const petto_solve_opts *o, bool apt, in
         ctx->ev_count.push_back(ce);
         ctx->ev_rhs.push_back(rhs != nullptr);
     }
-    ctx->launches += ce + 1;
-    // ce is even: the buffer roles are back where they started
+    ctx->launches += ge->launches + 1;
+    // the buffer roles after the chunk's launches
+    if (ge->flips & 1) ctx->cur ^= 1;
+    if (ge->swaps & 1) std::swap(ctx->w, ctx->w_alt);
     *done = true;
     return PETTO_OK;
 }
@@ -1542,9 +1586,12 @@ petto_status petto_sweep_rhs(petto_ctx *ctx, int kind, int64_t n, double a, doub
     }
     SweepCtl sc;
     sc.rhs = rhs;
-    for (int64_t t = 0; t < n; ++t) {
-        st = one_sweep(ctx, kind, a, b, s1, local_dt, res_norm2 && t == n - 1, sc);
+    for (int64_t t = 0; t < n;) {
+        const int g = sweep_group(ctx, t, n);
+        sc.idx = t;
+        st = one_sweep(ctx, kind, a, b, s1, local_dt, res_norm2 && t + g == n, sc, g);
         if (st != PETTO_OK) return st;
+        t += g;
     }
     if (res_norm2) {
         if (n == 0) {
@@ -2404,6 +2451,7 @@ namespace {
 
 // The sweep-kernel variants that apply to a problem, by name: the 3D marching kernels
 // (TMA two-row, TMA one-row 32x8 / 32x16, register-staged) x z-segment lengths, the 2D
+// kernel running several sweeps per launch x sweeps per launch (region in nodes), the 2D
 // y-marching kernel x rows per warp, and the node-gather kernel x block shapes.
 std::vector<std::pair<std::string, Tiling>> kernel_candidates_all(const petto_ctx *ctx);
 
@@ -2448,6 +2496,13 @@ std::vector<std::pair<std::string, Tiling>> kernel_candidates_all(const petto_ct
         }
         // and the node gather below (slower here, but it takes slabs of any kind)
     }
+    if (L.dim == 2 && ctx->nrhs == 1)
+        for (int k : {4, 2}) {
+            const Tiling t = tb2d_tiling(L, ctx->physics, ctx->precision, k);
+            cand.emplace_back("tb2d/k" + std::to_string(k) + "/" + std::to_string(t.ox + 2 * k) + "x" +
+                                  std::to_string(t.oy + 2 * k),
+                              t);
+        }
     if (march2d_ok(ctx))
         for (int ly : {4, 8, 16}) {
             const Tiling t = march2d_tiling(L, ly);
@@ -2475,6 +2530,19 @@ petto_status petto_select_kernel(petto_ctx *ctx, const char *name) {
     if (!ctx || !name) return fail(ctx, PETTO_EINVAL, "null argument");
     ctx->tune_pending = false;
     const std::string want(name);
+    // "tb2d/k<K>/<rx>x<ry>": the 2D kernel of K sweeps per launch on a region of rx x ry
+    // nodes (output tile rx - 2K by ry - 2K, at least 4 x 4; shared memory within the limit)
+    int k = 0, rx = 0, ry = 0;
+    if (ctx->L.dim == 2 && ctx->nrhs == 1 && std::sscanf(name, "tb2d/k%d/%dx%d", &k, &rx, &ry) == 3) {
+        if ((k != 1 && k != 2 && k != 4) || rx - 2 * k < 4 || ry - 2 * k < 4)
+            return fail(ctx, PETTO_EINVAL, "tb2d: K is 1, 2 or 4 and the output tile at least 4 x 4");
+        int dev = 0, opt = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&opt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (tb2d_smem(rx, ry, ctx->ncomp, ctx->precision) + 1024 > (size_t)opt)
+            return fail(ctx, PETTO_EINVAL, "tb2d: the region does not fit in shared memory");
+        return set_tiling(ctx, tb2d_tiling(ctx->L, ctx->physics, ctx->precision, k, rx, ry));
+    }
     for (auto &c : kernel_candidates(ctx)) {
         // "march2d" or "tma2" alone: the first (default-parameter) entry of that kernel
         if (c.first == want || c.first.compare(0, want.size() + 1, want + "/") == 0) return set_tiling(ctx, c.second);
@@ -2486,10 +2554,13 @@ petto_status petto_kernel_info(petto_ctx *ctx, char *name, int name_len, int *rh
     if (!ctx) return fail(ctx, PETTO_EINVAL, "null context");
     const Tiling &t = ctx->tiling;
     std::string nm = "custom";
-    for (auto &c : kernel_candidates(ctx)) {
+    if (t.kind == 7)
+        nm = "tb2d/k" + std::to_string(t.ly) + "/" + std::to_string(t.ox + 2 * t.ly) + "x" +
+             std::to_string(t.oy + 2 * t.ly);
+    else for (auto &c : kernel_candidates(ctx)) {
         const Tiling q = own_planes(ctx, c.second);
         if (q.kind == t.kind && q.bx == t.bx && q.by == t.by && q.zs == t.zs && q.ox == t.ox && q.oy == t.oy &&
-            (q.kind != 5 || q.ly == t.ly)) {
+            ((q.kind != 5 && q.kind != 7) || q.ly == t.ly)) {
             nm = c.first;
             break;
         }
@@ -2528,9 +2599,11 @@ petto_status petto_autotune(petto_ctx *ctx, int n, char *report, int report_len)
         if (st != PETTO_OK) break;
         double ms = 0;
         int64_t cnt = 0;
-        for (int t = 0; t < n + 2 && st == PETTO_OK; ++t) {
-            if (t == 2) st = petto_profile_read(ctx, &ms, &cnt, nullptr);  // drop two warm-up sweeps
-            if (st == PETTO_OK) st = one_sweep(ctx, 0, 0.99, 0.5, 0.5, 1, false);
+        // launches of as many sweeps as the kernel runs per launch: two to warm up, then n sweeps
+        const int g = sweep_group(ctx, 0, 4);
+        for (int64_t t = 0; t < n + 2 * g && st == PETTO_OK; t += g) {
+            if (t == 2 * g) st = petto_profile_read(ctx, &ms, &cnt, nullptr);
+            if (st == PETTO_OK) st = one_sweep(ctx, 0, 0.99, 0.5, 0.5, 1, false, SweepCtl(), g);
         }
         if (st == PETTO_OK) st = petto_profile_read(ctx, &ms, &cnt, nullptr);
         if (st != PETTO_OK) break;

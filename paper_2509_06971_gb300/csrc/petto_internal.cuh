@@ -126,6 +126,12 @@ struct SweepArgs {
     double *res2;             // receives sum R^2 (if want_res)
     RedBuf red;
     int wait_tries = WAIT_TRIES;  // TMA marching kernels: attempts of each bounded ring wait
+    // 2D sweeps several per launch (sweep2d_tb, kind 7): this launch runs tb_k sweeps, the
+    // last of them with index sweep_idx (the R^2 and <R, w> sums are taken on that one); w
+    // is read from w and written to w_out, a second buffer when tb_k > 1 (a block reads the
+    // old w of the halo nodes it shares with its neighbours)
+    int tb_k = 1;
+    void *w_out = nullptr;
 };
 
 // ---------------------------------------------------------------- batches
@@ -292,8 +298,10 @@ struct Tiling {
     int ox, oy;        // output nodes per tile in x, y (== bx, by for gather kernels)
     int kind;          // 0 gather, 1 3D z-marching (register-staged), 2/3 3D TMA one row per
                        // thread (32x8 / 32x16), 4 3D TMA two rows per thread, 5 2D y-marching,
-                       // 6 3D TMA two rows per thread, lean per-plane path
-    int ly;            // kind 5: output rows per warp (a block's warps take consecutive segments)
+                       // 6 3D TMA two rows per thread, lean per-plane path, 7 2D sweeps several per
+                       // launch on a shared-memory copy of the tile and its halo
+    int ly;            // kind 5: output rows per warp (a block's warps take consecutive segments);
+                       // kind 7: sweeps per launch (1, 2 or 4)
     int zlo, zn;       // 3D: output node planes [zlo, zlo + zn) (zn = 0: all planes, zlo = 0)
     int zb;            // first plane of the first z tile / segment (<= zlo)
     int order;         // 0: tiles numbered x fastest; 1: z fastest (tile column by column)
@@ -342,6 +350,16 @@ cudaError_t launch_march3d_tma3(const SweepArgs &a, const Tiling &t, const TmaMa
 // the two-row marching kernels (kinds 4 and 6): one tiling, one set of tensor maps, FP16
 // refinement right-hand side, slabs of a decomposed grid
 inline bool two_row_kind(int kind) { return kind == 4 || kind == 6; }
+
+// 2D sweeps several per launch (kind 7).  A block stages the region of (ox + 2 ly) x
+// (oy + 2 ly) nodes around its ox x oy output tile; rx, ry give that region for ly sweeps.
+constexpr int TB_THREADS = 256;  // 32 x 8
+size_t tb2d_smem(int rx, int ry, int ncomp, int precision);
+cudaError_t tb2d_prepare();  // shared-memory opt-in of the kernels on the current device (host, once)
+// the region (rx, ry) for k sweeps per launch with the lowest modelled cost (rx = ry = 0
+// picks it), or the given one; ox = rx - 2k, oy = ry - 2k
+Tiling tb2d_tiling(const Layout &L, int physics, int precision, int k, int rx = 0, int ry = 0);
+cudaError_t launch_sweep2d_tb(const SweepArgs &a, const Tiling &t, int precision, cudaStream_t s);
 bool make_tma_maps(const Layout &L, int ty, int ncomp, void *u0, void *u1, void *w, const void *E, TmaMaps &m);
 
 cudaError_t launch_sweep(const SweepArgs &a, const Tiling &t, int precision, cudaStream_t s,

@@ -212,9 +212,9 @@ def test_batch_state_reused_after_alone_sweeps(P):
 
 
 def test_batch_matches_default_single_path_within_fp32(P):
-    """Against problems solved alone on the default (node-gather) 2D kernel: the same
-    iteration in another summation order, so FP32 results agree to rounding: converged
-    fields to the solve tolerance and compliance to 1e-4."""
+    """Against problems solved alone on the default 2D kernel (four sweeps per launch,
+    node-gather arithmetic): the same iteration in another summation order, so FP32 results
+    agree to rounding: converged fields to the solve tolerance and compliance to 1e-4."""
     specs = small_batch(4, seed=17)
     seeds = [80, 81, 82, 83]
     kw = dict(tol=1e-6, check_every=20, max_sweeps=40000)

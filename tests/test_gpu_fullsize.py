@@ -1,9 +1,10 @@
 """The benchmark's workload at full size -- the 3D cantilever 256 x 128 x 128 in FP32, on the
 sweep kernel and launch configuration that bench.py times -- against the oracle; and the
-2D cantilever 1024 x 512 and heat 1024 x 1024 grids on their default (y-marching) kernel.
+2D cantilever 1024 x 512 and heat 1024 x 1024 grids on their default kernel (four sweeps
+per launch on shared-memory copies of the tiles).
 
-* One APT and one PT sweep from a seeded random state and design, field by field against
-  the oracle's sweeps.  Global pseudo-time steps: the oracle's local-step form recomputes
+* APT and PT sweeps from a seeded random state and design (one each in 3D, one launch of
+  four each in 2D), field by field against the oracle's sweeps.  Global pseudo-time steps: the oracle's local-step form recomputes
   diag(K) on every call, about a minute per sweep at this size; the local-step path is held
   element by element on the smaller grids of test_gpu_parity.py.
 * The refined solve of the first design iteration (local steps, adaptive momentum, FP64
@@ -20,7 +21,7 @@ from tests._util import nodes_to_oracle, oracle_materials, oracle_problem, oracl
 pytestmark = pytest.mark.gpu
 
 SIZE = (256, 128, 128)
-# the other full-size workloads: the 2D cantilever and heat grids (y-marching kernel)
+# the other full-size workloads: the 2D cantilever and heat grids
 FULL_2D = {"cantilever2d_1024x512": lambda: W.cantilever2d(1024, 512), "heat2d_1024x1024": lambda: W.heat2d(1024)}
 
 
@@ -39,8 +40,8 @@ def _spec(name):
     return W.cantilever3d(*SIZE) if name == "cantilever3d" else FULL_2D[name]()
 
 
-@pytest.mark.parametrize("name,kernel", [("cantilever3d", "tma3/"), ("cantilever2d_1024x512", "march2d/"),
-                                         ("heat2d_1024x1024", "march2d/")])
+@pytest.mark.parametrize("name,kernel", [("cantilever3d", "tma3/"), ("cantilever2d_1024x512", "tb2d/k4/"),
+                                         ("heat2d_1024x1024", "tb2d/k4/")])
 def test_fullsize_sweeps_match_oracle(P, name, kernel):
     spec = _spec(name)
     phi = W.random_design(spec, seed=41)
@@ -51,8 +52,9 @@ def test_fullsize_sweeps_match_oracle(P, name, kernel):
     assert prob.kernel_info()[0].startswith(kernel)  # the kernel the benchmark times
     prob.set_design(phi)
     prob.set_state(u0, w0)
-    r2a = prob.sweep(0, 1, a, b, 0.0, False)
-    r2p = prob.sweep(1, 1, 0.0, 0.0, s1, False)
+    n = 4 if kernel.startswith("tb2d") else 1  # the 2D kernel runs four sweeps per launch
+    r2a = prob.sweep(0, n, a, b, 0.0, False)
+    r2p = prob.sweep(1, n, 0.0, 0.0, s1, False)
     ug, wg = prob.get_state(with_w=True)
     prob.close()
 
@@ -60,8 +62,10 @@ def test_fullsize_sweeps_match_oracle(P, name, kernel):
     E = om.modulus(np.asarray(phi, np.float32).astype(np.float64))
     F, fixed = op.load_vector(), op.fixed_mask()
     uo, wo = nodes_to_oracle(u0.astype(np.float64)), nodes_to_oracle(w0.astype(np.float64))
-    r2a_o = op.apt_sweep(E, F, fixed, a, b, uo, wo)
-    r2p_o = op.pt_sweep(E, F, fixed, s1, uo)
+    for _ in range(n):
+        r2a_o = op.apt_sweep(E, F, fixed, a, b, uo, wo)
+    for _ in range(n):
+        r2p_o = op.pt_sweep(E, F, fixed, s1, uo)
     un, wn = oracle_to_nodes(uo, spec.ncomp), oracle_to_nodes(wo, spec.ncomp)
     for c in range(spec.ncomp):
         assert rel_l2(ug[c], un[c]) < 1e-5
