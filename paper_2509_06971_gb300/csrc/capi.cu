@@ -375,8 +375,8 @@ struct SweepCtl {
 // Sweeps of one kind (0 APT, 1 PT) from u[cur] into u[1-cur] in one launch, flipping cur:
 // one sweep, or (the 2D kernel that runs several per launch, kind 7) nsw sweeps with indices
 // sc.idx .. sc.idx + nsw - 1, the last of them the one that sums R^2 / tests <R, w> (the
-// caller ends its groups on those sweeps); w then goes to the second buffer and the two
-// swap.
+// caller ends its groups on those sweeps); APT sweeps then write w to the second buffer
+// and the two swap (PT sweeps leave w alone).
 petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, int local_dt, bool want_res,
                        const SweepCtl &sc = SweepCtl(), int nsw = 1) {
     if (nsw > 1 && (ctx->tiling.kind != 7 || nsw > ctx->tiling.ly || !ctx->w_alt))
@@ -401,7 +401,8 @@ petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, 
     A.u_out = ctx->u[1 - ctx->cur];
     A.w = ctx->w;
     A.tb_k = nsw;
-    A.w_out = nsw > 1 ? ctx->w_alt : ctx->w;
+    const bool w_swap = nsw > 1 && kind == 0;  // PT sweeps neither read nor write w
+    A.w_out = w_swap ? ctx->w_alt : ctx->w;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ctx->profiling && !sc.base_from_ctrl) {
         for (cudaEvent_t *e : {&e0, &e1}) {
@@ -423,7 +424,7 @@ petto_status one_sweep(petto_ctx *ctx, int kind, double a, double b, double s1, 
     }
     ctx->launches++;
     ctx->cur ^= 1;
-    if (nsw > 1) std::swap(ctx->w, ctx->w_alt);
+    if (w_swap) std::swap(ctx->w, ctx->w_alt);
     return PETTO_OK;
 }
 
@@ -812,6 +813,7 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
     alloc(&ctx->u[0], nb);
     alloc(&ctx->u[1], nb);
     alloc(&ctx->w, nb);
+    if (ctx->tiling.kind == 7) alloc(&ctx->w_alt, nb);  // 2D sweeps several per launch
     alloc(&ctx->E, eb);
     alloc(&ctx->phi, (size_t)ctx->P * nc * ctx->ssize());
     alloc(&ctx->s, (size_t)ctx->P * nc * ctx->tsize());
@@ -849,6 +851,8 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
     if (e == cudaSuccess && ctx->n_loads > 0)
         e = cudaMemcpyAsync(ctx->gloads, gent.data(), sizeof(LoadEntry) * ctx->n_loads, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ctrl, 0, sizeof(double) * CT_N, s);
+    if (e == cudaSuccess && ctx->w_alt) e = cudaMemsetAsync(ctx->w_alt, 0, nb, s);
+    if (e == cudaSuccess && ctx->tiling.kind == 7) e = tb2d_prepare();
     // phi = V
     double *dvol = nullptr;
     if (e == cudaSuccess) e = cudaMalloc(&dvol, sizeof(double) * ctx->P);
@@ -1087,7 +1091,7 @@ petto_status graph_chunk(petto_ctx *ctx, const petto_solve_opts *o, bool apt, in
             sc.rhs = rhs;
             st = one_sweep(ctx, apt ? 0 : 1, o->a, o->b, o->s1, o->local_dt, res_last && j + g == ce, sc, g);
             ++flips;
-            if (g > 1) ++swaps;
+            if (g > 1 && apt) ++swaps;
             j += g;
         }
         cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
@@ -2531,11 +2535,13 @@ petto_status petto_select_kernel(petto_ctx *ctx, const char *name) {
     ctx->tune_pending = false;
     const std::string want(name);
     // "tb2d/k<K>/<rx>x<ry>": the 2D kernel of K sweeps per launch on a region of rx x ry
-    // nodes (output tile rx - 2K by ry - 2K, at least 4 x 4; shared memory within the limit)
+    // nodes (rx = 32, 62, 122 or 242; output tile rx - 2K by ry - 2K, at least 4 x 4; shared
+    // memory within the limit)
     int k = 0, rx = 0, ry = 0;
     if (ctx->L.dim == 2 && ctx->nrhs == 1 && std::sscanf(name, "tb2d/k%d/%dx%d", &k, &rx, &ry) == 3) {
-        if ((k != 1 && k != 2 && k != 4) || rx - 2 * k < 4 || ry - 2 * k < 4)
-            return fail(ctx, PETTO_EINVAL, "tb2d: K is 1, 2 or 4 and the output tile at least 4 x 4");
+        if ((k != 1 && k != 2 && k != 4) || !tb2d_region_ok(rx, ry, k))
+            return fail(ctx, PETTO_EINVAL,
+                        "tb2d: K is 1, 2 or 4, rx is 32, 62, 122 or 242 and the output tile at least 4 x 4");
         int dev = 0, opt = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&opt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));

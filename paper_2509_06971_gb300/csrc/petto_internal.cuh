@@ -356,6 +356,9 @@ inline bool two_row_kind(int kind) { return kind == 4 || kind == 6; }
 constexpr int TB_THREADS = 256;  // 32 x 8
 size_t tb2d_smem(int rx, int ry, int ncomp, int precision);
 cudaError_t tb2d_prepare();  // shared-memory opt-in of the kernels on the current device (host, once)
+// the regions the kernel takes: rx = 30 nsx + 2 (nsx = 1, 2, 4, 8 warp column strips), an
+// output tile of at least 4 x 4
+bool tb2d_region_ok(int rx, int ry, int k);
 // the region (rx, ry) for k sweeps per launch with the lowest modelled cost (rx = ry = 0
 // picks it), or the given one; ox = rx - 2k, oy = ry - 2k
 Tiling tb2d_tiling(const Layout &L, int physics, int precision, int k, int rx = 0, int ry = 0);

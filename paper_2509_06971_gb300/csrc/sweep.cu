@@ -229,33 +229,12 @@ __device__ __forceinline__ void march2d_tile(const M2View<T, TE> &V, int tile, U
         const T El = __shfl_up_sync(FULL, Ec, 1);
 #pragma unroll
         for (int c = 0; c < C; ++c) un1[c] = __shfl_down_sync(FULL, u1[c], 1);
-        const T Ex = Eb + Ec, Ey = El + Ec;
-        T own[C], mx[C], gn[C];
-        T cyn[C];
-        if (PHYS == 0) {
-            const T ax0 = un[0] - u0[0], ax1 = un[1] - u0[1];
-            const T ay0 = u1[0] - u0[0], ay1 = u1[1] - u0[1];
-            const T fx0 = k.ce_par * Ex * ax0, fx1 = k.ce_perp * Ex * ax1;
-            const T fy0 = k.ce_perp * Ey * ay0, fy1 = k.ce_par * Ey * ay1;
-            const T SA0 = ax0 + (un1[0] - u1[0]), SA1 = ax1 + (un1[1] - u1[1]);
-            const T SB0 = ay0 + (un1[0] - un[0]), SB1 = ay1 + (un1[1] - un[1]);
-            const T G0 = Ec * (k.cf_lam * SB1 + k.cf_mu * SA1), G1 = Ec * (k.cf_mu * SB0 + k.cf_lam * SA0);
-            const T H0 = Ec * (k.cf_lam * SB1 - k.cf_mu * SA1), H1 = Ec * (k.cf_mu * SB0 - k.cf_lam * SA0);
-            own[0] = -fx0 - fy0 - G0;
-            own[1] = -fx1 - fy1 - G1;
-            mx[0] = __shfl_up_sync(FULL, fx0 + H0, 1);
-            mx[1] = __shfl_up_sync(FULL, fx1 + H1, 1);
-            gn[0] = __shfl_up_sync(FULL, G0, 1);
-            gn[1] = __shfl_up_sync(FULL, G1, 1);
-            cyn[0] = fy0 - H0;
-            cyn[1] = fy1 - H1;
-        } else {
-            const T fx = k.ct * Ex * (un[0] - u0[0]);
-            const T fy = k.ct * Ey * (u1[0] - u0[0]);
-            own[0] = -fx - fy;
-            mx[0] = __shfl_up_sync(FULL, fx, 1);
-            gn[0] = T(0);
-            cyn[0] = fy;
+        T own[C], mx[C], gn[C], cyn[C], tx[C], tg[C];
+        m2_terms<T, PHYS>(u0, un, u1, un1, Eb, Ec, El, k, own, tx, cyn, tg);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            mx[c] = __shfl_up_sync(FULL, tx[c], 1);
+            gn[c] = PHYS == 0 ? __shfl_up_sync(FULL, tg[c], 1) : T(0);
         }
         if (j >= y0 && out) {
             const int n = (j + 1) * SX + ncol;
@@ -264,7 +243,7 @@ __device__ __forceinline__ void march2d_tile(const M2View<T, TE> &V, int tile, U
                 const Box &bx = V.boxes->b[__ffs(bb) - 1];
                 if (j >= bx.lo[1] && j <= bx.hi[1]) fm |= bx.mask;
             }
-            const T diag = k.cdiag * ((Elb + Eb) + (El + Ec));
+            const T diag = m2_diag(k, Elb, Eb, El, Ec);
             T F[C];
 #pragma unroll
             for (int c = 0; c < C; ++c) F[c] = fv[c];
@@ -282,8 +261,8 @@ __device__ __forceinline__ void march2d_tile(const M2View<T, TE> &V, int tile, U
             }
 #pragma unroll
             for (int c = 0; c < C; ++c)
-                up.apply_v(c * cs + n, (fm >> c) & 1u, own[c] + mx[c] + cy[c] + gd[c], F[c], diag, u0[c], wv[c], V.uo,
-                           V.w);
+                up.apply_v(c * cs + n, (fm >> c) & 1u, m2_ku(own[c], mx[c], cy[c], gd[c]), F[c], diag, u0[c], wv[c],
+                           V.uo, V.w);
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) {

@@ -8,9 +8,11 @@
 // neighbourhood sweep s - 1 has updated.  After the K-th sweep it writes the output tile
 // back.  Halo nodes are updated redundantly, by every block that stages them, with the same
 // arithmetic as in the block that owns them, so every node ends with the value K single
-// sweeps give: a node is evaluated as the node-gather kernel evaluates it (ku_elastic_2d /
-// ku_thermal_2d, Upd::apply, loads added in list order), so the two agree bit for bit.
-// One read of the grid (from L2 or HBM) and one launch then serve K sweeps.
+// sweeps give.  A node is evaluated as the y-marching kernel evaluates it (m2_terms: each
+// edge and face term once, at its owner node, its shares passed by warp shuffles along x and
+// in registers along y; m2_ku, m2_diag, Upd::apply_v; loads added in list order after the
+// source term), so the two agree bit for bit.  One read of the grid (from L2 or HBM) and one
+// launch then serve K sweeps.
 //
 // The u field ping-pongs between two global buffers as with single sweeps.  w is updated in
 // place within a launch, in shared memory, but a launch of K > 1 sweeps reads the w of its
@@ -30,21 +32,36 @@ namespace {
 
 constexpr unsigned char TB_OUTSIDE = 0x80;  // mask bit of a staged node outside the grid
 
+// Asynchronous copy of one element from global to shared memory; the element is zero when
+// !valid (source size 0: nothing is read, and src only has to be a valid address).
+template <typename T>
+__device__ __forceinline__ void cp_async_zfill(T *dst, const T *src, bool valid) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+
 template <typename T, int PHYS>
-__global__ void __launch_bounds__(TB_THREADS, 2) sweep2d_tb(const __grid_constant__ SweepArgs A, int ox, int oy) {
+__global__ void __launch_bounds__(TB_THREADS, 2) sweep2d_tb(const __grid_constant__ SweepArgs A, int ox, int oy, int halo) {
     constexpr int C = PHYS == 0 ? 2 : 1;
     extern __shared__ __align__(16) unsigned char tb_raw[];
     const Layout &L = A.L;
-    const int K = A.tb_k;
-    const int RX = ox + 2 * K, RY = oy + 2 * K, RN = RX * RY, EX = RX - 1;
+    // the region is the output tile and a halo of the tiling's sweeps per launch; a launch of
+    // K sweeps (fewer at the end of a run) starts d = halo - K nodes further in
+    const int K = A.tb_k, d = halo - K;
+    const int RX = ox + 2 * halo, RY = oy + 2 * halo, RN = RX * RY;
     T *su0 = reinterpret_cast<T *>(tb_raw);  // [C][RN], the state before odd sweeps
     T *su1 = su0 + C * RN;                   // [C][RN], the state before even sweeps
     T *sw = su1 + C * RN;                    // [C][RN] w (APT), or R (residual mode)
     T *sf = sw + C * RN;                     // [C][RN] F
-    T *se = sf + C * RN;                     // [RY - 1][RX - 1] cell moduli
-    unsigned char *sm = reinterpret_cast<unsigned char *>(se + (RY - 1) * EX);  // [RN] support mask
+    T *se = sf + C * RN;                     // [RY][RX] moduli of the cells whose lower-left node is
+                                             // the region node of the same index
+    unsigned char *sm = reinterpret_cast<unsigned char *>(se + RN);  // [RN] support mask
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
-    const int x0 = (int)blockIdx.x * ox - K, y0 = (int)blockIdx.y * oy - K;  // grid node of region node (0, 0)
+    const int x0 = (int)blockIdx.x * ox - halo, y0 = (int)blockIdx.y * oy - halo;  // grid node of region node (0, 0)
     const KC<T> kc = kconst<T>(A);
     const T *__restrict__ ui = static_cast<const T *>(A.u_in);
     const T *__restrict__ wi = static_cast<const T *>(A.w);
@@ -52,7 +69,8 @@ __global__ void __launch_bounds__(TB_THREADS, 2) sweep2d_tb(const __grid_constan
     const T *__restrict__ E = static_cast<const T *>(A.E);
     const int64_t cs = L.cstride;
 
-    // ---- stage the region: nodes (outside the grid: 0 in both state copies, never updated)
+    // ---- stage the region with asynchronous copies (cp.async, zero-filled where the source
+    // is outside the grid or not needed), so that every load of the block is in flight at once
     for (int ly = ty; ly < RY; ly += 8) {
         const int j = y0 + ly;
         for (int lx = tx; lx < RX; lx += 32) {
@@ -61,30 +79,30 @@ __global__ void __launch_bounds__(TB_THREADS, 2) sweep2d_tb(const __grid_constan
             const bool in = i >= 0 && i < L.NX && j >= 0 && j < L.NY;
             // w is read only where the first sweep updates (the region's border is never
             // updated, and a one-sweep launch reads no node its neighbours write)
-            const bool upd = in && lx >= 1 && lx < RX - 1 && ly >= 1 && ly < RY - 1;
+            const bool upd = in && lx >= d + 1 && lx < RX - d - 1 && ly >= d + 1 && ly < RY - d - 1;
             const int64_t g = in ? L.node(i, j, 0) : 0;
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                su0[c * RN + n] = in ? ui[c * cs + g] : T(0);
+                cp_async_zfill(&su0[c * RN + n], ui + c * cs + g, in);  // outside the grid: 0
                 if (!in) su1[c * RN + n] = T(0);
-                sw[c * RN + n] = (upd && A.mode == 0) ? wi[c * cs + g] : T(0);
-                T f = T(0);
-                if (rhs) f = in ? rhs[c * cs + g] : T(0);
-                else if (PHYS == 1 && in) f = kc.src * (T)(((i > 0) + (i < L.nx)) * ((j > 0) + (j < L.ny)));
-                sf[c * RN + n] = f;
+                cp_async_zfill(&sw[c * RN + n], wi + c * cs + g, upd && A.mode == 0);
+                if (rhs) cp_async_zfill(&sf[c * RN + n], rhs + c * cs + g, in);
+                else sf[c * RN + n] = (PHYS == 1 && in) ? kc.src * (T)(((i > 0) + (i < L.nx)) * ((j > 0) + (j < L.ny)))
+                                                        : T(0);
             }
             sm[n] = in ? (unsigned char)fixed_mask(A.boxes, i, j, 0) : TB_OUTSIDE;
         }
     }
     // cells (outside the grid: modulus 0, as in the zero ring of the global layout)
-    for (int cy = ty; cy < RY - 1; cy += 8) {
+    for (int cy = ty; cy < RY; cy += 8) {
         const int cj = y0 + cy;
-        for (int cx = tx; cx < EX; cx += 32) {
+        for (int cx = tx; cx < RX; cx += 32) {
             const int ci = x0 + cx;
             const bool in = ci >= 0 && ci < L.nx && cj >= 0 && cj < L.ny;
-            se[cy * EX + cx] = in ? E[L.cell(ci, cj, 0)] : T(0);
+            cp_async_zfill(&se[cy * RX + cx], E + (in ? L.cell(ci, cj, 0) : 0), in);
         }
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     // point loads of the region's nodes, from the load lists of the 3 x 3 tiles around this
     // one (the halo is narrower than a tile): one thread per list, so a node's loads are
@@ -103,7 +121,15 @@ __global__ void __launch_bounds__(TB_THREADS, 2) sweep2d_tb(const __grid_constan
     }
     __syncthreads();
 
-    // ---- K sweeps on the staged copy
+    // ---- K sweeps on the staged copy, in the y-marching form of the single-sweep kernel
+    // (m2_terms): the block's 8 warps are nsx column strips x (8 / nsx) row segments.  A warp's
+    // lanes hold 32 consecutive region columns, lanes 1..30 its outputs (lane 0 and 31 only
+    // pass messages), and it marches its segment's rows from the row below the first, which
+    // only produces the messages that row receives.
+    constexpr unsigned FULL = 0xffffffffu;
+    const int nsx = (RX - 2) / 30, nsy = 8 / nsx;
+    const int lane = tx, strip = ty % nsx, segm = ty / nsx;
+    const int lx = 30 * strip + lane;  // this lane's region column
     const long long last = sweep_index(A);  // index of this launch's last sweep
     const long long rst = A.adaptive ? reinterpret_cast<const long long *>(A.ctrl)[CT_RESTART_AT] : 0;
     Upd<T> up{kc, T(0), A.mode, A.local_dt, 0, 0, nullptr, T(0), T(0)};
@@ -112,42 +138,59 @@ __global__ void __launch_bounds__(TB_THREADS, 2) sweep2d_tb(const __grid_constan
         T *wr = (s & 1) ? su1 : su0;
         up.a_eff = momentum_k<T>(A.adaptive, kc.a, A.adaptive ? last - (K - s) - rst : 0);
         const bool final_sweep = s == K;
-        for (int ly = s + ty; ly < RY - s; ly += 8) {
-            const bool own_row = final_sweep && ly >= K && ly < K + oy;
-            for (int lx = s + tx; lx < RX - s; lx += 32) {
-                const int n = ly * RX + lx;
-                const unsigned m = sm[n];
-                if (m & TB_OUTSIDE) continue;
-                const bool own = own_row && lx >= K && lx < K + ox;
-                up.want_res = own && A.want_res;
-                up.test_dot = own && A.test_dot;
-                T Ec[2][2];
-                Ec[0][0] = se[(ly - 1) * EX + lx - 1];
-                Ec[0][1] = se[(ly - 1) * EX + lx];
-                Ec[1][0] = se[ly * EX + lx - 1];
-                Ec[1][1] = se[ly * EX + lx];
-                const T S = Ec[0][0] + Ec[0][1] + Ec[1][0] + Ec[1][1];
-                const T diag = kc.cdiag * S;
-                if (PHYS == 0) {
-                    T U[3][3][2];
+        const int e = s + d;  // sweep s updates the region shrunk by e nodes on every side
+        const int sl = (RY - 2 * e + nsy - 1) / nsy;
+        const int ys = e + segm * sl, ye = min(ys + sl, RY - e);
+        const bool xin = lane >= 1 && lane <= 30 && lx >= e && lx < RX - e;
+        if (ys < ye) {  // warp-uniform
+            int j = ys - 1;
+            T u0[C], u1[C], un[C], un1[C], cy[C], gd[C];
 #pragma unroll
-                    for (int a = 0; a < 2; ++a)
+            for (int c = 0; c < C; ++c) {
+                u0[c] = rd[c * RN + j * RX + lx];
+                u1[c] = rd[c * RN + (j + 1) * RX + lx];
+                un[c] = __shfl_down_sync(FULL, u0[c], 1);
+                cy[c] = gd[c] = T(0);
+            }
+            T Eb = j >= 1 ? se[(j - 1) * RX + lx] : T(0), Ec = se[j * RX + lx], Elb = T(0);
+            for (; j < ye; ++j) {
+                const T El = __shfl_up_sync(FULL, Ec, 1);
 #pragma unroll
-                        for (int dy = 0; dy < 3; ++dy)
+                for (int c = 0; c < C; ++c) un1[c] = __shfl_down_sync(FULL, u1[c], 1);
+                T own[C], tx_[C], cyn[C], tg[C], mx[C], gn[C];
+                m2_terms<T, PHYS>(u0, un, u1, un1, Eb, Ec, El, kc, own, tx_, cyn, tg);
 #pragma unroll
-                            for (int dx = 0; dx < 3; ++dx) U[dy][dx][a] = rd[a * RN + n + (dy - 1) * RX + (dx - 1)];
-                    T Ku[2];
-                    ku_elastic_2d<T>(U, Ec, kc, Ku);
+                for (int c = 0; c < C; ++c) {
+                    mx[c] = __shfl_up_sync(FULL, tx_[c], 1);
+                    gn[c] = PHYS == 0 ? __shfl_up_sync(FULL, tg[c], 1) : T(0);
+                }
+                if (j >= ys && xin) {
+                    const int n = j * RX + lx;
+                    const unsigned m = sm[n];
+                    if (!(m & TB_OUTSIDE)) {
+                        const bool own_node = final_sweep && j >= halo && j < halo + oy && lx >= halo && lx < halo + ox;
+                        up.want_res = own_node && A.want_res;
+                        up.test_dot = own_node && A.test_dot;
+                        const T diag = m2_diag(kc, Elb, Eb, El, Ec);
 #pragma unroll
-                    for (int a = 0; a < 2; ++a) up.apply(a * RN + n, (m >> a) & 1u, Ku[a], sf[a * RN + n], diag, wr, rd, sw);
-                } else {
-                    T U[3][3];
+                        for (int c = 0; c < C; ++c)
+                            up.apply_v(c * RN + n, (m >> c) & 1u, m2_ku(own[c], mx[c], cy[c], gd[c]), sf[c * RN + n],
+                                       diag, u0[c], sw[c * RN + n], wr, sw);
+                    }
+                }
 #pragma unroll
-                    for (int dy = 0; dy < 3; ++dy)
+                for (int c = 0; c < C; ++c) {
+                    cy[c] = cyn[c];
+                    gd[c] = gn[c];
+                    u0[c] = u1[c];
+                    un[c] = un1[c];
+                }
+                Eb = Ec;
+                Elb = El;
+                if (j + 1 < ye) {
 #pragma unroll
-                        for (int dx = 0; dx < 3; ++dx) U[dy][dx] = rd[n + (dy - 1) * RX + (dx - 1)];
-                    const T Ku = ku_thermal_2d<T>(U, Ec, kc);
-                    up.apply(n, m & 1u, Ku, sf[n], diag, wr, rd, sw);
+                    for (int c = 0; c < C; ++c) u1[c] = rd[c * RN + (j + 2) * RX + lx];
+                    Ec = se[(j + 1) * RX + lx];
                 }
             }
         }
@@ -158,10 +201,10 @@ __global__ void __launch_bounds__(TB_THREADS, 2) sweep2d_tb(const __grid_constan
     const T *fin = (K & 1) ? su1 : su0;
     T *uo = static_cast<T *>(A.u_out);
     T *wo = static_cast<T *>(A.w_out);
-    for (int ly = K + ty; ly < K + oy; ly += 8) {
+    for (int ly = halo + ty; ly < halo + oy; ly += 8) {
         const int j = y0 + ly;
         if (j >= L.NY) break;
-        for (int lx = K + tx; lx < K + ox; lx += 32) {
+        for (int lx = halo + tx; lx < halo + ox; lx += 32) {
             const int i = x0 + lx;
             if (i >= L.NX) break;
             const int n = ly * RX + lx;
@@ -196,13 +239,21 @@ cudaError_t tb2d_prepare() {
 
 size_t tb2d_smem(int rx, int ry, int ncomp, int precision) {
     const size_t ts = precision == 0 ? sizeof(float) : sizeof(double);
-    return ((size_t)4 * ncomp * rx * ry + (size_t)(rx - 1) * (ry - 1)) * ts + (size_t)rx * ry;
+    return (size_t)(4 * ncomp + 1) * rx * ry * ts + (size_t)rx * ry;
 }
 
-// Cost model of a region shape: the busiest SM's tiles x the node updates of one tile over
-// K sweeps (rows split over 8 warps and 32-lane column groups, as the loops run), plus half
-// a node update per staged node, with a penalty for one block per SM (its barriers leave the
-// SM idle while the slowest warp finishes a sweep).
+// The regions the kernel takes: rx = 30 nsx + 2 columns for nsx = 1, 2, 4 or 8 column
+// strips of warps (the other 8 / nsx warps split the rows), any ry.
+bool tb2d_region_ok(int rx, int ry, int k) {
+    const int nsx = (rx - 2) / 30;
+    return rx == 30 * nsx + 2 && (nsx == 1 || nsx == 2 || nsx == 4 || nsx == 8) && rx - 2 * k >= 4 &&
+           ry - 2 * k >= 4;
+}
+
+// Cost model of a region shape: the busiest SM's tiles x the warp row steps of one tile over
+// K sweeps (each warp marches its share of the rows plus one row below it), plus the
+// staging, with a penalty for one block per SM (its barriers leave the SM idle while the
+// slowest warp finishes a sweep).
 Tiling tb2d_tiling(const Layout &L, int physics, int precision, int k, int rx, int ry) {
     Tiling t{};
     t.kind = 7;
@@ -213,7 +264,7 @@ Tiling tb2d_tiling(const Layout &L, int physics, int precision, int k, int rx, i
     k = k >= 4 ? 4 : (k >= 2 ? 2 : 1);
     t.ly = k;
     const int C = physics == 0 ? 2 : 1;
-    if (rx <= 0 || ry <= 0) {
+    if (!tb2d_region_ok(rx, ry, k)) {
         int dev = 0, sms = 152, opt = 232448, per_sm = 233472;
         if (cudaGetDevice(&dev) == cudaSuccess) {
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -221,18 +272,19 @@ Tiling tb2d_tiling(const Layout &L, int physics, int precision, int k, int rx, i
             cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         }
         double best = INFINITY;
-        for (int rxc : {32, 48, 64, 80, 96, 128, 160, 192})
-            for (int ryc : {12, 16, 20, 24, 32, 40, 48, 56, 64, 80, 96, 128}) {
-                const int ox = rxc - 2 * k, oy = ryc - 2 * k;
-                if (ox < 8 || oy < 4) continue;
+        rx = ry = 0;
+        for (int nsx : {1, 2, 4, 8})
+            for (int ryc = 8; ryc <= 256; ryc += 4) {
+                const int rxc = 30 * nsx + 2, nsy = 8 / nsx;
+                if (!tb2d_region_ok(rxc, ryc, k)) continue;
                 const size_t smem = tb2d_smem(rxc, ryc, C, precision) + 1024;
                 if (smem > (size_t)opt) continue;
                 const int blocks_sm = std::min<int>(8, (int)((size_t)per_sm / (smem + 1024)));
                 if (blocks_sm < 1) continue;
+                const int ox = rxc - 2 * k, oy = ryc - 2 * k;
                 const int64_t tiles = (int64_t)((L.NX + ox - 1) / ox) * ((L.NY + oy - 1) / oy);
-                double work = 0.5 * rxc * ryc;
-                for (int s = 1; s <= k; ++s)
-                    work += (double)((rxc - 2 * s + 31) / 32 * 32) * ((ryc - 2 * s + 7) / 8 * 8);
+                double work = 0.25 * rxc * ryc / 32.0;  // staging, in warp row steps
+                for (int s = 1; s <= k; ++s) work += 8.0 * ((ryc - 2 * s + nsy - 1) / nsy + 1);
                 const double busiest = std::ceil((double)tiles / sms);
                 const double cost = busiest * work / (blocks_sm >= 2 ? 1.0 : 0.8);
                 if (cost < best * 0.999) {
@@ -241,9 +293,9 @@ Tiling tb2d_tiling(const Layout &L, int physics, int precision, int k, int rx, i
                     ry = ryc;
                 }
             }
-        if (rx <= 0) {  // nothing fits (a very small device): the smallest region
+        if (rx == 0) {  // nothing fits (a very small device): the smallest region
             rx = 32;
-            ry = 12;
+            ry = 2 * k + 4;
         }
     }
     t.ox = rx - 2 * k;
@@ -260,14 +312,14 @@ cudaError_t launch_sweep2d_tb(const SweepArgs &a0, const Tiling &t, int precisio
     cudaError_t e = tb2d_prepare();
     if (e != cudaSuccess) return e;
     const int C = a.physics == 0 ? 2 : 1;
-    const size_t smem = tb2d_smem(t.ox + 2 * a.tb_k, t.oy + 2 * a.tb_k, C, precision);
+    const size_t smem = tb2d_smem(t.ox + 2 * t.ly, t.oy + 2 * t.ly, C, precision);
     const dim3 grid(t.gx, t.gy, 1), block(32, 8, 1);
     if (precision == 0) {
-        if (a.physics == 0) sweep2d_tb<float, 0><<<grid, block, smem, s>>>(a, t.ox, t.oy);
-        else sweep2d_tb<float, 1><<<grid, block, smem, s>>>(a, t.ox, t.oy);
+        if (a.physics == 0) sweep2d_tb<float, 0><<<grid, block, smem, s>>>(a, t.ox, t.oy, t.ly);
+        else sweep2d_tb<float, 1><<<grid, block, smem, s>>>(a, t.ox, t.oy, t.ly);
     } else {
-        if (a.physics == 0) sweep2d_tb<double, 0><<<grid, block, smem, s>>>(a, t.ox, t.oy);
-        else sweep2d_tb<double, 1><<<grid, block, smem, s>>>(a, t.ox, t.oy);
+        if (a.physics == 0) sweep2d_tb<double, 0><<<grid, block, smem, s>>>(a, t.ox, t.oy, t.ly);
+        else sweep2d_tb<double, 1><<<grid, block, smem, s>>>(a, t.ox, t.oy, t.ly);
     }
     return cudaGetLastError();
 }

@@ -97,6 +97,62 @@ __device__ __forceinline__ T ku_thermal_2d(const T (&U)[3][3], const T (&Ec)[2][
                  Eyp * (U[2][1] - U[1][1]));
 }
 
+// Products rounded on their own (never fused into an FMA by the compiler), so that every
+// kernel that evaluates an expression built from them gets the same bits whatever code
+// surrounds it.
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+
+// The owner terms of the 2D y-marching form: at node (i, j), the x-edge to (i+1, j), the
+// y-edge to (i, j+1) and the face of cell (i, j), from u at the four corners of that cell
+// (u0 = u(i, j), un = u(i+1, j), u1 = u(i, j+1), un1 = u(i+1, j+1)) and the moduli of cells
+// (i, j-1) (Eb), (i, j) (Ec) and (i-1, j) (El).  Their forces go to four nodes: own to (i, j),
+// tx (x-message) to (i+1, j), cyn (carried up) to (i, j+1) and tg (diagonal) to (i+1, j+1);
+// the node's K u is then own + tx(i-1, j) + cyn(i, j-1) + tg(i-1, j-1), summed in that order
+// (m2_ku).  Every kernel of the marching form evaluates these expressions, so they agree
+// bit for bit.
+template <typename T, int PHYS>
+__device__ __forceinline__ void m2_terms(const T *u0, const T *un, const T *u1, const T *un1, T Eb, T Ec, T El,
+                                         const KC<T> &k, T *own, T *tx, T *cyn, T *tg) {
+    const T Ex = Eb + Ec, Ey = El + Ec;
+    if (PHYS == 0) {
+        const T ax0 = un[0] - u0[0], ax1 = un[1] - u0[1];
+        const T ay0 = u1[0] - u0[0], ay1 = u1[1] - u0[1];
+        const T fx0 = rn_mul(rn_mul(k.ce_par, Ex), ax0), fx1 = rn_mul(rn_mul(k.ce_perp, Ex), ax1);
+        const T fy0 = rn_mul(rn_mul(k.ce_perp, Ey), ay0), fy1 = rn_mul(rn_mul(k.ce_par, Ey), ay1);
+        const T SA0 = ax0 + (un1[0] - u1[0]), SA1 = ax1 + (un1[1] - u1[1]);
+        const T SB0 = ay0 + (un1[0] - un[0]), SB1 = ay1 + (un1[1] - un[1]);
+        const T lb1 = rn_mul(k.cf_lam, SB1), ma1 = rn_mul(k.cf_mu, SA1);
+        const T mb0 = rn_mul(k.cf_mu, SB0), la0 = rn_mul(k.cf_lam, SA0);
+        const T G0 = rn_mul(Ec, lb1 + ma1), G1 = rn_mul(Ec, mb0 + la0);
+        const T H0 = rn_mul(Ec, lb1 - ma1), H1 = rn_mul(Ec, mb0 - la0);
+        own[0] = -fx0 - fy0 - G0;
+        own[1] = -fx1 - fy1 - G1;
+        tx[0] = fx0 + H0;
+        tx[1] = fx1 + H1;
+        tg[0] = G0;
+        tg[1] = G1;
+        cyn[0] = fy0 - H0;
+        cyn[1] = fy1 - H1;
+    } else {
+        const T fx = rn_mul(rn_mul(k.ct, Ex), un[0] - u0[0]);
+        const T fy = rn_mul(rn_mul(k.ct, Ey), u1[0] - u0[0]);
+        own[0] = -fx - fy;
+        tx[0] = fx;
+        tg[0] = T(0);
+        cyn[0] = fy;
+    }
+}
+template <typename T>
+__device__ __forceinline__ T m2_ku(T own, T mx, T cy, T gd) {
+    return own + mx + cy + gd;
+}
+// diag(K) of node (i, j) from its four cells (i-1, j-1), (i, j-1), (i-1, j), (i, j)
+template <typename T>
+__device__ __forceinline__ T m2_diag(const KC<T> &k, T Elb, T Eb, T El, T Ec) {
+    return k.cdiag * ((Elb + Eb) + (El + Ec));
+}
+
 // ------------------------------------------------------------- 3D operator
 // U[dz][dy][dx][a], Ec[cz][cy][cx] (cell (i-1+cx, j-1+cy, k-1+cz)).
 template <typename T>
@@ -263,19 +319,20 @@ struct Upd {
             w[idx_c] = R;
         }
     }
-    // the same update with u and w (APT) already in registers
+    // the same update with u and w (APT) already in registers (the marching kernels: products
+    // rounded on their own, so that every kernel of that form gets the same bits)
     __device__ __forceinline__ void apply_v(int64_t idx_c, bool fixed, T Ku, T F, T diag, T u, T wi, T *uo, T *w) {
         T R = fixed ? T(0) : F - Ku;
         if (want_res) res += R * R;
         if (mode == 0) {
             const T step = local_dt ? k.b * fast_rcp(diag) : k.b;
             if (test_dot) dot += R * wi;
-            const T wn = fixed ? T(0) : a_eff * wi + step * R;
+            const T wn = fixed ? T(0) : rn_mul(a_eff, wi) + rn_mul(step, R);
             w[idx_c] = wn;
             uo[idx_c] = fixed ? T(0) : u + wn;
         } else if (mode == 1) {
             const T step = local_dt ? k.s1 * fast_rcp(diag) : k.s1;
-            uo[idx_c] = fixed ? T(0) : u + step * R;
+            uo[idx_c] = fixed ? T(0) : u + rn_mul(step, R);
         } else {
             w[idx_c] = R;
         }
