@@ -69,11 +69,13 @@ PAPER_DERIVED_GCELL_SWEEPS = {
 }
 METRIC = "APT Gcell-sweeps/s & % HBM roofline; s/design-iter at rel.res 1e-6"
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant sweep
-# kernel from one ncu capture of the workload: the refinement sweep of the lean two-row
-# marching kernel, nearly all of the sweeps of a design iteration.  Keyed by workload and
-# kernel name, so that any other kernel reports null; re-captured whenever that kernel changes.
-NCU_TRAFFIC = {("cantilever3d_256x128x128", "tma3/zs12"): 171960576 + 64645888}
+# DRAM bytes per sweep (dram__bytes_read.sum + dram__bytes_write.sum of one launch, divided
+# by the sweeps it runs) of the dominant sweep kernel from one ncu capture of the workload:
+# in 3D the refinement sweep of the lean two-row marching kernel, nearly all of the sweeps
+# of a design iteration; in 2D a launch of four sweeps.  Keyed by workload and kernel name,
+# so that any other kernel reports null; re-captured whenever that kernel changes.
+NCU_TRAFFIC = {("cantilever3d_256x128x128", "tma3/zs12"): 171960576 + 64645888,
+               ("cantilever2d_4096x2048", "tb2d/k4/62x48"): (169576704 + 91509504) / 4}
 
 
 def sweep_bytes(spec, tsize=4, method="apt"):
@@ -261,6 +263,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     spec = WORKLOADS[args.workload]()
     prob = PR.Problem(spec)
+    if args.kernel:
+        prob.select_kernel(args.kernel)
     solve_kw = dict(tol=args.tol, max_sweeps=args.max_sweeps, check_every=spec.check_every)
     if args.method == "pt":
         solve_kw["momentum"] = 2  # the plain first-order method: PT sweeps throughout
@@ -278,7 +282,7 @@ def run_ours(args):
     # 3D elastic FP32 grids from 2^20 nodes: the library's first solve picked the sweep kernel
     # by timing the applicable ones (petto_autotune)
     tuned = (args.warmup > 0 and spec.dim == 3 and spec.physics == W.ELASTIC and spec.precision == "f32"
-             and spec.nnodes >= (1 << 20))
+             and spec.nnodes >= (1 << 20) and not args.kernel)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -367,7 +371,9 @@ def run_ours(args):
                      "rhs_bytes_per_launch": bytes_rhs, "achieved_with_rhs": achieved_rhs,
                      "frac_with_rhs": (achieved_rhs / peak) if achieved_rhs else None,
                      "rhs_sweep_fraction": kern_rhs / max(kern_n, 1), "rhs_bytes": rhs_b,
-                     "sweep_kernel": kname, "sweep_kernel_choice": "autotuned on the first solve" if tuned else "default",
+                     "sweeps_per_launch": int(kname.split("/")[1][1:]) if kname.startswith("tb2d/") else 1,
+                     "sweep_kernel": kname, "sweep_kernel_choice": ("autotuned on the first solve" if tuned else
+                                             ("selected" if args.kernel else "default")),
                      "peak_kind": peak_kind},
         "e2e": {"value": e_value, "unit": "Gcell-sweeps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e_steps},
@@ -395,6 +401,8 @@ def run_time_to_design(args):
     spec = WORKLOADS[args.workload]()
     steps = args.design_steps or spec.design_steps
     prob = PR.Problem(spec)
+    if args.kernel:
+        prob.select_kernel(args.kernel)
     solve_kw = dict(tol=spec.tol, max_sweeps=args.max_sweeps, check_every=spec.check_every)
     warm = PR.Problem(spec)  # graph capture and first-touch outside the timed run
     warm.optimize(1, solve_kw=solve_kw)
@@ -609,6 +617,8 @@ def run_sweeps_only(args):
         return 0
     spec = WORKLOADS[args.workload]()
     prob = PR.Problem(spec)
+    if args.kernel:
+        prob.select_kernel(args.kernel)
     u0 = W.random_state(spec, seed=1, scale=1e-3).astype("float32")
     prob.set_state(u0)
     prob.sweep(0, 2, 0.99, 0.9, 0.75, True)
@@ -642,6 +652,8 @@ def main():
     ap.add_argument("--time-to-design", action="store_true",
                     help="time the workload's whole design run instead (one JSON line)")
     ap.add_argument("--design-steps", type=int, default=0, help="with --time-to-design: override the step count")
+    ap.add_argument("--kernel", default="",
+                    help="sweep kernel by name (petto_select_kernel), instead of the default or autotuned one")
     args = ap.parse_args()
     if args.sweeps_only:
         return run_sweeps_only(args)
