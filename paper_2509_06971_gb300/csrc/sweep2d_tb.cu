@@ -44,7 +44,9 @@ __device__ __forceinline__ void cp_async_zfill(T *dst, const T *src, bool valid)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
 }
 
-template <typename T, int PHYS>
+// MODE: 0 APT, 1 PT, 2 residual only; LOCAL: local pseudo-time steps (both compile-time, so
+// the per-node update carries no branches on them)
+template <typename T, int PHYS, int MODE, int LOCAL>
 __global__ void __launch_bounds__(TB_THREADS, 2) sweep2d_tb(const __grid_constant__ SweepArgs A, int ox, int oy, int halo) {
     constexpr int C = PHYS == 0 ? 2 : 1;
     extern __shared__ __align__(16) unsigned char tb_raw[];
@@ -85,7 +87,7 @@ __global__ void __launch_bounds__(TB_THREADS, 2) sweep2d_tb(const __grid_constan
             for (int c = 0; c < C; ++c) {
                 cp_async_zfill(&su0[c * RN + n], ui + c * cs + g, in);  // outside the grid: 0
                 if (!in) su1[c * RN + n] = T(0);
-                cp_async_zfill(&sw[c * RN + n], wi + c * cs + g, upd && A.mode == 0);
+                cp_async_zfill(&sw[c * RN + n], wi + c * cs + g, upd && MODE == 0);
                 if (rhs) cp_async_zfill(&sf[c * RN + n], rhs + c * cs + g, in);
                 else sf[c * RN + n] = (PHYS == 1 && in) ? kc.src * (T)(((i > 0) + (i < L.nx)) * ((j > 0) + (j < L.ny)))
                                                         : T(0);
@@ -132,12 +134,14 @@ __global__ void __launch_bounds__(TB_THREADS, 2) sweep2d_tb(const __grid_constan
     const int lx = 30 * strip + lane;  // this lane's region column
     const long long last = sweep_index(A);  // index of this launch's last sweep
     const long long rst = A.adaptive ? reinterpret_cast<const long long *>(A.ctrl)[CT_RESTART_AT] : 0;
-    Upd<T> up{kc, T(0), A.mode, A.local_dt, 0, 0, nullptr, T(0), T(0)};
+    Upd<T> up{kc, T(0), MODE, LOCAL, 0, 0, nullptr, T(0), T(0)};
     for (int s = 1; s <= K; ++s) {
         const T *rd = (s & 1) ? su0 : su1;
         T *wr = (s & 1) ? su1 : su0;
         up.a_eff = momentum_k<T>(A.adaptive, kc.a, A.adaptive ? last - (K - s) - rst : 0);
-        const bool final_sweep = s == K;
+        // the sums are taken over the output tile on the last sweep only
+        const bool sums = s == K && (A.want_res || A.test_dot);
+        up.want_res = up.test_dot = 0;
         const int e = s + d;  // sweep s updates the region shrunk by e nodes on every side
         const int sl = (RY - 2 * e + nsy - 1) / nsy;
         const int ys = e + segm * sl, ye = min(ys + sl, RY - e);
@@ -168,9 +172,11 @@ __global__ void __launch_bounds__(TB_THREADS, 2) sweep2d_tb(const __grid_constan
                     const int n = j * RX + lx;
                     const unsigned m = sm[n];
                     if (!(m & TB_OUTSIDE)) {
-                        const bool own_node = final_sweep && j >= halo && j < halo + oy && lx >= halo && lx < halo + ox;
-                        up.want_res = own_node && A.want_res;
-                        up.test_dot = own_node && A.test_dot;
+                        if (sums) {
+                            const bool own_node = j >= halo && j < halo + oy && lx >= halo && lx < halo + ox;
+                            up.want_res = own_node && A.want_res;
+                            up.test_dot = own_node && MODE == 0 && A.test_dot;
+                        }
                         const T diag = m2_diag(kc, Elb, Eb, El, Ec);
 #pragma unroll
                         for (int c = 0; c < C; ++c)
@@ -211,8 +217,8 @@ __global__ void __launch_bounds__(TB_THREADS, 2) sweep2d_tb(const __grid_constan
             const int64_t g = L.node(i, j, 0);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                if (A.mode != 2) uo[c * cs + g] = fin[c * RN + n];
-                if (A.mode != 1) wo[c * cs + g] = sw[c * RN + n];
+                if (MODE != 2) uo[c * cs + g] = fin[c * RN + n];
+                if (MODE != 1) wo[c * cs + g] = sw[c * RN + n];
             }
         }
     }
@@ -220,6 +226,25 @@ __global__ void __launch_bounds__(TB_THREADS, 2) sweep2d_tb(const __grid_constan
 }
 
 }  // namespace
+
+template <typename T, int PHYS, int MODE>
+cudaError_t tb2d_set_smem2(int mx) {
+    cudaError_t e = cudaFuncSetAttribute(sweep2d_tb<T, PHYS, MODE, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sweep2d_tb<T, PHYS, MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    return e;
+}
+template <typename T>
+cudaError_t tb2d_set_smem(int mx) {
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = tb2d_set_smem2<T, 0, 0>(mx);
+    if (e == cudaSuccess) e = tb2d_set_smem2<T, 0, 1>(mx);
+    if (e == cudaSuccess) e = tb2d_set_smem2<T, 0, 2>(mx);
+    if (e == cudaSuccess) e = tb2d_set_smem2<T, 1, 0>(mx);
+    if (e == cudaSuccess) e = tb2d_set_smem2<T, 1, 1>(mx);
+    if (e == cudaSuccess) e = tb2d_set_smem2<T, 1, 2>(mx);
+    return e;
+}
 
 cudaError_t tb2d_prepare() {
     static unsigned long long prepared = 0;  // one bit per device
@@ -229,10 +254,8 @@ cudaError_t tb2d_prepare() {
     int mx = 0;
     e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     mx -= 1024;  // the reduction scratch of finish_sweep is static shared memory
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep2d_tb<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep2d_tb<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep2d_tb<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(sweep2d_tb<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = tb2d_set_smem<float>(mx);
+    if (e == cudaSuccess) e = tb2d_set_smem<double>(mx);
     if (e == cudaSuccess) prepared |= 1ull << dev;
     return e;
 }
@@ -305,6 +328,23 @@ Tiling tb2d_tiling(const Layout &L, int physics, int precision, int k, int rx, i
     return t;
 }
 
+template <typename T, int PHYS, int MODE>
+void tb2d_launch3(const SweepArgs &a, const Tiling &t, dim3 grid, dim3 block, size_t smem, cudaStream_t s) {
+    if (a.local_dt) sweep2d_tb<T, PHYS, MODE, 1><<<grid, block, smem, s>>>(a, t.ox, t.oy, t.ly);
+    else sweep2d_tb<T, PHYS, MODE, 0><<<grid, block, smem, s>>>(a, t.ox, t.oy, t.ly);
+}
+template <typename T, int PHYS>
+void tb2d_launch2(const SweepArgs &a, const Tiling &t, dim3 grid, dim3 block, size_t smem, cudaStream_t s) {
+    if (a.mode == 0) tb2d_launch3<T, PHYS, 0>(a, t, grid, block, smem, s);
+    else if (a.mode == 1) tb2d_launch3<T, PHYS, 1>(a, t, grid, block, smem, s);
+    else tb2d_launch3<T, PHYS, 2>(a, t, grid, block, smem, s);
+}
+template <typename T>
+void tb2d_launch(const SweepArgs &a, const Tiling &t, dim3 grid, dim3 block, size_t smem, cudaStream_t s) {
+    if (a.physics == 0) tb2d_launch2<T, 0>(a, t, grid, block, smem, s);
+    else tb2d_launch2<T, 1>(a, t, grid, block, smem, s);
+}
+
 cudaError_t launch_sweep2d_tb(const SweepArgs &a0, const Tiling &t, int precision, cudaStream_t s) {
     SweepArgs a = a0;
     if (!a.w_out) a.w_out = a.w;
@@ -314,13 +354,8 @@ cudaError_t launch_sweep2d_tb(const SweepArgs &a0, const Tiling &t, int precisio
     const int C = a.physics == 0 ? 2 : 1;
     const size_t smem = tb2d_smem(t.ox + 2 * t.ly, t.oy + 2 * t.ly, C, precision);
     const dim3 grid(t.gx, t.gy, 1), block(32, 8, 1);
-    if (precision == 0) {
-        if (a.physics == 0) sweep2d_tb<float, 0><<<grid, block, smem, s>>>(a, t.ox, t.oy, t.ly);
-        else sweep2d_tb<float, 1><<<grid, block, smem, s>>>(a, t.ox, t.oy, t.ly);
-    } else {
-        if (a.physics == 0) sweep2d_tb<double, 0><<<grid, block, smem, s>>>(a, t.ox, t.oy, t.ly);
-        else sweep2d_tb<double, 1><<<grid, block, smem, s>>>(a, t.ox, t.oy, t.ly);
-    }
+    if (precision == 0) tb2d_launch<float>(a, t, grid, block, smem, s);
+    else tb2d_launch<double>(a, t, grid, block, smem, s);
     return cudaGetLastError();
 }
 
