@@ -321,6 +321,51 @@ petto_status petto_slab_solve(petto_ctx *ctx, const petto_solve_opts *opts, pett
 petto_status petto_get_plane(petto_ctx *ctx, int64_t k, void *dst, int dtype, int on_device);
 petto_status petto_set_plane(petto_ctx *ctx, int64_t k, const void *src, int dtype, int on_device);
 
+/* Cell layers of a slab's design fields, for the decomposed design step.  A slab owns the
+ * cell layers whose lower node plane it owns; it holds one more below (its lower ghost
+ * layer, between its lower ghost plane and its first own plane) and keeps a copy of the
+ * layer above its top layer (local index nz), which only the Cahn-Hilliard step reads.
+ *   field PETTO_LAYER_PHI: phase `phase` of the design, in the context's storage type
+ *   field PETTO_LAYER_MU:  the Cahn-Hilliard chemical potential, in the sweep precision
+ * petto_layer_bytes: bytes of one layer (nx ny elements), 0 for a bad field or a 2D grid.
+ * petto_get_layer / petto_set_layer copy layer k (0..nz-1 local, or nz: the copy of the
+ * layer above) out to / in from dst / src; on_device as petto_get_plane.  PETTO_EINVAL for
+ * a bad field, phase or layer, PETTO_EUNSUPPORTED in 2D. */
+enum { PETTO_LAYER_PHI = 0, PETTO_LAYER_MU = 1 };
+int64_t petto_layer_bytes(const petto_ctx *ctx, int field);
+petto_status petto_get_layer(petto_ctx *ctx, int field, int phase, int64_t k, void *dst, int on_device);
+petto_status petto_set_layer(petto_ctx *ctx, int field, int phase, int64_t k, const void *src, int on_device);
+
+/* Hook of the decomposed design step: for every interface, copy the lower slab's top layer
+ * (local nz - 1) of `field` (phase `phase` of phi, or mu) into the upper slab's layer 0 and
+ * the upper slab's layer 1 into the lower slab's layer nz (petto_get_layer /
+ * petto_set_layer); called by every slab in the same order.  PETTO_OK or a status that ends
+ * the step with that status. */
+typedef petto_status (*petto_layer_exchange_fn)(petto_ctx *ctx, int field, int phase, void *user);
+
+/* One design loop (Fig. 5: state solve, sensitivity, update, Cahn-Hilliard, modulus) on one
+ * slab of a z-decomposed grid, every slab calling it with the same options: the state solve
+ * of petto_slab_solve; one more exchange; the sensitivity of every held cell (a ghost layer
+ * gets its owner's bits), with C and F.u summed over the slab's own layers and planes and
+ * max |s_i| taken over the whole grid (allreduce, allreduce_max); the update with the whole
+ * grid's means (penalty) or the bisection's bracket moved on the host from the whole grid's
+ * sums, one allreduce per halving (projected), so every slab takes the same multiplier and
+ * a ghost layer keeps its owner's values; each Cahn-Hilliard half step preceded by
+ * exchange_layer of the field it reads (phi before mu is formed, mu before phi moves) and
+ * phi's layers exchanged at the end; the modulus refreshed.  allreduce_max replaces
+ * values[0..n) by their maxima over the slabs.  metrics [8] (may be NULL) receives, as the
+ * petto_optimize callback does: step, C, F.u, rel_res, sweeps, seconds, mean phi_0, and the
+ * multiplier of phase 0 (projected) or mean phi_0 before the step (penalty) -- all of the
+ * whole grid.  Every slab owns two node planes or more (then a slab's top layer has a layer
+ * above it exactly when the slab has an upper neighbour; PETTO_EINVAL for a slab of one).
+ * Elasticity with one load case, no keep-out term (PETTO_EUNSUPPORTED otherwise); FP64
+ * refinement is not decomposed (as petto_slab_solve).  PETTO_EINVAL for a null hook or bad
+ * options; PETTO_ENOTCONV when the solve missed its tolerance (the step is still taken). */
+petto_status petto_slab_design_step(petto_ctx *ctx, const petto_solve_opts *so, const petto_pf_opts *po,
+                                    petto_exchange_fn exchange, petto_layer_exchange_fn exchange_layer,
+                                    petto_allreduce_fn allreduce, petto_allreduce_fn allreduce_max, void *user,
+                                    double *metrics);
+
 /* opts->ch_steps explicit Cahn-Hilliard steps (Sec. 2.4); refreshes the modulus field. */
 petto_status petto_cahn_hilliard(petto_ctx *ctx, const petto_pf_opts *opts);
 

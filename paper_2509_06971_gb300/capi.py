@@ -22,6 +22,7 @@ PETTO_F32, PETTO_F64, PETTO_BF16, PETTO_F16 = 0, 1, 2, 3
 PETTO_VOL_PROJECTED, PETTO_VOL_PENALTY = 0, 1
 PETTO_SOLVE_PAPER, PETTO_SOLVE_TOL = 0, 1
 PETTO_SWEEP_APT, PETTO_SWEEP_PT = 0, 1
+PETTO_LAYER_PHI, PETTO_LAYER_MU = 0, 1
 
 _i64 = ctypes.c_int64
 _dbl = ctypes.c_double
@@ -70,6 +71,7 @@ class petto_pf_opts(ctypes.Structure):
 petto_step_cb = ctypes.CFUNCTYPE(None, ctypes.POINTER(_dbl), _vp)
 petto_exchange_fn = ctypes.CFUNCTYPE(_int, _vp, _vp)
 petto_allreduce_fn = ctypes.CFUNCTYPE(_int, ctypes.POINTER(_dbl), _int, _vp)
+petto_layer_exchange_fn = ctypes.CFUNCTYPE(_int, _vp, _int, _int, _vp)
 
 _P = ctypes.POINTER
 _SIGS = {
@@ -106,6 +108,12 @@ _SIGS = {
     "petto_set_owned_planes": (_int, [_vp, _i64, _i64, _i64]),
     "petto_slab_solve": (_int, [_vp, _P(petto_solve_opts), petto_exchange_fn, petto_allreduce_fn, _vp,
                                 _P(petto_solve_report)]),
+    "petto_slab_design_step": (_int, [_vp, _P(petto_solve_opts), _P(petto_pf_opts), petto_exchange_fn,
+                                      petto_layer_exchange_fn, petto_allreduce_fn, petto_allreduce_fn, _vp,
+                                      _P(_dbl)]),
+    "petto_layer_bytes": (_i64, [_vp, _int]),
+    "petto_get_layer": (_int, [_vp, _int, _int, _i64, _vp, _int]),
+    "petto_set_layer": (_int, [_vp, _int, _int, _i64, _vp, _int]),
     "petto_get_plane": (_int, [_vp, _i64, _vp, _int, _int]),
     "petto_set_plane": (_int, [_vp, _i64, _vp, _int, _int]),
     "petto_set_keepout": (_int, [_vp, _P(_i64), _P(_dbl), _dbl]),

@@ -50,6 +50,9 @@ struct petto_ctx {
     void *w = nullptr, *E = nullptr, *phi = nullptr, *s = nullptr, *dscr = nullptr, *mu = nullptr;
     void *rbuf = nullptr, *stage = nullptr;
     void *w_alt = nullptr;  // second w buffer of the 2D sweeps several per launch (kind 7)
+    // a slab's copies of the cell layer above its top layer (the neighbour's first own layer):
+    // phi ([P][nx ny], storage type) and mu ([nx ny]), for the Cahn-Hilliard step
+    void *phi_hi = nullptr, *mu_hi = nullptr;
     size_t stage_bytes = 0;
     double *scal = nullptr;
     unsigned *counter = nullptr;
@@ -626,7 +629,7 @@ void petto_destroy(petto_ctx *ctx) {
     clear_graphs(ctx);
     void *bufs[] = {ctx->u[0], ctx->u[1], ctx->w, ctx->w_alt, ctx->E, ctx->phi, ctx->s, ctx->dscr, ctx->mu, ctx->rbuf,
                     ctx->stage, ctx->scal, ctx->counter, ctx->tile_ptr, ctx->loads, ctx->partials,
-                    ctx->gtile_ptr, ctx->gloads, ctx->ctrl, ctx->u64, ctx->r64, ctx->rhs32};
+                    ctx->gtile_ptr, ctx->gloads, ctx->ctrl, ctx->u64, ctx->r64, ctx->rhs32, ctx->phi_hi, ctx->mu_hi};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (ctx->owns_stream) cudaStreamDestroy(ctx->stream);
@@ -1469,6 +1472,54 @@ petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_sol
     return PETTO_OK;
 }
 
+int64_t petto_layer_bytes(const petto_ctx *ctx, int field) {
+    if (!ctx || ctx->dim != 3 || (field != PETTO_LAYER_PHI && field != PETTO_LAYER_MU)) return 0;
+    return (int64_t)ctx->L.nx * ctx->L.ny * (field == PETTO_LAYER_PHI ? ctx->ssize() : ctx->tsize());
+}
+
+}  // extern "C"
+
+namespace {
+
+// the address of cell layer k of a field (k = nz: the copy of the layer above the grid)
+petto_status layer_ptr(petto_ctx *ctx, int field, int phase, int64_t k, char **out) {
+    if (ctx->dim != 3) return fail(ctx, PETTO_EUNSUPPORTED, "cell layers are z layers of a 3D grid");
+    if (field != PETTO_LAYER_PHI && field != PETTO_LAYER_MU) return fail(ctx, PETTO_EINVAL, "field is phi or mu");
+    if (field == PETTO_LAYER_PHI && (phase < 0 || phase >= ctx->P)) return fail(ctx, PETTO_EINVAL, "no such phase");
+    if (k < 0 || k > ctx->L.nz) return fail(ctx, PETTO_EINVAL, "cell layer outside the grid");
+    const int64_t pl = (int64_t)ctx->L.nx * ctx->L.ny, nc = ctx->L.ncells();
+    const size_t es = field == PETTO_LAYER_PHI ? ctx->ssize() : ctx->tsize();
+    if (k == ctx->L.nz) {
+        void *&hi = field == PETTO_LAYER_PHI ? ctx->phi_hi : ctx->mu_hi;
+        if (!hi) {
+            const size_t bytes = (size_t)(field == PETTO_LAYER_PHI ? ctx->P : 1) * pl * es;
+            CK(cudaMalloc(&hi, bytes));
+            CK(cudaMemsetAsync(hi, 0, bytes, ctx->stream));
+        }
+        *out = static_cast<char *>(hi) + (field == PETTO_LAYER_PHI ? (int64_t)phase * pl * es : 0);
+        return PETTO_OK;
+    }
+    char *base = static_cast<char *>(field == PETTO_LAYER_PHI ? ctx->phi : ctx->mu);
+    *out = base + ((field == PETTO_LAYER_PHI ? (int64_t)phase * nc : 0) + k * pl) * (int64_t)es;
+    return PETTO_OK;
+}
+
+petto_status copy_layer(petto_ctx *ctx, int field, int phase, int64_t k, void *dst, const void *src, int on_device) {
+    if (!ctx || (!dst && !src)) return fail(ctx, PETTO_EINVAL, "null argument");
+    char *lp = nullptr;
+    petto_status st = layer_ptr(ctx, field, phase, k, &lp);
+    if (st != PETTO_OK) return st;
+    const size_t bytes = (size_t)petto_layer_bytes(ctx, field);
+    if (dst) CK(cudaMemcpyAsync(dst, lp, bytes, cudaMemcpyDefault, ctx->stream));
+    else CK(cudaMemcpyAsync(lp, src, bytes, cudaMemcpyDefault, ctx->stream));
+    if (!on_device) CK(cudaStreamSynchronize(ctx->stream));  // host memory is the caller's again on return
+    return PETTO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 petto_status petto_slab_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_exchange_fn exchange,
                               petto_allreduce_fn allreduce, void *user, petto_solve_report *rep) {
     if (!ctx || !o || !exchange || !allreduce) return fail(ctx, PETTO_EINVAL, "null argument");
@@ -1555,6 +1606,173 @@ petto_status petto_slab_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_e
     if (!std::isfinite(S.last) && S.sweeps > 0) return fail(ctx, PETTO_EDIVERGED, "residual not finite after PT fallback");
     if (o->mode == PETTO_SOLVE_TOL && !reached) return PETTO_ENOTCONV;
     return PETTO_OK;
+}
+
+petto_status petto_slab_design_step(petto_ctx *ctx, const petto_solve_opts *so, const petto_pf_opts *po,
+                                    petto_exchange_fn exchange, petto_layer_exchange_fn exchange_layer,
+                                    petto_allreduce_fn allreduce, petto_allreduce_fn allreduce_max, void *user,
+                                    double *metrics) {
+    if (!ctx || !so || !po || !exchange || !exchange_layer || !allreduce || !allreduce_max)
+        return fail(ctx, PETTO_EINVAL, "null argument");
+    if (ctx->dim != 3) return fail(ctx, PETTO_EUNSUPPORTED, "slabs are z ranges of a 3D grid");
+    if (ctx->physics != PETTO_ELASTIC || ctx->keep || ctx->nrhs != 1)
+        return fail(ctx, PETTO_EUNSUPPORTED, "the slab design step covers one-load-case elasticity without keep-out");
+    if (po->vol_mode != PETTO_VOL_PROJECTED && po->vol_mode != PETTO_VOL_PENALTY)
+        return fail(ctx, PETTO_EINVAL, "bad vol_mode");
+    if (po->n_bisect < 0 || po->n_bisect > 200 || po->ch_steps < 0) return fail(ctx, PETTO_EINVAL, "bad counts");
+    if (ctx->own_n == 1) return fail(ctx, PETTO_EINVAL, "a slab of the design step owns two node planes or more");
+    const auto t0 = std::chrono::steady_clock::now();
+    const int P = ctx->P;
+    const Layout &L = ctx->L;
+    const int64_t pl = (int64_t)L.nx * L.ny;
+    // the cell layers this slab counts: those whose lower node plane it owns
+    const int zc0 = ctx->own_n ? ctx->own_lo : 0;
+    const int zc1 = ctx->own_n ? std::min(ctx->own_lo + ctx->own_n, L.nz) : L.nz;
+    double ncount = (double)pl * (zc1 - zc0);
+    petto_status st = allreduce(&ncount, 1, user);
+    if (st != PETTO_OK) return st;
+    // 1. the state solve, then the ghost planes brought up to date for the sensitivity
+    petto_solve_report rep{};
+    st = petto_slab_solve(ctx, so, exchange, allreduce, user, &rep);
+    const bool notconv = st == PETTO_ENOTCONV;
+    if (st != PETTO_OK && !notconv) return st;
+    st = exchange(ctx, user);
+    if (st != PETTO_OK) return st;
+    // 2. sensitivity of every held cell (a ghost layer gets its owner's bits); C and F.u over
+    //    this slab's own layers and planes, max |s_i| over the whole grid
+    CK(cudaMemsetAsync(ctx->scal + SC_SMAX, 0, sizeof(double) * MAX_PHASES, ctx->stream));
+    SensArgs sa{};
+    sa.L = L;
+    sa.physics = ctx->physics;
+    sa.ncomp = ctx->ncomp;
+    sa.nrhs = ctx->nrhs;
+    sa.k = ctx->k;
+    sa.lam = ctx->lam0;
+    sa.mu = ctx->mu0;
+    sa.h = ctx->h;
+    sa.zc0 = zc0;
+    sa.zc1 = zc1;
+    DesignArgs d = design_args(ctx);
+    CK(launch_sensitivity(sa, d, ctx->u[ctx->cur], ctx->E, ctx->phi, ctx->s, ctx->scal, ctx->red(), ctx->stream));
+    CK(launch_work(L, ctx->ncomp, ctx->nrhs, ctx->precision, ctx->loads, ctx->n_loads, ctx->u[ctx->cur], 0.0,
+                   ctx->scal, ctx->red(), ctx->stream));
+    ctx->launches += 2;
+    double sc[SC_N];
+    st = read_scal(ctx, sc);
+    if (st != PETTO_OK) return st;
+    double cw[2] = {sc[SC_C], sc[SC_W]};
+    double smax[MAX_PHASES];
+    for (int q = 0; q < P; ++q) smax[q] = sc[SC_SMAX + q];
+    st = allreduce(cw, 2, user);
+    if (st == PETTO_OK) st = allreduce_max(smax, P, user);
+    if (st != PETTO_OK) return st;
+    CK(cudaMemcpyAsync(ctx->scal + SC_SMAX, smax, sizeof(double) * P, cudaMemcpyHostToDevice, ctx->stream));
+    // 3. the design update on every held cell, with the whole grid's sums: the means (penalty)
+    //    and the bisection's bracket (projected) move on the host
+    auto grid_means = [&](double *mean) -> petto_status {
+        CK(launch_layer_sums(L, P, ctx->storage, ctx->phi, zc0, zc1, ctx->scal, SC_SUM, ctx->red(), ctx->stream));
+        ctx->launches++;
+        double s2[SC_N];
+        petto_status e = read_scal(ctx, s2);
+        if (e != PETTO_OK) return e;
+        for (int q = 0; q < P; ++q) mean[q] = s2[SC_SUM + q];
+        e = allreduce(mean, P, user);
+        if (e != PETTO_OK) return e;
+        for (int q = 0; q < P; ++q) mean[q] /= ncount;
+        return PETTO_OK;
+    };
+    UpdateArgs ua{};
+    ua.ncell = L.ncells();
+    ua.P = P;
+    ua.vol_mode = po->vol_mode;
+    ua.n_bisect = po->n_bisect;
+    ua.precision = ctx->precision;
+    ua.storage = ctx->storage;
+    ua.alpha_h = po->alpha_h;
+    ua.kappa_v = po->kappa_v;
+    ua.kappa_1 = po->kappa_1;
+    for (int q = 0; q < P; ++q) ua.V[q] = ctx->vol[q];
+    ua.nx = L.nx;
+    ua.ny = L.ny;
+    ua.ext = 1;
+    ua.zc0 = zc0;
+    ua.zc1 = zc1;
+    ua.layer = pl;
+    double mean[MAX_PHASES] = {0}, lam[MAX_PHASES] = {0};
+    if (po->vol_mode == PETTO_VOL_PENALTY) {
+        st = grid_means(mean);
+        if (st != PETTO_OK) return st;
+        CK(cudaMemcpyAsync(ctx->scal + SC_MEAN, mean, sizeof(double) * P, cudaMemcpyHostToDevice, ctx->stream));
+        for (int q = 0; q < P; ++q) lam[q] = mean[q];
+    }
+    CK(launch_update(ua, ctx->phi, ctx->s, ctx->dscr, ctx->scal, ctx->red(), ctx->stream, &ctx->launches));
+    if (po->vol_mode == PETTO_VOL_PROJECTED) {
+        double br[2 * MAX_PHASES];  // [lo_0 .. lo_P-1 | hi_0 .. hi_P-1] as in scal
+        for (int q = 0; q < P; ++q) {
+            br[q] = -2.0;
+            br[MAX_PHASES + q] = 2.0;
+        }
+        for (int it = 0; it <= po->n_bisect; ++it) {
+            CK(cudaMemcpyAsync(ctx->scal + SC_LO, br, sizeof(double) * P, cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(ctx->scal + SC_HI, br + MAX_PHASES, sizeof(double) * P, cudaMemcpyHostToDevice,
+                               ctx->stream));
+            if (it == po->n_bisect) break;  // the final bracket is on the device
+            CK(launch_bisect_sums(ua, ctx->dscr, ctx->scal, ctx->red(), ctx->stream));
+            ctx->launches++;
+            double s2[SC_N], sums[MAX_PHASES];
+            st = read_scal(ctx, s2);
+            if (st != PETTO_OK) return st;
+            for (int q = 0; q < P; ++q) sums[q] = s2[SC_SUM + q];
+            st = allreduce(sums, P, user);
+            if (st != PETTO_OK) return st;
+            for (int q = 0; q < P; ++q) {
+                const double m = sums[q] / ncount, md = 0.5 * (br[q] + br[MAX_PHASES + q]);
+                if (m > ua.V[q]) br[q] = md;
+                else br[MAX_PHASES + q] = md;
+            }
+        }
+        CK(launch_update_apply(ua, ctx->phi, ctx->dscr, ctx->scal, ctx->stream));
+        ctx->launches++;
+        for (int q = 0; q < P; ++q) lam[q] = 0.5 * (br[q] + br[MAX_PHASES + q]);
+    }
+    ctx->have_sens = false;
+    // 4. Cahn-Hilliard: phi's layers next to each interface are exchanged before mu is formed,
+    //    mu's before phi moves, and phi's again at the end (the ghost layer and the copy of the
+    //    layer above then hold their owners' values)
+    for (int t = 0; t < po->ch_steps; ++t)
+        for (int q = 0; q < P; ++q) {
+            char *dummy = nullptr;
+            st = layer_ptr(ctx, PETTO_LAYER_PHI, q, L.nz, &dummy);  // makes the copies of the layer above
+            if (st == PETTO_OK) st = layer_ptr(ctx, PETTO_LAYER_MU, 0, L.nz, &dummy);
+            if (st == PETTO_OK) st = exchange_layer(ctx, PETTO_LAYER_PHI, q, user);
+            if (st != PETTO_OK) return st;
+            const void *phh = ctx->own_n && ctx->own_lo + ctx->own_n < L.NZ ? ctx->phi_hi : nullptr;
+            const void *muh = ctx->own_n && ctx->own_lo + ctx->own_n < L.NZ ? ctx->mu_hi : nullptr;
+            CK(launch_ch_half(L, q, 0, ctx->storage, ctx->precision, po->gamma_g, po->tau, ctx->phi, ctx->mu, phh, muh,
+                              ctx->stream));
+            st = exchange_layer(ctx, PETTO_LAYER_MU, q, user);
+            if (st != PETTO_OK) return st;
+            CK(launch_ch_half(L, q, 1, ctx->storage, ctx->precision, po->gamma_g, po->tau, ctx->phi, ctx->mu, phh, muh,
+                              ctx->stream));
+            ctx->launches += 2;
+        }
+    if (po->ch_steps > 0)
+        for (int q = 0; q < P; ++q) {
+            st = exchange_layer(ctx, PETTO_LAYER_PHI, q, user);
+            if (st != PETTO_OK) return st;
+        }
+    st = refresh_material(ctx);
+    if (st != PETTO_OK) return st;
+    ctx->step++;
+    if (metrics) {
+        double vol[MAX_PHASES];
+        st = grid_means(vol);
+        if (st != PETTO_OK) return st;
+        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        const double m[8] = {(double)ctx->step, cw[0], cw[1], rep.rel_res, (double)rep.sweeps, secs, vol[0], lam[0]};
+        std::memcpy(metrics, m, sizeof(m));
+    }
+    return notconv ? PETTO_ENOTCONV : PETTO_OK;
 }
 
 petto_status petto_set_wait_limit(petto_ctx *ctx, int tries) {
@@ -1788,6 +2006,14 @@ petto_status petto_get_plane(petto_ctx *ctx, int64_t k, void *dst, int dtype, in
 
 petto_status petto_set_plane(petto_ctx *ctx, int64_t k, const void *src, int dtype, int on_device) {
     return copy_plane(ctx, k, nullptr, src, dtype, on_device);
+}
+
+petto_status petto_get_layer(petto_ctx *ctx, int field, int phase, int64_t k, void *dst, int on_device) {
+    return copy_layer(ctx, field, phase, k, dst, nullptr, on_device);
+}
+
+petto_status petto_set_layer(petto_ctx *ctx, int field, int phase, int64_t k, const void *src, int on_device) {
+    return copy_layer(ctx, field, phase, k, nullptr, src, on_device);
 }
 
 petto_status petto_cahn_hilliard(petto_ctx *ctx, const petto_pf_opts *o) {

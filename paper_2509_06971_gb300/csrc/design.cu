@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256) sensitivity_kernel(const SensArgs sa, con
             e += cell_energy<T, DIM, PHYS>(lam, mu, hs, ul);
         }
         const T Ec = E[L.cell(i, j, k)];
-        comp += Ec * e;
+        if (k >= sa.zc0 && k < sa.zc1) comp += Ec * e;  // a slab counts its own cell layers
 #pragma unroll
         for (int p = 0; p < MAX_PHASES; ++p) {
             if (p >= d.P) break;
@@ -284,14 +284,22 @@ __global__ void __launch_bounds__(256) bis_step(const UpdateArgs ua, const T *__
     // element arithmetic in T (FP32 for the FP32 path: the FP64 pipe is narrow), FP64 block sums
     const T mid = (T)(0.5 * (scal[SC_LO + p] + scal[SC_HI + p]));
     T acc = 0;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
+    // ext: a slab of a decomposed grid sums its own cell layers only and leaves the
+    // bracket to the host, which adds the slabs' sums
+    const int64_t c0 = ua.ext ? (int64_t)ua.zc0 * ua.layer : 0, c1 = ua.ext ? (int64_t)ua.zc1 * ua.layer : nc;
+    for (int64_t c = c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < c1; c += (int64_t)gridDim.x * blockDim.x)
         acc += clamp01<T>(dbuf[(int64_t)p * nc + c] - mid);
     const double t = block_sum((double)acc, sh);
     if (publish_partial(t, rb, (int64_t)p * gridDim.x + blockIdx.x, gridDim.x * gridDim.y)) {
 #pragma unroll
         for (int q = 0; q < MAX_PHASES; ++q) {
             if (q >= ua.P) break;
-            const double m = sum_partials(rb, (int64_t)q * gridDim.x, gridDim.x, sh) / (double)nc;
+            const double sq = sum_partials(rb, (int64_t)q * gridDim.x, gridDim.x, sh);
+            if (ua.ext) {
+                if (threadIdx.x == 0) scal[SC_SUM + q] = sq;
+                continue;
+            }
+            const double m = sq / (double)nc;
             if (threadIdx.x == 0) {
                 volatile double *vs = scal;
                 const double md = 0.5 * (vs[SC_LO + q] + vs[SC_HI + q]);
@@ -316,8 +324,10 @@ __global__ void upd_apply(const UpdateArgs ua, S *__restrict__ phi, const T *__r
 
 // -------------------------------------------------------------- Cahn-Hilliard
 
+// hi: the cell layer above the grid's top layer (a slab's neighbour), or null for the no-flux
+// boundary there
 template <typename T, typename S>
-__device__ __forceinline__ T lap_at(const Layout &L, const S *v, int64_t c, int i, int j, int k) {
+__device__ __forceinline__ T lap_at(const Layout &L, const S *v, int64_t c, int i, int j, int k, const S *hi) {
     const T x = (T)Store<S>::ld(v, c);
     T s = 0;
     if (i > 0) s += (T)Store<S>::ld(v, c - 1) - x;
@@ -328,6 +338,7 @@ __device__ __forceinline__ T lap_at(const Layout &L, const S *v, int64_t c, int 
         const int64_t pl = (int64_t)L.nx * L.ny;
         if (k > 0) s += (T)Store<S>::ld(v, c - pl) - x;
         if (k < L.nz - 1) s += (T)Store<S>::ld(v, c + pl) - x;
+        else if (hi) s += (T)Store<S>::ld(hi, c - (int64_t)k * pl) - x;
     }
     return s;
 }
@@ -336,39 +347,44 @@ __device__ __forceinline__ float dwell(float x) { return sinpif(2.0f * x) * (flo
 __device__ __forceinline__ double dwell(double x) { return sinpi(2.0 * x) * (3.14159265358979323846 / 64.0); }
 
 template <typename T, typename S>
-__global__ void ch_mu(const Layout L, const S *__restrict__ phi, T *__restrict__ mu, double gamma_g) {
+__global__ void ch_mu(const Layout L, const S *__restrict__ phi, T *__restrict__ mu, double gamma_g,
+                      const S *__restrict__ phi_hi) {
     const int64_t nc = L.ncells();
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         int i, j, k;
         cell_ijk(L, c, i, j, k);
         const T ph = (T)Store<S>::ld(phi, c);
-        mu[c] = dwell(ph) - (T)gamma_g * lap_at<T, S>(L, phi, c, i, j, k);
+        mu[c] = dwell(ph) - (T)gamma_g * lap_at<T, S>(L, phi, c, i, j, k, phi_hi);
     }
 }
 
 template <typename T, typename S>
-__global__ void ch_phi(const Layout L, S *__restrict__ phi, const T *__restrict__ mu, double tau) {
+__global__ void ch_phi(const Layout L, S *__restrict__ phi, const T *__restrict__ mu, double tau,
+                       const T *__restrict__ mu_hi) {
     const int64_t nc = L.ncells();
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
         int i, j, k;
         cell_ijk(L, c, i, j, k);
-        const T nv = (T)Store<S>::ld(phi, c) + (T)tau * lap_at<T, T>(L, mu, c, i, j, k);
+        const T nv = (T)Store<S>::ld(phi, c) + (T)tau * lap_at<T, T>(L, mu, c, i, j, k, mu_hi);
         Store<S>::st(phi, c, nv);
     }
 }
 
+// scal[slot + p] = (sum of phase p over cells c0 .. c1 - 1) / div, in FP64 with the
+// deterministic reduction
 template <typename S>
-__global__ void mean_kernel(int64_t nc, int P, const S *__restrict__ phi, double *scal, const RedBuf rb) {
+__global__ void mean_kernel(int64_t nc, int P, const S *__restrict__ phi, double *scal, const RedBuf rb, int64_t c0,
+                            int64_t c1, double div, int slot) {
     __shared__ double sh[32];
     const int p = blockIdx.y;
     double acc = 0.0;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t c = c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < c1; c += (int64_t)gridDim.x * blockDim.x)
         acc += (double)Store<S>::ld(phi, (int64_t)p * nc + c);
     const double t = block_sum(acc, sh);
     if (publish_partial(t, rb, (int64_t)p * gridDim.x + blockIdx.x, gridDim.x * gridDim.y)) {
         for (int q = 0; q < P; ++q) {
             const double m = sum_partials(rb, (int64_t)q * gridDim.x, gridDim.x, sh);
-            if (threadIdx.x == 0) scal[SC_MEAN + q] = m / (double)nc;
+            if (threadIdx.x == 0) scal[slot + q] = m / div;
         }
         if (threadIdx.x == 0) *rb.counter = 0u;
     }
@@ -474,7 +490,32 @@ cudaError_t launch_mean(const Layout &L, int P, int storage, const void *phi, do
     const int64_t nc = L.ncells();
     dim3 grid(grid_for(nc, 256, 152 * 4), P);
     PETTO_DISPATCH_STORAGE(storage, S,
-        mean_kernel<S><<<grid, 256, 0, st>>>(nc, P, static_cast<const S *>(phi), scal, rb))
+        mean_kernel<S><<<grid, 256, 0, st>>>(nc, P, static_cast<const S *>(phi), scal, rb, 0, nc, (double)nc,
+                                             SC_MEAN))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_layer_sums(const Layout &L, int P, int storage, const void *phi, int zc0, int zc1, double *scal,
+                              int slot, RedBuf rb, cudaStream_t st) {
+    const int64_t nc = L.ncells(), pl = (int64_t)L.nx * L.ny;
+    dim3 grid(grid_for(nc, 256, 152 * 4), P);
+    PETTO_DISPATCH_STORAGE(storage, S,
+        mean_kernel<S><<<grid, 256, 0, st>>>(nc, P, static_cast<const S *>(phi), scal, rb, (int64_t)zc0 * pl,
+                                             (int64_t)zc1 * pl, 1.0, slot))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bisect_sums(const UpdateArgs &ua, const void *dscratch, double *scal, RedBuf rb, cudaStream_t st) {
+    dim3 grid(grid_for(ua.ncell, 256, 152 * 4), ua.P);
+    PETTO_DISPATCH_PREC(ua.precision, T, bis_step<T><<<grid, 256, 0, st>>>(ua, static_cast<const T *>(dscratch), scal, rb))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_apply(const UpdateArgs &ua, void *phi, const void *dscratch, double *scal, cudaStream_t st) {
+    dim3 grid2(grid_for(ua.ncell, 256), ua.P);
+    PETTO_DISPATCH_PREC(ua.precision, T,
+        PETTO_DISPATCH_STORAGE(ua.storage, S,
+            upd_apply<T, S><<<grid2, 256, 0, st>>>(ua, static_cast<S *>(phi), static_cast<const T *>(dscratch), scal)))
     return cudaGetLastError();
 }
 
@@ -494,7 +535,7 @@ cudaError_t launch_update(const UpdateArgs &ua, void *phi, const void *s, void *
             upd_prepare<T, S><<<g, 256, 0, st>>>(ua, static_cast<S *>(phi), static_cast<const T *>(s),
                                                  static_cast<T *>(dscratch), scal)))
     *launches += 1;
-    if (ua.vol_mode != 0) return cudaGetLastError();
+    if (ua.vol_mode != 0 || ua.ext) return cudaGetLastError();  // ext: the host runs the bisection
     bis_init<<<1, 32, 0, st>>>(ua.P, scal);
     *launches += 1;
     dim3 grid(grid_for(ua.ncell, 256, 152 * 4), ua.P);
@@ -519,10 +560,24 @@ cudaError_t launch_ch(const Layout &L, int P, int storage, int precision, double
         PETTO_DISPATCH_PREC(precision, T,
             PETTO_DISPATCH_STORAGE(storage, S,
                 S *ph = static_cast<S *>(phi) + (int64_t)p * nc;
-                ch_mu<T, S><<<g, 256, 0, st>>>(L, ph, static_cast<T *>(mu_scratch), gamma_g);
-                ch_phi<T, S><<<g, 256, 0, st>>>(L, ph, static_cast<const T *>(mu_scratch), tau)))
+                ch_mu<T, S><<<g, 256, 0, st>>>(L, ph, static_cast<T *>(mu_scratch), gamma_g, nullptr);
+                ch_phi<T, S><<<g, 256, 0, st>>>(L, ph, static_cast<const T *>(mu_scratch), tau, nullptr)))
         *launches += 2;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ch_half(const Layout &L, int p, int half, int storage, int precision, double gamma_g, double tau,
+                           void *phi, void *mu_scratch, const void *phi_hi, const void *mu_hi, cudaStream_t st) {
+    const int64_t nc = L.ncells(), pl = (int64_t)L.nx * L.ny;
+    const int g = grid_for(nc, 256);
+    PETTO_DISPATCH_PREC(precision, T,
+        PETTO_DISPATCH_STORAGE(storage, S,
+            S *ph = static_cast<S *>(phi) + (int64_t)p * nc;
+            const S *phh = phi_hi ? static_cast<const S *>(phi_hi) + (int64_t)p * pl : nullptr;
+            if (half == 0) ch_mu<T, S><<<g, 256, 0, st>>>(L, ph, static_cast<T *>(mu_scratch), gamma_g, phh);
+            else ch_phi<T, S><<<g, 256, 0, st>>>(L, ph, static_cast<const T *>(mu_scratch), tau,
+                                                  static_cast<const T *>(mu_hi))))
     return cudaGetLastError();
 }
 

@@ -383,6 +383,7 @@ struct SensArgs {
     OpConst k;
     double lam, mu;      // unit Lame constants (elastic)
     double h;
+    int zc0 = 0, zc1 = 1 << 30;  // cell layers whose energy enters the compliance (a slab's own)
 };
 
 // scal layout (device doubles): [0] sum R^2, [1] compliance, [2] work, [8..8+P) max|s_i|,
@@ -411,11 +412,26 @@ struct UpdateArgs {
     int klo[3], khi[3];
     double kappa_b;
     double Vb[MAX_PHASES];
+    // a slab of a decomposed grid (ext = 1): the bisection sums its own cell layers zc0 .. zc1 - 1
+    // (layer cells each) into scal[SC_SUM + p] and the host moves the bracket
+    int ext = 0;
+    int zc0 = 0, zc1 = 0;
+    int64_t layer = 0;
 };
 
 cudaError_t launch_update(const UpdateArgs &ua, void *phi, const void *s, void *dscratch, double *scal,
                           RedBuf rb, cudaStream_t st, int64_t *launches);
 
+// One half of a Cahn-Hilliard step for phase p (half 0: mu, 1: phi), with the cell layers above
+// the top layer taken from phi_hi ([P][layer]) / mu_hi ([layer]) when given (a slab's neighbour)
+cudaError_t launch_ch_half(const Layout &L, int p, int half, int storage, int precision, double gamma_g, double tau,
+                           void *phi, void *mu_scratch, const void *phi_hi, const void *mu_hi, cudaStream_t st);
+// scal[slot + p] = sum of phase p over cell layers zc0 .. zc1 - 1
+cudaError_t launch_layer_sums(const Layout &L, int P, int storage, const void *phi, int zc0, int zc1, double *scal,
+                              int slot, RedBuf rb, cudaStream_t st);
+// the bisection's sums at the bracket midpoint (ua.ext), and the clamp at lambda = its final midpoint
+cudaError_t launch_bisect_sums(const UpdateArgs &ua, const void *dscratch, double *scal, RedBuf rb, cudaStream_t st);
+cudaError_t launch_update_apply(const UpdateArgs &ua, void *phi, const void *dscratch, double *scal, cudaStream_t st);
 cudaError_t launch_ch(const Layout &L, int P, int storage, int precision, double gamma_g, double tau,
                       void *phi, void *mu_scratch, cudaStream_t st, int64_t *launches);
 

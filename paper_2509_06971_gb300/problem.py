@@ -344,6 +344,70 @@ class Problem:
         self._ck(st, allow=(C.PETTO_OK, C.PETTO_ENOTCONV))
         return _report(rep, st)
 
+    def slab_design_step(self, exchange, exchange_layer, allreduce, allreduce_max, solve_kw=None, pf_kw=None) -> dict:
+        """One design loop of one slab of a decomposed grid (petto_slab_design_step):
+        exchange() fills the ghost planes, exchange_layer(field, phase) the cell layers next to
+        each interface, allreduce / allreduce_max (list of floats) return the sums / maxima
+        over the slabs.  Returns the whole grid's metrics of the step."""
+        so = self.solve_opts(**(solve_kw or {}))
+        po = self.pf_opts(**(pf_kw or {}))
+        errors = []
+
+        def guard(fn):
+            def call(*args):
+                try:
+                    fn(*args)
+                    return C.PETTO_OK
+                except BaseException as e:  # noqa: BLE001 -- handed back to the caller below
+                    errors.append(e)
+                    return C.PETTO_EINVAL
+            return call
+
+        def reducer(fn):
+            def call(values, n, user):
+                out = fn([values[i] for i in range(n)])
+                for i in range(n):
+                    values[i] = float(out[i])
+            return guard(call)
+
+        ex = C.petto_exchange_fn(guard(lambda ctx, user: exchange()))
+        exl = C.petto_layer_exchange_fn(guard(lambda ctx, field, phase, user: exchange_layer(field, phase)))
+        ar, am = C.petto_allreduce_fn(reducer(allreduce)), C.petto_allreduce_fn(reducer(allreduce_max))
+        m = (ctypes.c_double * 8)()
+        st = self.lib.petto_slab_design_step(self.ctx, ctypes.byref(so), ctypes.byref(po), ex, exl, ar, am, None, m)
+        if errors:
+            raise errors[0]
+        self._ck(st, allow=(C.PETTO_OK, C.PETTO_ENOTCONV))
+        return {"step": int(m[0]), "compliance": m[1], "work": m[2], "rel_res": m[3], "sweeps": int(m[4]),
+                "seconds": m[5], "mean_phi0": m[6], "lambda0": m[7], "converged": st == C.PETTO_OK}
+
+    def layer_bytes(self, field: int) -> int:
+        return int(self.lib.petto_layer_bytes(self.ctx, int(field)))
+
+    def _layer_buf(self, field, buf):
+        """(pointer, on_device) of a layer buffer of petto_layer_bytes bytes: a contiguous CUDA
+        tensor (stream-ordered copy) or a host array / tensor."""
+        nb = self.layer_bytes(field)  # 0 for a field the library rejects (it reports the error)
+        if _is_cuda_tensor(buf):
+            if not buf.is_contiguous() or (nb and buf.numel() * buf.element_size() != nb):
+                raise ValueError("layer buffers are contiguous, petto_layer_bytes long")
+            return buf.data_ptr(), 1
+        arr = buf.numpy() if hasattr(buf, "numpy") else buf
+        if not arr.flags.c_contiguous or (nb and arr.nbytes != nb):
+            raise ValueError("layer buffers are contiguous, petto_layer_bytes long")
+        return arr.ctypes.data, 0
+
+    def get_layer(self, field: int, phase: int, k: int, out):
+        """Cell layer k (k = nz: the copy of the layer above) of phi's phase (field 0, storage
+        type) or mu (field 1, sweep precision) into out, raw bytes."""
+        ptr, dev = self._layer_buf(field, out)
+        self._ck(self.lib.petto_get_layer(self.ctx, int(field), int(phase), int(k), ctypes.c_void_p(ptr), dev))
+        return out
+
+    def set_layer(self, field: int, phase: int, k: int, src):
+        ptr, dev = self._layer_buf(field, src)
+        self._ck(self.lib.petto_set_layer(self.ctx, int(field), int(phase), int(k), ctypes.c_void_p(ptr), dev))
+
     def solve(self, mode=None, **kw) -> dict:
         o = self.solve_opts(mode, **kw)
         rep = C.petto_solve_report()

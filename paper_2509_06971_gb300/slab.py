@@ -21,8 +21,13 @@ Two drivers share this host logic:
 
 The state solve is decomposed: sweeps, residuals, and the solve loop itself, which runs in
 the library (``petto_slab_solve``) with this module's exchange and all-reduce as its hooks
-(fixed or adaptive-restart momentum, PT; the FP64 refinement is not decomposed).  The design
-step stays with a whole-grid context.
+(fixed or adaptive-restart momentum, PT; the FP64 refinement is not decomposed).  So is the
+design loop (``petto_slab_design_step``): a slab owns the cell layers whose lower node plane
+it owns, holds the layer below its first one (its ghost layer) and keeps a copy of the layer
+above its top one; the sensitivity, the update and the modulus are computed on every held
+layer (a ghost layer gets its owner's bits), the compliance, the means and the bisection's
+sums over the owned ones (all-reduced), and the Cahn-Hilliard step exchanges phi's and mu's
+interface layers around each half step.
 """
 from __future__ import annotations
 
@@ -121,6 +126,32 @@ def interface_copies(geom: list[SlabGeom]):
     return out
 
 
+def owned_layers(g: SlabGeom, nz: int) -> tuple[int, int]:
+    """The cell layers a slab owns, whole-grid indices [c0, c1): those whose lower node plane
+    it owns."""
+    return g.k0, min(g.k1 + 1, nz)
+
+
+def design_step_ok(geom: list[SlabGeom]) -> bool:
+    """The decomposed design step needs every slab to own two node planes or more: then
+    every slab owns a cell layer, and a slab's top layer has the grid's next layer above it
+    exactly when the slab has an upper neighbour."""
+    return all(g.k1 > g.k0 for g in geom)
+
+
+def interface_layer_copies(geom: list[SlabGeom]):
+    """The cell-layer copies of one design-field exchange, (src slab, src local layer, dst
+    slab, dst local layer): the lower slab's top layer into the upper slab's ghost layer 0,
+    and the upper slab's first own layer (1) into the lower slab's copy of the layer above
+    its top (local index nz)."""
+    out = []
+    for s in range(len(geom) - 1):
+        lo = geom[s]
+        out.append((s, lo.nz - 1, s + 1, 0))
+        out.append((s + 1, 1, s, lo.nz))
+    return out
+
+
 def _torch():
     import torch
     return torch
@@ -154,6 +185,27 @@ class _SlabDriver:
         return {"sweeps": rep["sweeps"], "rel_res": rep["rel_res"], "converged": rep["converged"],
                 "fell_back_to_pt": rep["fell_back_to_pt"]}
 
+    def design_step(self, solve_kw: dict | None = None, pf_kw: dict | None = None) -> dict:
+        """One design loop over the slabs (petto_slab_design_step on every slab, this driver
+        supplying the plane and cell-layer exchanges and the sums and maxima): the whole
+        grid's metrics.  The state solve as solve() (no FP64 refinement)."""
+        if not design_step_ok(self.geom):
+            raise ValueError("the decomposed design step needs two node planes or more per slab")
+        kw = dict(mode=1, refine=False)
+        kw.update(solve_kw or {})
+        return self._slab_design_step(kw, dict(pf_kw or {}))
+
+    def _gather_design(self, parts):
+        spec = self.spec
+        out = None
+        for g, phi in parts:
+            phi = np.asarray(phi)
+            if out is None:
+                out = np.empty((phi.shape[0], spec.nz, spec.ny, spec.nx), dtype=phi.dtype)
+            c0, c1 = owned_layers(g, spec.nz)
+            out[:, c0:c1] = phi.reshape(phi.shape[0], g.nz, spec.ny, spec.nx)[:, c0 - g.g0:c1 - g.g0]
+        return out.reshape(out.shape[0], -1)
+
 
 class SlabGrid(_SlabDriver):
     """Every slab of the grid in this process: n contexts on the current GPU, exchanged by
@@ -186,6 +238,7 @@ class SlabGrid(_SlabDriver):
         self.ncomp = p0.nrhs * p0.ncomp
         dt = torch.float64 if p0.np_dtype == np.float64 else torch.float32
         self._buf = torch.empty(p0.plane_shape(), dtype=dt, device="cuda")
+        self._lbuf = None  # cell-layer copies of the design step
         # ||F|| over the free DOFs: the residual of the zero state, summed over the slabs
         self.f_norm = float(np.sqrt(sum(p.residual(with_field=False)[0] for p in self.probs)))
 
@@ -240,35 +293,56 @@ class SlabGrid(_SlabDriver):
         self.exchange()
         return float(sum(p.residual(with_field=False)[0] for p in self.probs))
 
-    def _slab_solve(self, kw):
-        """One host thread per slab runs its petto_slab_solve; the hooks meet at a barrier:
-        the first slab's thread makes every interface copy (all contexts share one stream, so
-        the copies fall between the slabs' sweeps), and the sums are taken in slab order in
-        every thread, so all slabs take the same decisions."""
+    def get_design(self, dtype=np.float64):
+        """The whole grid's design, each cell layer from the slab that owns it."""
+        return self._gather_design([(g, p.get_design(dtype=dtype)) for g, p in zip(self.geom, self.probs)])
+
+    def exchange_layer(self, field: int, phase: int):
+        """Each interface's cell layers of phi's phase (field 0) or mu (field 1), from their
+        owners into the neighbours' ghost layer and copy of the layer above."""
+        torch = _torch()
+        nb = self.probs[0].layer_bytes(field)
+        if self._lbuf is None or self._lbuf.numel() < nb:
+            self._lbuf = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        buf = self._lbuf[:nb]
+        for src, ks, dst, kd in interface_layer_copies(self.geom):
+            self.probs[src].get_layer(field, phase, ks, buf)
+            self.probs[dst].set_layer(field, phase, kd, buf)
+
+    def _threads(self, call):
+        """One host thread per slab runs call(slab, hooks); the hooks meet at a barrier: the
+        first slab's thread makes every interface copy (all contexts share one stream, so the
+        copies fall between the slabs' kernels), and the sums and maxima are taken in slab
+        order in every thread, so all slabs take the same decisions."""
         import threading
         n = len(self.probs)
         bar = threading.Barrier(n, timeout=600)
         vals = [None] * n
-        reps, errs = [None] * n, []
+        out, errs = [None] * n, []
 
         def hooks(s):
-            def exchange():
-                bar.wait()
-                if s == 0:
-                    self.exchange()
-                bar.wait()
+            def copies(fn):
+                def run(*args):
+                    bar.wait()
+                    if s == 0:
+                        fn(*args)
+                    bar.wait()
+                return run
 
-            def allreduce(v):
-                vals[s] = list(v)
-                bar.wait()
-                out = [sum(vals[q][i] for q in range(n)) for i in range(len(v))]
-                bar.wait()
-                return out
-            return exchange, allreduce
+            def reducer(op):
+                def run(v):
+                    vals[s] = list(v)
+                    bar.wait()
+                    res = [op(vals[q][i] for q in range(n)) for i in range(len(v))]
+                    bar.wait()
+                    return res
+                return run
+            return {"exchange": copies(self.exchange), "exchange_layer": copies(self.exchange_layer),
+                    "allreduce": reducer(sum), "allreduce_max": reducer(max)}
 
         def run(s):
             try:
-                reps[s] = self.probs[s].slab_solve(*hooks(s), **kw)
+                out[s] = call(s, hooks(s))
             except BaseException as e:  # noqa: BLE001 -- re-raised below
                 errs.append(e)
                 bar.abort()
@@ -280,7 +354,14 @@ class SlabGrid(_SlabDriver):
             t.join()
         if errs:
             raise errs[0]
-        return reps[0]
+        return out[0]
+
+    def _slab_solve(self, kw):
+        return self._threads(lambda s, h: self.probs[s].slab_solve(h["exchange"], h["allreduce"], **kw))
+
+    def _slab_design_step(self, solve_kw, pf_kw):
+        return self._threads(lambda s, h: self.probs[s].slab_design_step(
+            h["exchange"], h["exchange_layer"], h["allreduce"], h["allreduce_max"], solve_kw=solve_kw, pf_kw=pf_kw))
 
 
 class DistributedSlabs(_SlabDriver):
@@ -371,6 +452,52 @@ class DistributedSlabs(_SlabDriver):
 
     def _slab_solve(self, kw):
         return self.prob.slab_solve(self.exchange, self._allreduce_list, **kw)
+
+    def _allreduce_max_list(self, values):
+        t = _torch().tensor(list(values), dtype=_torch().float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX, group=self.group)
+        return t.tolist()
+
+    def exchange_layer(self, field: int, phase: int):
+        """The design-field layers at this rank's interfaces: its top layer up (into the upper
+        neighbour's ghost layer), its first own layer down (into the lower neighbour's copy of
+        the layer above)."""
+        torch, dist, r, g = _torch(), self.dist, self.rank, self.g
+        nb = self.prob.layer_bytes(field)
+        bufs = [torch.empty(nb, dtype=torch.uint8, device=self.device) for _ in range(4)]
+        ops = []
+        if r + 1 < self.world:  # upper neighbour: send the top layer, receive its first own layer
+            self.prob.get_layer(field, phase, g.nz - 1, bufs[0])
+            ops.append(dist.P2POp(dist.isend, bufs[0], self._global_rank(r + 1), self.group))
+            ops.append(dist.P2POp(dist.irecv, bufs[1], self._global_rank(r + 1), self.group))
+        if r > 0:               # lower neighbour: send the first own layer, receive the ghost layer
+            self.prob.get_layer(field, phase, 1, bufs[2])
+            ops.append(dist.P2POp(dist.isend, bufs[2], self._global_rank(r - 1), self.group))
+            ops.append(dist.P2POp(dist.irecv, bufs[3], self._global_rank(r - 1), self.group))
+        if not ops:
+            return
+        cuda = self.device.type == "cuda"
+        if cuda:
+            self.prob.synchronize()
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+        if cuda:
+            torch.cuda.current_stream().synchronize()
+        if r + 1 < self.world:
+            self.prob.set_layer(field, phase, g.nz, bufs[1])
+        if r > 0:
+            self.prob.set_layer(field, phase, 0, bufs[3])
+
+    def _slab_design_step(self, solve_kw, pf_kw):
+        return self.prob.slab_design_step(self.exchange, self.exchange_layer, self._allreduce_list,
+                                          self._allreduce_max_list, solve_kw=solve_kw, pf_kw=pf_kw)
+
+    def get_design(self, dtype=np.float64):
+        """The whole grid's design, assembled on every rank."""
+        mine = np.asarray(self.prob.get_design(dtype=np.float64))
+        parts = [None] * self.world
+        self.dist.all_gather_object(parts, (self.rank, mine), group=self.group)
+        return self._gather_design([(self.geom[r], phi) for r, phi in parts]).astype(dtype)
 
     def set_design(self, phi):
         self.prob.set_design(slab_cells(phi, self.spec, self.g))

@@ -167,3 +167,81 @@ def test_library_slab_solve_with_adaptive_momentum_equals_whole_grid(P, precisio
     assert rep_w["converged"] and rep_s["converged"], (rep_w, rep_s)
     assert rep_s["sweeps"] == rep_w["sweeps"]
     _same(us, uw, spec)
+
+
+def _design_spec(precision, vol_mode):
+    base = W.cantilever3d(24, 12, 14).with_(precision=precision, storage=precision)
+    spec = base.with_(loads=base.loads + [((12, 6, 5), 0, 0.5), ((20, 3, 9), 1, -0.3)],
+                      phi0=W.random_design(base, seed=37, lo=0.2, hi=0.6))
+    # the penalty form with a volume term, so that the step reads the whole grid's means
+    return spec.with_(vol_mode=vol_mode, kappa_v=0.5 if vol_mode == 1 else spec.kappa_v)
+
+
+@pytest.mark.parametrize("precision,kernel,n_slabs,vol_mode", [("f64", None, 2, 0), ("f64", None, 3, 0),
+                                                               ("f64", None, 3, 1), ("f32", "tma3", 2, 0)])
+def test_slab_design_steps_equal_whole_grid(P, precision, kernel, n_slabs, vol_mode):
+    """petto_slab_design_step on every slab (Fig. 5 loop: solve, sensitivity, update,
+    Cahn-Hilliard, modulus; plane and cell-layer exchanges, sums and maxima over the slabs)
+    against petto_optimize on the whole grid, two loops from the same design: the same sweep
+    counts, and compliance, multiplier, volume and design equal up to the order of the sums
+    (the bisection and the means add the slabs' partial sums; FP64 1e-11, FP32 1e-5)."""
+    spec = _design_spec(precision, vol_mode)
+    tol = 1e-9 if precision == "f64" else 1e-3
+    solve_kw = dict(tol=tol, check_every=20, max_sweeps=60000, momentum=1, local_dt=True, refine=False)
+    p = P.Problem(spec)
+    if kernel:
+        p.select_kernel(kernel)
+    hist, _ = p.optimize(2, solve_kw=solve_kw)
+    phi_w = p.get_design()
+    p.close()
+    with S.SlabGrid(spec, n_slabs, kernel=kernel) as g:
+        rows = [g.design_step(solve_kw=solve_kw) for _ in range(2)]
+        phi_s = g.get_design()
+    rtol = 1e-11 if precision == "f64" else 1e-5
+    for a, b in zip(rows, hist):
+        assert a["sweeps"] == b["sweeps"], (a, b)
+        for key in ("compliance", "work", "mean_phi0", "lambda0"):
+            assert abs(a[key] - b[key]) <= rtol * max(abs(b[key]), 1e-3), (key, a[key], b[key])
+    assert np.abs(phi_s - phi_w).max() <= rtol * 10
+
+
+def test_slab_design_step_oracle_loops_fp64(P):
+    """Two decomposed design loops against the oracle's two loops (Sec. 3.3 update and
+    Cahn-Hilliard step), FP64, three slabs: compliance within 1e-7, design within 1e-6."""
+    from oracle import oracle as O
+    spec = _design_spec("f64", 0)
+    with S.SlabGrid(spec, 3) as g:
+        rows = [g.design_step(solve_kw=dict(tol=1e-10, check_every=20, max_sweeps=100000, momentum=1,
+                                            local_dt=True)) for _ in range(2)]
+        phi_s = g.get_design()
+    op, om = oracle_problem(spec), oracle_materials(spec)
+    F, fixed = op.load_vector(), op.fixed_mask()
+    phi, u = spec.phi0.copy(), np.zeros(op.ndof)
+    for t in range(2):
+        m = O.design_step(op, om, phi, u, F, fixed, spec.vol_frac,
+                          dict(mode=1, a=1.0, b=spec.apt_b, s1=spec.pt_s1, tol=1e-10, max_sweeps=400000,
+                               check_every=20, local_dt=True, momentum=1),
+                          dict(alpha_h=spec.alpha_h, gamma_g=spec.gamma_g, tau=spec.tau, vol_mode=spec.vol_mode,
+                               kappa_v=spec.kappa_v, kappa_1=spec.kappa_1, n_bisect=spec.n_bisect))
+        assert abs(rows[t]["compliance"] - m["compliance"]) <= 1e-7 * m["compliance"]
+    assert np.abs(phi_s - phi).max() <= 1e-6
+
+
+def test_slab_design_step_checks(P):
+    from paper_2509_06971_gb300 import capi as C
+    spec = _design_spec("f64", 0)
+    with S.SlabGrid(W.cantilever3d(8, 4, 2).with_(precision="f64", storage="f64"), 2) as g2:
+        with pytest.raises(ValueError):
+            g2.design_step()  # the upper slab would own one node plane and no cell layer
+    with S.SlabGrid(spec, 2) as g:
+        p = g.probs[1]
+        nb = p.layer_bytes(C.PETTO_LAYER_PHI)
+        assert nb == spec.nx * spec.ny * 8 and p.layer_bytes(C.PETTO_LAYER_MU) == nb
+        buf = np.zeros(nb, np.uint8)
+        for field, phase, k in ((2, 0, 0), (0, 1, 0), (0, 0, -1), (0, 0, p.spec.nz + 1)):
+            with pytest.raises(C.PettoError) as e:
+                p.get_layer(field, phase, k, buf)
+            assert e.value.status == C.PETTO_EINVAL
+        phi = p.get_design()
+        p.get_layer(C.PETTO_LAYER_PHI, 0, 3, buf)
+        assert np.array_equal(buf.view(np.float64), phi[0].reshape(p.spec.nz, -1)[3])

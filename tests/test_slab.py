@@ -45,6 +45,43 @@ def test_interface_copies_fill_every_ghost_plane_from_its_owner(nz, n):
         assert g.g0 >= 0 and g.g1 <= nz and g.g1 - g.g0 <= g.k1 - g.k0 + 2
 
 
+@pytest.mark.parametrize("nz,n", [(3, 2), (7, 3), (20, 5), (17, 9)])
+def test_cell_layers_are_owned_once_and_every_copy_comes_from_its_owner(nz, n):
+    """The decomposed design step: the owned cell layers partition the grid's; each slab
+    holds its own layers, plus the layer below (ghost, filled from its owner) where it has a
+    lower neighbour; each slab with an upper neighbour gets that neighbour's first own layer
+    as its copy of the layer above (local index nz).  Every slab owns two node planes or more
+    (so every slab owns a cell layer), which the design step requires."""
+    geom = S.slab_geometry(nz, n)
+    assert S.design_step_ok(geom)
+    owner = {}
+    for s, g in enumerate(geom):
+        c0, c1 = S.owned_layers(g, nz)
+        assert g.g0 <= c0 <= c1 <= g.g0 + g.nz  # held by the slab
+        for c in range(c0, c1):
+            assert c not in owner
+            owner[c] = s
+    assert sorted(owner) == list(range(nz))
+    filled = {s: set() for s in range(n)}
+    for src, ks, dst, kd in S.interface_layer_copies(geom):
+        gs, gd = geom[src], geom[dst]
+        c = gs.g0 + ks
+        assert owner[c] == src                  # sent by its owner
+        assert gd.g0 + kd == c                  # the same layer of the whole grid
+        assert owner.get(c) != dst
+        filled[dst].add(kd)
+    for s, g in enumerate(geom):
+        c0, c1 = S.owned_layers(g, nz)
+        held_not_owned = {c - g.g0 for c in range(g.g0, g.g0 + g.nz) if not c0 <= c < c1}
+        above = {g.nz} if s + 1 < n else set()
+        assert filled[s] == held_not_owned | above
+
+
+def test_design_step_needs_two_planes_per_slab():
+    assert not S.design_step_ok(S.slab_geometry(2, 2))   # the top slab would own no cell layer
+    assert S.design_step_ok(S.slab_geometry(3, 2))
+
+
 def test_slab_spec_restricts_loads_boxes_and_design():
     base = W.cantilever3d(12, 6, 9)
     loads = base.loads + [((3, 2, 4), 0, 0.5), ((5, 5, 5), 1, -0.25), ((0, 0, 9), 2, 1.0)]
