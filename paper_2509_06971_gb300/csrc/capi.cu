@@ -2717,8 +2717,17 @@ std::vector<std::pair<std::string, Tiling>> kernel_candidates_all(const petto_ct
             }
             march3d_tma_tiling(L, 16, t);
             cand.emplace_back("tma16/zs" + std::to_string(t.zs), t);
-            march3d_tma3_tiling(L, t);
-            cand.emplace_back("tma3/zs" + std::to_string(t.zs), t);
+            for (int zs : {0, 8, 16, 24}) {
+                march3d_tma3_tiling(L, t);
+                if (zs && zs != t.zs) {
+                    if (zs >= L.NZ) continue;
+                    t.zs = zs;
+                    t.gz = (L.NZ + t.zs - 1) / t.zs;
+                } else if (zs) {
+                    continue;  // the default length already listed
+                }
+                cand.emplace_back("tma3/zs" + std::to_string(t.zs), t);
+            }
         }
         if (ctx->nrhs == 1) {
             march3d_tiling(L, t);

@@ -432,11 +432,12 @@ def test_autograd_function_matches_finite_difference(P):
     prob.close()
 
 
-@pytest.mark.parametrize("variant", ["tma3", "tma8", "tma16", "tma2", "v1"])
+@pytest.mark.parametrize("variant", ["tma3", "tma8", "tma16", "tma2", "v1", "tma3/zs8", "tma3/zs24"])
 def test_march3d_multi_tile_and_segment(P, variant, monkeypatch):
     """Every z-marching FP32 kernel variant on a grid spanning several x/y tiles and z
-    segments with ragged tails, point loads on tile edges and supports on several faces."""
-    monkeypatch.setenv("PETTO_MARCH", variant)
+    segments with ragged tails, point loads on tile edges and supports on several faces (the
+    lean kernel also with the autotuner's other segment lengths)."""
+    monkeypatch.setenv("PETTO_MARCH", variant.split("/")[0])
     nx, ny, nz = 70, 40, 37
     base = W.cantilever3d(nx, ny, nz)
     loads = base.loads + [((31, 7, 16), 0, 0.7), ((30, 6, 15), 1, -0.4), ((62, 14, 32), 2, 0.25),
@@ -444,6 +445,9 @@ def test_march3d_multi_tile_and_segment(P, variant, monkeypatch):
     boxes = base.boxes + [((nx, 0, nz), (nx, ny, nz), 0b010), ((10, 21, 0), (40, 22, 5), 0b101)]
     spec = base.with_(loads=loads, boxes=boxes)
     spec, prob, op, om, phi = _setup(P, spec, seed=21, precision="f32")
+    if "/" in variant:
+        prob.select_kernel(variant)
+        assert prob.kernel_info()[0] == variant
     u0 = W.random_state(spec, seed=22)
     w0 = W.random_state(spec, seed=23, scale=0.1)
     prob.set_state(u0.astype(np.float32), w0.astype(np.float32))
