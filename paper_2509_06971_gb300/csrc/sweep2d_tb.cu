@@ -30,8 +30,6 @@
 namespace petto {
 namespace {
 
-constexpr unsigned char TB_OUTSIDE = 0x80;  // mask bit of a staged node outside the grid
-
 // Asynchronous copy of one element from global to shared memory; the element is zero when
 // !valid (source size 0: nothing is read, and src only has to be a valid address).
 template <typename T>
@@ -92,7 +90,9 @@ __global__ void __launch_bounds__(TB_THREADS, 2) sweep2d_tb(const __grid_constan
                 else sf[c * RN + n] = (PHYS == 1 && in) ? kc.src * (T)(((i > 0) + (i < L.nx)) * ((j > 0) + (j < L.ny)))
                                                         : T(0);
             }
-            sm[n] = in ? (unsigned char)fixed_mask(A.boxes, i, j, 0) : TB_OUTSIDE;
+            // a node outside the grid is staged as held in every component: its update writes
+            // the zeros it already has, with no branch in the sweep loop
+            sm[n] = in ? (unsigned char)fixed_mask(A.boxes, i, j, 0) : (unsigned char)((1u << C) - 1u);
         }
     }
     // cells (outside the grid: modulus 0, as in the zero ring of the global layout)
@@ -171,18 +171,16 @@ __global__ void __launch_bounds__(TB_THREADS, 2) sweep2d_tb(const __grid_constan
                 if (j >= ys && xin) {
                     const int n = j * RX + lx;
                     const unsigned m = sm[n];
-                    if (!(m & TB_OUTSIDE)) {
-                        if (sums) {
-                            const bool own_node = j >= halo && j < halo + oy && lx >= halo && lx < halo + ox;
-                            up.want_res = own_node && A.want_res;
-                            up.test_dot = own_node && MODE == 0 && A.test_dot;
-                        }
-                        const T diag = m2_diag(kc, Elb, Eb, El, Ec);
-#pragma unroll
-                        for (int c = 0; c < C; ++c)
-                            up.apply_v(c * RN + n, (m >> c) & 1u, m2_ku(own[c], mx[c], cy[c], gd[c]), sf[c * RN + n],
-                                       diag, u0[c], sw[c * RN + n], wr, sw);
+                    if (sums) {
+                        const bool own_node = j >= halo && j < halo + oy && lx >= halo && lx < halo + ox;
+                        up.want_res = own_node && A.want_res;
+                        up.test_dot = own_node && MODE == 0 && A.test_dot;
                     }
+                    const T diag = m2_diag(kc, Elb, Eb, El, Ec);
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+                        up.apply_v(c * RN + n, (m >> c) & 1u, m2_ku(own[c], mx[c], cy[c], gd[c]), sf[c * RN + n], diag,
+                                   u0[c], sw[c * RN + n], wr, sw);
                 }
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
