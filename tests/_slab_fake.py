@@ -15,7 +15,7 @@ class OracleSlab:
         self.nrhs, self.ncomp = 1, spec.ncomp
         self.op, self.om = oracle_problem(spec), oracle_materials(spec)
         self.F, self.fixed = self.op.load_vector(), self.op.fixed_mask()
-        self.E = self.om.modulus(np.asarray(spec.phi0, np.float64))
+        self.set_design(spec.phi0)
         self.u = np.zeros(self.op.ndof)
         self.w = np.zeros(self.op.ndof)
         self.zlo, self.zhi = 0, spec.nz
@@ -40,9 +40,6 @@ class OracleSlab:
 
     def set_plane(self, k, src):
         self._grid(self.u)[k] = np.moveaxis(src.numpy(), 0, -1)
-
-    def set_design(self, phi):
-        self.E = self.om.modulus(np.asarray(phi, np.float64))
 
     def set_state(self, u, w=None):
         self.u = np.ascontiguousarray(np.asarray(u, np.float64).T.reshape(-1))
@@ -101,3 +98,101 @@ class OracleSlab:
         conv = bool(np.isfinite(rn) and rn <= tol * fn)
         return {"sweeps": sweeps, "rel_res": rn / fn if fn else float("nan"), "converged": conv,
                 "fell_back_to_pt": False}
+
+    # ---------------------------------------------------------------- decomposed design step
+    # The hook protocol of petto_slab_design_step on the host stand-in, from the oracle's
+    # pieces: cell energies, sensitivity, the update written with the slabs' sums, and the
+    # Cahn-Hilliard half steps with the oracle's no-flux cell Laplacian on the held layers
+    # plus the copy of the layer above.
+
+    def set_design(self, phi):
+        self.phi = np.array(phi, dtype=np.float64).reshape(self.om.n_phases, -1)
+        self.E = self.om.modulus(self.phi)
+        s = self.spec
+        self.mu = np.zeros(self.phi.shape[1])
+        self.phi_hi = np.zeros((self.phi.shape[0], s.nx * s.ny))
+        self.mu_hi = np.zeros(s.nx * s.ny)
+
+    def get_design(self, dtype=np.float64):
+        return self.phi.astype(dtype)
+
+    def layer_bytes(self, field):
+        return self.spec.nx * self.spec.ny * 8 if field in (0, 1) else 0
+
+    def _layer(self, field, phase, k):
+        s, pl = self.spec, self.spec.nx * self.spec.ny
+        if k == s.nz:
+            return self.phi_hi[phase] if field == 0 else self.mu_hi
+        arr = self.phi[phase] if field == 0 else self.mu
+        return arr[k * pl:(k + 1) * pl]
+
+    def get_layer(self, field, phase, k, out):
+        out.numpy().view(np.float64)[:] = self._layer(field, phase, k)
+        return out
+
+    def set_layer(self, field, phase, k, src):
+        self._layer(field, phase, k)[:] = src.numpy().view(np.float64)
+
+    def _lap(self, v, hi):
+        """No-flux cell Laplacian of v over the held layers, with the layer above (hi) when the
+        slab has an upper neighbour."""
+        from oracle import oracle as O
+        s = self.spec
+        if hi is None:
+            return O.OracleProblem(3, s.nx, s.ny, s.nz).cell_laplacian(v)
+        ext = np.concatenate([v, hi])
+        return O.OracleProblem(3, s.nx, s.ny, s.nz + 1).cell_laplacian(ext)[:v.size]
+
+    def slab_design_step(self, exchange, exchange_layer, allreduce, allreduce_max, solve_kw=None, pf_kw=None):
+        from oracle import oracle as O
+        s = self.spec
+        sk = dict(solve_kw or {})
+        rep = self.slab_solve(exchange, allreduce, **sk)
+        exchange()
+        pl = s.nx * s.ny
+        c0, c1 = self.zlo * pl, min(self.zhi + 1, s.nz) * pl  # own cell layers
+        ncount = allreduce([float(c1 - c0)])[0]
+        e = self.op.cell_energy(self.u)
+        sens, _ = self.om.sensitivity(self.phi, self.E, e)
+        C = allreduce([float((self.E * e)[c0:c1].sum())])[0]
+        own_nodes = self._grid(np.ones_like(self.u))
+        own_nodes[:self.zlo] = 0
+        own_nodes[self.zhi + 1:] = 0
+        W = allreduce([float((self.F * self.u * own_nodes.reshape(-1)).sum())])[0]
+        smax = allreduce_max([float(np.abs(sens[p]).max()) for p in range(self.phi.shape[0])])
+        pf = dict(alpha_h=s.alpha_h, kappa_v=s.kappa_v, kappa_1=s.kappa_1, gamma_g=s.gamma_g, tau=s.tau,
+                  vol_mode=s.vol_mode, n_bisect=s.n_bisect)
+        pf.update(pf_kw or {})
+        P = self.phi.shape[0]
+        g = np.stack([pf["alpha_h"] * sens[p] / smax[p] if smax[p] > 0 else 0 * sens[p] for p in range(P)])
+        dv = self.phi - g - pf["kappa_1"] * (self.phi.sum(axis=0) - 1.0)
+        lam = np.zeros(P)
+        if pf["vol_mode"] == O.PROJECTED:
+            lo, hi = np.full(P, -2.0), np.full(P, 2.0)
+            for _ in range(pf["n_bisect"]):
+                mid = 0.5 * (lo + hi)
+                sums = allreduce([float(np.clip(dv[p, c0:c1] - mid[p], 0, 1).sum()) for p in range(P)])
+                for p in range(P):
+                    if sums[p] / ncount > s.vol_frac[p]:
+                        lo[p] = mid[p]
+                    else:
+                        hi[p] = mid[p]
+            lam = 0.5 * (lo + hi)
+            self.phi = np.clip(dv - lam[:, None], 0.0, 1.0)
+        else:
+            mean = np.array(allreduce([float(self.phi[p, c0:c1].sum()) for p in range(P)])) / ncount
+            lam = mean
+            self.phi = dv - (pf["kappa_v"] * (mean - np.asarray(s.vol_frac)))[:, None]
+        upper = self.zhi < s.nz  # the slab has an upper neighbour
+        for p in range(P):
+            exchange_layer(0, p)
+            self.mu[:] = [O.double_well_deriv(x) for x in self.phi[p]] - pf["gamma_g"] * self._lap(
+                self.phi[p], self.phi_hi[p] if upper else None)
+            exchange_layer(1, p)
+            self.phi[p] += pf["tau"] * self._lap(self.mu, self.mu_hi if upper else None)
+        for p in range(P):
+            exchange_layer(0, p)
+        self.E = self.om.modulus(self.phi)
+        mean0 = allreduce([float(self.phi[0, c0:c1].sum())])[0] / ncount
+        return {"step": 1, "compliance": C, "work": W, "rel_res": rep["rel_res"], "sweeps": rep["sweeps"],
+                "seconds": 0.0, "mean_phi0": mean0, "lambda0": float(lam[0]), "converged": rep["converged"]}
