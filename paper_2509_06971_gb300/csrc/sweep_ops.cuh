@@ -97,11 +97,14 @@ __device__ __forceinline__ T ku_thermal_2d(const T (&U)[3][3], const T (&Ec)[2][
                  Eyp * (U[2][1] - U[1][1]));
 }
 
-// Products rounded on their own (never fused into an FMA by the compiler), so that every
-// kernel that evaluates an expression built from them gets the same bits whatever code
-// surrounds it.
+// Products rounded on their own and fused multiply-adds written out (the compiler fuses
+// nothing it is not told to), so that every kernel that evaluates an expression built from
+// them gets the same bits whatever code surrounds it.
 __device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+// a b + c rounded once, wherever it stands
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // The owner terms of the 2D y-marching form: at node (i, j), the x-edge to (i+1, j), the
 // y-edge to (i, j+1) and the face of cell (i, j), from u at the four corners of that cell
@@ -122,10 +125,9 @@ __device__ __forceinline__ void m2_terms(const T *u0, const T *un, const T *u1, 
         const T fy0 = rn_mul(rn_mul(k.ce_perp, Ey), ay0), fy1 = rn_mul(rn_mul(k.ce_par, Ey), ay1);
         const T SA0 = ax0 + (un1[0] - u1[0]), SA1 = ax1 + (un1[1] - u1[1]);
         const T SB0 = ay0 + (un1[0] - un[0]), SB1 = ay1 + (un1[1] - un[1]);
-        const T lb1 = rn_mul(k.cf_lam, SB1), ma1 = rn_mul(k.cf_mu, SA1);
-        const T mb0 = rn_mul(k.cf_mu, SB0), la0 = rn_mul(k.cf_lam, SA0);
-        const T G0 = rn_mul(Ec, lb1 + ma1), G1 = rn_mul(Ec, mb0 + la0);
-        const T H0 = rn_mul(Ec, lb1 - ma1), H1 = rn_mul(Ec, mb0 - la0);
+        const T ma1 = rn_mul(k.cf_mu, SA1), la0 = rn_mul(k.cf_lam, SA0);
+        const T G0 = rn_mul(Ec, rn_fma(k.cf_lam, SB1, ma1)), G1 = rn_mul(Ec, rn_fma(k.cf_mu, SB0, la0));
+        const T H0 = rn_mul(Ec, rn_fma(k.cf_lam, SB1, -ma1)), H1 = rn_mul(Ec, rn_fma(k.cf_mu, SB0, -la0));
         own[0] = -fx0 - fy0 - G0;
         own[1] = -fx1 - fy1 - G1;
         tx[0] = fx0 + H0;
@@ -327,12 +329,12 @@ struct Upd {
         if (mode == 0) {
             const T step = local_dt ? k.b * fast_rcp(diag) : k.b;
             if (test_dot) dot += R * wi;
-            const T wn = fixed ? T(0) : rn_mul(a_eff, wi) + rn_mul(step, R);
+            const T wn = fixed ? T(0) : rn_fma(a_eff, wi, rn_mul(step, R));
             w[idx_c] = wn;
             uo[idx_c] = fixed ? T(0) : u + wn;
         } else if (mode == 1) {
             const T step = local_dt ? k.s1 * fast_rcp(diag) : k.s1;
-            uo[idx_c] = fixed ? T(0) : u + rn_mul(step, R);
+            uo[idx_c] = fixed ? T(0) : rn_fma(step, R, u);
         } else {
             w[idx_c] = R;
         }

@@ -169,8 +169,12 @@ def test_adaptive_solve_takes_the_marching_solves_decisions_fp64(P, name):
     assert relmax(ut, oracle_to_nodes(ud, spec.ncomp)) < 1e-8
 
 
-def test_fp32_refined_solve_matches_direct_solve(P):
-    spec = W.cantilever2d(128, 64).with_(precision="f32", storage="f32")
+@pytest.mark.parametrize("name", ["cantilever", "heat"])
+def test_fp32_refined_solve_matches_direct_solve(P, name):
+    """FP32 sweeps four per launch with the FP64 refinement (dense FP32 right-hand sides)
+    to 1e-6: the compliance of the oracle's direct solve (elasticity and heat)."""
+    spec = (W.cantilever2d(128, 64) if name == "cantilever" else W.heat2d(96)).with_(precision="f32",
+                                                                                    storage="f32")
     prob = P.Problem(spec)
     assert prob.kernel_info()[0].startswith("tb2d/k4/")
     phi = W.random_design(spec, seed=7, lo=0.2, hi=0.9)
