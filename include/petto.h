@@ -400,11 +400,14 @@ petto_status petto_profile_read(petto_ctx *ctx, double *sweep_ms, int64_t *sweep
 /* Sweep-kernel autotuner: times every kernel variant and tile shape that applies to this
  * problem (for 3D elasticity in FP32: TMA-staged marching kernels with one or two owner
  * rows per thread, 32x16 tiles, the register-staged kernel, several z-segment lengths;
- * in 2D with one load case: the y-marching kernel with several rows per warp; always the
- * node-gather kernel's block shapes) for n APT sweeps each from the current state,
+ * in 2D with one load case: four and two sweeps per launch ("tb2d/k4/..", timed per
+ * sweep over whole launches) and the y-marching kernel with several rows per warp; always
+ * the node-gather kernel's block shapes) for n APT sweeps each from the current state,
  * restores the state, and keeps the fastest.  report (may be NULL) receives a JSON object
  * of milliseconds per sweep for each candidate, keyed by the names petto_select_kernel
- * takes.  Uses temporary device memory. */
+ * takes.  Uses temporary device memory.  The first solve of a 3D elastic FP32 context of
+ * 2^17 nodes or more runs it (unless a kernel was selected) and remembers the choice per
+ * grid shape for the process. */
 petto_status petto_autotune(petto_ctx *ctx, int n, char *report, int report_len);
 
 /* Selects the sweep kernel by the name the autotuner reports ("tma2/zs16", "march2d/ly8",
