@@ -375,7 +375,10 @@ petto_status petto_phase_field_step(petto_ctx *ctx, const petto_pf_opts *opts, d
 
 /* n_steps PeTTO loops (Fig. 5): solve, sensitivity, update, Cahn-Hilliard.  cb (may be
  * NULL) is called on the host after each loop with the metrics described above.
- * Returns PETTO_ENOTCONV if any solve missed its tolerance (the loop still runs). */
+ * Returns PETTO_ENOTCONV if any solve missed its tolerance (the loop still runs).  With the
+ * paper's fixed-count schedule (PETTO_SOLVE_PAPER, check_every 0) no host decision falls
+ * inside a loop: once a loop has run on the context, each loop is one replay of a captured
+ * CUDA graph of the same launches (the same results), read back only for cb. */
 petto_status petto_optimize(petto_ctx *ctx, int n_steps, const petto_solve_opts *sopts,
                             const petto_pf_opts *popts, petto_step_cb cb, void *user);
 

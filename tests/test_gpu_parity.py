@@ -756,3 +756,52 @@ def test_ring_wait_time_out_is_reported_and_the_context_recovers(P, kernel):
     F = op.load_vector()
     Co = float(F @ op.direct_solve(om.modulus(np.asarray(phi, np.float32).astype(np.float64)), F, op.fixed_mask()))
     assert abs(Cg - Co) < 1e-4 * abs(Co)
+
+
+@pytest.mark.parametrize("name", ["mbb_multimat", "mbb_multimat_projected", "heat_paper_adaptive",
+                                  "multimat3d_paper", "drone_fp64"])
+def test_paper_loops_replayed_as_graphs_equal_direct_launches(P, name, monkeypatch):
+    """The paper's fixed-count loops (Fig. 5, no checks): after the first loop petto_optimize
+    replays each whole loop -- sweeps, sensitivity, update, Cahn-Hilliard, modulus -- as one
+    captured graph.  The same launches in the same order: designs and metrics equal bit for
+    bit to a context that launches every kernel directly (PETTO_NO_GRAPHS)."""
+    specs = {
+        "mbb_multimat": lambda: W.mbb_multimat2d(64, 16),
+        "mbb_multimat_projected": lambda: W.mbb_multimat2d(64, 16).with_(vol_mode=0),
+        "heat_paper_adaptive": lambda: W.heat2d_paper(48).with_(momentum=1),
+        "multimat3d_paper": lambda: W.multimat3d_paper(32, 9, 11),
+        "drone_fp64": lambda: W.drone3d(16, 8, 16).with_(precision="f64", storage="f64"),  # keep-out term too
+    }
+    spec = specs[name]()
+    spec = spec.with_(n_apt=min(spec.n_apt, 10), n_pt=min(spec.n_pt, 6))  # short loops, one APT block ragged
+    out = {}
+    for mode in ("graphs", "direct"):
+        if mode == "direct":
+            monkeypatch.setenv("PETTO_NO_GRAPHS", "1")
+        p = P.Problem(spec)
+        hist, _ = p.optimize(4)
+        out[mode] = (hist, p.get_design(), p.get_state())
+        p.close()
+        monkeypatch.delenv("PETTO_NO_GRAPHS", raising=False)
+    (hg, dg, ug), (hd, dd, ud) = out["graphs"], out["direct"]
+    assert np.array_equal(dg, dd) and np.array_equal(ug, ud)
+    for a, b in zip(hg, hd):
+        for key in ("compliance", "work", "rel_res", "sweeps", "mean_phi0", "lambda0"):
+            assert a[key] == b[key], (key, a[key], b[key])
+
+
+def test_replayed_paper_loops_are_timed(P):
+    """Kernel timing (petto_profile) over paper loops replayed as graphs: every sweep is
+    counted, in the ordinary first loop and in the replays (event records inside the graph
+    around its sweeps), and the time per sweep is positive."""
+    spec = W.mbb_multimat2d(64, 16)
+    spec = spec.with_(n_apt=10, n_pt=6)
+    p = P.Problem(spec)
+    p.profile(True)
+    p.profile_read()
+    hist, _ = p.optimize(4)
+    ms, n = p.profile_read()
+    p.profile(False)
+    p.close()
+    assert n == 4 * 16 and ms > 0.0
+    assert all(h["sweeps"] == 16 for h in hist)
