@@ -686,6 +686,25 @@ def test_autotune_keeps_state_and_picks_a_variant(P):
     prob.close()
 
 
+def test_autotune_2d_times_launches_of_several_sweeps(P):
+    """The autotuner on a 2D grid: the kernels of four and two sweeps per launch are timed
+    per sweep over whole launches next to the one-sweep kernels; u and w come back as they
+    were, the kept kernel is one of the candidates, and a solve on it converges."""
+    spec = W.cantilever2d(256, 128)
+    prob = P.Problem(spec)
+    u0 = W.random_state(spec, seed=27).astype(np.float32)
+    w0 = W.random_state(spec, seed=28, scale=0.1).astype(np.float32)
+    prob.set_state(u0, w0)
+    rep = prob.autotune(sweeps=8)
+    assert any(k.startswith("tb2d/k4/") for k in rep) and any(k.startswith("tb2d/k2/") for k in rep)
+    assert any(k.startswith("march2d/") for k in rep) and all(v > 0 for v in rep.values())
+    u, w = prob.get_state(with_w=True, dtype=np.float32)
+    assert np.array_equal(u, u0) and np.array_equal(w, w0)
+    assert prob.kernel_info()[0] in rep
+    assert prob.solve(tol=1e-6, max_sweeps=200000)["converged"]
+    prob.close()
+
+
 def test_lean_march_kernel_equals_two_row_kernel(P):
     """The lean two-row marching kernel (tma3: the default 3D FP32 sweep) against the
     two-row kernel it was derived from (tma2) on a ragged grid whose tiles take all three of
