@@ -13,6 +13,8 @@ tile and a K-node halo, against single sweeps and the oracle.
 * Solves: the adaptive-restart APT solve on this kernel takes the y-marching solve's
   decisions in FP64 (the same sweep count, the same field); the FP32 refined solve and a
   design loop land on the oracle's direct solve / FP64 loop.
+* Degenerate grids (one cell, one cell row or column, grids narrower than a tile) follow the
+  FP64 rule with the kernel's own region and with regions far larger than the grid.
 """
 import numpy as np
 import pytest
@@ -199,3 +201,28 @@ def test_bad_regions_are_rejected(P):
     prob.select_kernel("tb2d/k2/62x24")
     assert prob.kernel_info() == ("tb2d/k2/62x24", 4)
     prob.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (2, 1), (1, 5), (33, 1), (3, 200), (200, 3), (61, 47)])
+@pytest.mark.parametrize("kernel", [None, "tb2d/k4/122x14", "tb2d/k2/32x16"])
+def test_degenerate_grids_fp64(P, shape, kernel):
+    """Grids of one cell, one cell row or column, and grids narrower than a tile (so one
+    block's halo reaches past every edge): 9 sweeps (launches of 4 + 4 + 1, or 2 + ... + 1)
+    equal 9 y-marching sweeps bit for bit and the oracle's 9 sweeps."""
+    nx, ny = shape
+    spec = W.ProblemSpec(name="thin", dim=2, nx=nx, ny=ny, nz=0, precision="f64", storage="f64",
+                         boxes=[((0, 0, 0), (0, ny, 0), 3)], loads=[((nx, ny, 0), 1, -1.0)], vol_frac=[0.5])
+    n, consts, local = 9, (0.93, 0.9, 0.0), True
+    ut, wt, r2t, kname, phi = _run(P, spec, kernel, 0, n, consts, local)
+    assert kname.startswith("tb2d/") and (kernel is None or kname == kernel)
+    ug, wg, r2g, gname, _ = _run(P, spec, "march2d", 0, n, consts, local)
+    assert np.array_equal(ut, ug), relmax(ut, ug)
+    assert np.array_equal(wt, wg), relmax(wt, wg)
+    assert abs(r2t - r2g) <= 1e-13 * r2g
+    op, om = oracle_problem(spec), oracle_materials(spec)
+    E, F, fixed = om.modulus(phi), op.load_vector(), op.fixed_mask()
+    u0, w0 = _state(spec)
+    uo, wo = nodes_to_oracle(u0), nodes_to_oracle(w0)
+    for _ in range(n):
+        op.apt_sweep(E, F, fixed, *consts[:2], uo, wo, local_dt=local)
+    assert relmax(ut, oracle_to_nodes(uo, 2)) < 1e-12
