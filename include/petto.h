@@ -238,6 +238,17 @@ petto_status petto_set_wait_limit(petto_ctx *ctx, int tries);
  * NULL; res_norm2 (may be NULL) receives sum R^2. */
 petto_status petto_residual(petto_ctx *ctx, double *res_norm2, void *R, int dtype, int on_device);
 
+/* The FP64 defect of the iterative refinement (petto_solve_opts.refine) for a given FP64
+ * state: R = F - K(E) u in FP64 arithmetic with the context's FP32 cell moduli, 0 on
+ * supports (the Sec. 3.2 operator; Sec. 2.2 systems).  u [C][nodes] (C = ncomp x load cases,
+ * host or device memory as on_device says) is read, not kept: the current state is left as
+ * it was.  res_norm2 (may be NULL) receives sum R^2 over free DOFs, R [C][nodes] (may be
+ * NULL) the field, in the same memory kind as u.  On a whole 3D elastic grid this is the
+ * FP64 z-marching defect kernel (the node gather with PETTO_DEFECT=gather), elsewhere the
+ * FP64 node gather.  Synchronises.  PETTO_EUNSUPPORTED for FP64 contexts (their own
+ * petto_residual is the FP64 residual), PETTO_EINVAL for a null context or state. */
+petto_status petto_residual64(petto_ctx *ctx, const double *u, int on_device, double *res_norm2, double *R);
+
 /* Hybrid APT/PT solve of K(E) u = F from the current u (Sec. 2.2). */
 petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *opts, petto_solve_report *rep);
 

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libpetto.so")
-SOURCES = ["sweep.cu", "sweep2d_tb.cu", "sweep3d_march.cu", "design.cu", "capi.cu"]
+SOURCES = ["sweep.cu", "sweep2d_tb.cu", "sweep3d_march.cu", "defect3d.cu", "design.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -89,6 +89,7 @@ _SIGS = {
     "petto_set_wait_limit": (_int, [_vp, _int]),
     "petto_sweep_rhs": (_int, [_vp, _int, _i64, _dbl, _dbl, _dbl, _int, _vp, _int, _P(_dbl)]),
     "petto_residual": (_int, [_vp, _P(_dbl), _vp, _int, _int]),
+    "petto_residual64": (_int, [_vp, _vp, _int, _P(_dbl), _vp]),
     "petto_pt_solve": (_int, [_vp, _P(petto_solve_opts), _P(petto_solve_report)]),
     "petto_sensitivity": (_int, [_vp, _P(_dbl), _P(_dbl), _vp, _int, _int]),
     "petto_design_update": (_int, [_vp, _P(petto_pf_opts), _P(_dbl)]),

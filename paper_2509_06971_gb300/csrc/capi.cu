@@ -516,6 +516,18 @@ petto_status drain_profile(petto_ctx *ctx) {
 // the TMA-staged kernels), growing the tile and partial-sum buffers when needed.
 // A tiling restricted to the context's output planes (a slab of a decomposed grid): z tiles
 // (gather) or z segments (marching) start at the slab's first plane.
+// Tiling of the FP64 defect of the refinement: the FP64 z-marching kernel on a whole 3D
+// elastic grid, the node gather otherwise (2D, heat, slabs; PETTO_DEFECT=gather forces it)
+Tiling defect_tiling(const petto_ctx *ctx) {
+    const char *env = std::getenv("PETTO_DEFECT");
+    if (ctx->dim == 3 && ctx->physics == 0 && !ctx->own_n && !(env && std::strcmp(env, "gather") == 0)) {
+        Tiling t{};
+        defect3d_tiling(ctx->L, t);
+        return t;
+    }
+    return gather_tiling(ctx->L);
+}
+
 Tiling own_planes(const petto_ctx *ctx, Tiling t) {
     if (!ctx->own_n) return t;
     t.zlo = ctx->own_lo;
@@ -768,7 +780,7 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
             merged[std::make_pair(n, r * ctx->ncomp + a)] += loads->value[e];
         }
     }
-    ctx->gtiling = gather_tiling(ctx->L);
+    ctx->gtiling = defect_tiling(ctx);
     ctx->load_list.assign(merged.begin(), merged.end());
     auto table = [&](const Tiling &t, std::vector<int> &tptr, std::vector<LoadEntry> &ent) {
         const int nt = t.ntiles();
@@ -796,7 +808,9 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
     std::vector<LoadEntry> tent, gent;
     table(ctx->tiling, tptr, tent);
     table(ctx->gtiling, gptr, gent);
-    const int ntiles = ctx->tiling.ntiles(), gntiles = ctx->gtiling.ntiles();
+    // the defect's load table also serves the node-gather tiling a slab switches to
+    const int ntiles = ctx->tiling.ntiles(),
+              gntiles = std::max(ctx->gtiling.ntiles(), gather_tiling(ctx->L).ntiles());
     ctx->n_loads = (int)tent.size();
     // ||F|| over free DOFs (point loads plus the body source)
     double f2 = 0.0;
@@ -871,7 +885,7 @@ petto_status petto_create(const petto_grid *grid, const petto_materials *mat, co
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->tile_ptr, tptr.data(), sizeof(int) * (ntiles + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->gtile_ptr, gptr.data(), sizeof(int) * (gntiles + 1), cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(ctx->gtile_ptr, gptr.data(), sizeof(int) * gptr.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && ctx->n_loads > 0)
         e = cudaMemcpyAsync(ctx->loads, tent.data(), sizeof(LoadEntry) * ctx->n_loads, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && ctx->n_loads > 0)
@@ -1219,7 +1233,11 @@ constexpr int REFINE_STALL = 20;
 // the FP64 state, defect and right-hand side buffers of the refinement
 petto_status refine_alloc(petto_ctx *ctx) {
     const size_t nb64 = (size_t)ctx->ndofc() * ctx->L.cstride * sizeof(double);
-    if (!ctx->u64) CK(cudaMalloc(&ctx->u64, nb64));
+    if (!ctx->u64) {
+        CK(cudaMalloc(&ctx->u64, nb64));
+        // the node-gather defect reads the padding around the grid: zero, as in every state
+        CK(cudaMemsetAsync(ctx->u64, 0, nb64, ctx->stream));
+    }
     if (!ctx->r64) {
         CK(cudaMalloc(&ctx->r64, nb64));
         // the defect kernel writes grid nodes only: the padding stays zero (it enters max |r|)
@@ -1419,6 +1437,42 @@ petto_status tune_first_solve(petto_ctx *ctx) {
 }  // namespace
 
 extern "C" {
+
+petto_status petto_residual64(petto_ctx *ctx, const double *u, int on_device, double *res_norm2, double *R) {
+    if (!ctx || !u) return fail(ctx, PETTO_EINVAL, "null argument");
+    if (ctx->precision != PETTO_F32) return fail(ctx, PETTO_EUNSUPPORTED, "the FP64 defect belongs to FP32 contexts");
+    petto_status st = refine_alloc(ctx);
+    if (st != PETTO_OK) return st;
+    const int C = ctx->ndofc();
+    const int64_t nn = (int64_t)C * ctx->L.nnodes();
+    const double *src = u;
+    if (!on_device) {
+        st = ensure_stage(ctx, nn * sizeof(double));
+        if (st != PETTO_OK) return st;
+        CK(cudaMemcpyAsync(ctx->stage, u, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        src = static_cast<const double *>(ctx->stage);
+    }
+    pack_nodes<double, double><<<grid_of(nn), 256, 0, ctx->stream>>>(ctx->L, C, src, (double *)ctx->u64, 1);
+    CK(cudaGetLastError());
+    ctx->launches++;
+    double norm = 0.0;
+    st = refine_defect(ctx, &norm);
+    if (st != PETTO_OK) return st;
+    if (res_norm2) *res_norm2 = norm * norm;
+    if (!R) return PETTO_OK;
+    double *dst = R;
+    if (!on_device) {
+        st = ensure_stage(ctx, nn * sizeof(double));
+        if (st != PETTO_OK) return st;
+        dst = static_cast<double *>(ctx->stage);
+    }
+    pack_nodes<double, double><<<grid_of(nn), 256, 0, ctx->stream>>>(ctx->L, C, (const double *)ctx->r64, dst, 0);
+    CK(cudaGetLastError());
+    ctx->launches++;
+    if (!on_device) CK(cudaMemcpyAsync(R, ctx->stage, nn * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return PETTO_OK;
+}
 
 petto_status petto_pt_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_solve_report *rep) {
     if (!ctx || !o) return fail(ctx, PETTO_EINVAL, "null argument");
@@ -1969,8 +2023,8 @@ petto_status petto_set_owned_planes(petto_ctx *ctx, int64_t zlo, int64_t zhi, in
     t.zn = 0;
     ctx->own_lo = whole ? 0 : (int)zlo;
     ctx->own_n = whole ? 0 : (int)(zhi - zlo + 1);
-    // the node-gather tiling of the FP64 defect and residual kernels, restricted the same way
-    const Tiling g = own_planes(ctx, gather_tiling(ctx->L));
+    // the tiling of the FP64 defect (the node gather on a slab), restricted the same way
+    const Tiling g = own_planes(ctx, defect_tiling(ctx));
     const int NX = ctx->L.NX, NY = ctx->L.NY, gnt = g.ntiles();
     std::vector<int> gptr(gnt + 1, 0);
     std::vector<std::pair<int, LoadEntry>> tmp;

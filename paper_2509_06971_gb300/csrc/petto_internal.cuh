@@ -299,7 +299,8 @@ struct Tiling {
     int kind;          // 0 gather, 1 3D z-marching (register-staged), 2/3 3D TMA one row per
                        // thread (32x8 / 32x16), 4 3D TMA two rows per thread, 5 2D y-marching,
                        // 6 3D TMA two rows per thread, lean per-plane path, 7 2D sweeps several per
-                       // launch on a shared-memory copy of the tile and its halo
+                       // launch on a shared-memory copy of the tile and its halo, 8 3D FP64 defect
+                       // (z-marching, residual only)
     int ly;            // kind 5: output rows per warp (a block's warps take consecutive segments);
                        // kind 7: sweeps per launch (1, 2 or 4)
     int zlo, zn;       // 3D: output node planes [zlo, zlo + zn) (zn = 0: all planes, zlo = 0)
@@ -322,7 +323,14 @@ Tiling gather_tiling(const Layout &L);
 // per warp (ly = 0: chosen from the grid size)
 Tiling march2d_tiling(const Layout &L, int ly = 0);
 constexpr int M2W = 4;  // warps per block of the 2D marching kernel
-cudaError_t launch_residual64(const SweepArgs &a, const Tiling &gather, cudaStream_t s);
+// FP64 residual R = F - K(E) u of an FP64 state (the defect of the refinement), with the
+// node-gather kernels or, on a whole 3D elastic grid, the FP64 z-marching kernel (kind 8)
+cudaError_t launch_residual64(const SweepArgs &a, const Tiling &t, cudaStream_t s);
+void defect3d_tiling(const Layout &L, Tiling &t);
+cudaError_t launch_defect3d(const SweepArgs &a, const Tiling &t, cudaStream_t s);
+// z segment length of a marching tiling: fewest (waves of `resident` blocks) x (planes per
+// block, with the one-plane halo) over `columns` tile columns
+int choose_zseg(int NZ, int columns, int resident);
 void march3d_tiling(const Layout &L, Tiling &t);
 cudaError_t launch_march3d(const SweepArgs &a, const Tiling &t, cudaStream_t s);
 

@@ -517,6 +517,7 @@ Tiling choose_tiling(const Layout &L, int physics, int precision, int nrhs) {
 // FP64 residual R = F - K(E) u of an FP64 state with the FP32 modulus field (mode 2):
 // the defect of the iterative refinement around FP32 sweeps.
 cudaError_t launch_residual64(const SweepArgs &a0, const Tiling &t, cudaStream_t s) {
+    if (t.kind == 8) return launch_defect3d(a0, t, s);
     SweepArgs a = a0;
     a.zb = t.zn ? t.zb : 0;
     dim3 block(t.bx, t.by, 1), grid(t.gx, t.gy, t.gz);

@@ -295,6 +295,16 @@ class Problem:
                                          _DT[np.dtype(dtype)], 0))
         return r.value, R
 
+    def residual64(self, u, with_field: bool = True):
+        """The FP64 defect F - K(E) u of an FP64 state u [C][nodes] (petto_residual64: the
+        refinement's defect kernel; FP32 contexts).  Returns (sum R^2, R or None)."""
+        u = np.ascontiguousarray(np.asarray(u, np.float64).reshape(self.nrhs * self.ncomp, self.nnodes))
+        r = ctypes.c_double(0.0)
+        R = np.empty_like(u) if with_field else None
+        self._ck(self.lib.petto_residual64(self.ctx, u.ctypes.data_as(ctypes.c_void_p), 0, ctypes.byref(r),
+                                           R.ctypes.data_as(ctypes.c_void_p) if with_field else None))
+        return r.value, R
+
     def solve_opts(self, mode=None, **kw) -> C.petto_solve_opts:
         """Defaults: the workload's constants and schedule (tolerance mode unless the
         workload is the paper's fixed-count loop); momentum from the workload (adaptive

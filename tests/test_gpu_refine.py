@@ -11,6 +11,9 @@
   cantilever in FP64, on a 32 x 16 x 16 copy: against central finite differences (step
   1e-4) of the GPU compliance on 32 cells drawn by PCG64 seed 3, and against the oracle's
   gradient at the oracle's direct solution.
+* The FP64 defect F - K(E) u of the refinement (the z-marching FP64 kernel and the node
+  gather) against the oracle's FP64 residual, node by node to 1e-12 of max |R|, on ragged,
+  tiny and full-size grids and with several load cases.
 """
 import numpy as np
 import pytest
@@ -120,3 +123,80 @@ def test_adjoint_3d_cantilever_matches_finite_differences_and_oracle(P):
     s, Co = om.sensitivity(phi0, E, op.cell_energy(u))
     assert abs(Cv.item() - Co) < 1e-9 * Co
     assert np.abs(g - s).max() < 1e-7 * np.abs(s).max()
+
+
+def _dyadic_design(spec, seed):
+    """A seeded design of densities in {0, 1/4, 1/2, 3/4, 1}: rho^3 and the SIMP modulus
+    rounded to FP32 are then the same whether computed in FP32 or in FP64 and rounded, so
+    the oracle's FP64 moduli rounded to FP32 are the context's FP32 moduli exactly."""
+    return np.round(np.asarray(W.random_design(spec, seed=seed), np.float64) * 4.0) / 4.0
+
+
+def _defect_oracle(spec, phi, u, loads=None):
+    """The oracle's FP64 residual F - K(E) u with its moduli rounded to FP32 (the defect
+    runs with the FP32 moduli of an FP32 context)."""
+    op, om = oracle_problem(spec, loads=loads), oracle_materials(spec)
+    E = om.modulus(phi).astype(np.float32).astype(np.float64)
+    R, r2 = op.residual(E, op.load_vector(), op.fixed_mask(), nodes_to_oracle(u))
+    return oracle_to_nodes(R, spec.ncomp), r2
+
+
+@pytest.mark.parametrize("name", ["ragged70x40x37", "tiny3x2x1", "cantilever3d_256x128x128"])
+def test_fp64_defect_matches_oracle(P, name, monkeypatch):
+    """The FP64 defect of the refinement, R = F - K(E) u in FP64 with the FP32 moduli (the
+    z-marching defect kernel), field by field against the oracle's FP64 residual at the same
+    state, and against the node-gather defect kernel: on a ragged grid of several tiles and z
+    segments with supports ending inside segments and loads on tile edges, on a grid smaller
+    than one tile, and on the benchmark's full grid."""
+    if name.startswith("ragged"):
+        spec = _ragged()
+    elif name.startswith("tiny"):
+        spec = W.cantilever3d(3, 2, 1)
+    else:
+        spec = W.cantilever3d(256, 128, 128)
+    phi = _dyadic_design(spec, 61)
+    u = W.random_state(spec, seed=62, scale=1e-2)
+    out = {}
+    for kernel in ("march", "gather"):
+        if kernel == "gather":
+            monkeypatch.setenv("PETTO_DEFECT", "gather")
+        prob = P.Problem(spec)
+        prob.set_design(phi)
+        out[kernel] = prob.residual64(u)
+        prob.close()
+    monkeypatch.delenv("PETTO_DEFECT", raising=False)
+    Ro, r2o = _defect_oracle(spec, phi, u)
+    scale = np.abs(Ro).max()
+    for kernel, (r2, R) in out.items():
+        assert np.abs(R - Ro).max() <= 1e-12 * scale, (kernel, np.abs(R - Ro).max() / scale)
+        assert abs(r2 - r2o) <= 1e-12 * r2o, kernel
+    # supports hold R = 0 exactly
+    fixed = oracle_to_nodes(oracle_problem(spec).fixed_mask().astype(np.float64), 3) != 0
+    assert np.all(out["march"][1][fixed] == 0.0)
+
+
+def test_fp64_defect_of_several_load_cases(P):
+    """One defect launch per load case, the sums accumulated across them."""
+    spec, cases = W.multirhs3d(40, 20, 20, n_rhs=3, seed=4)
+    prob = P.Problem(spec, nrhs=3, load_cases=cases)
+    phi = _dyadic_design(spec, 63)
+    prob.set_design(phi)
+    u = np.random.default_rng(64).standard_normal((9, spec.nnodes)) * 1e-2
+    r2, R = prob.residual64(u)
+    prob.close()
+    r2o = 0.0
+    for r, case in enumerate(cases):
+        Ro, r2c = _defect_oracle(spec, phi, u[3 * r:3 * r + 3], loads=case)
+        assert np.abs(R[3 * r:3 * r + 3] - Ro).max() <= 1e-12 * np.abs(Ro).max(), r
+        r2o += r2c
+    assert abs(r2 - r2o) <= 1e-12 * r2o
+
+
+def test_fp64_defect_rejects_fp64_contexts(P):
+    from paper_2509_06971_gb300 import capi as C
+    spec = W.cantilever3d(8, 4, 4).with_(precision="f64", storage="f64")
+    prob = P.Problem(spec)
+    with pytest.raises(C.PettoError) as e:
+        prob.residual64(np.zeros((3, spec.nnodes)))
+    assert e.value.status == C.PETTO_EUNSUPPORTED
+    prob.close()
