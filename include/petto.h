@@ -243,9 +243,9 @@ petto_status petto_residual(petto_ctx *ctx, double *res_norm2, void *R, int dtyp
  * supports (the Sec. 3.2 operator; Sec. 2.2 systems).  u [C][nodes] (C = ncomp x load cases,
  * host or device memory as on_device says) is read, not kept: the current state is left as
  * it was.  res_norm2 (may be NULL) receives sum R^2 over free DOFs, R [C][nodes] (may be
- * NULL) the field, in the same memory kind as u.  On a whole 3D elastic grid this is the
- * FP64 z-marching defect kernel (the node gather with PETTO_DEFECT=gather), elsewhere the
- * FP64 node gather.  Synchronises.  PETTO_EUNSUPPORTED for FP64 contexts (their own
+ * NULL) the field, in the same memory kind as u.  On a 3D elastic grid (or a slab of one:
+ * its own planes) this is the FP64 z-marching defect kernel (the node gather with
+ * PETTO_DEFECT=gather), elsewhere the FP64 node gather.  Synchronises.  PETTO_EUNSUPPORTED for FP64 contexts (their own
  * petto_residual is the FP64 residual), PETTO_EINVAL for a null context or state. */
 petto_status petto_residual64(petto_ctx *ctx, const double *u, int on_device, double *res_norm2, double *R);
 
@@ -306,7 +306,8 @@ petto_status petto_set_owned_planes(petto_ctx *ctx, int64_t zlo, int64_t zhi, in
  *   exchange   fills this slab's ghost planes with its neighbours' interface planes and
  *              sends its own (petto_get_plane / petto_set_plane on ctx); called before every
  *              sweep, by every slab in the same order
- *   allreduce  replaces values[0..n) by their sums over all slabs
+ *   allreduce  replaces values[0..n) by their sums over all slabs (allreduce_max: by
+ *              their maxima)
  * Each returns PETTO_OK, or a status that ends the solve with that status. */
 typedef petto_status (*petto_exchange_fn)(petto_ctx *ctx, void *user);
 typedef petto_status (*petto_allreduce_fn)(double *values, int n, void *user);
@@ -317,12 +318,18 @@ typedef petto_status (*petto_allreduce_fn)(double *values, int n, void *user);
  * the slabs' sums), so every slab takes the same decisions.  Adaptive-restart momentum
  * (momentum 1) tests the whole grid's <R, w> (allreduce on every fourth sweep, which
  * synchronises the stream) and restarts every slab together; fixed momentum (0) and PT only
- * (2) need no such test.  FP64 refinement is not decomposed: opts->refine is ignored, so an
- * FP32 slab solve stops at the FP32 floor (about 1e-4 of ||F||).  rep as in petto_pt_solve,
- * with the whole grid's residuals.  Every slab calls it with the same opts.  PETTO_EINVAL
- * for a null hook or bad options; PETTO_ENOTCONV as petto_pt_solve. */
+ * (2) need no such test.  The FP64 refinement of FP32 contexts (opts->refine, as in
+ * petto_pt_solve) runs slab by slab: each slab keeps the FP64 state of its planes and its
+ * ghost planes (one more exchange before the FP64 state takes u or d), the FP64 defect of
+ * its own planes with the whole grid's norm (allreduce), and the FP16 right-hand side of
+ * the two-row marching kernel scaled by the whole grid's max |r| (allreduce_max, which may
+ * be NULL when no refinement runs): a slab computes what the whole grid computes on its
+ * planes.  rep as in petto_pt_solve, with the whole grid's residuals.  Every slab calls it
+ * with the same opts.  PETTO_EINVAL for a null hook (allreduce_max when a refinement would
+ * run) or bad options; PETTO_ENOTCONV as petto_pt_solve. */
 petto_status petto_slab_solve(petto_ctx *ctx, const petto_solve_opts *opts, petto_exchange_fn exchange,
-                              petto_allreduce_fn allreduce, void *user, petto_solve_report *rep);
+                              petto_allreduce_fn allreduce, petto_allreduce_fn allreduce_max, void *user,
+                              petto_solve_report *rep);
 
 /* Copy node plane k (local index) of the current state, every component (load cases
  * included), out to / in from a dense [ndof components][ny+1][nx+1] array in the sweep
@@ -369,8 +376,8 @@ typedef petto_status (*petto_layer_exchange_fn)(petto_ctx *ctx, int field, int p
  * multiplier of phase 0 (projected) or mean phi_0 before the step (penalty) -- all of the
  * whole grid.  Every slab owns two node planes or more (then a slab's top layer has a layer
  * above it exactly when the slab has an upper neighbour; PETTO_EINVAL for a slab of one).
- * Elasticity with one load case, no keep-out term (PETTO_EUNSUPPORTED otherwise); FP64
- * refinement is not decomposed (as petto_slab_solve).  PETTO_EINVAL for a null hook or bad
+ * Elasticity with one load case, no keep-out term (PETTO_EUNSUPPORTED otherwise); the
+ * solve refines FP32 states as petto_slab_solve does.  PETTO_EINVAL for a null hook or bad
  * options; PETTO_ENOTCONV when the solve missed its tolerance (the step is still taken). */
 petto_status petto_slab_design_step(petto_ctx *ctx, const petto_solve_opts *so, const petto_pf_opts *po,
                                     petto_exchange_fn exchange, petto_layer_exchange_fn exchange_layer,

@@ -107,8 +107,8 @@ _SIGS = {
     "petto_select_kernel": (_int, [_vp, ctypes.c_char_p]),
     "petto_kernel_info": (_int, [_vp, ctypes.c_char_p, _int, _P(_int)]),
     "petto_set_owned_planes": (_int, [_vp, _i64, _i64, _i64]),
-    "petto_slab_solve": (_int, [_vp, _P(petto_solve_opts), petto_exchange_fn, petto_allreduce_fn, _vp,
-                                _P(petto_solve_report)]),
+    "petto_slab_solve": (_int, [_vp, _P(petto_solve_opts), petto_exchange_fn, petto_allreduce_fn,
+                                petto_allreduce_fn, _vp, _P(petto_solve_report)]),
     "petto_slab_design_step": (_int, [_vp, _P(petto_solve_opts), _P(petto_pf_opts), petto_exchange_fn,
                                       petto_layer_exchange_fn, petto_allreduce_fn, petto_allreduce_fn, _vp,
                                       _P(_dbl)]),

@@ -516,11 +516,11 @@ petto_status drain_profile(petto_ctx *ctx) {
 // the TMA-staged kernels), growing the tile and partial-sum buffers when needed.
 // A tiling restricted to the context's output planes (a slab of a decomposed grid): z tiles
 // (gather) or z segments (marching) start at the slab's first plane.
-// Tiling of the FP64 defect of the refinement: the FP64 z-marching kernel on a whole 3D
-// elastic grid, the node gather otherwise (2D, heat, slabs; PETTO_DEFECT=gather forces it)
+// Tiling of the FP64 defect of the refinement: the FP64 z-marching kernel on 3D elastic
+// grids and their slabs, the node gather otherwise (2D, heat; PETTO_DEFECT=gather forces it)
 Tiling defect_tiling(const petto_ctx *ctx) {
     const char *env = std::getenv("PETTO_DEFECT");
-    if (ctx->dim == 3 && ctx->physics == 0 && !ctx->own_n && !(env && std::strcmp(env, "gather") == 0)) {
+    if (ctx->dim == 3 && ctx->physics == 0 && !(env && std::strcmp(env, "gather") == 0)) {
         Tiling t{};
         defect3d_tiling(ctx->L, t);
         return t;
@@ -1597,33 +1597,26 @@ petto_status copy_layer(petto_ctx *ctx, int field, int phase, int64_t k, void *d
 
 extern "C" {
 
-petto_status petto_slab_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_exchange_fn exchange,
-                              petto_allreduce_fn allreduce, void *user, petto_solve_report *rep) {
-    if (!ctx || !o || !exchange || !allreduce) return fail(ctx, PETTO_EINVAL, "null argument");
-    if (o->mode != PETTO_SOLVE_PAPER && o->mode != PETTO_SOLVE_TOL) return fail(ctx, PETTO_EINVAL, "bad mode");
-    if (o->n_apt < 0 || o->n_pt < 0 || o->max_sweeps < 0 || o->check_every < 0)
-        return fail(ctx, PETTO_EINVAL, "negative count");
-    if (o->momentum < 0 || o->momentum > 2) return fail(ctx, PETTO_EINVAL, "momentum is 0, 1 or 2");
-    petto_status st = tune_first_solve(ctx);
-    // ||F|| of the whole grid: each slab holds the loads of its own planes
-    double fn2 = ctx->f_norm * ctx->f_norm;
-    if (st == PETTO_OK) st = allreduce(&fn2, 1, user);
-    if (st != PETTO_OK) return st;
-    const double fn = std::sqrt(fn2);
-    CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
-    st = set_ctrl(ctx, CT_RESTART_AT, 0);
-    if (st == PETTO_OK) st = set_ctrl(ctx, CT_ERR, 0);
-    if (st != PETTO_OK) return st;
-    ctx->slab_restart_at = 0;
-    SolveState S;
-    S.use_pt = o->momentum == 2;
-    S.total = o->mode == PETTO_SOLVE_PAPER ? o->n_apt + o->n_pt : o->max_sweeps;
+}  // extern "C"
+
+namespace {
+
+struct SlabHooks {
+    petto_exchange_fn exchange;
+    petto_allreduce_fn allreduce, allreduce_max;
+    void *user;
+};
+
+// The sweeps of one phase of a slab's solve, as sweep_phase runs them on a whole grid: an
+// exchange of the ghost planes before every sweep, the whole grid's <R, w> deciding each
+// restart test and the whole grid's residual each check.
+petto_status slab_phase(petto_ctx *ctx, const petto_solve_opts *o, SolveState &S, double stop_abs, int64_t n_apt,
+                        int stall_checks, const void *rhs, const SlabHooks &H, int *reached) {
+    *reached = 0;
     const int ce = o->check_every;
-    const double stop = o->mode == PETTO_SOLVE_TOL ? o->tol * fn : -1.0;
-    int reached = 0;
     while (S.sweeps < S.total) {
-        const bool apt = !S.use_pt && (o->mode == PETTO_SOLVE_TOL || S.sweeps < o->n_apt);
-        st = exchange(ctx, user);
+        const bool apt = !S.use_pt && (o->mode == PETTO_SOLVE_TOL || S.sweeps < n_apt);
+        petto_status st = H.exchange(ctx, H.user);
         if (st != PETTO_OK) return st;
         const bool check = ce > 0 && (S.sweeps + 1) % ce == 0;
         const bool final_report = S.sweeps + 1 == S.total;
@@ -1632,6 +1625,7 @@ petto_status petto_slab_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_e
         // the restart test of the adaptive momentum, on the whole grid's <R, w>
         sc.test_dot = apt && sc.adaptive && ((ce > 0 ? S.sweeps % ce : S.sweeps) % 4) == 3;
         sc.idx = S.sweeps;
+        sc.rhs = rhs;
         st = one_sweep(ctx, apt ? 0 : 1, o->a, o->b, o->s1, o->local_dt, check || final_report, sc);
         if (st != PETTO_OK) return st;
         if (apt) ++S.na; else ++S.np;
@@ -1642,7 +1636,7 @@ petto_status petto_slab_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_e
             CK(cudaMemcpyAsync(ctrl, ctx->ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost, ctx->stream));
             CK(cudaStreamSynchronize(ctx->stream));
             double dot = ctrl[CT_DOT];
-            st = allreduce(&dot, 1, user);
+            st = H.allreduce(&dot, 1, H.user);
             if (st != PETTO_OK) return st;
             long long at = 0;
             std::memcpy(&at, &ctrl[CT_RESTART_AT], sizeof(at));
@@ -1660,14 +1654,140 @@ petto_status petto_slab_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_e
         st = read_scal(ctx, scal);
         if (st != PETTO_OK) return st;
         double r2 = scal[SC_RES];
-        st = allreduce(&r2, 1, user);
+        st = H.allreduce(&r2, 1, H.user);
         if (st != PETTO_OK) return st;
         const double rn = std::sqrt(r2);
         S.last = rn;
+        if (ctx->trace)
+            std::fprintf(stderr, "petto: slab %d sweep %lld res %.6e%s\n", ctx->own_lo, (long long)S.sweeps, rn,
+                         rhs ? " (correction)" : "");
         bool ended = false;
-        st = apply_check(ctx, o, S, rn, check, stop, 0, &ended, &reached);
+        st = apply_check(ctx, o, S, rn, check, stop_abs, stall_checks, &ended, reached);
         if (st != PETTO_OK) return st;
         if (ended) break;
+    }
+    return PETTO_OK;
+}
+
+// The FP64 defect of a slab's own planes and the whole grid's norm of it (the ghost planes
+// of u64 hold the neighbours' values)
+petto_status slab_defect(petto_ctx *ctx, const SlabHooks &H, double *norm) {
+    double local = 0.0;
+    petto_status st = refine_defect(ctx, &local);
+    if (st != PETTO_OK) return st;
+    double r2 = local * local;
+    st = H.allreduce(&r2, 1, H.user);
+    if (st != PETTO_OK) return st;
+    *norm = std::sqrt(r2);
+    return PETTO_OK;
+}
+
+// The defect as the correction sweeps' right-hand side, d <- 0.  The FP16 form takes its
+// power-of-two scale from the whole grid's max |r| (the ghost planes of r64 stay zero), so
+// every slab rounds as the whole grid does.
+petto_status slab_correction(petto_ctx *ctx, const SlabHooks &H) {
+    const int64_t nel = (int64_t)ctx->ndofc() * ctx->L.cstride;
+    ctx->rhs_half = two_row_kind(ctx->tiling.kind);
+    if (ctx->rhs_half) {
+        CK(cudaMemsetAsync(ctx->ctrl + CT_RMAX, 0, sizeof(double), ctx->stream));
+        abs_max_f64<<<grid_of(nel), 256, 0, ctx->stream>>>(nel, (const double *)ctx->r64, ctx->ctrl + CT_RMAX);
+        CK(cudaGetLastError());
+        double m = 0.0;
+        CK(cudaMemcpyAsync(&m, ctx->ctrl + CT_RMAX, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        petto_status st = H.allreduce_max(&m, 1, H.user);
+        if (st != PETTO_OK) return st;
+        CK(cudaMemcpyAsync(ctx->ctrl + CT_RMAX, &m, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        f64_to_f16_scaled<<<grid_of(nel), 256, 0, ctx->stream>>>(nel, (const double *)ctx->r64, ctx->ctrl + CT_RMAX,
+                                                                  ctx->ctrl + CT_RSCALE, (__half *)ctx->rhs32);
+        CK(cudaGetLastError());
+        // the copy above reads m from this frame: done before it returns
+        CK(cudaStreamSynchronize(ctx->stream));
+        ctx->launches += 2;
+        if (!ctx->tma.rvalid || ctx->tma.rbuf != ctx->rhs32) {
+            if (!make_tma_rhs_map(ctx->L, ctx->ndofc(), ctx->rhs32, ctx->tma))
+                return fail(ctx, PETTO_ECUDA, "tensor map creation failed");
+            clear_graphs(ctx);
+        }
+    } else {
+        f64_to_f32<<<grid_of(nel), 256, 0, ctx->stream>>>(nel, (const double *)ctx->r64, (float *)ctx->rhs32);
+        CK(cudaGetLastError());
+        ctx->launches++;
+    }
+    CK(cudaMemsetAsync(ctx->u[ctx->cur], 0, ctx->node_bytes(), ctx->stream));
+    return PETTO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+petto_status petto_slab_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_exchange_fn exchange,
+                              petto_allreduce_fn allreduce, petto_allreduce_fn allreduce_max, void *user,
+                              petto_solve_report *rep) {
+    if (!ctx || !o || !exchange || !allreduce) return fail(ctx, PETTO_EINVAL, "null argument");
+    if (o->mode != PETTO_SOLVE_PAPER && o->mode != PETTO_SOLVE_TOL) return fail(ctx, PETTO_EINVAL, "bad mode");
+    if (o->n_apt < 0 || o->n_pt < 0 || o->max_sweeps < 0 || o->check_every < 0)
+        return fail(ctx, PETTO_EINVAL, "negative count");
+    if (o->momentum < 0 || o->momentum > 2) return fail(ctx, PETTO_EINVAL, "momentum is 0, 1 or 2");
+    const bool refine = o->mode == PETTO_SOLVE_TOL && o->refine && ctx->precision == PETTO_F32 && o->tol < 1e-3;
+    if (refine && !allreduce_max) return fail(ctx, PETTO_EINVAL, "the refinement of a slab solve needs allreduce_max");
+    const SlabHooks H{exchange, allreduce, allreduce_max, user};
+    petto_status st = tune_first_solve(ctx);
+    // ||F|| of the whole grid: each slab holds the loads of its own planes
+    double fn2 = ctx->f_norm * ctx->f_norm;
+    if (st == PETTO_OK) st = allreduce(&fn2, 1, user);
+    if (st != PETTO_OK) return st;
+    const double fn = std::sqrt(fn2);
+    CK(cudaMemsetAsync(ctx->w, 0, ctx->node_bytes(), ctx->stream));
+    st = set_ctrl(ctx, CT_RESTART_AT, 0);
+    if (st == PETTO_OK) st = set_ctrl(ctx, CT_ERR, 0);
+    if (st != PETTO_OK) return st;
+    ctx->slab_restart_at = 0;
+    SolveState S;
+    S.use_pt = o->momentum == 2;
+    S.total = o->mode == PETTO_SOLVE_PAPER ? o->n_apt + o->n_pt : o->max_sweeps;
+    int reached = 0;
+    bool conv = false;
+    if (!refine) {
+        const double stop = o->mode == PETTO_SOLVE_TOL ? o->tol * fn : -1.0;
+        st = slab_phase(ctx, o, S, stop, o->n_apt, 0, nullptr, H, &reached);
+        if (st != PETTO_OK) return st;
+        conv = reached != 0;
+    } else {
+        // the refinement of petto_pt_solve, slab by slab: FP32 sweeps of the state down to
+        // REFINE_FROM, then rounds of (FP64 defect, correction sweeps of d, u64 += d).  Before
+        // u64 takes u or d, one more exchange brings their ghost planes up to date, so a
+        // slab's u64 holds its neighbours' values on its ghost planes throughout.
+        st = slab_phase(ctx, o, S, REFINE_FROM * fn, 0, REFINE_STALL, nullptr, H, &reached);
+        if (st == PETTO_OK) st = exchange(ctx, user);
+        if (st == PETTO_OK) st = refine_begin(ctx);
+        if (st != PETTO_OK) return st;
+        double true_res = NAN;
+        while (true) {
+            st = slab_defect(ctx, H, &true_res);
+            if (st != PETTO_OK) return st;
+            if (ctx->trace)
+                std::fprintf(stderr, "petto: slab %d FP64 defect %.6e after %lld sweeps\n", ctx->own_lo, true_res,
+                             (long long)S.sweeps);
+            if (true_res <= o->tol * fn) {
+                conv = true;
+                break;
+            }
+            if (S.sweeps >= S.total || !std::isfinite(true_res)) break;
+            st = slab_correction(ctx, H);
+            if (st != PETTO_OK) return st;
+            S.improve_ref = INFINITY;
+            S.since_improve = 0;
+            const double stop = std::max(true_res / 8.0, 0.5 * o->tol * fn);
+            st = slab_phase(ctx, o, S, stop, 0, 20, ctx->rhs32, H, &reached);
+            if (st == PETTO_OK) st = exchange(ctx, user);
+            if (st == PETTO_OK) st = refine_absorb(ctx);
+            if (st != PETTO_OK) return st;
+        }
+        st = refine_finish(ctx);
+        if (st != PETTO_OK) return st;
+        S.last = true_res;
     }
     if (rep) {
         rep->sweeps = S.sweeps;
@@ -1677,11 +1797,11 @@ petto_status petto_slab_solve(petto_ctx *ctx, const petto_solve_opts *o, petto_e
         rep->f_norm = fn;
         rep->rel_res = fn > 0 ? S.last / fn : NAN;
         rep->r_pde = NAN;
-        rep->converged = reached ? 1 : 0;
+        rep->converged = conv ? 1 : 0;
         rep->fell_back_to_pt = S.fell ? 1 : 0;
     }
     if (!std::isfinite(S.last) && S.sweeps > 0) return fail(ctx, PETTO_EDIVERGED, "residual not finite after PT fallback");
-    if (o->mode == PETTO_SOLVE_TOL && !reached) return PETTO_ENOTCONV;
+    if (o->mode == PETTO_SOLVE_TOL && !conv) return PETTO_ENOTCONV;
     return PETTO_OK;
 }
 
@@ -1710,7 +1830,7 @@ petto_status petto_slab_design_step(petto_ctx *ctx, const petto_solve_opts *so, 
     if (st != PETTO_OK) return st;
     // 1. the state solve, then the ghost planes brought up to date for the sensitivity
     petto_solve_report rep{};
-    st = petto_slab_solve(ctx, so, exchange, allreduce, user, &rep);
+    st = petto_slab_solve(ctx, so, exchange, allreduce, allreduce_max, user, &rep);
     const bool notconv = st == PETTO_ENOTCONV;
     if (st != PETTO_OK && !notconv) return st;
     st = exchange(ctx, user);

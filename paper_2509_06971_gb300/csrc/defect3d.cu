@@ -20,7 +20,10 @@
 //   * the moduli sums of the edges and faces reuse each other and the previous plane's
 //     (seven additions a node instead of twelve).
 //
-// Whole grids only (a slab context keeps the node-gather kernel); one launch per load case.
+// One launch per load case.  On a slab of a z-decomposed grid the segments start at the
+// slab's first plane (its ghost plane below is the first segment's warm-up plane) and only
+// the slab's own planes are written; a node's arithmetic does not depend on where the
+// segments start, so a slab's defect equals the whole grid's bit for bit.
 #include "petto_internal.cuh"
 
 namespace petto {
@@ -71,10 +74,11 @@ __global__ void __launch_bounds__(DNT, 2) defect3d_march(const SweepArgs A) {
     const float *__restrict__ E = static_cast<const float *>(A.E);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * DX + tx;
-    const int x0 = blockIdx.x * (DX - 1), y0 = blockIdx.y * (DTY - 1), z0 = blockIdx.z * A.zseg;
+    const int x0 = blockIdx.x * (DX - 1), y0 = blockIdx.y * (DTY - 1), z0 = A.zb + blockIdx.z * A.zseg;
     const int X = x0 - 1 + tx, Y = y0 - 1 + ty;
     const bool outxy = tx >= 1 && ty >= 1 && X < L.NX && Y < L.NY;
-    const int zend = min(z0 + A.zseg, L.NZ);
+    const int zend = min(z0 + A.zseg, A.zhi + 1);
+    const int zo = max(z0, A.zlo);  // first plane written
     const double cpar = A.k.ce_par, cperp = A.k.ce_perp, cl = A.k.cf_lam, cm = A.k.cf_mu;
 
     unsigned boxbits = 0;  // support boxes containing this (X, Y) column
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(DNT, 2) defect3d_march(const SweepArgs A) {
         my[3][ty][tx] = Gxy[1];
         __syncthreads();
 
-        if (outxy && zp >= z0) {
+        if (outxy && zp >= zo) {
             const double Ku0 = -(Fx[0] + Fy[0] + Fz[0]) - Gxy[0] - Gxz[0] + mx[0][ty][tx - 1] + my[0][ty - 1][tx] +
                                Szp[0] + mx[3][ty - 1][tx - 1];
             const double Ku1 = -(Fx[1] + Fy[1] + Fz[1]) - Gxy[1] - Gyz[0] + mx[1][ty][tx - 1] + my[1][ty - 1][tx] +
@@ -303,6 +307,7 @@ cudaError_t launch_defect3d(const SweepArgs &a0, const Tiling &t, cudaStream_t s
     for (int r = 0; r < a0.nrhs; ++r) {
         SweepArgs a = a0;
         a.zseg = t.zs;
+        a.zb = t.zn ? t.zb : 0;
         a.rhs_index = r;
         defect3d_march<<<grid, block, 0, s>>>(a);
         const cudaError_t e = cudaGetLastError();

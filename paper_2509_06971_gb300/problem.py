@@ -321,10 +321,11 @@ class Problem:
                                   int(bool(kw.get("local_dt", s.local_dt))), momentum,
                                   int(bool(kw.get("refine", True))))
 
-    def slab_solve(self, exchange, allreduce, mode=None, **kw) -> dict:
+    def slab_solve(self, exchange, allreduce, allreduce_max=None, mode=None, **kw) -> dict:
         """The state solve of one slab of a decomposed grid (petto_slab_solve): exchange()
-        fills the ghost planes before every sweep, allreduce(list of floats) returns their sums
-        over the slabs.  Options as solve() (no FP64 refinement)."""
+        fills the ghost planes before every sweep, allreduce / allreduce_max (list of floats)
+        return their sums / maxima over the slabs.  Options as solve(); the FP64 refinement of
+        an FP32 solve (refine, the default) needs allreduce_max."""
         o = self.solve_opts(mode, **kw)
         errors = []
 
@@ -336,19 +337,22 @@ class Problem:
                 errors.append(e)
                 return C.PETTO_EINVAL
 
-        def _ar(values, n, user):
-            try:
-                out = allreduce([values[i] for i in range(n)])
-                for i in range(n):
-                    values[i] = float(out[i])
-                return C.PETTO_OK
-            except BaseException as e:  # noqa: BLE001
-                errors.append(e)
-                return C.PETTO_EINVAL
+        def reducer(fn):
+            def call(values, n, user):
+                try:
+                    out = fn([values[i] for i in range(n)])
+                    for i in range(n):
+                        values[i] = float(out[i])
+                    return C.PETTO_OK
+                except BaseException as e:  # noqa: BLE001
+                    errors.append(e)
+                    return C.PETTO_EINVAL
+            return C.petto_allreduce_fn(call)
 
-        ex, ar = C.petto_exchange_fn(_ex), C.petto_allreduce_fn(_ar)
+        ex, ar = C.petto_exchange_fn(_ex), reducer(allreduce)
+        am = reducer(allreduce_max) if allreduce_max is not None else C.petto_allreduce_fn()
         rep = C.petto_solve_report()
-        st = self.lib.petto_slab_solve(self.ctx, ctypes.byref(o), ex, ar, None, ctypes.byref(rep))
+        st = self.lib.petto_slab_solve(self.ctx, ctypes.byref(o), ex, ar, am, None, ctypes.byref(rep))
         if errors:
             raise errors[0]
         self._ck(st, allow=(C.PETTO_OK, C.PETTO_ENOTCONV))

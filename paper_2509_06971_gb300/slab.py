@@ -21,7 +21,9 @@ Two drivers share this host logic:
 
 The state solve is decomposed: sweeps, residuals, and the solve loop itself, which runs in
 the library (``petto_slab_solve``) with this module's exchange and all-reduce as its hooks
-(fixed or adaptive-restart momentum, PT; the FP64 refinement is not decomposed).  So is the
+(fixed or adaptive-restart momentum, PT, and the FP64 refinement of FP32 states: each slab
+keeps the FP64 state of its planes and ghost planes, its own planes' defect, the whole
+grid's defect norm and the whole grid's scale of the FP16 right-hand side).  So is the
 design loop (``petto_slab_design_step``): a slab owns the cell layers whose lower node plane
 it owns, holds the layer below its first one (its ghost layer) and keeps a copy of the layer
 above its top one; the sensitivity, the update and the modulus are computed on every held
@@ -170,15 +172,16 @@ class _SlabDriver:
 
     def solve(self, tol: float = 1e-6, kind: int = 0, a: float | None = None, b: float | None = None,
               s1: float | None = None, local_dt: bool | None = None, check_every: int = 50,
-              max_sweeps: int = 200000, momentum: int | None = None) -> dict:
+              max_sweeps: int = 200000, momentum: int | None = None, refine: bool = True) -> dict:
         """The state solve over the slabs, one petto_slab_solve per slab (the loop runs in the
         library; this driver supplies its exchange and all-reduce hooks): APT with fixed
         momentum (kind 0, momentum 0), PT only (kind 1, momentum 2) or the adaptive-restart
         momentum (momentum 1), until ||R|| <= tol ||F|| of the whole grid at a check (every
-        check_every sweeps) or max_sweeps."""
+        check_every sweeps) or max_sweeps; FP32 grids below tol 1e-3 with the FP64 refinement
+        (refine, as Problem.solve)."""
         if momentum is None:
             momentum = 0 if kind == 0 else 2
-        kw = dict(mode=1, tol=tol, check_every=check_every, max_sweeps=max_sweeps, momentum=momentum, refine=False)
+        kw = dict(mode=1, tol=tol, check_every=check_every, max_sweeps=max_sweeps, momentum=momentum, refine=refine)
         # constants left out take the problem's defaults (Problem.solve_opts), as a whole-grid solve does
         kw.update({k: v for k, v in dict(a=a, b=b, s1=s1, local_dt=local_dt).items() if v is not None})
         rep = self._slab_solve(kw)
@@ -188,10 +191,10 @@ class _SlabDriver:
     def design_step(self, solve_kw: dict | None = None, pf_kw: dict | None = None) -> dict:
         """One design loop over the slabs (petto_slab_design_step on every slab, this driver
         supplying the plane and cell-layer exchanges and the sums and maxima): the whole
-        grid's metrics.  The state solve as solve() (no FP64 refinement)."""
+        grid's metrics.  The state solve as solve()."""
         if not design_step_ok(self.geom):
             raise ValueError("the decomposed design step needs two node planes or more per slab")
-        kw = dict(mode=1, refine=False)
+        kw = dict(mode=1)
         kw.update(solve_kw or {})
         return self._slab_design_step(kw, dict(pf_kw or {}))
 
@@ -357,7 +360,8 @@ class SlabGrid(_SlabDriver):
         return out[0]
 
     def _slab_solve(self, kw):
-        return self._threads(lambda s, h: self.probs[s].slab_solve(h["exchange"], h["allreduce"], **kw))
+        return self._threads(lambda s, h: self.probs[s].slab_solve(h["exchange"], h["allreduce"],
+                                                                   allreduce_max=h["allreduce_max"], **kw))
 
     def _slab_design_step(self, solve_kw, pf_kw):
         return self._threads(lambda s, h: self.probs[s].slab_design_step(
@@ -451,7 +455,7 @@ class DistributedSlabs(_SlabDriver):
         return t.tolist()
 
     def _slab_solve(self, kw):
-        return self.prob.slab_solve(self.exchange, self._allreduce_list, **kw)
+        return self.prob.slab_solve(self.exchange, self._allreduce_list, allreduce_max=self._allreduce_max_list, **kw)
 
     def _allreduce_max_list(self, values):
         t = _torch().tensor(list(values), dtype=_torch().float64, device=self.device)

@@ -2,7 +2,9 @@
 to device before every sweep, against the same sweeps of the whole grid.  A node's update
 reads only its 3 x 3 x 3 neighbourhood and its 8 cells, in the same order in both, so the
 owned planes must match bit for bit (node-gather and two-row marching kernels, FP64 and
-FP32); the FP64 decomposed solve is also held against the oracle's direct solve."""
+FP32); the FP64 decomposed solve is also held against the oracle's direct solve.  The FP64
+refinement of FP32 solves, decomposed, gives the whole grid's refined solve bit for bit,
+alone and inside the decomposed design loop."""
 import numpy as np
 import pytest
 
@@ -245,3 +247,89 @@ def test_slab_design_step_checks(P):
         phi = p.get_design()
         p.get_layer(C.PETTO_LAYER_PHI, 0, 3, buf)
         assert np.array_equal(buf.view(np.float64), phi[0].reshape(p.spec.nz, -1)[3])
+
+
+@pytest.mark.parametrize("kernel,n_slabs", [("tma3", 2), ("tma3", 3), ("gather/32x4", 2)])
+def test_slab_refined_fp32_solve_equals_whole_grid(P, kernel, n_slabs):
+    """The FP64 refinement of an FP32 solve, decomposed: each slab's FP64 state with its
+    ghost planes, the defect of its own planes (the FP64 marching defect, whose per-node
+    arithmetic does not depend on where its z segments start), the whole grid's defect norm
+    and the whole grid's scale of the FP16 right-hand side (allreduce_max).  To 1e-6: the
+    whole grid's refined solve's sweep count, residual and field bit for bit."""
+    spec = _spec(precision="f32")
+    kw = dict(tol=1e-6, check_every=20, max_sweeps=100000, momentum=1, local_dt=True)
+    p = P.Problem(spec)
+    p.select_kernel(kernel)
+    rep_w = p.solve(mode=1, refine=True, **kw)
+    uw = p.get_state(dtype=np.float32)
+    p.close()
+    with S.SlabGrid(spec, n_slabs, kernel=kernel) as g:
+        rep_s = g.solve(refine=True, **kw)
+        us = g.get_state(dtype=np.float32)
+    assert rep_w["converged"] and rep_s["converged"], (rep_w, rep_s)
+    assert rep_w["rel_res"] <= 1e-6
+    assert rep_s["sweeps"] == rep_w["sweeps"], (rep_s, rep_w)
+    assert abs(rep_s["rel_res"] - rep_w["rel_res"]) <= 1e-9 * rep_w["rel_res"]  # sums in another order
+    _same(us, uw, spec)
+
+
+def test_slab_refined_fp32_solve_matches_direct_solve(P):
+    """An FP32 solve over three slabs (two-row marching kernel) refined to ||R|| <= 1e-6 ||F||:
+    the compliance of the oracle's direct solve (FP64 moduli of the FP32 design) to 1e-5."""
+    base = W.cantilever3d(24, 12, 14)
+    spec = base.with_(loads=base.loads + [((12, 6, 5), 0, 0.5), ((20, 3, 9), 1, -0.3)],
+                      phi0=W.random_design(base, seed=36, lo=0.3, hi=0.95))
+    with S.SlabGrid(spec, 3, kernel="tma3") as g:
+        rep = g.solve(tol=1e-6, check_every=20, max_sweeps=100000, momentum=1, local_dt=True)
+        u = g.get_state(dtype=np.float64)
+    assert rep["converged"] and rep["rel_res"] <= 1e-6, rep
+    op, om = oracle_problem(spec), oracle_materials(spec)
+    F = op.load_vector()
+    ud = op.direct_solve(om.modulus(np.asarray(spec.phi0, np.float32).astype(np.float64)), F, op.fixed_mask())
+    Cs, Cd = float(F @ nodes_to_oracle(u)), float(F @ ud)
+    assert abs(Cs - Cd) <= 1e-5 * abs(Cd), (Cs, Cd)
+
+
+def test_slab_refined_design_steps_equal_whole_grid(P):
+    """Two decomposed design loops with FP32 state solves refined to 1e-6 (the benchmark's
+    solve) against petto_optimize on the whole grid: the same sweep counts, the step's
+    metrics and the design equal up to the order of the sums."""
+    spec = _design_spec("f32", 0)
+    solve_kw = dict(tol=1e-6, check_every=20, max_sweeps=100000, momentum=1, local_dt=True)
+    p = P.Problem(spec)
+    p.select_kernel("tma3")
+    hist, _ = p.optimize(2, solve_kw=solve_kw)
+    phi_w = p.get_design()
+    p.close()
+    with S.SlabGrid(spec, 2, kernel="tma3") as g:
+        rows = [g.design_step(solve_kw=solve_kw) for _ in range(2)]
+        phi_s = g.get_design()
+    for a, b in zip(rows, hist):
+        assert a["sweeps"] == b["sweeps"], (a, b)
+        assert a["rel_res"] <= 1e-6 and b["rel_res"] <= 1e-6
+        for key in ("compliance", "work", "mean_phi0", "lambda0"):
+            assert abs(a[key] - b[key]) <= 1e-5 * max(abs(b[key]), 1e-3), (key, a[key], b[key])
+    assert np.abs(phi_s - phi_w).max() <= 1e-4
+
+
+def test_slab_refinement_needs_the_max_hook(P):
+    """A one-slab decomposition of the whole grid (no-op exchange, identity all-reduces) is
+    petto_pt_solve: the refined FP32 solve takes its decisions and gives its field; without
+    allreduce_max the refinement is refused."""
+    from paper_2509_06971_gb300 import capi as C
+    spec = _spec(precision="f32")
+    kw = dict(tol=1e-6, check_every=20, max_sweeps=100000, momentum=1, local_dt=True)
+    p = P.Problem(spec)
+    p.select_kernel("tma3")
+    with pytest.raises(C.PettoError) as e:
+        p.slab_solve(lambda: None, lambda v: v, mode=1, **kw)
+    assert e.value.status == C.PETTO_EINVAL
+    p.set_state(np.zeros((3, spec.nnodes), np.float32))
+    rep_s = p.slab_solve(lambda: None, lambda v: v, allreduce_max=lambda v: v, mode=1, **kw)
+    us = p.get_state(dtype=np.float32)
+    p.set_state(np.zeros((3, spec.nnodes), np.float32))
+    rep_w = p.solve(mode=1, **kw)
+    uw = p.get_state(dtype=np.float32)
+    p.close()
+    assert rep_s["converged"] and rep_s["sweeps"] == rep_w["sweeps"]
+    _same(us, uw, spec)
