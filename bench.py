@@ -635,6 +635,35 @@ def run_sweeps_only(args):
     return 0
 
 
+def run_defects_only(args):
+    """N FP64 defects F - K(E) u of the refinement (petto_residual64 on device buffers, a
+    seeded FP64 state): few launches, for ncu captures of the defect kernel."""
+    import ctypes
+    import torch
+    from paper_2509_06971_gb300 import problem as PR
+    torch.cuda.set_device(0)
+    spec = WORKLOADS[args.workload]()
+    prob = PR.Problem(spec)
+    prob.set_design(W.random_design(spec, seed=61))
+    u = torch.from_numpy(W.random_state(spec, seed=62, scale=1e-2).reshape(-1)).to("cuda")
+    R = torch.empty_like(u)
+    r2 = ctypes.c_double(0.0)
+
+    def defect():
+        prob._ck(prob.lib.petto_residual64(prob.ctx, ctypes.c_void_p(u.data_ptr()), 1, ctypes.byref(r2),
+                                           ctypes.c_void_p(R.data_ptr())))
+    defect()
+    t0 = time.perf_counter()
+    for _ in range(args.defects_only):
+        defect()
+    ms = (time.perf_counter() - t0) * 1e3 / args.defects_only
+    print(json.dumps({"workload": args.workload, "defects": args.defects_only, "ms_per_call": ms,
+                      "note": "petto_residual64 wall time: two packing kernels and a synchronisation included",
+                      "res2": r2.value}))
+    prob.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -649,6 +678,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweeps-only", type=int, default=0,
                     help="only run this many APT sweeps of the workload (for profiler captures)")
+    ap.add_argument("--defects-only", type=int, default=0,
+                    help="only run this many FP64 refinement defects of the workload (for profiler captures)")
     ap.add_argument("--time-to-design", action="store_true",
                     help="time the workload's whole design run instead (one JSON line)")
     ap.add_argument("--design-steps", type=int, default=0, help="with --time-to-design: override the step count")
@@ -657,6 +688,8 @@ def main():
     args = ap.parse_args()
     if args.sweeps_only:
         return run_sweeps_only(args)
+    if args.defects_only:
+        return run_defects_only(args)
     if args.time_to_design:
         return run_time_to_design(args)
     if args.impl == "reference":
