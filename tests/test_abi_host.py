@@ -64,6 +64,9 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu():
     lib = C.load()
     assert lib.petto_sweep(None, 0, 1, 0.9, 1.0, 0.5, 0, None) == C.PETTO_EINVAL
     assert lib.petto_pt_solve(None, None, None) == C.PETTO_EINVAL
+    assert lib.petto_residual64(None, None, 0, None, None) == C.PETTO_EINVAL
+    assert lib.petto_slab_solve(None, None, C.petto_exchange_fn(), C.petto_allreduce_fn(), C.petto_allreduce_fn(),
+                                None, None) == C.PETTO_EINVAL
 
 
 def test_create_without_gpu_fails_cleanly():
